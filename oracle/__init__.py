@@ -1,0 +1,296 @@
+"""CPU oracle for the batched BDF/Newton hot path.
+
+TEST INFRASTRUCTURE ONLY.  This package may be imported only by ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py``.  The library under ``paper_2011_12984_b300`` never
+imports it, and it never imports that library: the two share no code; only
+the seeded input generators (``paper_2011_12984_b300.gen``, which contain no
+method arithmetic) feed both.
+
+The arithmetic lives in plain C (``oracle/*.c``: IEEE double, no FMA
+contraction), loaded here through ctypes.  ctypes releases the GIL during a
+foreign call, so independent cells can be integrated on several host threads.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_d = C.c_double
+_i64 = C.c_int64
+_pd = C.POINTER(C.c_double)
+_pi32 = C.POINTER(C.c_int32)
+_pi64 = C.POINTER(C.c_int64)
+_pu8 = C.POINTER(C.c_uint8)
+_pi = C.POINTER(C.c_int)
+
+SUCCESS, TOO_MUCH_WORK, ERR_FAILURE, CONV_FAILURE = 0, -1, -3, -4
+QMAX = 5
+
+
+class Options(C.Structure):
+    _fields_ = [("rtol", _d), ("atol", _d), ("mxstep", _i64), ("qmax", C.c_int),
+                ("fixed_h", _d), ("fixed_q", C.c_int), ("h0", _d),
+                ("trace_y", _pd), ("trace_acor", _pd), ("trace_cap", _i64), ("z_init", _pd)]
+
+
+class Cells(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ncell", _i64), ("n", _pi32), ("y_off", _pi64),
+                ("rxn_off", _pi64), ("reac", _pu8), ("prod", _pu8), ("k", _pd)]
+
+
+class Bruss(C.Structure):
+    _fields_ = [("nx", C.c_int), ("A", _d), ("B", _d), ("eps", _d), ("D", _d)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(_build.build())
+        L.or_wrms_norm.restype = _d
+        L.or_linear_integrate.argtypes = [_i64, _pd, C.c_int, _pd, _d, _pd, _d,
+                                          C.POINTER(Options), _pd, _pi64, _pi64]
+        L.or_cells_integrate.argtypes = [C.POINTER(Cells), _i64, _i64, _d, _pd, _d, _d, _d,
+                                         _i64, _pd, _pi32, _pi64]
+        L.or_bruss_gmres.argtypes = [C.POINTER(Bruss), _pd, _d, _pd, _d, C.c_int, _pd, _pd]
+        L.or_bruss_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, C.c_int, _i64,
+                                         _pd, _pi64]
+        _lib = L
+    return _lib
+
+
+def _p(a, t=_pd):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptrs(vs):
+    return (_pd * len(vs))(*[_p(v) for v in vs])
+
+
+# ---------------------------------------------------------------- vectors
+def linear_sum(a, x, b, y):
+    x, y = _f64(x), _f64(y)
+    z = np.empty_like(x)
+    lib().or_linear_sum(_i64(x.size), _d(a), _p(x), _d(b), _p(y), _p(z))
+    return z
+
+
+def linear_combination(c, xs):
+    xs = [_f64(x) for x in xs]
+    c = _f64(c)
+    z = np.empty_like(xs[0])
+    lib().or_linear_combination(_i64(z.size), C.c_int(len(xs)), _p(c), _ptrs(xs), _p(z))
+    return z
+
+
+def scale_add_multi(a, x, ys):
+    x = _f64(x)
+    ys = [_f64(y) for y in ys]
+    a = _f64(a)
+    zs = [np.empty_like(x) for _ in ys]
+    lib().or_scale_add_multi(_i64(x.size), C.c_int(len(ys)), _p(a), _p(x), _ptrs(ys), _ptrs(zs))
+    return zs
+
+
+def dot_prod_multi(x, ys):
+    """returns (d, sum |x_i y_ji|) per j"""
+    x = _f64(x)
+    ys = [_f64(y) for y in ys]
+    d = np.empty(len(ys))
+    s = np.empty(len(ys))
+    lib().or_dot_prod_multi(_i64(x.size), C.c_int(len(ys)), _p(x), _ptrs(ys), _p(d), _p(s))
+    return d, s
+
+
+def wrms_norm(x, w):
+    x, w = _f64(x), _f64(w)
+    return lib().or_wrms_norm(_i64(x.size), _p(x), _p(w))
+
+
+# ---------------------------------------------------------------- dense LU
+def lu_factor(A):
+    A = _f64(A).copy()
+    n = A.shape[0]
+    piv = np.zeros(n, dtype=np.int32)
+    info = lib().or_lu_factor(C.c_int(n), _p(A), _p(piv, _pi))
+    return A, piv, info
+
+
+def lu_solve(lu, piv, b):
+    b = _f64(b).copy()
+    lib().or_lu_solve(C.c_int(lu.shape[0]), _p(lu), _p(piv, _pi), _p(b))
+    return b
+
+
+# ---------------------------------------------------------------- BDF core
+def bdf_constants(q):
+    """(l[0..q], E_q, E_{q-1}, E_{q+1})"""
+    l = np.zeros(QMAX + 2)
+    out = np.zeros(3)
+    lib().or_bdf_constants(C.c_int(q), _p(l), _p(out))
+    return l[:q + 1], out[0], out[1], out[2]
+
+
+def linear_integrate(A, Cs, t0, y0, tout, rtol=1e-6, atol=1e-10, fixed_h=0.0, fixed_q=0,
+                     h0=0.0, mxstep=100000, trace=0, z_init=None):
+    """y' = A y + sum_k Cs[k] t^k.  Returns (ret, y, stats, trace_y, trace_acor)."""
+    A = _f64(np.atleast_2d(A))
+    N = A.shape[0]
+    Cs = _f64(np.zeros((1, N)) if Cs is None or len(Cs) == 0 else np.atleast_2d(Cs))
+    y0 = _f64(y0)
+    y = np.empty(N)
+    st = np.zeros(8, dtype=np.int64)
+    ty = np.zeros((max(trace, 1), N))
+    ta = np.zeros((max(trace, 1), N))
+    zi = None if z_init is None else _f64(z_init)
+    opt = Options(rtol, atol, mxstep, QMAX, fixed_h, fixed_q, h0,
+                  _p(ty) if trace else None, _p(ta) if trace else None, trace,
+                  None if zi is None else _p(zi))
+    nt = _i64(0)
+    ret = lib().or_linear_integrate(N, _p(A), Cs.shape[0], _p(Cs), t0, _p(y0), tout,
+                                    C.byref(opt), _p(y), _p(st, _pi64), C.byref(nt))
+    return ret, y, st, ty[:nt.value], ta[:nt.value]
+
+
+# ---------------------------------------------------------------- problems
+def robertson_rhs(k, y):
+    k, y = _f64(k), _f64(y)
+    f = np.empty(3)
+    lib().or_robertson_rhs(_p(k), _p(y), _p(f))
+    return f
+
+
+def robertson_jac(k, y):
+    k, y = _f64(k), _f64(y)
+    J = np.empty((3, 3))
+    lib().or_robertson_jac(_p(k), _p(y), _p(J))
+    return J
+
+
+def massaction_rhs(reac, prod, k, y):
+    reac = np.ascontiguousarray(reac, np.uint8)
+    prod = np.ascontiguousarray(prod, np.uint8)
+    k, y = _f64(k), _f64(y)
+    f = np.empty(y.size)
+    lib().or_massaction_rhs(C.c_int(y.size), C.c_int(k.size), _p(reac, _pu8), _p(prod, _pu8),
+                            _p(k), _p(y), _p(f))
+    return f
+
+
+def massaction_jac(reac, prod, k, y):
+    reac = np.ascontiguousarray(reac, np.uint8)
+    prod = np.ascontiguousarray(prod, np.uint8)
+    k, y = _f64(k), _f64(y)
+    n = y.size
+    J = np.empty((n, n))
+    lib().or_massaction_jac(C.c_int(n), C.c_int(k.size), _p(reac, _pu8), _p(prod, _pu8),
+                            _p(k), _p(y), _p(J))
+    return J
+
+
+def _cells_struct(prob):
+    """ctypes view of a generator problem; the arrays stay alive in ``keep``."""
+    if prob.kind == "robertson":
+        n = np.ascontiguousarray(prob.n, np.int32)
+        y_off = np.ascontiguousarray(prob.y_off, np.int64)
+        k = _f64(prob.k)
+        keep = (n, y_off, k)
+        s = Cells(0, prob.ncell, _p(n, _pi32), _p(y_off, _pi64), None, None, None, _p(k))
+    else:
+        n = np.ascontiguousarray(prob.n, np.int32)
+        y_off = np.ascontiguousarray(prob.y_off, np.int64)
+        rxn_off = np.ascontiguousarray(prob.rxn_off, np.int64)
+        reac = np.ascontiguousarray(prob.reactants, np.uint8)
+        prod = np.ascontiguousarray(prob.products, np.uint8)
+        k = _f64(prob.k)
+        keep = (n, y_off, rxn_off, reac, prod, k)
+        s = Cells(1, prob.ncell, _p(n, _pi32), _p(y_off, _pi64), _p(rxn_off, _pi64),
+                  _p(reac, _pu8), _p(prod, _pu8), _p(k))
+    return s, keep
+
+
+def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threads=1,
+                    y0=None):
+    """Integrate the listed cells (default all) independently; returns
+    (y, status, stats[ncell, 8]) over the whole problem (cells not listed keep y0
+    and status 1).  ``threads`` > 1 spreads cell ranges over host threads."""
+    s, keep = _cells_struct(prob)
+    y0 = _f64(prob.y0 if y0 is None else y0)
+    y = y0.copy()
+    status = np.full(prob.ncell, 1, np.int32)
+    stats = np.zeros((prob.ncell, 8), np.int64)
+    L = lib()
+    if cells is None:
+        nch = max(1, threads * 8) if threads > 1 else 1
+        b = np.linspace(0, prob.ncell, nch + 1).astype(np.int64)
+        ranges = [(int(b[i]), int(b[i + 1])) for i in range(nch) if b[i + 1] > b[i]]
+    else:
+        cells = np.sort(np.asarray(cells, dtype=np.int64))
+        ranges = [(int(c), int(c) + 1) for c in cells]
+
+    def run(r):
+        return L.or_cells_integrate(C.byref(s), r[0], r[1], t0, _p(y0), tout, rtol, atol, mxstep,
+                                    _p(y), _p(status, _pi32), _p(stats, _pi64))
+
+    if threads <= 1:
+        for r in ranges:
+            run(r)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, ranges))
+    del keep
+    return y, status, stats
+
+
+def bruss_struct(p):
+    return Bruss(p.nx, p.A, p.B, p.eps, p.D)
+
+
+def bruss_rhs(p, y):
+    s = bruss_struct(p)
+    y = _f64(y)
+    f = np.empty_like(y)
+    lib().or_bruss_rhs(C.byref(s), _p(y), _p(f))
+    return f
+
+
+def bruss_jv(p, y, v):
+    s = bruss_struct(p)
+    y, v = _f64(y), _f64(v)
+    jv = np.empty_like(y)
+    lib().or_bruss_jv(C.byref(s), _p(y), _p(v), _p(jv))
+    return jv
+
+
+def bruss_gmres(p, y, gamma, ewt, tol, maxl, b):
+    s = bruss_struct(p)
+    y, ewt = _f64(y), _f64(ewt)
+    x = _f64(b).copy()
+    rn = _d(0)
+    it = lib().or_bruss_gmres(C.byref(s), _p(y), gamma, _p(ewt), tol, maxl, _p(x), C.byref(rn))
+    return x, it, rn.value
+
+
+def bruss_integrate(p, t0, tout, rtol, atol, maxl=5, mxstep=100000, y0=None):
+    s = bruss_struct(p)
+    y0 = _f64(p.y0 if y0 is None else y0)
+    y = np.empty_like(y0)
+    st = np.zeros(8, np.int64)
+    ret = lib().or_bruss_integrate(C.byref(s), t0, _p(y0), tout, rtol, atol, maxl, mxstep,
+                                   _p(y), _p(st, _pi64))
+    return ret, y, st
+
+
+def host_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
