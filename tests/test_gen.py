@@ -1,0 +1,60 @@
+"""The seeded input generators: published SplitMix64 output, reproducibility,
+independence from chunking, and the distributions the recipes state."""
+import numpy as np
+
+from paper_2011_12984_b300 import gen
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 seeded with 0: first output 0xE220A8397B1DCDAF (Vigna's reference code)
+    assert int(gen._mix64(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+
+
+def test_mass_action_reproducible_and_chunk_independent():
+    a = gen.mass_action(300, seed=11)
+    b = gen.mass_action(300, seed=11, chunk=7)
+    for f in ("n", "y_off", "rxn_off", "reactants", "products", "k", "y0"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
+    c = gen.mass_action(300, seed=12)
+    assert not np.array_equal(a.k, c.k)
+
+
+def test_mass_action_distributions():
+    p = gen.mass_action(4000, seed=1)
+    counts = np.array([(p.n == s).sum() for s in (3, 10, 32, 54)])
+    assert counts.sum() == 4000 and np.all(np.abs(counts - 1000) < 150)
+    assert np.all(p.rxn_off[1:] - p.rxn_off[:-1] == 2 * p.n)
+    lk = np.log10(p.k)
+    assert lk.min() >= -2 and lk.max() < 8 and abs(lk.mean() - 3.0) < 0.1
+    for c in range(0, 4000, 97):
+        n = p.n[c]
+        y = p.y0[p.y_off[c]:p.y_off[c + 1]]
+        assert abs(y.sum() - 1.0) < 1e-14 and np.all(y > 0)
+        for r in range(p.rxn_off[c], p.rxn_off[c + 1]):
+            ra = p.reactants[r][p.reactants[r] != 255]
+            pa = p.products[r][p.products[r] != 255]
+            assert len(ra) == len(pa) and 2 <= len(ra) <= min(4, n)
+            assert len(set(ra.tolist())) == len(ra) and len(set(pa.tolist())) == len(pa)
+            assert ra.max() < n and pa.max() < n
+
+
+def test_subset_repacks():
+    p = gen.mass_action(50, seed=2)
+    s = p.subset([3, 7])
+    assert s.ncell == 2
+    assert np.array_equal(s.y0[:p.n[3]], p.y0[p.y_off[3]:p.y_off[4]])
+    assert np.array_equal(s.k[s.rxn_off[1]:], p.k[p.rxn_off[7]:p.rxn_off[8]])
+
+
+def test_robertson_factors():
+    p = gen.robertson(5000)
+    f = p.k / np.array(gen.ROBERTSON_K)
+    assert f.min() >= 0.5 and f.max() <= 2.0
+    assert abs(np.log(f).mean()) < 0.02
+
+
+def test_brusselator_noise():
+    b = gen.brusselator3d(16)
+    ss = np.repeat(np.array(gen.brusselator_steady_state(b.A, b.B, b.eps)), b.npts)
+    rel = b.y0 / ss - 1.0
+    assert np.max(np.abs(rel)) <= 0.01 and abs(rel.mean()) < 1e-3
