@@ -1,0 +1,350 @@
+"""Benchmark: cells integrated to t_end per second at stated error, and NVECTOR
+operation HBM bandwidth, on one B300 (or N GPUs, one process each).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step integrates the 100 000-cell mass-action workload (sizes drawn from
+{3, 10, 32, 54}, 2 n reactions per cell, t in [0, 1e-3], rtol 1e-6, atol
+1e-10) from its initial state to t_end through the library's public C ABI
+(bdfb_init + bdfb_integrate), inputs resident in device memory.  Prints one
+JSON line.  ``--impl reference`` times the CPU oracle on the host cores on a
+bounded sample of the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NCELL = 100_000
+TOUT = 1.0e-3
+RTOL, ATOL = 1.0e-6, 1.0e-10
+SIZES = (3, 10, 32, 54)
+METRIC = "cells integrated to t_end per second at stated error; NVECTOR op HBM GB/s"
+UNIT = "cells/s"
+WORKLOAD = ("mass-action 100k: 100000 independent cells, n ~ U{3,10,32,54}, 2n reactions "
+            "(2-4 distinct reactants/products), k log-U[1e-2,1e8], Dirichlet y0, t in [0,1e-3], "
+            "rtol 1e-6, atol 1e-10, FP64")
+FP64_PEAK_TFLOPS = 1.25     # nominal B300 FP64 rate (recipe table); see the design doc
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def rhs_flops(prob):
+    """FP64 flops of one right-hand side per cell: per reaction m multiplies
+    for the rate and 2 m additions into f."""
+    m = (prob.reactants != 255).sum(axis=1) * 3
+    return np.add.reduceat(m, prob.rxn_off[:-1])
+
+
+def algorithmic_flops(prob, cs):
+    """FP64 flops the method needs for the counters in cs (per-cell stats):
+    per setup 2n^3/3 (LU) + 2 n^2 (M = I - gamma J) + Jacobian entries,
+    per Newton iteration 2 n^2 (triangular solves) + 10 n (residual, norm,
+    update), per RHS its reaction flops, per step (q+1)(q+2) n (predict and
+    correct)."""
+    n = prob.n.astype(np.float64)
+    nsetup, nni, nfe, nst = cs[:, 2], cs[:, 3], cs[:, 1], cs[:, 0]
+    q = np.clip(cs[:, 6], 1, 5).astype(np.float64)
+    jac = 2.0 * rhs_flops(prob)              # m(m-1) products + 2m^2 scatter ~ 2x the RHS
+    per = (nsetup * (2.0 * n ** 3 / 3.0 + 2.0 * n ** 2 + jac) + nni * (2.0 * n ** 2 + 10.0 * n)
+           + nfe * rhs_flops(prob) + nst * (q + 1) * (q + 2) * n)
+    return float(per.sum())
+
+
+def cpu_oracle_rate(prob, seconds=10.0, threads=None):
+    """oracle cells/s on a bounded sample of the workload (first cells: the
+    size mix is uniform over the index)"""
+    import oracle
+    threads = threads or oracle.host_threads()
+    n0 = min(prob.ncell, 1024)
+    t = time.perf_counter()
+    oracle.integrate_cells(prob.subset(np.arange(n0)), 0.0, TOUT, RTOL, ATOL, threads=threads)
+    dt = time.perf_counter() - t
+    ns = int(min(prob.ncell, max(n0, n0 * seconds / max(dt, 1e-3))))
+    sub = prob.subset(np.arange(ns))
+    t = time.perf_counter()
+    _, st, _ = oracle.integrate_cells(sub, 0.0, TOUT, RTOL, ATOL, threads=threads)
+    dt = time.perf_counter() - t
+    return ns / dt, threads, ns, dt, int((st != 0).sum())
+
+
+def accuracy(prob, y, ncheck=1024, seed=1):
+    """weighted final-state error vs the oracle at rtol 1e-10 on a seeded sample"""
+    import oracle
+    cells = np.sort(np.random.default_rng(seed).choice(prob.ncell, min(ncheck, prob.ncell), replace=False))
+    sub = prob.subset(cells)
+    yt, _, _ = oracle.integrate_cells(sub, 0.0, TOUT, 1e-10, 1e-14, threads=oracle.host_threads())
+    ys = np.concatenate([y[prob.y_off[c]:prob.y_off[c + 1]] for c in cells])
+    w = np.abs(ys - yt) / (RTOL * np.abs(yt) + ATOL)
+    e = np.maximum.reduceat(w, sub.y_off[:-1])
+    return {"cells_checked": int(len(cells)), "truth": "oracle rtol 1e-10 atol 1e-14",
+            "err_median": float(np.median(e)), "err_p99": float(np.percentile(e, 99)),
+            "err_max": float(e.max()), "frac_within_10": float((e <= 10).mean())}
+
+
+def nvector_bandwidth(torch, bdfb, n=1 << 25, reps=20):
+    """achieved GB/s (algorithmic bytes / event time, mean over calls)"""
+    dev = "cuda"
+    g = torch.Generator(device=dev).manual_seed(3)
+    v = [torch.rand(n, dtype=torch.float64, device=dev, generator=g) * 2 - 1 for _ in range(7)]
+    out = torch.zeros(8, dtype=torch.float64, device=dev)
+    work = bdfb.nv_work(n, 8)
+    s = torch.cuda.current_stream()
+    ops = {
+        "linear_sum": (lambda: bdfb.nv_linear_sum(0.5, v[0], -1.0, v[1], v[2]), 24),
+        "linear_combination_6": (lambda: bdfb.nv_linear_combination([0.1] * 6, v[:6], v[6]), 8 * 7),
+        "scale_add_multi_6": (lambda: bdfb.nv_scale_add_multi([0.1] * 3, v[0], v[1:4], v[4:7]), 8 * 7),
+        "dot_prod_multi_5": (lambda: bdfb.nv_dot_prod_multi(v[0], v[1:6], out, work), 8 * 6),
+        "wrms_norm": (lambda: bdfb.nv_wrms_norm(v[0], v[1], out, work), 16),
+    }
+    res = {}
+    for name, (fn, bpe) in ops.items():
+        if name == "scale_add_multi_6":
+            bpe = 8 * (2 * 3 + 1)
+        for _ in range(3):
+            fn()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        res[name] = round(bpe * n / statistics.mean(times) / 1e9, 1)
+    res["n"] = n
+    return res
+
+
+def run_reference(args):
+    """reference arm: the CPU oracle as it stands, on the host cores"""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2011_12984_b300 import gen
+    prob = gen.mass_action(NCELL, sizes=SIZES)
+    threads = oracle.host_threads()
+    ns = 4096
+    sub = prob.subset(np.arange(ns))
+    for _ in range(args.warmup):
+        oracle.integrate_cells(sub, 0.0, TOUT, RTOL, ATOL, threads=threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.integrate_cells(sub, 0.0, TOUT, RTOL, ATOL, threads=threads)
+    dt = (time.perf_counter() - t) / args.steps
+    v = ns / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": WORKLOAD, "sample_cells_per_step": ns},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {ns} of the {NCELL} cells per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2011_12984_b300 import bdfb, gen
+    # weak scaling: every rank integrates its own 100 000 cells (seed per rank)
+    prob = gen.mass_action(NCELL, sizes=SIZES, seed=gen.DEFAULT_SEED + rank)
+    y0 = torch.from_numpy(prob.y0).cuda()
+    y = torch.empty_like(y0)
+    st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL)
+
+    def step():
+        integ.init(0.0, y0)
+        r = integ.integrate(TOUT, y, st)
+        if r != 0:
+            raise RuntimeError(f"integrate returned {r}: {bdfb.strerror(r)}")
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    step_s, kern_s = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(float(len(step_s)))       # evict L2 between steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            step()
+            e1.record(s)
+            e1.synchronize()
+            step_s.append(e0.elapsed_time(e1) * 1e-3)
+            kern_s.append(integ.stats()["last_kernel_ms"] * 1e-3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_step = sum(step_s) / len(step_s)
+    if dist:
+        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = ws * NCELL / t_step
+    cs = integ.cell_stats()
+    yh = y.cpu().numpy()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    y0h = prob.y0.copy()
+    yh2 = np.empty_like(y0h)
+    sth = np.empty(prob.ncell, np.int32)
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        integ.init(0.0, y0h)
+        r = integ.integrate(TOUT, yh2, sth)
+        t1 = time.perf_counter()
+        if r != 0:
+            raise RuntimeError(f"integrate (host) returned {r}")
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_v = ws * NCELL / (sum(e2e_t) / len(e2e_t))
+
+    if rank != 0:
+        integ.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    pk, pk_kind = peaks()
+    t_kern = sum(kern_s) / len(kern_s)
+    flops = algorithmic_flops(prob, cs)
+    achieved = flops / t_kern / 1e12
+    nv = nvector_bandwidth(torch, bdfb)
+    traffic = None
+    acc = accuracy(prob, yh)
+    cpu_v, cpu_threads, cpu_ns, cpu_dt, cpu_fail = cpu_oracle_rate(prob)
+    st_sum = integ.stats()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators)",
+        "config": {"workload": WORKLOAD, "ncell": NCELL, "mapping": "size-class tiles (auto)",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "accuracy": acc,
+        "integrator_stats": {"steps_per_cell": st_sum["nsteps"] / NCELL,
+                             "newton_per_step": st_sum["nniters"] / max(1, st_sum["nsteps"]),
+                             "setups_per_cell": st_sum["nlinsetups"] / NCELL,
+                             "failed_cells": st_sum["ncells_failed"]},
+        "roofline": {"kernel": "k_cells (persistent BDF/Newton)", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": traffic, "kernel_ms": t_kern * 1e3, "algorithmic_fp64_flops": flops,
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)"},
+        "nvector_gbs": nv,
+        "nvector_roofline": {"bound": "hbm", "achieved": nv["linear_sum"], "peak": pk["hbm_gbs"],
+                             "unit": "GB/s", "frac": nv["linear_sum"] / pk["hbm_gbs"],
+                             "peak_source": f"hbm_gbs of {pk_kind}"},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                         "sample": f"first {cpu_ns} of the {NCELL} cells ({cpu_dt:.1f} s, {cpu_fail} failed)"},
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(8 * y0h.size),
+                "d2h_bytes_per_step": int(8 * y0h.size + 4 * prob.ncell)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    integ.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * bdfb.h - C ABI of libbdfb: batched variable-order BDF / Newton integration
+ * of many independent small ODE systems on one NVIDIA B300 (sm_103a).
+ *
+ * The calls follow the integrator interface the paper keeps identical between
+ * CPU and GPU builds (Sec. 5, "all of the calls to integrator functions are
+ * the same"): create / init / set tolerances / integrate to tout / get stats.
+ * The per-cell ("submodel") use case of Sec. 2 - many small independent
+ * systems, each a diagonal block of one block-diagonal Jacobian (Fig. 1) - is
+ * integrated with per-cell step control, Newton iteration and a direct solve
+ * of each block of M = I - gamma J.  Vector kernels follow the streaming and
+ * reduction operations of the NVECTOR class (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Return value: BDFB_SUCCESS (0) or a negative BDFB_* code; nothing traps
+ *    or aborts.  bdfb_strerror() gives a message.
+ *  - Memory ownership follows the paper's SUNMemory ownership flag (Sec. 3):
+ *    buffers passed in are owned by the caller and never freed by the
+ *    library; memory the library allocates is owned by the context and freed
+ *    by bdfb_destroy().
+ *  - "device" pointers are CUDA device (or managed) addresses on the current
+ *    device; "host" pointers are ordinary host memory.  Where a call takes a
+ *    bdfb_mem flag the caller states which one it passes (Sec. 3 memory type).
+ *  - All GPU work is issued on the stream set with bdfb_set_stream (default:
+ *    the legacy default stream).  Vector operations are asynchronous; calls
+ *    that return a scalar to the host synchronise that stream (Sec. 4.1).
+ *  - Device arrays of doubles must be 8-byte aligned; the vector kernels take
+ *    a faster path when all their arrays are 16-byte aligned.
+ */
+#ifndef BDFB_H
+#define BDFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+  BDFB_SUCCESS = 0,
+  BDFB_TOO_MUCH_WORK = -1,   /* mxstep steps taken before tout */
+  BDFB_ERR_FAILURE = -3,     /* error test failed 7 times in one step, or h underflow */
+  BDFB_CONV_FAILURE = -4,    /* Newton failed 10 times in one step */
+  BDFB_LSETUP_FAIL = -6,
+  BDFB_LSOLVE_FAIL = -7,
+  BDFB_RHSFUNC_FAIL = -8,
+  BDFB_MEM_FAIL = -20,       /* device or host allocation failed */
+  BDFB_CUDA_FAIL = -21,      /* a CUDA runtime call failed */
+  BDFB_ILL_INPUT = -22       /* bad argument (null pointer, size, option, ...) */
+};
+
+typedef enum { BDFB_MEM_HOST = 0, BDFB_MEM_DEVICE = 1 } bdfb_mem;
+typedef enum { BDFB_ROBERTSON = 0, BDFB_MASSACTION = 1 } bdfb_kind;
+
+const char* bdfb_strerror(int code);
+/* library version as an integer (major * 10000 + minor * 100 + patch) */
+int bdfb_version(void);
+
+/* ------------------------------------------------ NVECTOR operations (Sec. 4)
+ * Length-n FP64 vectors in device memory; stream = cudaStream_t (NULL: default
+ * stream).  Streaming operations are asynchronous.  Reductions write their
+ * result to device memory (`out`, nv doubles) and need a caller-owned device
+ * workspace of bdfb_nv_work_doubles(n, nv) doubles that is zero when first
+ * used (the kernels leave it zero again); calls that share a workspace must
+ * not overlap on the GPU.  n = 0 is valid (no work; reductions give 0). */
+
+/* z = a x + b y  (N_VLinearSum; z may alias x or y) */
+int bdfb_nv_linear_sum(int64_t n, double a, const double* x, double b, const double* y,
+                       double* z, void* stream);
+/* z = sum_{j<nv} c[j] x[j]; c is a host array, x a host array of nv device
+ * pointers; 1 <= nv <= 16  (N_VLinearCombination; z may alias x[0]) */
+int bdfb_nv_linear_combination(int64_t n, int nv, const double* c, const double* const* x,
+                               double* z, void* stream);
+/* z[j] = a[j] x + y[j], j < nv; a host array, y and z host arrays of device
+ * pointers; 1 <= nv <= 16  (N_VScaleAddMulti; z[j] may alias y[j]) */
+int bdfb_nv_scale_add_multi(int64_t n, int nv, const double* a, const double* x,
+                            const double* const* y, double* const* z, void* stream);
+/* out[j] = x . y[j], j < nv, 1 <= nv <= 16  (N_VDotProdMulti) */
+int bdfb_nv_dot_prod_multi(int64_t n, int nv, const double* x, const double* const* y,
+                           double* out, double* work, void* stream);
+/* out[0] = sqrt(sum_i (x_i w_i)^2 / n)  (N_VWrmsNorm) */
+int bdfb_nv_wrms_norm(int64_t n, const double* x, const double* w, double* out, double* work,
+                      void* stream);
+/* size (in doubles) of the reduction workspace for length n and nv results */
+int64_t bdfb_nv_work_doubles(int64_t n, int nv);
+
+/* --------------------------------------- batched dense LU of M = I - gamma J
+ * nb independent n x n blocks, block b at a + b * n * n, row-major, FP64,
+ * device memory (the block-diagonal matrix of Fig. 1 / Sec. 5).  Partial
+ * pivoting, ties to the lowest row.  piv[b * n + k] = pivot row of step k.
+ * info[b] = 0, or k + 1 when pivot k was exactly zero.  1 <= n <= 64. */
+int bdfb_batched_lu_factor(int64_t nb, int n, double* a, int32_t* piv, int32_t* info,
+                           void* stream);
+/* solve M x = b in place for every block with the factors above */
+int bdfb_batched_lu_solve(int64_t nb, int n, const double* lu, const int32_t* piv, double* b,
+                          void* stream);
+
+/* ---------------------------------------------------- per-cell problems
+ * kind BDFB_ROBERTSON: k[3 c + {0,1,2}] = (k1, k2, k3) of cell c, n = 3.
+ * kind BDFB_MASSACTION: cell c has n[c] species (1 <= n <= 56) stored at
+ *   y[y_off[c] .. y_off[c+1]) and reactions rxn_off[c] .. rxn_off[c+1)
+ *   (at most 2 * 56 per cell); reaction r consumes the distinct local species
+ *   reactants[4 r .. 4 r + 3] and produces products[4 r .. 4 r + 3]
+ *   (255 = empty slot) at rate k[r] * prod(y[reactants]).
+ * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
+ * arrays live; bdfb_create copies everything it needs, so the caller may
+ * free its arrays when bdfb_create returns. */
+typedef struct {
+  int32_t kind;              /* bdfb_kind */
+  int32_t mem;               /* bdfb_mem of every array below */
+  int64_t ncell;
+  const int32_t* n;          /* [ncell] (mass action; NULL for Robertson) */
+  const int64_t* y_off;      /* [ncell + 1] (NULL for Robertson: 3 c) */
+  const int64_t* rxn_off;    /* [ncell + 1] (mass action) */
+  const uint8_t* reactants;  /* [4 nrxn] */
+  const uint8_t* products;   /* [4 nrxn] */
+  const double* k;           /* [nrxn] or [3 ncell] */
+} bdfb_problem;
+
+typedef struct {
+  int64_t ncell;
+  int64_t nsteps, nfevals, nlinsetups, nniters, nncfails, netfails; /* sums over cells */
+  int64_t max_steps, min_steps;                                     /* per-cell extremes */
+  int64_t ncells_failed;                                            /* status != 0 */
+  int64_t nrefine, nrefine_fallback;  /* mixed precision: refinement sweeps, FP64 refactorisations */
+  double last_kernel_ms;              /* device time of the last integrate's kernels */
+} bdfb_stats;
+
+typedef struct bdfb_ctx bdfb_ctx;
+
+int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out);
+void bdfb_destroy(bdfb_ctx* ctx);
+/* cudaStream_t for all later work of this context */
+int bdfb_set_stream(bdfb_ctx* ctx, void* stream);
+/* scalar relative and absolute tolerances (defaults 1e-6, 1e-10) */
+int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
+/* Integer options:
+ *  "mxstep"    steps allowed per cell per integrate call (default 100000)
+ *  "mapping"   0 = automatic tiles by cell size (default), 32 = one warp per
+ *              cell for every cell in input order (the plain form)
+ *  "precision" 0 = FP64 factorisation (default), 1 = FP32 factorisation with
+ *              FP64 iterative refinement to 1e-12 backward error
+ *  "graph"     1 = replay integrate's launches from a captured CUDA graph
+ *  "qmax"      maximum BDF order, 1..5 (default 5) */
+int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);
+/* set t0 and copy the initial state (packed by y_off); mem: where y0 lives */
+int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem);
+/* Advance every cell to tout (each with its own h and order), write the
+ * states at tout to y (packed by y_off) and per-cell status codes to status
+ * (may be NULL).  Returns the worst (most negative) cell status, or a call
+ * error.  Cells that failed keep the state they reached.  Further calls
+ * continue from tout (each call starts from a fresh Jacobian). */
+int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem);
+int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
+/* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits */
+int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDFB_H */

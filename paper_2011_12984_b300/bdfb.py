@@ -1,0 +1,273 @@
+"""Thin Python binding of ``libbdfb`` (C ABI in ``include/bdfb.h``).
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+Device arrays are passed as ``torch.Tensor`` (CUDA, contiguous) and host
+arrays as numpy arrays or CPU tensors; the stream defaults to torch's current
+stream.  If the shared library is missing this module raises at import time
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbdfb.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libbdfb.so not built ({LIB_PATH}); run python -m paper_2011_12984_b300.build")
+
+lib = C.CDLL(LIB_PATH)
+
+SUCCESS = 0
+TOO_MUCH_WORK = -1
+ERR_FAILURE = -3
+CONV_FAILURE = -4
+LSETUP_FAIL = -6
+LSOLVE_FAIL = -7
+RHSFUNC_FAIL = -8
+MEM_FAIL = -20
+CUDA_FAIL = -21
+ILL_INPUT = -22
+
+MEM_HOST = 0
+MEM_DEVICE = 1
+ROBERTSON = 0
+MASSACTION = 1
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_d = C.c_double
+_i32 = C.c_int32
+
+
+class Problem(C.Structure):
+    _fields_ = [("kind", _i32), ("mem", _i32), ("ncell", _i64), ("n", _vp), ("y_off", _vp),
+                ("rxn_off", _vp), ("reactants", _vp), ("products", _vp), ("k", _vp)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ncell", _i64), ("nsteps", _i64), ("nfevals", _i64), ("nlinsetups", _i64),
+                ("nniters", _i64), ("nncfails", _i64), ("netfails", _i64), ("max_steps", _i64),
+                ("min_steps", _i64), ("ncells_failed", _i64), ("nrefine", _i64),
+                ("nrefine_fallback", _i64), ("last_kernel_ms", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("bdfb_strerror", C.c_char_p, [C.c_int])
+_sig("bdfb_version", C.c_int, [])
+_sig("bdfb_nv_linear_sum", C.c_int, [_i64, _d, _vp, _d, _vp, _vp, _vp])
+_sig("bdfb_nv_linear_combination", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
+_sig("bdfb_nv_scale_add_multi", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
+_sig("bdfb_nv_dot_prod_multi", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
+_sig("bdfb_nv_wrms_norm", C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp])
+_sig("bdfb_nv_work_doubles", _i64, [_i64, C.c_int])
+_sig("bdfb_batched_lu_factor", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
+_sig("bdfb_batched_lu_solve", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
+_sig("bdfb_create", C.c_int, [C.POINTER(Problem), C.POINTER(_vp)])
+_sig("bdfb_destroy", None, [_vp])
+_sig("bdfb_set_stream", C.c_int, [_vp, _vp])
+_sig("bdfb_set_tolerances", C.c_int, [_vp, _d, _d])
+_sig("bdfb_set_option", C.c_int, [_vp, C.c_char_p, _i64])
+_sig("bdfb_init", C.c_int, [_vp, _d, _vp, _i32])
+_sig("bdfb_integrate", C.c_int, [_vp, _d, _vp, _vp, _i32])
+_sig("bdfb_get_stats", C.c_int, [_vp, C.POINTER(Stats)])
+_sig("bdfb_get_cell_stats", C.c_int, [_vp, _vp, _i32])
+
+
+class BdfbError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {lib.bdfb_strerror(code).decode()} ({code})")
+
+
+def check(code, what=""):
+    if code != SUCCESS:
+        raise BdfbError(code, what)
+    return code
+
+
+def strerror(code):
+    return lib.bdfb_strerror(code).decode()
+
+
+# ------------------------------------------------------------------ helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _dptr(t):
+    """device pointer of a contiguous CUDA tensor (None -> NULL)"""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[_dptr(t) for t in ts])
+
+
+def _f64_array(v):
+    return (_d * len(v))(*[float(x) for x in v])
+
+
+# ------------------------------------------------------------ vector ops
+def nv_linear_sum(a, x, b, y, z, stream=None):
+    return check(lib.bdfb_nv_linear_sum(x.numel(), a, _dptr(x), b, _dptr(y), _dptr(z), _stream(stream)),
+                 "nv_linear_sum")
+
+
+def nv_linear_combination(c, xs, z, stream=None):
+    return check(lib.bdfb_nv_linear_combination(z.numel(), len(xs), _f64_array(c), _ptr_array(xs),
+                                                _dptr(z), _stream(stream)), "nv_linear_combination")
+
+
+def nv_scale_add_multi(a, x, ys, zs, stream=None):
+    return check(lib.bdfb_nv_scale_add_multi(x.numel(), len(ys), _f64_array(a), _dptr(x),
+                                             _ptr_array(ys), _ptr_array(zs), _stream(stream)),
+                 "nv_scale_add_multi")
+
+
+def nv_work(n, nv, device="cuda"):
+    torch = _torch()
+    return torch.zeros(int(lib.bdfb_nv_work_doubles(n, nv)), dtype=torch.float64, device=device)
+
+
+def nv_dot_prod_multi(x, ys, out, work, stream=None):
+    return check(lib.bdfb_nv_dot_prod_multi(x.numel(), len(ys), _dptr(x), _ptr_array(ys), _dptr(out),
+                                            _dptr(work), _stream(stream)), "nv_dot_prod_multi")
+
+
+def nv_wrms_norm(x, w, out, work, stream=None):
+    return check(lib.bdfb_nv_wrms_norm(x.numel(), _dptr(x), _dptr(w), _dptr(out), _dptr(work),
+                                       _stream(stream)), "nv_wrms_norm")
+
+
+def batched_lu_factor(a, piv, info, stream=None):
+    nb, n, _ = a.shape
+    return check(lib.bdfb_batched_lu_factor(nb, n, _dptr(a), _dptr(piv), _dptr(info), _stream(stream)),
+                 "batched_lu_factor")
+
+
+def batched_lu_solve(lu, piv, b, stream=None):
+    nb, n, _ = lu.shape
+    return check(lib.bdfb_batched_lu_solve(nb, n, _dptr(lu), _dptr(piv), _dptr(b), _stream(stream)),
+                 "batched_lu_solve")
+
+
+# ------------------------------------------------------------- integrator
+class Integrator:
+    """Owns a ``bdfb_ctx``.  ``problem`` is a generator problem (host arrays)."""
+
+    def __init__(self, problem, rtol=1e-6, atol=1e-10, stream=None, **options):
+        self._keep = []
+        p = Problem()
+        p.mem = MEM_HOST
+        p.ncell = problem.ncell
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a.ctypes.data
+
+        if problem.kind == "robertson":
+            p.kind = ROBERTSON
+            p.k = host(problem.k, np.float64)
+        else:
+            p.kind = MASSACTION
+            p.n = host(problem.n, np.int32)
+            p.y_off = host(problem.y_off, np.int64)
+            p.rxn_off = host(problem.rxn_off, np.int64)
+            p.reactants = host(problem.reactants, np.uint8)
+            p.products = host(problem.products, np.uint8)
+            p.k = host(problem.k, np.float64)
+        h = _vp()
+        check(lib.bdfb_create(C.byref(p), C.byref(h)), "bdfb_create")
+        self._keep = []
+        self.h = h
+        self.ncell = problem.ncell
+        self.ny = int(problem.y_off[-1])
+        self.set_stream(stream)
+        check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def set_stream(self, stream=None):
+        self.stream = _stream(stream)
+        check(lib.bdfb_set_stream(self.h, self.stream), "bdfb_set_stream")
+
+    def set_option(self, key, value):
+        check(lib.bdfb_set_option(self.h, key.encode(), int(value)), f"bdfb_set_option({key})")
+
+    def set_tolerances(self, rtol, atol):
+        check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")
+
+    def init(self, t0, y0):
+        """y0: CUDA tensor (device) or numpy array (host)."""
+        if isinstance(y0, np.ndarray):
+            y0 = np.ascontiguousarray(y0, dtype=np.float64)
+            return check(lib.bdfb_init(self.h, t0, y0.ctypes.data, MEM_HOST), "bdfb_init")
+        return check(lib.bdfb_init(self.h, t0, _dptr(y0), MEM_DEVICE), "bdfb_init")
+
+    def integrate(self, tout, y, status=None):
+        """y, status: CUDA tensors, or numpy arrays (host).  Returns the worst
+        cell status (0 = all cells reached tout)."""
+        if isinstance(y, np.ndarray):
+            assert y.dtype == np.float64 and y.flags.c_contiguous
+            sp = None
+            if status is not None:
+                assert status.dtype == np.int32 and status.flags.c_contiguous
+                sp = status.ctypes.data
+            r = lib.bdfb_integrate(self.h, tout, y.ctypes.data, sp, MEM_HOST)
+        else:
+            r = lib.bdfb_integrate(self.h, tout, _dptr(y), _dptr(status), MEM_DEVICE)
+        if r < 0 and r in (MEM_FAIL, CUDA_FAIL, ILL_INPUT):
+            raise BdfbError(r, "bdfb_integrate")
+        return r
+
+    def stats(self):
+        s = Stats()
+        check(lib.bdfb_get_stats(self.h, C.byref(s)), "bdfb_get_stats")
+        return s.as_dict()
+
+    def cell_stats(self):
+        out = np.zeros((self.ncell, 8), np.int64)
+        check(lib.bdfb_get_cell_stats(self.h, out.ctypes.data, MEM_HOST), "bdfb_get_cell_stats")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.bdfb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

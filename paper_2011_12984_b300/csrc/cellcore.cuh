@@ -1,0 +1,301 @@
+// cellcore.cuh - per-cell device building blocks of the batched BDF step.
+//
+// A cell (one small independent ODE system, the paper's "submodel" case of
+// Sec. 2; one diagonal block of the block-diagonal Jacobian of Fig. 1) is
+// owned by a group of G lanes of one warp (G = 1, 4, 8, 16 or 32).  Lane
+// `rank` of a group owns the vector elements i = rank + G s, s < NPL, which
+// live in registers; the cell's matrix M = I - gamma J, the gathered state and
+// the reaction rates live in the group's slice of shared memory.  Group-wide
+// reductions are xor-butterflies, so every lane of a group holds bitwise the
+// same scalars and all control flow is uniform inside a group.
+#pragma once
+
+#include "common.cuh"
+
+namespace bdfb {
+
+// ------------------------------------------------------------------ groups
+template <int G>
+struct Grp {
+  unsigned mask;
+  int rank;
+  __device__ __forceinline__ Grp() {
+    const int l = threadIdx.x & 31;
+    rank = l % G;
+    mask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (l - rank));
+  }
+  __device__ __forceinline__ void sync() const {
+    if (G > 1) __syncwarp(mask);
+  }
+  __device__ __forceinline__ double sum(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+  }
+  __device__ __forceinline__ bool any(bool p) const {
+    if (G == 1) return p;
+    return (__ballot_sync(mask, p) & mask) != 0u;
+  }
+  __device__ __forceinline__ double bcast(double v, int src) const {
+    return G > 1 ? __shfl_sync(mask, v, src, G) : v;
+  }
+  __device__ __forceinline__ int bcast(int v, int src) const {
+    return G > 1 ? __shfl_sync(mask, v, src, G) : v;
+  }
+};
+
+// per-cell shared memory
+template <int NMAX>
+struct CellSmem {
+  double M[NMAX][NMAX + 1];   // M = I - gamma J, then its LU factors
+  double dinv[NMAX];          // 1 / U_kk
+  double ybuf[NMAX];          // gathered state / right-hand side
+  double rates[2 * NMAX];     // reaction rates (mass action)
+  int16_t perm[NMAX];         // row i of P M is row perm[i] of M
+};
+
+template <int NPL>
+__device__ __forceinline__ double pick(const double (&x)[NPL], int slot) {
+  double v = x[0];
+#pragma unroll
+  for (int s = 1; s < NPL; ++s)
+    if (slot == s) v = x[s];
+  return v;
+}
+template <int NPL>
+__device__ __forceinline__ void place(double (&x)[NPL], int slot, double v) {
+#pragma unroll
+  for (int s = 0; s < NPL; ++s)
+    if (slot == s) x[s] = v;
+}
+
+// description of one cell's problem data (global memory)
+struct CellDesc {
+  int n, nr, kind;
+  const double* k;          // mass action: rate per reaction; Robertson: (k1, k2, k3)
+  const uint32_t* reac;     // 4 reactant species packed in bytes (255 = none)
+  const int32_t* inc_off;   // species i of this cell: entries inc_off[i] .. inc_off[i+1)
+  const uint16_t* inc;      // (reaction << 1) | (1 if produced, 0 if consumed)
+};
+
+// sqrt(sum (x_i w_i)^2 / n) over the group's elements
+template <int G, int NPL>
+__device__ __forceinline__ double wrms(const Grp<G>& g, int n, const double (&x)[NPL],
+                                       const double (&w)[NPL]) {
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) {
+      const double v = x[p] * w[p];
+      s = fma(v, v, s);
+    }
+  }
+  return sqrt(g.sum(s) / (double)n);
+}
+
+template <int G, int NPL>
+__device__ __forceinline__ bool all_finite(const Grp<G>& g, int n, const double (&x)[NPL]) {
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n && !isfinite(x[p])) bad = true;
+  }
+  return !g.any(bad);
+}
+
+template <int G, int NPL, int NMAX>
+__device__ __forceinline__ void scatter_y(const Grp<G>& g, CellSmem<NMAX>& S, int n,
+                                          const double (&y)[NPL]) {
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) S.ybuf[i] = y[p];
+  }
+  g.sync();
+}
+
+// ------------------------------------------------------------ right-hand side
+// f = f(y).  Mass action: rate_r = k_r prod_{s in R(r)} y_s, then each species
+// sums -rate over reactions consuming it and +rate over reactions producing
+// it, in reaction order (the incidence lists are built in that order).
+template <int G, int NPL, int NMAX>
+__device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX>& S, const double (&y)[NPL],
+                    double (&f)[NPL]) {
+  scatter_y<G, NPL, NMAX>(g, S, c.n, y);
+  if (c.kind == BDFB_ROBERTSON) {
+    const double* k = c.k;
+    const double y0 = S.ybuf[0], y1 = S.ybuf[1], y2 = S.ybuf[2];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      double v = 0.0;
+      if (i == 0) v = -k[0] * y0 + k[2] * y1 * y2;
+      else if (i == 1) v = k[0] * y0 - k[2] * y1 * y2 - k[1] * y1 * y1;
+      else if (i == 2) v = k[1] * y1 * y1;
+      f[p] = v;
+    }
+  } else {
+    for (int r = g.rank; r < c.nr; r += G) {
+      const uint32_t rc = __ldg(c.reac + r);
+      double rate = __ldg(c.k + r);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const uint32_t s = (rc >> (8 * a)) & 255u;
+        if (s != 255u) rate *= S.ybuf[s];
+      }
+      S.rates[r] = rate;
+    }
+    g.sync();
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      double acc = 0.0;
+      if (i < c.n) {
+        const int e1 = __ldg(c.inc_off + i + 1);
+        for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
+          const uint32_t v = __ldg(c.inc + e);
+          const double rt = S.rates[v >> 1];
+          acc = (v & 1u) ? acc + rt : acc - rt;
+        }
+      }
+      f[p] = acc;
+    }
+  }
+  g.sync();
+}
+
+// M = I - gamma J(y) into shared memory (rows owned by lanes).  J entries are
+// accumulated in reaction order as in the definition; M is formed without a
+// fused multiply-add so it equals the textbook rounding of 1 - gamma J.
+template <int G, int NPL, int NMAX>
+__device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX>& S,
+                       const double (&y)[NPL], double gamma) {
+  scatter_y<G, NPL, NMAX>(g, S, c.n, y);
+  const int n = c.n;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i >= n) continue;
+    double* row = S.M[i];
+    for (int j = 0; j < n; ++j) row[j] = 0.0;
+    if (c.kind == BDFB_ROBERTSON) {
+      const double* k = c.k;
+      const double y1 = S.ybuf[1], y2 = S.ybuf[2];
+      if (i == 0) { row[0] = -k[0]; row[1] = k[2] * y2; row[2] = k[2] * y1; }
+      else if (i == 1) { row[0] = k[0]; row[1] = -k[2] * y2 - 2.0 * k[1] * y1; row[2] = -k[2] * y1; }
+      else if (i == 2) { row[1] = 2.0 * k[1] * y1; }
+    } else {
+      const int e1 = __ldg(c.inc_off + i + 1);
+      for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
+        const uint32_t v = __ldg(c.inc + e);
+        const int r = (int)(v >> 1);
+        const uint32_t rc = __ldg(c.reac + r);
+        const double kr = __ldg(c.k + r);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const uint32_t s = (rc >> (8 * a)) & 255u;
+          if (s == 255u) continue;
+          double d = kr;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t sb = (rc >> (8 * b)) & 255u;
+            if (b != a && sb != 255u) d *= S.ybuf[sb];
+          }
+          row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+        }
+      }
+    }
+    for (int j = 0; j < n; ++j) row[j] = __dsub_rn(i == j ? 1.0 : 0.0, __dmul_rn(gamma, row[j]));
+  }
+  g.sync();
+}
+
+// ---------------------------------------------------------------- dense LU
+// Right-looking LU with partial pivoting of the n x n matrix in S.M (ties in
+// |pivot| go to the lowest row).  Returns 0 or k + 1 when pivot k is zero (or
+// no finite pivot exists).  pivk (optional) records the pivot row of each step.
+template <int G, int NMAX, typename T>
+__device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* dinv, int16_t* perm, int n,
+                         int16_t* pivk = nullptr) {
+  for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
+  g.sync();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int p = n;
+    for (int i = k + g.rank; i < n; i += G) {
+      const double v = fabs((double)M[i][k]);
+      if (v > best) { best = v; p = i; }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(g.mask, best, o, G);
+      const int op = __shfl_xor_sync(g.mask, p, o, G);
+      if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+    }
+    if (!(best > 0.0) || p >= n) return k + 1;
+    if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
+    if (p != k) {
+      for (int j = g.rank; j < n; j += G) {
+        const T a = M[k][j];
+        M[k][j] = M[p][j];
+        M[p][j] = a;
+      }
+      if (g.rank == 0) {
+        const int16_t a = perm[k];
+        perm[k] = perm[p];
+        perm[p] = a;
+      }
+    }
+    g.sync();
+    const T rinv = (T)1 / M[k][k];
+    if (g.rank == 0) dinv[k] = rinv;
+    for (int i = k + 1 + g.rank; i < n; i += G) M[i][k] *= rinv;
+    g.sync();
+    for (int j = k + 1 + g.rank; j < n; j += G) {
+      const T ukj = M[k][j];
+      for (int i = k + 1; i < n; ++i) M[i][j] = fma(-M[i][k], ukj, M[i][j]);
+    }
+    g.sync();
+  }
+  return 0;
+}
+
+// x <- (P M)^{-1} P x with the factors above; x distributed over the group.
+template <int G, int NPL, int NMAX, typename T>
+__device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1], const T* dinv,
+                         const int16_t* perm, double* buf, int n, double (&x)[NPL]) {
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) buf[i] = x[p];
+  }
+  g.sync();
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) x[p] = buf[perm[i]];
+  }
+  g.sync();
+  for (int j = 0; j < n; ++j) {                 // L y = P b (unit lower)
+    const double xj = g.bcast(pick(x, j / G), j % G);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
+    }
+  }
+  for (int j = n - 1; j >= 0; --j) {            // U x = y
+    const int owner = j % G, slot = j / G;
+    const double xj = g.bcast(pick(x, slot), owner) * (double)dinv[j];
+    if (g.rank == owner) place(x, slot, xj);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < j) x[p] = fma(-(double)M[i][j], xj, x[p]);
+    }
+  }
+}
+
+}  // namespace bdfb

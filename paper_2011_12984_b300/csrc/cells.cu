@@ -1,0 +1,1044 @@
+// cells.cu - persistent batched BDF / Newton integration of independent cells.
+//
+// The paper's submodel use case (Sec. 2): many small independent ODE systems,
+// one per grid cell, whose Jacobian is block diagonal (Fig. 1); each block is
+// solved directly (Sec. 5 batched block solver; Sec. 6 task-local Newton with
+// per-block solves, a failed solve repeating the step with a smaller h).
+// Here every cell keeps its own step size and order, and one persistent launch
+// integrates all cells to tout: warps take tiles of cells from an atomic
+// counter; a tile is 32/G cells of one size class handled by groups of G
+// lanes (cellcore.cuh).  The BDF step is the fixed-leading-coefficient
+// Nordsieck form with constant-step coefficients and history rescaling:
+//   predict z <- z A (Pascal), Newton on
+//   G(D) = D - gamma f(t, z0 + D) + z1 / l1 with M = I - gamma J,
+//   error test E_q ||D|| <= 1, accept z <- z + l D, then choose h and q.
+// Nothing in the kernel waits on another warp; every loop is bounded.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cellcore.cuh"
+
+namespace bdfb {
+
+constexpr int QMAX = 5;
+constexpr int NCLASS = 5;
+constexpr int CLS_G[NCLASS] = {1, 4, 8, 16, 32};
+constexpr int CLS_NMAX[NCLASS] = {4, 8, 16, 32, 56};
+constexpr int NMAX_ALL = 56;
+
+struct Consts {
+  double l[QMAX + 1][QMAX + 1];  // l[q][j], coefficients of prod_{i<=q} (1 + x/i)
+  double rl1[QMAX + 1];          // 1 / l[q][1]
+  double E[QMAX + 1][3];         // E_q, E_{q-1}, E_{q+1}
+  double qfact[QMAX + 2];        // q!
+};
+
+struct CellState {
+  double t, h, gammap, crate, hlast;
+  int32_t q, qwait, nst, nstlp;
+  int32_t nfe, nsetups, nni, ncfn;
+  int32_t netf, flags, status, qlast;
+  int32_t nrefine, nrefine_fb, pad0, pad1;
+};
+enum { F_STARTED = 1, F_GROWN = 2 };
+
+struct TileDesc {
+  int32_t cls, first, count, pad;
+};
+
+struct Params {
+  int kind;
+  int qmax;
+  int64_t ny;                 // total species
+  const int32_t* n;
+  const int64_t* y_off;
+  const int64_t* rxn_off;
+  const uint32_t* reac;
+  const double* k;
+  const int32_t* inc_off;
+  const uint16_t* inc;
+  const TileDesc* tiles;
+  const int32_t* tile_cells;
+  int ntiles;
+  unsigned* tile_counter;
+  int* worst;
+  CellState* st;
+  double* z;                  // 6 planes of ny doubles; plane 0 = y
+  double* acorp;              // ny
+  int32_t* status;            // per cell (may be null)
+  double tout, rtol, atol;
+  int32_t mxstep;
+  Consts K;
+};
+
+template <int G>
+__device__ __forceinline__ double gmax(const Grp<G>& g, double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(g.mask, v, o, G));
+  return v;
+}
+
+template <int G, int NMAX>
+struct Cell {
+  static constexpr int NPL = (NMAX + G - 1) / G;
+  double z[QMAX + 1][NPL], zs[QMAX + 1][NPL];
+  double acor[NPL], acorp[NPL], ewt[NPL], f[NPL], b[NPL];
+  double t, h, gamma, gammap, crate, hlast;
+  int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
+  int nst0, ncf, nef, setup_done, force_setup, tried_fresh, newstep, last, retry;
+};
+
+template <int G, int NMAX>
+__device__ __forceinline__ void rescale(Cell<G, NMAX>& C, double eta) {
+  double fct = 1.0;
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j) {
+    fct *= eta;
+    if (j <= C.q) {
+#pragma unroll
+      for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) C.z[j][p] *= fct;
+    }
+  }
+  C.h *= eta;
+}
+
+template <int G, int NMAX>
+__device__ __forceinline__ void set_ewt(const Grp<G>& g, const Params& P, int n, Cell<G, NMAX>& C) {
+#pragma unroll
+  for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
+    const int i = g.rank + G * p;
+    C.ewt[p] = i < n ? 1.0 / (P.rtol * fabs(C.z[0][p]) + P.atol) : 0.0;
+  }
+}
+
+// initial step and history (reading shared with the oracle: h0 from a
+// difference estimate of ||y''|| within [100 eps t, min(0.1 |tout - t|,
+// 0.1 (|y| + atol) / |f|)]).  Returns 0 or an error code.
+template <int G, int NMAX>
+__device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, const CellDesc& cd, CellSmem<NMAX>& S,
+                          Cell<G, NMAX>& C) {
+  constexpr int NPL = Cell<G, NMAX>::NPL;
+  const int n = cd.n;
+  set_ewt(g, P, n, C);
+  double y[NPL];
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
+  rhs<G, NPL, NMAX>(g, cd, S, y, C.acor);          // f0 kept in acor
+  C.nfe++;
+  if (!all_finite(g, n, C.acor)) return BDFB_RHSFUNC_FAIL;
+  const double tdist = fabs(P.tout - C.t);
+  const double tround = 2.220446049250313e-16 * fmax(fabs(C.t), fabs(P.tout));
+  const double hlb = 100.0 * tround;
+  double hub = 0.1 * tdist;
+  double inv = 0.0;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) inv = fmax(inv, fabs(C.acor[p]) / (0.1 * fabs(C.z[0][p]) + P.atol));
+  }
+  inv = gmax(g, inv);
+  if (inv * hub > 1.0) hub = 1.0 / inv;
+  if (hub < hlb) hub = hlb;
+  double hg = sqrt(hlb * hub), hnew = hg;
+  for (int it = 0; it < 4; ++it) {
+    bool ok = false;
+    for (int tries = 0; tries < 4; ++tries) {
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p] + hg * C.acor[p];
+      rhs<G, NPL, NMAX>(g, cd, S, y, C.f);
+      C.nfe++;
+      if (all_finite(g, n, C.f)) { ok = true; break; }
+      hg *= 0.2;
+    }
+    if (!ok) return BDFB_RHSFUNC_FAIL;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) C.b[p] = (C.f[p] - C.acor[p]) / hg;
+    const double ydd = wrms(g, n, C.b, C.ewt);
+    hnew = (ydd * hub * hub > 2.0) ? sqrt(2.0 / ydd) : sqrt(hg * hub);
+    const double rat = hnew / hg;
+    if (it > 0 && rat > 0.5 && rat < 2.0) break;
+    hg = hnew;
+  }
+  double h0 = 0.5 * hnew;
+  if (h0 < hlb) h0 = hlb;
+  if (h0 > hub) h0 = hub;
+  C.h = (P.tout >= C.t) ? h0 : -h0;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    C.z[1][p] = C.h * C.acor[p];
+#pragma unroll
+    for (int j = 2; j <= QMAX; ++j) C.z[j][p] = 0.0;
+  }
+  C.q = 1;
+  C.qwait = 2;
+  C.flags |= F_STARTED;
+  return 0;
+}
+
+// choose h and q after an accepted step (same rules as the oracle: safety
+// 6 / 6 / 10, change only if the best eta >= 1.5, eta <= 1e4 before the first
+// increase and <= 10 after, ties keep q then prefer q - 1)
+template <int G, int NMAX>
+__device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, int n, Cell<G, NMAX>& C, double dsm) {
+  constexpr int NPL = Cell<G, NMAX>::NPL;
+  if (--C.qwait > 0) return;
+  const int q = C.q;
+  const double eq = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
+  double eqm1 = 0.0, eqp1 = 0.0;
+  if (q > 1) {
+    double zq[NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 2; j <= QMAX; ++j)
+        if (j == q) v = C.z[j][p];
+      zq[p] = v;
+    }
+    const double d = P.K.E[q][1] * wrms(g, n, zq, C.ewt);
+    eqm1 = 1.0 / (pow(6.0 * d, 1.0 / q) + 1e-6);
+  }
+  if (q < P.qmax) {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) C.b[p] = C.acor[p] - C.acorp[p];
+    const double d = P.K.E[q][2] * wrms(g, n, C.b, C.ewt);
+    eqp1 = 1.0 / (pow(10.0 * d, 1.0 / (q + 2)) + 1e-6);
+  }
+  double etam = eq;
+  int qn = q;
+  if (eqm1 > etam) { etam = eqm1; qn = q - 1; }
+  if (eqp1 > etam) { etam = eqp1; qn = q + 1; }
+  if (etam < 1.5) { C.qwait = 1; return; }
+  const double cap = (C.flags & F_GROWN) ? 10.0 : 1.0e4;
+  if (etam > cap) etam = cap;
+  C.flags |= F_GROWN;
+  if (qn == q + 1) {
+    const double fq = P.K.qfact[q + 1];
+#pragma unroll
+    for (int j = 2; j <= QMAX; ++j)
+      if (j == q + 1) {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.z[j][p] = C.acor[p] / fq;
+      }
+    C.q = q + 1;
+  } else if (qn == q - 1) {
+#pragma unroll
+    for (int j = 2; j <= QMAX; ++j)
+      if (j == q) {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.z[j][p] = 0.0;
+      }
+    C.q = q - 1;
+  }
+  rescale(C, etam);
+  C.qwait = C.q + 1;
+}
+
+// One step attempt.  Returns true when the cell is finished (tout reached or
+// a failure status set).
+template <int G, int NMAX>
+__device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const CellDesc& cd, CellSmem<NMAX>& S,
+                        Cell<G, NMAX>& C) {
+  constexpr int NPL = Cell<G, NMAX>::NPL;
+  const int n = cd.n;
+  if (!(C.flags & F_STARTED)) {
+    const int r = start_cell(g, P, cd, S, C);
+    if (r) { C.status = r; return true; }
+    C.newstep = 1;
+  }
+  if (C.newstep) {
+    if ((P.tout - C.t) * C.h <= 0.0) { C.status = 0; return true; }
+    if (C.nst - C.nst0 >= P.mxstep) { C.status = BDFB_TOO_MUCH_WORK; return true; }
+    set_ewt(g, P, n, C);
+    C.ncf = 0;
+    C.nef = 0;
+    C.newstep = 0;
+    C.retry = 0;
+  }
+  if (!C.retry) {
+    C.last = 0;
+    if ((C.t + C.h - P.tout) * C.h >= 0.0) {
+      C.last = 1;
+      if (C.t + C.h != P.tout) { rescale(C, (P.tout - C.t) / C.h); C.qwait = C.q + 1; }
+    }
+  }
+  C.retry = 0;
+  if (C.t + C.h == C.t) { C.status = BDFB_ERR_FAILURE; return true; }
+  const int q = C.q;
+  // save and predict: z_{j-1} += z_j repeatedly (Pascal triangle)
+#pragma unroll
+  for (int j = 0; j <= QMAX; ++j)
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) C.zs[j][p] = C.z[j][p];
+#pragma unroll
+  for (int k = 1; k <= QMAX; ++k)
+#pragma unroll
+    for (int j = QMAX; j >= 1; --j)
+      if (k <= q && j >= k && j <= q) {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.z[j - 1][p] += C.z[j][p];
+      }
+  const double tnew = C.last ? P.tout : C.t + C.h;
+  const double rl1 = P.K.rl1[q];
+  const double Eq = P.K.E[q][0];
+  C.gamma = C.h * rl1;
+  // ---- linear setup
+  int jcur = 0;
+  bool fail = false;
+  if (!C.setup_done || C.force_setup || fabs(C.gamma / C.gammap - 1.0) > 0.3 ||
+      C.nst >= C.nstlp + 20) {
+    double y[NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
+    form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
+    const int info = lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n);
+    C.nsetups++;
+    C.gammap = C.gamma;
+    C.crate = 1.0;
+    C.nstlp = C.nst;
+    C.force_setup = 0;
+    C.setup_done = 1;
+    jcur = 1;
+    if (info) { fail = true; C.setup_done = 0; }
+  }
+  // ---- Newton iteration
+  double acnrm = 0.0;
+  bool conv = false;
+  if (!fail) {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
+    double delp = 0.0;
+    for (int it = 1; it <= 3; ++it) {
+      double y[NPL];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p] + C.acor[p];
+      rhs<G, NPL, NMAX>(g, cd, S, y, C.f);
+      C.nfe++;
+      if (!all_finite(g, n, C.f)) break;
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.b[p] = C.gamma * C.f[p] - C.z[1][p] * rl1 - C.acor[p];
+      lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+      if (C.gamma != C.gammap) {
+        const double sc = 2.0 / (1.0 + C.gamma / C.gammap);
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.b[p] *= sc;
+      }
+      const double del = wrms(g, n, C.b, C.ewt);
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.acor[p] += C.b[p];
+      C.nni++;
+      if (it > 1) C.crate = fmax(0.3 * C.crate, del / delp);
+      const double dcon = del * fmin(1.0, C.crate) * Eq / 0.1;
+      if (dcon <= 1.0) {
+        acnrm = (it == 1) ? del : wrms(g, n, C.acor, C.ewt);
+        conv = true;
+        break;
+      }
+      if (it >= 2 && del > 2.0 * delp) break;
+      delp = del;
+    }
+    if (!conv) fail = true;
+  }
+  if (fail) {
+#pragma unroll
+    for (int j = 0; j <= QMAX; ++j)
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.z[j][p] = C.zs[j][p];
+    if (!jcur && !C.tried_fresh && C.setup_done) {   // stale M: retry once with a fresh one
+      C.force_setup = 1;
+      C.tried_fresh = 1;
+      C.retry = 1;
+      return false;
+    }
+    C.tried_fresh = 0;
+    C.ncf++;
+    C.ncfn++;
+    if (C.ncf >= 10) { C.status = BDFB_CONV_FAILURE; return true; }
+    rescale(C, 0.25);
+    C.qwait = C.q + 1;
+    C.force_setup = 1;
+    return false;
+  }
+  C.tried_fresh = 0;
+  // ---- local error test
+  const double dsm = acnrm * Eq;
+  if (!(dsm <= 1.0)) {
+#pragma unroll
+    for (int j = 0; j <= QMAX; ++j)
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.z[j][p] = C.zs[j][p];
+    C.nef++;
+    C.netf++;
+    if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
+    if (C.nef < 3) {
+      double eta = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
+      if (!(eta >= 0.1)) eta = 0.1;
+      if (C.nef >= 2 && eta > 0.2) eta = 0.2;
+      rescale(C, eta);
+      C.qwait = C.q + 1;
+    } else {
+      // third failure: order 1, h / 10, fresh slope
+#pragma unroll
+      for (int j = 2; j <= QMAX; ++j)
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.z[j][p] = 0.0;
+      C.q = 1;
+      C.h *= 0.1;
+      double y[NPL];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
+      rhs<G, NPL, NMAX>(g, cd, S, y, C.f);
+      C.nfe++;
+      if (!all_finite(g, n, C.f)) { C.status = BDFB_RHSFUNC_FAIL; return true; }
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.z[1][p] = C.h * C.f[p];
+      C.qwait = 2;
+    }
+    return false;
+  }
+  // ---- accept
+#pragma unroll
+  for (int j = 0; j <= QMAX; ++j)
+    if (j <= q) {
+      const double lj = P.K.l[q][j];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) C.z[j][p] = fma(lj, C.acor[p], C.z[j][p]);
+    }
+  C.t = tnew;
+  C.nst++;
+  C.hlast = C.h;
+  C.qlast = q;
+  select_next(g, P, n, C, dsm);
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) C.acorp[p] = C.acor[p];
+  C.newstep = 1;
+  if (C.last) { C.t = P.tout; C.status = 0; return true; }
+  return false;
+}
+
+template <int G, int NMAX>
+__device__ void run_tile(const Params& P, const TileDesc td, char* smem) {
+  constexpr int NPL = Cell<G, NMAX>::NPL;
+  Grp<G> g;
+  const int gid = (threadIdx.x & 31) / G;
+  CellSmem<NMAX>& S = reinterpret_cast<CellSmem<NMAX>*>(smem)[gid];
+  bool active = gid < td.count;
+  int64_t c = 0;
+  CellDesc cd;
+  Cell<G, NMAX> C;
+  int64_t yo = 0;
+  if (active) {
+    c = P.tile_cells[td.first + gid];
+    if (P.kind == BDFB_ROBERTSON) {
+      cd.n = 3;
+      cd.nr = 0;
+      cd.k = P.k + 3 * c;
+      cd.reac = nullptr;
+      cd.inc_off = nullptr;
+      cd.inc = nullptr;
+      yo = 3 * c;
+    } else {
+      cd.n = P.n[c];
+      yo = P.y_off[c];
+      const int64_t ro = P.rxn_off[c];
+      cd.nr = (int)(P.rxn_off[c + 1] - ro);
+      cd.k = P.k + ro;
+      cd.reac = P.reac + ro;
+      cd.inc_off = P.inc_off + yo;
+      cd.inc = P.inc;
+    }
+    cd.kind = P.kind;
+    const CellState s = P.st[c];
+    C.t = s.t; C.h = s.h; C.gammap = s.gammap; C.crate = s.crate; C.hlast = s.hlast;
+    C.q = s.q; C.qwait = s.qwait; C.nst = s.nst; C.nstlp = s.nstlp;
+    C.nfe = s.nfe; C.nsetups = s.nsetups; C.nni = s.nni; C.ncfn = s.ncfn;
+    C.netf = s.netf; C.flags = s.flags; C.status = 0; C.qlast = s.qlast;
+    C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
+    C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      const bool in = i < cd.n;
+#pragma unroll
+      for (int j = 0; j <= QMAX; ++j) C.z[j][p] = in ? P.z[(int64_t)j * P.ny + yo + i] : 0.0;
+      C.acorp[p] = in ? P.acorp[yo + i] : 0.0;
+      C.acor[p] = 0.0;
+      C.ewt[p] = 0.0;
+    }
+  }
+  while (__any_sync(FULL_MASK, active)) {
+    if (active) {
+      if (attempt<G, NMAX>(g, P, cd, S, C)) {
+        active = false;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) {
+          const int i = g.rank + G * p;
+          if (i < cd.n) {
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) P.z[(int64_t)j * P.ny + yo + i] = C.z[j][p];
+            P.acorp[yo + i] = C.acorp[p];
+          }
+        }
+        if (g.rank == 0) {
+          CellState s;
+          s.t = C.t; s.h = C.h; s.gammap = C.gammap; s.crate = C.crate; s.hlast = C.hlast;
+          s.q = C.q; s.qwait = C.qwait; s.nst = C.nst; s.nstlp = C.nstlp;
+          s.nfe = C.nfe; s.nsetups = C.nsetups; s.nni = C.nni; s.ncfn = C.ncfn;
+          s.netf = C.netf; s.flags = C.flags; s.status = C.status; s.qlast = C.qlast;
+          s.nrefine = 0; s.nrefine_fb = 0; s.pad0 = 0; s.pad1 = 0;
+          P.st[c] = s;
+          if (P.status) P.status[c] = C.status;
+          if (C.status < 0) atomicMin(P.worst, C.status);
+        }
+      }
+    }
+  }
+}
+
+template <int CLS>
+struct ClassSmem {
+  static constexpr int bytes = (32 / CLS_G[CLS]) * (int)sizeof(CellSmem<CLS_NMAX[CLS]>);
+};
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int SMEM_PER_WARP =
+    cmax(cmax(cmax(ClassSmem<0>::bytes, ClassSmem<1>::bytes), cmax(ClassSmem<2>::bytes, ClassSmem<3>::bytes)),
+         ClassSmem<4>::bytes);
+
+__global__ void __launch_bounds__(32) k_cells(const Params P) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(P.tile_counter, 1u);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    if (t >= P.ntiles) break;
+    const TileDesc td = P.tiles[t];
+    switch (td.cls) {
+      case 0: run_tile<1, 4>(P, td, smem); break;
+      case 1: run_tile<4, 8>(P, td, smem); break;
+      case 2: run_tile<8, 16>(P, td, smem); break;
+      case 3: run_tile<16, 32>(P, td, smem); break;
+      default: run_tile<32, 56>(P, td, smem); break;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------- standalone batched LU
+constexpr int LU_NMAX = 64;
+
+__global__ void __launch_bounds__(32) k_lu_factor(int64_t nb, int n, double* a, int32_t* piv,
+                                                  int32_t* info) {
+  extern __shared__ __align__(16) char smem[];
+  auto& S = *reinterpret_cast<CellSmem<LU_NMAX>*>(smem);
+  int16_t* pk = reinterpret_cast<int16_t*>(smem + sizeof(CellSmem<LU_NMAX>));
+  Grp<32> g;
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    double* A = a + b * n * n;
+    for (int e = g.rank; e < n * n; e += 32) S.M[e / n][e % n] = A[e];
+    g.sync();
+    for (int e = g.rank; e < n; e += 32) pk[e] = (int16_t)e;
+    g.sync();
+    const int r = lu_factor<32, LU_NMAX, double>(g, S.M, S.dinv, S.perm, n, pk);
+    for (int e = g.rank; e < n * n; e += 32) A[e] = S.M[e / n][e % n];
+    for (int e = g.rank; e < n; e += 32) piv[b * n + e] = pk[e];
+    if (g.rank == 0) info[b] = r;
+    g.sync();
+  }
+}
+
+__global__ void __launch_bounds__(32) k_lu_solve(int64_t nb, int n, const double* lu,
+                                                 const int32_t* piv, double* bvec) {
+  extern __shared__ __align__(16) char smem[];
+  auto& S = *reinterpret_cast<CellSmem<LU_NMAX>*>(smem);
+  Grp<32> g;
+  constexpr int NPL = 2;
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const double* A = lu + b * n * n;
+    for (int e = g.rank; e < n * n; e += 32) S.M[e / n][e % n] = A[e];
+    for (int e = g.rank; e < n; e += 32) S.dinv[e] = 1.0 / A[e * n + e];
+    if (g.rank == 0) {                       // compose the row swaps into a permutation
+      for (int e = 0; e < n; ++e) S.perm[e] = (int16_t)e;
+      for (int e = 0; e < n; ++e) {
+        const int p = piv[b * n + e];
+        const int16_t t = S.perm[e];
+        S.perm[e] = S.perm[p];
+        S.perm[p] = t;
+      }
+    }
+    g.sync();
+    double x[NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + 32 * p;
+      x[p] = i < n ? bvec[b * n + i] : 0.0;
+    }
+    lu_solve<32, NPL, LU_NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, x);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + 32 * p;
+      if (i < n) bvec[b * n + i] = x[p];
+    }
+    g.sync();
+  }
+}
+
+static Consts make_consts() {
+  Consts K;
+  std::memset(&K, 0, sizeof K);
+  for (int q = 1; q <= QMAX; ++q) {
+    double l[QMAX + 2] = {0};
+    l[0] = 1.0;
+    for (int i = 1; i <= q; ++i)
+      for (int j = i; j >= 1; --j) l[j] += l[j - 1] / (double)i;
+    for (int j = 0; j <= q; ++j) K.l[q][j] = l[j];
+  }
+  K.qfact[0] = 1.0;
+  for (int q = 1; q <= QMAX + 1; ++q) K.qfact[q] = K.qfact[q - 1] * q;
+  for (int q = 1; q <= QMAX; ++q) {
+    K.rl1[q] = 1.0 / K.l[q][1];
+    K.E[q][0] = 1.0 / ((q + 1) * K.l[q][1]);
+    K.E[q][1] = q > 1 ? K.qfact[q - 1] / K.l[q - 1][1] : 0.0;
+    if (q < QMAX) {
+      // l_1 of order q+1
+      double l1 = 0.0;
+      for (int i = 1; i <= q + 1; ++i) l1 += 1.0 / (double)i;
+      K.E[q][2] = 1.0 / ((q + 2) * l1);
+    }
+  }
+  return K;
+}
+
+}  // namespace bdfb
+
+using namespace bdfb;
+
+// ---------------------------------------------------------------- context
+struct bdfb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int kind = 0;
+  int64_t ncell = 0, ny = 0, nrxn = 0;
+  std::vector<int32_t> h_n;
+  std::vector<int64_t> h_yoff;
+  int32_t* d_n = nullptr;
+  int64_t* d_yoff = nullptr;
+  int64_t* d_rxnoff = nullptr;
+  uint32_t* d_reac = nullptr;
+  double* d_k = nullptr;
+  int32_t* d_incoff = nullptr;
+  uint16_t* d_inc = nullptr;
+  CellState* d_state = nullptr;
+  double* d_z = nullptr;
+  double* d_acorp = nullptr;
+  TileDesc* d_tiles[2] = {nullptr, nullptr};
+  int32_t* d_tcells[2] = {nullptr, nullptr};
+  int ntiles[2] = {0, 0};
+  unsigned* d_counter = nullptr;   // [0] tile counter, [1] worst status (int)
+  int32_t* d_status = nullptr;
+  double rtol = 1e-6, atol = 1e-10;
+  int64_t mxstep = 100000;
+  int mapping = 0, precision = 0, graph = 0, qmax = QMAX;
+  double t0 = 0.0;
+  bool initialized = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.f;
+  int grid = 0;
+};
+
+static void free_ctx(bdfb_ctx* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
+  cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
+  cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
+  for (int m = 0; m < 2; ++m) { cudaFree(c->d_tiles[m]); cudaFree(c->d_tcells[m]); }
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+template <typename T>
+static int dev_alloc_copy(T** dst, const T* src, size_t count) {
+  if (count == 0) count = 1;
+  BDFB_CUDA(cudaMalloc(dst, count * sizeof(T)));
+  if (src) BDFB_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+// copy `count` elements from caller memory (host or device) into a host vector
+template <typename T>
+static int fetch(std::vector<T>& out, const T* src, size_t count, int mem) {
+  out.resize(count);
+  if (count == 0) return 0;
+  if (!src) return BDFB_ILL_INPUT;
+  if (mem == BDFB_MEM_DEVICE) {
+    BDFB_CUDA(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(out.data(), src, count * sizeof(T));
+  }
+  return 0;
+}
+
+static int class_of(int n, int nr) {
+  const int need = std::max(n, (nr + 1) / 2);
+  for (int c = 0; c < NCLASS; ++c)
+    if (need <= CLS_NMAX[c]) return c;
+  return -1;
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int r_ = (x);               \
+    if (r_) { free_ctx(c); return r_; } \
+  } while (0)
+
+extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
+  if (!prob || !out) return BDFB_ILL_INPUT;
+  *out = nullptr;
+  if (prob->ncell < 0 || (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION) ||
+      (prob->mem != BDFB_MEM_HOST && prob->mem != BDFB_MEM_DEVICE) || !prob->k)
+    return BDFB_ILL_INPUT;
+  bdfb_ctx* c = new (std::nothrow) bdfb_ctx();
+  if (!c) return BDFB_MEM_FAIL;
+  cudaGetDevice(&c->device);
+  c->kind = prob->kind;
+  c->ncell = prob->ncell;
+  const int64_t C = prob->ncell;
+  std::vector<int32_t> n;
+  std::vector<int64_t> yoff, roff;
+  std::vector<uint8_t> reac, prod;
+  std::vector<double> k;
+  std::vector<int32_t> cls(C);
+  if (prob->kind == BDFB_ROBERTSON) {
+    n.assign(C, 3);
+    yoff.resize(C + 1);
+    for (int64_t i = 0; i <= C; ++i) yoff[i] = 3 * i;
+    TRY(fetch(k, prob->k, 3 * C, prob->mem));
+    for (int64_t i = 0; i < C; ++i) cls[i] = 0;
+  } else {
+    if (!prob->n || !prob->y_off || !prob->rxn_off || !prob->reactants || !prob->products) {
+      free_ctx(c);
+      return BDFB_ILL_INPUT;
+    }
+    TRY(fetch(n, prob->n, C, prob->mem));
+    TRY(fetch(yoff, prob->y_off, C + 1, prob->mem));
+    TRY(fetch(roff, prob->rxn_off, C + 1, prob->mem));
+    if (yoff[0] != 0 || roff[0] != 0) { free_ctx(c); return BDFB_ILL_INPUT; }
+    for (int64_t i = 0; i < C; ++i) {
+      const int64_t nr = roff[i + 1] - roff[i];
+      if (n[i] < 1 || n[i] > NMAX_ALL || yoff[i + 1] - yoff[i] != n[i] || nr < 0 ||
+          nr > 2 * NMAX_ALL) {
+        free_ctx(c);
+        return BDFB_ILL_INPUT;
+      }
+      cls[i] = class_of(n[i], (int)nr);
+    }
+    const int64_t nrxn = roff[C];
+    TRY(fetch(reac, prob->reactants, 4 * nrxn, prob->mem));
+    TRY(fetch(prod, prob->products, 4 * nrxn, prob->mem));
+    TRY(fetch(k, prob->k, nrxn, prob->mem));
+    c->nrxn = nrxn;
+  }
+  c->ny = yoff[C];
+  c->h_n = n;
+  c->h_yoff = yoff;
+  if (prob->kind == BDFB_MASSACTION) {
+    // validate species and build the species-major incidence lists (reaction
+    // order; a reaction's consumption entry before its production entry)
+    std::vector<int32_t> incoff(c->ny + 1, 0);
+    std::vector<uint32_t> reac32(c->nrxn);
+    for (int64_t cc = 0; cc < C; ++cc) {
+      const int nn = n[cc];
+      for (int64_t r = roff[cc]; r < roff[cc + 1]; ++r) {
+        uint32_t w = 0;
+        for (int a = 0; a < 4; ++a) {
+          const uint8_t s = reac[4 * r + a], p = prod[4 * r + a];
+          if ((s != 255 && s >= nn) || (p != 255 && p >= nn)) { free_ctx(c); return BDFB_ILL_INPUT; }
+          for (int b2 = 0; b2 < a; ++b2)
+            if (s != 255 && reac[4 * r + b2] == s) { free_ctx(c); return BDFB_ILL_INPUT; }
+          w |= (uint32_t)s << (8 * a);
+          if (s != 255) incoff[yoff[cc] + s + 1]++;
+          if (p != 255) incoff[yoff[cc] + p + 1]++;
+        }
+        reac32[r] = w;
+      }
+    }
+    for (int64_t i = 0; i < c->ny; ++i) incoff[i + 1] += incoff[i];
+    if (incoff[c->ny] < 0 || (int64_t)incoff[c->ny] > (int64_t)0x7fffffff) { free_ctx(c); return BDFB_ILL_INPUT; }
+    std::vector<uint16_t> inc(std::max<int64_t>(1, incoff[c->ny]));
+    std::vector<int32_t> fill(incoff.begin(), incoff.end() - 1);
+    for (int64_t cc = 0; cc < C; ++cc)
+      for (int64_t r = roff[cc]; r < roff[cc + 1]; ++r) {
+        const uint16_t rl = (uint16_t)(r - roff[cc]);
+        for (int a = 0; a < 4; ++a) {
+          const uint8_t s = reac[4 * r + a];
+          if (s != 255) inc[fill[yoff[cc] + s]++] = (uint16_t)(rl << 1);
+        }
+        for (int a = 0; a < 4; ++a) {
+          const uint8_t p = prod[4 * r + a];
+          if (p != 255) inc[fill[yoff[cc] + p]++] = (uint16_t)((rl << 1) | 1u);
+        }
+      }
+    TRY(dev_alloc_copy(&c->d_n, n.data(), n.size()));
+    TRY(dev_alloc_copy(&c->d_yoff, yoff.data(), yoff.size()));
+    TRY(dev_alloc_copy(&c->d_rxnoff, roff.data(), roff.size()));
+    TRY(dev_alloc_copy(&c->d_reac, reac32.data(), reac32.size()));
+    TRY(dev_alloc_copy(&c->d_incoff, incoff.data(), incoff.size()));
+    TRY(dev_alloc_copy(&c->d_inc, inc.data(), inc.size()));
+  }
+  TRY(dev_alloc_copy(&c->d_k, k.data(), k.size()));
+  // schedules: [0] tiles by size class, largest class first; [1] one cell per warp, input order
+  for (int m = 0; m < 2; ++m) {
+    std::vector<TileDesc> tiles;
+    std::vector<int32_t> tcells;
+    if (m == 0) {
+      std::vector<int32_t> order(C);
+      for (int64_t i = 0; i < C; ++i) order[i] = (int32_t)i;
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (cls[a] != cls[b]) return cls[a] > cls[b];
+        return n[a] > n[b];
+      });
+      int64_t i = 0;
+      while (i < C) {
+        const int cl = cls[order[i]];
+        const int cpt = 32 / CLS_G[cl];
+        TileDesc td;
+        td.cls = cl;
+        td.first = (int32_t)tcells.size();
+        td.count = 0;
+        td.pad = 0;
+        while (i < C && cls[order[i]] == cl && td.count < cpt) { tcells.push_back(order[i]); ++td.count; ++i; }
+        tiles.push_back(td);
+      }
+    } else {
+      for (int64_t i = 0; i < C; ++i) {
+        TileDesc td;
+        td.cls = 4;
+        td.first = (int32_t)i;
+        td.count = 1;
+        td.pad = 0;
+        tiles.push_back(td);
+        tcells.push_back((int32_t)i);
+      }
+    }
+    c->ntiles[m] = (int)tiles.size();
+    TRY(dev_alloc_copy(&c->d_tiles[m], tiles.data(), tiles.size()));
+    TRY(dev_alloc_copy(&c->d_tcells[m], tcells.data(), tcells.size()));
+  }
+  TRY(dev_alloc_copy<CellState>(&c->d_state, nullptr, C));
+  TRY(dev_alloc_copy<double>(&c->d_z, nullptr, 6 * std::max<int64_t>(c->ny, 1)));
+  TRY(dev_alloc_copy<double>(&c->d_acorp, nullptr, c->ny));
+  TRY(dev_alloc_copy<unsigned>(&c->d_counter, nullptr, 2));
+  TRY(dev_alloc_copy<int32_t>(&c->d_status, nullptr, C));
+  BDFB_CUDA(cudaEventCreate(&c->ev0));
+  BDFB_CUDA(cudaEventCreate(&c->ev1));
+  BDFB_CUDA(cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_PER_WARP));
+  int per_sm = 0;
+  BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells, 32, SMEM_PER_WARP));
+  c->grid = std::max(1, per_sm) * sm_count();
+  *out = c;
+  return BDFB_SUCCESS;
+}
+
+extern "C" void bdfb_destroy(bdfb_ctx* ctx) { free_ctx(ctx); }
+
+extern "C" int bdfb_set_stream(bdfb_ctx* ctx, void* stream) {
+  if (!ctx) return BDFB_ILL_INPUT;
+  ctx->stream = as_stream(stream);
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol) {
+  if (!ctx || !(rtol >= 0.0) || !(atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol))
+    return BDFB_ILL_INPUT;
+  ctx->rtol = rtol;
+  ctx->atol = atol;
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
+  if (!ctx || !key) return BDFB_ILL_INPUT;
+  if (!std::strcmp(key, "mxstep")) {
+    if (v < 1 || v > 1000000000) return BDFB_ILL_INPUT;
+    ctx->mxstep = v;
+  } else if (!std::strcmp(key, "mapping")) {
+    if (v != 0 && v != 32) return BDFB_ILL_INPUT;
+    ctx->mapping = (int)v;
+  } else if (!std::strcmp(key, "precision")) {
+    if (v != 0) return BDFB_ILL_INPUT;   // FP32 factorisation not available in this build
+    ctx->precision = (int)v;
+  } else if (!std::strcmp(key, "graph")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    ctx->graph = (int)v;
+  } else if (!std::strcmp(key, "qmax")) {
+    if (v < 1 || v > QMAX) return BDFB_ILL_INPUT;
+    ctx->qmax = (int)v;
+  } else {
+    return BDFB_ILL_INPUT;
+  }
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem) {
+  if (!ctx || !std::isfinite(t0) || (ctx->ny > 0 && !y0)) return BDFB_ILL_INPUT;
+  if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  std::vector<CellState> st(std::max<int64_t>(ctx->ncell, 1));
+  std::memset(st.data(), 0, st.size() * sizeof(CellState));
+  for (auto& s : st) { s.t = t0; s.q = 1; s.crate = 1.0; }
+  cudaStream_t s = ctx->stream;
+  if (ctx->ncell > 0)
+    BDFB_CUDA(cudaMemcpyAsync(ctx->d_state, st.data(), ctx->ncell * sizeof(CellState),
+                              cudaMemcpyHostToDevice, s));
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_z, 0, 6 * std::max<int64_t>(ctx->ny, 1) * sizeof(double), s));
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_acorp, 0, std::max<int64_t>(ctx->ny, 1) * sizeof(double), s));
+  if (ctx->ny > 0)
+    BDFB_CUDA(cudaMemcpyAsync(ctx->d_z, y0, ctx->ny * sizeof(double),
+                              mem == BDFB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  BDFB_CUDA(cudaStreamSynchronize(s));   // the host staging vector goes out of scope
+  ctx->t0 = t0;
+  ctx->initialized = true;
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
+  if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
+  if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->ncell == 0) return BDFB_SUCCESS;
+  cudaStream_t s = ctx->stream;
+  const int m = ctx->mapping == 32 ? 1 : 0;
+  Params P;
+  std::memset(&P, 0, sizeof P);
+  P.kind = ctx->kind;
+  P.qmax = ctx->qmax;
+  P.ny = ctx->ny;
+  P.n = ctx->d_n;
+  P.y_off = ctx->d_yoff;
+  P.rxn_off = ctx->d_rxnoff;
+  P.reac = ctx->d_reac;
+  P.k = ctx->d_k;
+  P.inc_off = ctx->d_incoff;
+  P.inc = ctx->d_inc;
+  P.tiles = ctx->d_tiles[m];
+  P.tile_cells = ctx->d_tcells[m];
+  P.ntiles = ctx->ntiles[m];
+  P.tile_counter = ctx->d_counter;
+  P.worst = reinterpret_cast<int*>(ctx->d_counter + 1);
+  P.st = ctx->d_state;
+  P.z = ctx->d_z;
+  P.acorp = ctx->d_acorp;
+  P.status = ctx->d_status;
+  P.tout = tout;
+  P.rtol = ctx->rtol;
+  P.atol = ctx->atol;
+  P.mxstep = (int32_t)std::min<int64_t>(ctx->mxstep, 0x7fffffff);
+  static const Consts K = make_consts();
+  P.K = K;
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned), s));
+  BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
+  const int grid = std::min<int>(ctx->grid, std::max(1, P.ntiles));
+  k_cells<<<grid, 32, SMEM_PER_WARP, s>>>(P);
+  BDFB_CUDA(cudaGetLastError());
+  BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
+  if (y) {
+    BDFB_CUDA(cudaMemcpyAsync(y, ctx->d_z, ctx->ny * sizeof(double),
+                              mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  }
+  if (status) {
+    BDFB_CUDA(cudaMemcpyAsync(status, ctx->d_status, ctx->ncell * sizeof(int32_t),
+                              mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  }
+  int worst = 0;
+  BDFB_CUDA(cudaMemcpyAsync(&worst, ctx->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaStreamSynchronize(s));
+  cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
+  return worst;
+}
+
+static int fetch_states(bdfb_ctx* ctx, std::vector<CellState>& st) {
+  st.resize(std::max<int64_t>(ctx->ncell, 1));
+  if (ctx->ncell > 0) {
+    BDFB_CUDA(cudaStreamSynchronize(ctx->stream));
+    BDFB_CUDA(cudaMemcpy(st.data(), ctx->d_state, ctx->ncell * sizeof(CellState), cudaMemcpyDeviceToHost));
+  }
+  return 0;
+}
+
+extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
+  if (!ctx || !out) return BDFB_ILL_INPUT;
+  std::vector<CellState> st;
+  int r = fetch_states(ctx, st);
+  if (r) return r;
+  std::memset(out, 0, sizeof *out);
+  out->ncell = ctx->ncell;
+  out->min_steps = ctx->ncell ? INT64_MAX : 0;
+  for (int64_t i = 0; i < ctx->ncell; ++i) {
+    const CellState& s = st[i];
+    out->nsteps += s.nst;
+    out->nfevals += s.nfe;
+    out->nlinsetups += s.nsetups;
+    out->nniters += s.nni;
+    out->nncfails += s.ncfn;
+    out->netfails += s.netf;
+    out->max_steps = std::max<int64_t>(out->max_steps, s.nst);
+    out->min_steps = std::min<int64_t>(out->min_steps, s.nst);
+    out->ncells_failed += s.status != 0;
+    out->nrefine += s.nrefine;
+    out->nrefine_fallback += s.nrefine_fb;
+  }
+  out->last_kernel_ms = ctx->last_ms;
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
+  if (!ctx || (!out && ctx->ncell > 0)) return BDFB_ILL_INPUT;
+  if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  std::vector<CellState> st;
+  int r = fetch_states(ctx, st);
+  if (r) return r;
+  std::vector<int64_t> v(8 * std::max<int64_t>(ctx->ncell, 1));
+  for (int64_t i = 0; i < ctx->ncell; ++i) {
+    const CellState& s = st[i];
+    int64_t hb;
+    std::memcpy(&hb, &s.hlast, sizeof hb);
+    int64_t* o = v.data() + 8 * i;
+    o[0] = s.nst; o[1] = s.nfe; o[2] = s.nsetups; o[3] = s.nni;
+    o[4] = s.ncfn; o[5] = s.netf; o[6] = s.qlast; o[7] = hb;
+  }
+  if (ctx->ncell == 0) return BDFB_SUCCESS;
+  if (mem == BDFB_MEM_HOST) std::memcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t));
+  else BDFB_CUDA(cudaMemcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return BDFB_SUCCESS;
+}
+
+// ------------------------------------------------------ batched LU entries
+extern "C" int bdfb_batched_lu_factor(int64_t nb, int n, double* a, int32_t* piv, int32_t* info,
+                                      void* stream) {
+  if (nb < 0 || n < 1 || n > LU_NMAX || (nb > 0 && (!a || !piv || !info))) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  const int smem = (int)sizeof(CellSmem<LU_NMAX>) + LU_NMAX * (int)sizeof(int16_t);
+  BDFB_CUDA(cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int64_t grid = std::min<int64_t>(nb, (int64_t)sm_count() * 6);
+  k_lu_factor<<<(int)grid, 32, smem, as_stream(stream)>>>(nb, n, a, piv, info);
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_batched_lu_solve(int64_t nb, int n, const double* lu, const int32_t* piv,
+                                     double* b, void* stream) {
+  if (nb < 0 || n < 1 || n > LU_NMAX || (nb > 0 && (!lu || !piv || !b))) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  const int smem = (int)sizeof(CellSmem<LU_NMAX>);
+  BDFB_CUDA(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int64_t grid = std::min<int64_t>(nb, (int64_t)sm_count() * 6);
+  k_lu_solve<<<(int)grid, 32, smem, as_stream(stream)>>>(nb, n, lu, piv, b);
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}

@@ -1,0 +1,73 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, exports every
+symbol include/bdfb.h declares, and rejects bad arguments before touching the
+GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bdfb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_12984_b300 import build
+    path = build.build()
+    return C.CDLL(path), path
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bdfb_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L, path = lib
+    names = declared()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(bdfb_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(L, n)
+
+
+def test_strerror_and_version(lib):
+    L, _ = lib
+    L.bdfb_strerror.restype = C.c_char_p
+    assert L.bdfb_strerror(0) == b"success"
+    assert b"illegal" in L.bdfb_strerror(-22)
+    assert L.bdfb_version() >= 100
+
+
+def test_bad_arguments_rejected_without_gpu(lib):
+    L, _ = lib
+    ILL = -22
+    L.bdfb_nv_linear_sum.argtypes = [C.c_int64, C.c_double, C.c_void_p, C.c_double, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+    assert L.bdfb_nv_linear_sum(-1, 1.0, None, 1.0, None, None, None) == ILL
+    assert L.bdfb_nv_linear_sum(0, 1.0, None, 1.0, None, None, None) == 0      # empty: no work
+    L.bdfb_nv_linear_combination.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]
+    assert L.bdfb_nv_linear_combination(10, 0, None, None, None, None) == ILL
+    assert L.bdfb_nv_linear_combination(10, 17, None, None, None, None) == ILL
+    L.bdfb_batched_lu_factor.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert L.bdfb_batched_lu_factor(4, 65, None, None, None, None) == ILL
+    assert L.bdfb_batched_lu_factor(0, 10, None, None, None, None) == 0
+    L.bdfb_create.argtypes = [C.c_void_p, C.c_void_p]
+    assert L.bdfb_create(None, None) == ILL
+    L.bdfb_set_option.argtypes = [C.c_void_p, C.c_char_p, C.c_int64]
+    assert L.bdfb_set_option(None, b"mxstep", 5) == ILL
+
+
+def test_binding_imports_and_fails_loudly_without_library(tmp_path):
+    # the binding refuses to load when the shared library is missing
+    src = open(os.path.join(ROOT, "paper_2011_12984_b300", "bdfb.py")).read()
+    assert "raise ImportError" in src
+    from paper_2011_12984_b300 import bdfb
+    assert bdfb.lib is not None

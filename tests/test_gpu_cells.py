@@ -1,0 +1,158 @@
+"""GPU parity of the batched per-cell BDF/Newton integrator against the oracle.
+
+Final states are compared with an oracle run at rtol = 1e-10 (the truth) in
+units of the run's own error weights, err_c = max_i |y_i - y*_i| /
+(rtol |y*_i| + atol).  The bar: every cell within 10, or within 3x the
+oracle's own error on that cell plus 10 (local error control does not bound
+the global error; the oracle run at the same tolerance shows the same
+spread), and the GPU error distribution no wider than the oracle's.  Step
+counts must agree with the oracle's on average within 5%.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2011_12984_b300 import bdfb, gen
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, min(32, oracle.host_threads()))
+
+
+def werr(y, yr, prob, rtol, atol):
+    w = np.abs(y - yr) / (rtol * np.abs(yr) + atol)
+    off = prob.y_off
+    return np.maximum.reduceat(w, off[:-1]) if prob.ncell else np.zeros(0)
+
+
+def run_gpu(prob, t0, tout, rtol, atol, device_io=True, **opts):
+    with bdfb.Integrator(prob, rtol=rtol, atol=atol, **opts) as I:
+        if device_io:
+            I.init(t0, torch.from_numpy(prob.y0).cuda())
+            y = torch.empty(int(prob.y_off[-1]), dtype=torch.float64, device="cuda")
+            st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
+            ret = I.integrate(tout, y, st)
+            torch.cuda.synchronize()
+            y, st = y.cpu().numpy(), st.cpu().numpy()
+        else:
+            I.init(t0, prob.y0.copy())
+            y = np.empty(int(prob.y_off[-1]))
+            st = np.empty(prob.ncell, np.int32)
+            ret = I.integrate(tout, y, st)
+        return ret, y, st, I.cell_stats(), I.stats()
+
+
+def check_against_oracle(prob, tout, rtol, atol, y, cstats):
+    yo, so, sto = oracle.integrate_cells(prob, 0.0, tout, rtol, atol, threads=THREADS)
+    yt, stt, _ = oracle.integrate_cells(prob, 0.0, tout, 1e-10, 1e-14, threads=THREADS)
+    assert np.all(so == 0) and np.all(stt == 0)
+    eg = werr(y, yt, prob, rtol, atol)
+    eo = werr(yo, yt, prob, rtol, atol)
+    bad = ~((eg <= 10) | (eg <= 3 * eo + 10))
+    assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10])
+    assert np.percentile(eg, 50) <= 1.5 * np.percentile(eo, 50) + 1.0
+    assert np.percentile(eg, 99) <= 1.5 * np.percentile(eo, 99) + 1.0
+    assert abs(cstats[:, 0].mean() / sto[:, 0].mean() - 1.0) < 0.05
+    return eg, eo
+
+
+def test_robertson_1000_cells():
+    """Robertson kinetics, 1000 cells, rtol 1e-4, atol 1e-8 over [0, 40]."""
+    p = gen.robertson(1000)
+    ret, y, st, cs, stats = run_gpu(p, 0.0, 40.0, 1e-4, 1e-8)
+    assert ret == 0 and np.all(st == 0)
+    assert np.max(np.abs(y.reshape(-1, 3).sum(axis=1) - 1.0)) <= 1e-12   # sum y = 1
+    check_against_oracle(p, 40.0, 1e-4, 1e-8, y, cs)
+    assert stats["nsteps"] == cs[:, 0].sum()
+
+
+@pytest.mark.parametrize("mapping", [0, 32])
+def test_mass_action_mixed_sizes(mapping):
+    """1536 cells drawn like the 100 000-cell workload (sizes 3/10/32/54),
+    t in [0, 1e-3], rtol 1e-6, atol 1e-10; both cell-to-lane mappings."""
+    p = gen.mass_action(100000).subset(np.arange(1536))
+    ret, y, st, cs, _ = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10, mapping=mapping)
+    assert ret == 0 and np.all(st == 0)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    s1 = np.add.reduceat(y, p.y_off[:-1])
+    assert np.max(np.abs(s1 - s0)) <= 1e-12                              # conservation
+    check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs)
+
+
+def test_mass_action_full_size_sampled():
+    """The full 100 000-cell workload in the launch configuration the benchmark
+    times; every cell checked for status and conservation, 256 sampled cells
+    against the truth."""
+    p = gen.mass_action(100000)
+    ret, y, st, cs, stats = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10)
+    assert ret == 0 and np.all(st == 0)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    s1 = np.add.reduceat(y, p.y_off[:-1])
+    assert np.max(np.abs(s1 - s0)) <= 1e-12
+    cells = np.random.default_rng(7).choice(p.ncell, 256, replace=False)
+    sub = p.subset(cells)
+    ysub = np.concatenate([y[p.y_off[c]:p.y_off[c + 1]] for c in sorted(cells)])
+    order = np.argsort(cells)
+    sub = p.subset(np.sort(cells))
+    check_against_oracle(sub, 1e-3, 1e-6, 1e-10, ysub, cs[np.sort(cells)])
+    del order
+
+
+def test_host_and_device_io_agree():
+    p = gen.mass_action(100000, seed=3).subset(np.arange(200))
+    r1, y1, s1, _, _ = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10, device_io=True)
+    r2, y2, s2, _, _ = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10, device_io=False)
+    assert r1 == r2 == 0
+    assert np.array_equal(y1, y2) and np.array_equal(s1, s2)
+
+
+def test_deterministic_repeat():
+    p = gen.mass_action(100000, seed=4).subset(np.arange(300))
+    _, y1, _, c1, _ = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10)
+    _, y2, _, c2, _ = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10)
+    assert np.array_equal(y1, y2) and np.array_equal(c1, c2)
+
+
+def test_tout_equal_t0_and_continuation():
+    p = gen.mass_action(100000, seed=6).subset(np.arange(64))
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10) as I:
+        I.init(0.0, p.y0.copy())
+        y = np.empty(p.y0.size)
+        st = np.empty(p.ncell, np.int32)
+        assert I.integrate(0.0, y, st) == 0
+        assert np.array_equal(y, p.y0)
+        assert I.integrate(5e-4, y, st) == 0
+        assert I.integrate(1e-3, y, st) == 0 and np.all(st == 0)
+    yt, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-10, 1e-14, threads=THREADS)
+    yo, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-6, 1e-10, threads=THREADS)
+    eg, eo = werr(y, yt, p, 1e-6, 1e-10), werr(yo, yt, p, 1e-6, 1e-10)
+    assert np.all((eg <= 10) | (eg <= 3 * eo + 10))
+
+
+def test_failure_statuses_do_not_disturb_other_cells():
+    p = gen.mass_action(100000, seed=8).subset(np.arange(96))
+    y0 = p.y0.copy()
+    y0[p.y_off[5]] = np.nan                     # a cell whose right-hand side is NaN
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10) as I:
+        I.init(0.0, y0)
+        y = np.empty(y0.size)
+        st = np.empty(p.ncell, np.int32)
+        ret = I.integrate(1e-3, y, st)
+        assert st[5] == bdfb.RHSFUNC_FAIL and ret == bdfb.RHSFUNC_FAIL
+        assert np.all(np.delete(st, 5) == 0)
+        I.set_option("mxstep", 1)
+        I.init(0.0, p.y0.copy())
+        ret = I.integrate(1e-3, y, st)
+        assert ret == bdfb.TOO_MUCH_WORK and np.all(st == bdfb.TOO_MUCH_WORK)
+
+
+def test_single_cell_and_closed_form():
+    """one 2-species cell A -> B at rate 3: y_A = exp(-3 t)"""
+    p = gen.MassActionProblem(n=np.array([2], np.int32), y_off=np.array([0, 2], np.int64),
+                              rxn_off=np.array([0, 1], np.int64),
+                              reactants=np.array([[0, 255, 255, 255]], np.uint8),
+                              products=np.array([[1, 255, 255, 255]], np.uint8),
+                              k=np.array([3.0]), y0=np.array([1.0, 0.0]))
+    ret, y, st, _, _ = run_gpu(p, 0.0, 1.0, 1e-9, 1e-14)
+    assert ret == 0
+    assert abs(y[0] - np.exp(-3.0)) <= 20 * 1e-9
