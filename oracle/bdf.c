@@ -385,6 +385,10 @@ static int step(or_bdf* m, double tout, int* reached) {
 int or_bdf_solve(or_bdf* m, double tout, double* yout) {
   int64_t N = m->N;
   int ret = 0;
+  if (tout == m->t) {            /* nothing to integrate; the first step waits for tout != t0 */
+    memcpy(yout, Z(m, 0), sizeof(double) * N);
+    return 0;
+  }
   if (!m->started) {
     set_ewt(m);
     int r = m->sys.rhs(m->sys.user, m->t, Z(m, 0), m->f);

@@ -245,6 +245,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   constexpr int NPL = Cell<G, NMAX>::NPL;
   const int n = cd.n;
   if (!(C.flags & F_STARTED)) {
+    if (P.tout == C.t) { C.status = 0; return true; }   // first step waits for tout != t0
     const int r = start_cell(g, P, cd, S, C);
     if (r) { C.status = r; return true; }
     C.newstep = 1;
