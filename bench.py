@@ -232,7 +232,10 @@ def run_ours(args):
     y = torch.empty_like(y0)
     st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL)
+    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping)
+    # one persistent launch per non-empty size class (bounds 4, 8, 16, 32, 56)
+    need = np.maximum(prob.n, (np.diff(prob.rxn_off) + 1) // 2)
+    launches_per_step = len(set(np.searchsorted([4, 8, 16, 32, 56], need).tolist())) if args.mapping == 0 else 1
 
     def step():
         integ.init(0.0, y0)
@@ -270,6 +273,16 @@ def run_ours(args):
     value = ws * NCELL / t_step
     cs = integ.cell_stats()
     yh = y.cpu().numpy()
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+                              "kernel_ms": 1e3 * sum(kern_s) / len(kern_s), "ncell": NCELL,
+                              "mapping": args.mapping, "quick": True}))
+        integ.close()
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     y0h = prob.y0.copy()
@@ -305,7 +318,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": WORKLOAD, "ncell": NCELL, "mapping": "size-class tiles (auto)",
+        "config": {"workload": WORKLOAD, "ncell": NCELL, "mapping": "size-class tiles (auto)" if args.mapping == 0 else "one warp per cell",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "accuracy": acc,
         "integrator_stats": {"steps_per_cell": st_sum["nsteps"] / NCELL,
@@ -324,7 +337,7 @@ def run_ours(args):
                          "sample": f"first {cpu_ns} of the {NCELL} cells ({cpu_dt:.1f} s, {cpu_fail} failed)"},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(8 * y0h.size),
                 "d2h_bytes_per_step": int(8 * y0h.size + 4 * prob.ncell)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))
@@ -339,7 +352,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ncell", type=int, default=NCELL, help="cells per GPU (default: the workload)")
+    ap.add_argument("--mapping", type=int, default=0, choices=[0, 32],
+                    help="0: size-class tiles; 32: one warp per cell in input order (plain form)")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the device path only (no e2e, accuracy, CPU or vector legs)")
     args = ap.parse_args()
+    globals()["NCELL"] = args.ncell
     if args.impl == "reference":
         run_reference(args)
     else:

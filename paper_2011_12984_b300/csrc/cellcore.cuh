@@ -44,10 +44,20 @@ struct Grp {
   }
 };
 
+// lane grid for 2-D work on a group's matrix: R rows x C columns of lanes
+template <int G>
+struct LaneGrid {
+  static constexpr int R = G >= 16 ? 4 : (G >= 4 ? 2 : 1);
+  static constexpr int C = G / R;
+};
+
+constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
+
 // per-cell shared memory
 template <int NMAX>
 struct CellSmem {
   double M[NMAX][NMAX + 1];   // M = I - gamma J, then its LU factors
+  double zs[ZCOLS][NMAX];     // history saved before a step attempt
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side
   double rates[2 * NMAX];     // reaction rates (mass action)
@@ -253,9 +263,25 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     if (g.rank == 0) dinv[k] = rinv;
     for (int i = k + 1 + g.rank; i < n; i += G) M[i][k] *= rinv;
     g.sync();
-    for (int j = k + 1 + g.rank; j < n; j += G) {
-      const T ukj = M[k][j];
-      for (int i = k + 1; i < n; ++i) M[i][j] = fma(-M[i][k], ukj, M[i][j]);
+    // rank-1 update of the trailing block, lanes on an R x C grid
+    {
+      constexpr int R = LaneGrid<G>::R, C = LaneGrid<G>::C;
+      constexpr int NJ = (NMAX + C - 1) / C;
+      const int li = g.rank / C, lj = g.rank % C;
+      T u[NJ];
+#pragma unroll
+      for (int b = 0; b < NJ; ++b) {
+        const int j = k + 1 + lj + C * b;
+        u[b] = j < n ? M[k][j] : (T)0;
+      }
+      for (int i = k + 1 + li; i < n; i += R) {
+        const T lik = M[i][k];
+#pragma unroll
+        for (int b = 0; b < NJ; ++b) {
+          const int j = k + 1 + lj + C * b;
+          if (j < n) M[i][j] = fma(-lik, u[b], M[i][j]);
+        }
+      }
     }
     g.sync();
   }

@@ -84,7 +84,7 @@ __device__ __forceinline__ double gmax(const Grp<G>& g, double v) {
 template <int G, int NMAX>
 struct Cell {
   static constexpr int NPL = (NMAX + G - 1) / G;
-  double z[QMAX + 1][NPL], zs[QMAX + 1][NPL];
+  double z[QMAX + 1][NPL];
   double acor[NPL], acorp[NPL], ewt[NPL], f[NPL], b[NPL];
   double t, h, gamma, gammap, crate, hlast;
   int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
@@ -237,6 +237,19 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
   C.qwait = C.q + 1;
 }
 
+template <int G, int NMAX>
+__device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem<NMAX>& S,
+                                          Cell<G, NMAX>& C) {
+#pragma unroll
+  for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) {
+#pragma unroll
+      for (int j = 0; j <= QMAX; ++j) C.z[j][p] = S.zs[j][i];
+    }
+  }
+}
+
 // One step attempt.  Returns true when the cell is finished (tout reached or
 // a failure status set).
 template <int G, int NMAX>
@@ -271,9 +284,13 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   const int q = C.q;
   // save and predict: z_{j-1} += z_j repeatedly (Pascal triangle)
 #pragma unroll
-  for (int j = 0; j <= QMAX; ++j)
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) {
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) C.zs[j][p] = C.z[j][p];
+      for (int j = 0; j <= QMAX; ++j) S.zs[j][i] = C.z[j][p];
+    }
+  }
 #pragma unroll
   for (int k = 1; k <= QMAX; ++k)
 #pragma unroll
@@ -344,10 +361,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     if (!conv) fail = true;
   }
   if (fail) {
-#pragma unroll
-    for (int j = 0; j <= QMAX; ++j)
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) C.z[j][p] = C.zs[j][p];
+    restore_z(g, n, S, C);
     if (!jcur && !C.tried_fresh && C.setup_done) {   // stale M: retry once with a fresh one
       C.force_setup = 1;
       C.tried_fresh = 1;
@@ -367,10 +381,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   // ---- local error test
   const double dsm = acnrm * Eq;
   if (!(dsm <= 1.0)) {
-#pragma unroll
-    for (int j = 0; j <= QMAX; ++j)
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) C.z[j][p] = C.zs[j][p];
+    restore_z(g, n, S, C);
     C.nef++;
     C.netf++;
     if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
@@ -421,7 +432,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
 }
 
 template <int G, int NMAX>
-__device__ void run_tile(const Params& P, const TileDesc td, char* smem) {
+__device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
@@ -504,30 +515,28 @@ struct ClassSmem {
   static constexpr int bytes = (32 / CLS_G[CLS]) * (int)sizeof(CellSmem<CLS_NMAX[CLS]>);
 };
 
-constexpr int cmax(int a, int b) { return a > b ? a : b; }
-constexpr int SMEM_PER_WARP =
-    cmax(cmax(cmax(ClassSmem<0>::bytes, ClassSmem<1>::bytes), cmax(ClassSmem<2>::bytes, ClassSmem<3>::bytes)),
-         ClassSmem<4>::bytes);
-
-__global__ void __launch_bounds__(32) k_cells(const Params P) {
+// Persistent kernel of one size class: each warp takes the next tile of the
+// class range [t0, t1) from `counter` until none is left.
+template <int CLS>
+__global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, int t0, int t1,
+                                              unsigned* counter) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
   for (;;) {
     int t = 0;
-    if (lane == 0) t = (int)atomicAdd(P.tile_counter, 1u);
+    if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
     t = __shfl_sync(FULL_MASK, t, 0);
-    if (t >= P.ntiles) break;
-    const TileDesc td = P.tiles[t];
-    switch (td.cls) {
-      case 0: run_tile<1, 4>(P, td, smem); break;
-      case 1: run_tile<4, 8>(P, td, smem); break;
-      case 2: run_tile<8, 16>(P, td, smem); break;
-      case 3: run_tile<16, 32>(P, td, smem); break;
-      default: run_tile<32, 56>(P, td, smem); break;
-    }
+    if (t >= t1) break;
+    run_tile<CLS_G[CLS], CLS_NMAX[CLS]>(P, P.tiles[t], smem);
     __syncwarp();
   }
 }
+
+typedef void (*cells_kernel_t)(const Params, int, int, unsigned*);
+static const cells_kernel_t CELLS_KERNELS[NCLASS] = {k_cells<0>, k_cells<1>, k_cells<2>, k_cells<3>,
+                                                     k_cells<4>};
+static const int CELLS_SMEM[NCLASS] = {ClassSmem<0>::bytes, ClassSmem<1>::bytes, ClassSmem<2>::bytes,
+                                       ClassSmem<3>::bytes, ClassSmem<4>::bytes};
 
 // ------------------------------------------------- standalone batched LU
 constexpr int LU_NMAX = 64;
@@ -639,16 +648,19 @@ struct bdfb_ctx {
   TileDesc* d_tiles[2] = {nullptr, nullptr};
   int32_t* d_tcells[2] = {nullptr, nullptr};
   int ntiles[2] = {0, 0};
-  unsigned* d_counter = nullptr;   // [0] tile counter, [1] worst status (int)
+  int cls_begin[2][NCLASS] = {}, cls_end[2][NCLASS] = {};  // tile range of each class
+  unsigned* d_counter = nullptr;   // [c] tile counter of class c, [NCLASS] worst status (int)
   int32_t* d_status = nullptr;
   double rtol = 1e-6, atol = 1e-10;
   int64_t mxstep = 100000;
   int mapping = 0, precision = 0, graph = 0, qmax = QMAX;
   double t0 = 0.0;
   bool initialized = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
+  cudaEvent_t evjoin[NCLASS] = {};
+  cudaStream_t cstream[NCLASS] = {};  // one per size class, forked from `stream`
   float last_ms = 0.f;
-  int grid = 0;
+  int grid[NCLASS] = {};
 };
 
 static void free_ctx(bdfb_ctx* c) {
@@ -662,6 +674,11 @@ static void free_ctx(bdfb_ctx* c) {
   for (int m = 0; m < 2; ++m) { cudaFree(c->d_tiles[m]); cudaFree(c->d_tcells[m]); }
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evfork) cudaEventDestroy(c->evfork);
+  for (int k = 0; k < NCLASS; ++k) {
+    if (c->evjoin[k]) cudaEventDestroy(c->evjoin[k]);
+    if (c->cstream[k]) cudaStreamDestroy(c->cstream[k]);
+  }
   cudaSetDevice(prev);
   delete c;
 }
@@ -684,6 +701,24 @@ static int fetch(std::vector<T>& out, const T* src, size_t count, int mem) {
     BDFB_CUDA(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
   } else {
     std::memcpy(out.data(), src, count * sizeof(T));
+  }
+  return 0;
+}
+
+// events, per-class streams and persistent grid sizes (resident warps per SM
+// x SM count) of every class kernel
+static int setup_launch(bdfb_ctx* c) {
+  BDFB_CUDA(cudaEventCreate(&c->ev0));
+  BDFB_CUDA(cudaEventCreate(&c->ev1));
+  BDFB_CUDA(cudaEventCreateWithFlags(&c->evfork, cudaEventDisableTiming));
+  for (int k = 0; k < NCLASS; ++k) {
+    BDFB_CUDA(cudaEventCreateWithFlags(&c->evjoin[k], cudaEventDisableTiming));
+    BDFB_CUDA(cudaStreamCreateWithFlags(&c->cstream[k], cudaStreamNonBlocking));
+    BDFB_CUDA(cudaFuncSetAttribute(CELLS_KERNELS[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   CELLS_SMEM[k]));
+    int per_sm = 0;
+    BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CELLS_KERNELS[k], 32, CELLS_SMEM[k]));
+    c->grid[k] = std::max(1, per_sm) * sm_count();
   }
   return 0;
 }
@@ -831,20 +866,21 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
       }
     }
     c->ntiles[m] = (int)tiles.size();
+    for (int k2 = 0; k2 < NCLASS; ++k2) { c->cls_begin[m][k2] = 0; c->cls_end[m][k2] = 0; }
+    for (int t = 0; t < (int)tiles.size(); ++t) {   // tiles of a class are contiguous
+      const int cl = tiles[t].cls;
+      if (c->cls_end[m][cl] == 0) c->cls_begin[m][cl] = t;
+      c->cls_end[m][cl] = t + 1;
+    }
     TRY(dev_alloc_copy(&c->d_tiles[m], tiles.data(), tiles.size()));
     TRY(dev_alloc_copy(&c->d_tcells[m], tcells.data(), tcells.size()));
   }
   TRY(dev_alloc_copy<CellState>(&c->d_state, nullptr, C));
   TRY(dev_alloc_copy<double>(&c->d_z, nullptr, 6 * std::max<int64_t>(c->ny, 1)));
   TRY(dev_alloc_copy<double>(&c->d_acorp, nullptr, c->ny));
-  TRY(dev_alloc_copy<unsigned>(&c->d_counter, nullptr, 2));
+  TRY(dev_alloc_copy<unsigned>(&c->d_counter, nullptr, NCLASS + 1));
   TRY(dev_alloc_copy<int32_t>(&c->d_status, nullptr, C));
-  BDFB_CUDA(cudaEventCreate(&c->ev0));
-  BDFB_CUDA(cudaEventCreate(&c->ev1));
-  BDFB_CUDA(cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_PER_WARP));
-  int per_sm = 0;
-  BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells, 32, SMEM_PER_WARP));
-  c->grid = std::max(1, per_sm) * sm_count();
+  TRY(setup_launch(c));
   *out = c;
   return BDFB_SUCCESS;
 }
@@ -931,7 +967,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.tile_cells = ctx->d_tcells[m];
   P.ntiles = ctx->ntiles[m];
   P.tile_counter = ctx->d_counter;
-  P.worst = reinterpret_cast<int*>(ctx->d_counter + 1);
+  P.worst = reinterpret_cast<int*>(ctx->d_counter + NCLASS);
   P.st = ctx->d_state;
   P.z = ctx->d_z;
   P.acorp = ctx->d_acorp;
@@ -942,11 +978,22 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.mxstep = (int32_t)std::min<int64_t>(ctx->mxstep, 0x7fffffff);
   static const Consts K = make_consts();
   P.K = K;
-  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned), s));
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NCLASS + 1) * sizeof(unsigned), s));
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
-  const int grid = std::min<int>(ctx->grid, std::max(1, P.ntiles));
-  k_cells<<<grid, 32, SMEM_PER_WARP, s>>>(P);
-  BDFB_CUDA(cudaGetLastError());
+  // fork: one persistent launch per size class, largest cells first, each on
+  // its own stream so smaller classes fill the SMs the larger ones release
+  BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
+  for (int cl = NCLASS - 1; cl >= 0; --cl) {
+    const int t0 = ctx->cls_begin[m][cl], t1 = ctx->cls_end[m][cl];
+    if (t1 <= t0) continue;
+    cudaStream_t cs = ctx->cstream[cl];
+    BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
+    const int grid = std::min(ctx->grid[cl], t1 - t0);
+    CELLS_KERNELS[cl]<<<grid, 32, CELLS_SMEM[cl], cs>>>(P, t0, t1, ctx->d_counter + cl);
+    BDFB_CUDA(cudaGetLastError());
+    BDFB_CUDA(cudaEventRecord(ctx->evjoin[cl], cs));
+    BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[cl], 0));
+  }
   BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
   if (y) {
     BDFB_CUDA(cudaMemcpyAsync(y, ctx->d_z, ctx->ny * sizeof(double),
@@ -957,7 +1004,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
                               mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   }
   int worst = 0;
-  BDFB_CUDA(cudaMemcpyAsync(&worst, ctx->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaMemcpyAsync(&worst, ctx->d_counter + NCLASS, sizeof(int), cudaMemcpyDeviceToHost, s));
   BDFB_CUDA(cudaStreamSynchronize(s));
   cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
   return worst;
