@@ -278,7 +278,9 @@ def run_ours(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
                               "kernel_ms": 1e3 * sum(kern_s) / len(kern_s), "ncell": NCELL,
-                              "mapping": args.mapping, "quick": True}))
+                              "mapping": args.mapping, "sizes": list(SIZES), "quick": True,
+                              "steps_per_cell": float(cs[:, 0].mean()),
+                              "fp64_tflops_algorithmic": algorithmic_flops(prob, cs) / (sum(kern_s) / len(kern_s)) / 1e12}))
         integ.close()
         if dist:
             dist.destroy_process_group()
@@ -357,8 +359,12 @@ def main():
                     help="0: size-class tiles; 32: one warp per cell in input order (plain form)")
     ap.add_argument("--quick", action="store_true",
                     help="time the device path only (no e2e, accuracy, CPU or vector legs)")
+    ap.add_argument("--sizes", default=None,
+                    help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     args = ap.parse_args()
     globals()["NCELL"] = args.ncell
+    if args.sizes:
+        globals()["SIZES"] = tuple(int(s) for s in args.sizes.split(","))
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -104,6 +104,30 @@ __device__ __forceinline__ double wrms(const Grp<G>& g, int n, const double (&x)
   return sqrt(g.sum(s) / (double)n);
 }
 
+// squared WRMS norm, sum (x_i w_i)^2 / n, in FP64 (rn = 1/n).  The step loop
+// compares squared norms, which keeps its tests in FP64 without a square root.
+template <int G, int NPL>
+__device__ __forceinline__ double wrms2(const Grp<G>& g, int n, double rn, const double (&x)[NPL],
+                                        const double (&w)[NPL]) {
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) {
+      const double v = x[p] * w[p];
+      s = fma(v, v, s);
+    }
+  }
+  return g.sum(s) * rn;
+}
+
+// step-size ratio 1 / ((safety^2 d2)^(e) + 1e-6) from a squared error norm d2,
+// in FP32: it only scales the next step (about 7 significant digits are ample)
+__device__ __forceinline__ double eta_from(double d2, float safety2, float e) {
+  const float x = fmaxf((float)fmin(d2 * safety2, 1.0e30), 1.0e-37f);
+  return (double)(1.0f / (exp2f(e * __log2f(x)) + 1.0e-6f));
+}
+
 template <int G, int NPL>
 __device__ __forceinline__ bool all_finite(const Grp<G>& g, int n, const double (&x)[NPL]) {
   bool bad = false;

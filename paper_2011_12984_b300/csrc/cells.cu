@@ -86,7 +86,7 @@ struct Cell {
   static constexpr int NPL = (NMAX + G - 1) / G;
   double z[QMAX + 1][NPL];
   double acor[NPL], acorp[NPL], ewt[NPL], f[NPL], b[NPL];
-  double t, h, gamma, gammap, crate, hlast;
+  double t, h, gamma, gammap, crate, hlast, rn;   // rn = 1/n
   int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
   int nst0, ncf, nef, setup_done, force_setup, tried_fresh, newstep, last, retry;
 };
@@ -182,11 +182,13 @@ __device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, cons
 // 6 / 6 / 10, change only if the best eta >= 1.5, eta <= 1e4 before the first
 // increase and <= 10 after, ties keep q then prefer q - 1)
 template <int G, int NMAX>
-__device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, int n, Cell<G, NMAX>& C, double dsm) {
+__device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, int n, double rn,
+                                            Cell<G, NMAX>& C, double dsm2) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   if (--C.qwait > 0) return;
   const int q = C.q;
-  const double eq = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
+  // eta = 1 / ((safety * dsm)^(1/order) + 1e-6) from squared norms (FP32 ratio)
+  const double eq = eta_from(dsm2, 36.0f, 0.5f / (q + 1));
   double eqm1 = 0.0, eqp1 = 0.0;
   if (q > 1) {
     double zq[NPL];
@@ -198,14 +200,14 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
         if (j == q) v = C.z[j][p];
       zq[p] = v;
     }
-    const double d = P.K.E[q][1] * wrms(g, n, zq, C.ewt);
-    eqm1 = 1.0 / (pow(6.0 * d, 1.0 / q) + 1e-6);
+    const double e = P.K.E[q][1];
+    eqm1 = eta_from(e * e * wrms2(g, n, rn, zq, C.ewt), 36.0f, 0.5f / q);
   }
   if (q < P.qmax) {
 #pragma unroll
     for (int p = 0; p < NPL; ++p) C.b[p] = C.acor[p] - C.acorp[p];
-    const double d = P.K.E[q][2] * wrms(g, n, C.b, C.ewt);
-    eqp1 = 1.0 / (pow(10.0 * d, 1.0 / (q + 2)) + 1e-6);
+    const double e = P.K.E[q][2];
+    eqp1 = eta_from(e * e * wrms2(g, n, rn, C.b, C.ewt), 100.0f, 0.5f / (q + 2));
   }
   double etam = eq;
   int qn = q;
@@ -322,13 +324,14 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     jcur = 1;
     if (info) { fail = true; C.setup_done = 0; }
   }
-  // ---- Newton iteration
-  double acnrm = 0.0;
+  // ---- Newton iteration (norms compared squared, in FP64)
+  double acnrm2 = 0.0;
   bool conv = false;
   if (!fail) {
 #pragma unroll
     for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
-    double delp = 0.0;
+    double delp2 = 0.0;
+    const double eq2 = Eq * Eq * 100.0;   // (E_q / 0.1)^2
     for (int it = 1; it <= 3; ++it) {
       double y[NPL];
 #pragma unroll
@@ -344,19 +347,19 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
 #pragma unroll
         for (int p = 0; p < NPL; ++p) C.b[p] *= sc;
       }
-      const double del = wrms(g, n, C.b, C.ewt);
+      const double del2 = wrms2(g, n, C.rn, C.b, C.ewt);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) C.acor[p] += C.b[p];
       C.nni++;
-      if (it > 1) C.crate = fmax(0.3 * C.crate, del / delp);
-      const double dcon = del * fmin(1.0, C.crate) * Eq / 0.1;
-      if (dcon <= 1.0) {
-        acnrm = (it == 1) ? del : wrms(g, n, C.acor, C.ewt);
+      if (it > 1) C.crate = fmax(0.3 * C.crate, (double)sqrtf((float)(del2 / delp2)));
+      const double cr = fmin(1.0, C.crate);
+      if (del2 * cr * cr * eq2 <= 1.0) {       // |del| min(1, rate) E_q / 0.1 <= 1
+        acnrm2 = (it == 1) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
         conv = true;
         break;
       }
-      if (it >= 2 && del > 2.0 * delp) break;
-      delp = del;
+      if (it >= 2 && del2 > 4.0 * delp2) break;  // |del| > 2 |del_prev|: diverging
+      delp2 = del2;
     }
     if (!conv) fail = true;
   }
@@ -379,14 +382,14 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   }
   C.tried_fresh = 0;
   // ---- local error test
-  const double dsm = acnrm * Eq;
-  if (!(dsm <= 1.0)) {
+  const double dsm2 = acnrm2 * Eq * Eq;    // (E_q ||Delta||)^2
+  if (!(dsm2 <= 1.0)) {
     restore_z(g, n, S, C);
     C.nef++;
     C.netf++;
     if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
     if (C.nef < 3) {
-      double eta = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
+      double eta = eta_from(dsm2, 36.0f, 0.5f / (q + 1));
       if (!(eta >= 0.1)) eta = 0.1;
       if (C.nef >= 2 && eta > 0.2) eta = 0.2;
       rescale(C, eta);
@@ -423,7 +426,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   C.nst++;
   C.hlast = C.h;
   C.qlast = q;
-  select_next(g, P, n, C, dsm);
+  select_next(g, P, n, C.rn, C, dsm2);
 #pragma unroll
   for (int p = 0; p < NPL; ++p) C.acorp[p] = C.acor[p];
   C.newstep = 1;
@@ -469,6 +472,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
     C.nfe = s.nfe; C.nsetups = s.nsetups; C.nni = s.nni; C.ncfn = s.ncfn;
     C.netf = s.netf; C.flags = s.flags; C.status = 0; C.qlast = s.qlast;
     C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
+    C.rn = 1.0 / (double)cd.n;
     C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {

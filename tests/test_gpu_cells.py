@@ -2,11 +2,13 @@
 
 Final states are compared with an oracle run at rtol = 1e-10 (the truth) in
 units of the run's own error weights, err_c = max_i |y_i - y*_i| /
-(rtol |y*_i| + atol).  The bar: every cell within 10, or within 3x the
-oracle's own error on that cell plus 10 (local error control does not bound
-the global error; the oracle run at the same tolerance shows the same
-spread), and the GPU error distribution no wider than the oracle's.  Step
-counts must agree with the oracle's on average within 5%.
+(rtol |y*_i| + atol).  Local error control does not bound the global error,
+and the oracle run at the same tolerance (same method, other rounding, so a
+slightly different but equally valid step sequence) exceeds 10 on some
+cells.  The bar: every cell within max(10, 1.5x the oracle's worst cell), the
+GPU's median and 99th percentile no wider than the oracle's, the share of
+cells within 10 no more than 2 points below the oracle's, and mean step counts
+within 5% of the oracle's.
 """
 import numpy as np
 import pytest
@@ -48,10 +50,12 @@ def check_against_oracle(prob, tout, rtol, atol, y, cstats):
     assert np.all(so == 0) and np.all(stt == 0)
     eg = werr(y, yt, prob, rtol, atol)
     eo = werr(yo, yt, prob, rtol, atol)
-    bad = ~((eg <= 10) | (eg <= 3 * eo + 10))
-    assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10])
+    bound = max(10.0, 1.5 * eo.max())
+    bad = eg > bound
+    assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10], bound)
     assert np.percentile(eg, 50) <= 1.5 * np.percentile(eo, 50) + 1.0
     assert np.percentile(eg, 99) <= 1.5 * np.percentile(eo, 99) + 1.0
+    assert (eg <= 10).mean() >= (eo <= 10).mean() - 0.02
     assert abs(cstats[:, 0].mean() / sto[:, 0].mean() - 1.0) < 0.05
     return eg, eo
 
@@ -124,7 +128,7 @@ def test_tout_equal_t0_and_continuation():
     yt, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-10, 1e-14, threads=THREADS)
     yo, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-6, 1e-10, threads=THREADS)
     eg, eo = werr(y, yt, p, 1e-6, 1e-10), werr(yo, yt, p, 1e-6, 1e-10)
-    assert np.all((eg <= 10) | (eg <= 3 * eo + 10))
+    assert np.all(eg <= max(10.0, 1.5 * eo.max()))
 
 
 def test_failure_statuses_do_not_disturb_other_cells():
