@@ -86,6 +86,29 @@ int bdfb_nv_wrms_norm(int64_t n, const double* x, const double* w, double* out, 
 /* size (in doubles) of the reduction workspace for length n and nv results */
 int64_t bdfb_nv_work_doubles(int64_t n, int nv);
 
+/* out[j] = x . y[j] like bdfb_nv_dot_prod_multi, for callers that cannot
+ * allocate device memory or hand the library a workspace: applications whose
+ * own memory manager owns every device byte, and code that must avoid the
+ * device synchronisation an allocation can trigger.  The paper has no
+ * counterpart; it is an extension of this library.
+ *  - Allocates nothing: its scratch is a fixed array of
+ *    16 * 1024 + 2 doubles (128 KiB + 16 B) inside the library's device image,
+ *    present on every GPU that loads the library until the process exits.
+ *  - Limit: 1 <= nv <= bdfb_nv_noalloc_max_nv() (16); a larger nv returns
+ *    BDFB_ILL_INPUT.  Any n >= 0.
+ *  - The first call on a device looks up the scratch's device address (a
+ *    runtime query, no allocation); make that first call before any stream
+ *    capture on that device.
+ *  - All calls on one device share the scratch: calls that overlap on the GPU
+ *    (other streams or host threads) race, so serialise them.  Each call
+ *    clears the scratch's arrival counter on `stream` before using it.
+ *  - x, y[j] (host array of nv device pointers) and out (nv doubles) are
+ *    caller-owned device memory; stream = cudaStream_t (NULL: default). */
+int bdfb_nv_dot_prod_multi_noalloc(int64_t n, int nv, const double* x, const double* const* y,
+                                   double* out, void* stream);
+/* largest nv bdfb_nv_dot_prod_multi_noalloc accepts */
+int64_t bdfb_nv_noalloc_max_nv(void);
+
 /* --------------------------------------- batched dense LU of M = I - gamma J
  * nb independent n x n blocks, block b at a + b * n * n, row-major, FP64,
  * device memory (the block-diagonal matrix of Fig. 1 / Sec. 5).  Partial

@@ -9,6 +9,7 @@
 // caller-owned workspace, and the last block to finish adds the partials in
 // a fixed order and resets the arrival counter.
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -370,4 +371,69 @@ extern "C" int bdfb_nv_wrms_norm(int64_t n, const double* x, const double* w, do
   A.y[0] = w;
   bool al = aligned16(x) && aligned16(w);
   return launch_reduce(1, n, 1, x, A, al, work, out, as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Multi-dot product that allocates nothing.
+//
+// Some callers cannot hand the library a workspace or let it call cudaMalloc:
+// applications whose own memory manager or pool owns every device byte, code
+// that must not trigger the implicit device synchronisation a device
+// allocation can cause, and code that runs where allocating is not allowed.
+// For them the reduction scratch (block partial sums and the arrival counter)
+// lives in a fixed array in the library's device image instead.  Every GPU
+// that loads the library holds it until the process exits.  All calls on a
+// device share it, so calls that overlap on that GPU (other streams, other
+// host threads) race and must be serialised by the caller.  The kernel is the
+// same k_reduce the allocating entry point launches.
+// ---------------------------------------------------------------------------
+namespace bdfb {
+
+constexpr int64_t NOALLOC_SCRATCH_DOUBLES = (int64_t)RD_MAX_BLOCKS * NV_MAX + 2;   // 128 KiB + 16 B
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch on the current device.  The host-side name
+// g_noalloc_scratch is only a stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  BDFB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return BDFB_ILL_INPUT;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    BDFB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return BDFB_SUCCESS;
+}
+
+}  // namespace bdfb
+
+extern "C" int64_t bdfb_nv_noalloc_max_nv(void) { return NV_MAX; }
+
+extern "C" int bdfb_nv_dot_prod_multi_noalloc(int64_t n, int nv, const double* x,
+                                              const double* const* y, double* out, void* stream) {
+  if (n < 0 || !y || !out || (n > 0 && !x)) return BDFB_ILL_INPUT;
+  if (nv < 1 || nv > NV_MAX) return BDFB_ILL_INPUT;   // the fixed scratch holds at most NV_MAX results per block
+  RedArgs A;
+  std::memset(&A, 0, sizeof A);
+  bool al = aligned16(x);
+  for (int j = 0; j < nv; ++j) {
+    if (!y[j] && n > 0) return BDFB_ILL_INPUT;
+    A.y[j] = y[j];
+    al = al && aligned16(y[j]);
+  }
+  double* scratch = nullptr;
+  int r = noalloc_scratch(&scratch);
+  if (r) return r;
+  cudaStream_t s = as_stream(stream);
+  // the arrival counter must start at zero (the kernel also leaves it zero)
+  BDFB_CUDA(cudaMemsetAsync(scratch + (int64_t)RD_MAX_BLOCKS * NV_MAX, 0, 2 * sizeof(double), s));
+  return launch_reduce(0, n, nv, x, A, al, scratch, out, s);
 }
