@@ -232,7 +232,7 @@ def run_ours(args):
     y = torch.empty_like(y0)
     st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping)
+    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping, precision=args.precision)
     # one persistent launch per non-empty size class (bounds 4, 8, 16, 32, 56)
     need = np.maximum(prob.n, (np.diff(prob.rxn_off) + 1) // 2)
     launches_per_step = len(set(np.searchsorted([4, 8, 16, 32, 56], need).tolist())) if args.mapping == 0 else 1
@@ -279,6 +279,7 @@ def run_ours(args):
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
                               "kernel_ms": 1e3 * sum(kern_s) / len(kern_s), "ncell": NCELL,
                               "mapping": args.mapping, "sizes": list(SIZES), "quick": True,
+                              "precision": args.precision, "stats": integ.stats(),
                               "steps_per_cell": float(cs[:, 0].mean()),
                               "fp64_tflops_algorithmic": algorithmic_flops(prob, cs) / (sum(kern_s) / len(kern_s)) / 1e12}))
         integ.close()
@@ -359,6 +360,8 @@ def main():
                     help="0: size-class tiles; 32: one warp per cell in input order (plain form)")
     ap.add_argument("--quick", action="store_true",
                     help="time the device path only (no e2e, accuracy, CPU or vector legs)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP64 factorisation; 1: FP32 factorisation + FP64 refinement")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     args = ap.parse_args()

@@ -119,6 +119,15 @@ int bdfb_batched_lu_factor(int64_t nb, int n, double* a, int32_t* piv, int32_t* 
 /* solve M x = b in place for every block with the factors above */
 int bdfb_batched_lu_solve(int64_t nb, int n, const double* lu, const int32_t* piv, double* b,
                           void* stream);
+/* Mixed precision (FP32 factorisation, FP64 refinement): for every FP64
+ * block a (not modified) solve a x = b: LU of the block in FP32, then
+ * x += LU^{-1} r with the FP64 residual r = b - a x until the normwise
+ * backward error |r|_inf / (|a|_inf |x|_inf + |b|_inf) <= 1e-12, at most 5
+ * sweeps.  sweeps[blk] = sweeps used, -1 if 1e-12 was not reached (x holds
+ * the last iterate), -2 if the FP32 factorisation met a zero pivot.
+ * 1 <= n <= 64; all arrays device memory. */
+int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b, double* x,
+                             int32_t* sweeps, void* stream);
 
 /* ---------------------------------------------------- per-cell problems
  * kind BDFB_ROBERTSON: k[3 c + {0,1,2}] = (k1, k2, k3) of cell c, n = 3.

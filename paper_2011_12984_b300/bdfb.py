@@ -75,6 +75,7 @@ _sig("bdfb_nv_wrms_norm", C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp])
 _sig("bdfb_nv_work_doubles", _i64, [_i64, C.c_int])
 _sig("bdfb_batched_lu_factor", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
 _sig("bdfb_batched_lu_solve", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
+_sig("bdfb_batched_solve_mixed", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("bdfb_create", C.c_int, [C.POINTER(Problem), C.POINTER(_vp)])
 _sig("bdfb_destroy", None, [_vp])
 _sig("bdfb_set_stream", C.c_int, [_vp, _vp])
@@ -173,6 +174,13 @@ def batched_lu_solve(lu, piv, b, stream=None):
     nb, n, _ = lu.shape
     return check(lib.bdfb_batched_lu_solve(nb, n, _dptr(lu), _dptr(piv), _dptr(b), _stream(stream)),
                  "batched_lu_solve")
+
+
+def batched_solve_mixed(a, b, x, sweeps, stream=None):
+    """FP32 LU + FP64 refinement of every block of a (nb, n, n) for rhs b (nb, n)"""
+    nb, n, _ = a.shape
+    return check(lib.bdfb_batched_solve_mixed(nb, n, _dptr(a), _dptr(b), _dptr(x), _dptr(sweeps),
+                                              _stream(stream)), "batched_solve_mixed")
 
 
 # ------------------------------------------------------------- integrator

@@ -53,27 +53,29 @@ struct LaneGrid {
 
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
 
-// per-cell shared memory
-template <int NMAX>
+// per-cell shared memory (PREC = 1 adds the reaction derivatives that the
+// mixed-precision solve needs for its FP64 residual)
+template <int NMAX, int PREC = 0>
 struct CellSmem {
-  double M[NMAX][NMAX + 1];   // M = I - gamma J, then its LU factors
+  double M[NMAX][NMAX + 1];   // M = I - gamma J, then its LU factors (FP64, or FP32 packed)
   double zs[ZCOLS][NMAX];     // history saved before a step attempt
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side
   double rates[2 * NMAX];     // reaction rates (mass action)
+  double dr[PREC ? 2 * NMAX : 1][4];  // d rate_r / d y_(reactant a) at the setup point
   int16_t perm[NMAX];         // row i of P M is row perm[i] of M
 };
 
-template <int NPL>
-__device__ __forceinline__ double pick(const double (&x)[NPL], int slot) {
-  double v = x[0];
+template <int NPL, typename T>
+__device__ __forceinline__ T pick(const T (&x)[NPL], int slot) {
+  T v = x[0];
 #pragma unroll
   for (int s = 1; s < NPL; ++s)
     if (slot == s) v = x[s];
   return v;
 }
-template <int NPL>
-__device__ __forceinline__ void place(double (&x)[NPL], int slot, double v) {
+template <int NPL, typename T>
+__device__ __forceinline__ void place(T (&x)[NPL], int slot, T v) {
 #pragma unroll
   for (int s = 0; s < NPL; ++s)
     if (slot == s) x[s] = v;
@@ -139,8 +141,8 @@ __device__ __forceinline__ bool all_finite(const Grp<G>& g, int n, const double 
   return !g.any(bad);
 }
 
-template <int G, int NPL, int NMAX>
-__device__ __forceinline__ void scatter_y(const Grp<G>& g, CellSmem<NMAX>& S, int n,
+template <int G, int NPL, int NMAX, int PREC>
+__device__ __forceinline__ void scatter_y(const Grp<G>& g, CellSmem<NMAX, PREC>& S, int n,
                                           const double (&y)[NPL]) {
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
@@ -154,8 +156,8 @@ __device__ __forceinline__ void scatter_y(const Grp<G>& g, CellSmem<NMAX>& S, in
 // f = f(y).  Mass action: rate_r = k_r prod_{s in R(r)} y_s, then each species
 // sums -rate over reactions consuming it and +rate over reactions producing
 // it, in reaction order (the incidence lists are built in that order).
-template <int G, int NPL, int NMAX>
-__device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX>& S, const double (&y)[NPL],
+template <int G, int NPL, int NMAX, int PREC>
+__device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, PREC>& S, const double (&y)[NPL],
                     double (&f)[NPL]) {
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   if (c.kind == BDFB_ROBERTSON) {
@@ -203,8 +205,8 @@ __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem
 // M = I - gamma J(y) into shared memory (rows owned by lanes).  J entries are
 // accumulated in reaction order as in the definition; M is formed without a
 // fused multiply-add so it equals the textbook rounding of 1 - gamma J.
-template <int G, int NPL, int NMAX>
-__device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX>& S,
+template <int G, int NPL, int NMAX, int PREC>
+__device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, PREC>& S,
                        const double (&y)[NPL], double gamma) {
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   const int n = c.n;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "cellcore.cuh"
+#include "mixed.cuh"
 
 namespace bdfb {
 
@@ -89,6 +90,8 @@ struct Cell {
   double t, h, gamma, gammap, crate, hlast, rn;   // rn = 1/n
   int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
   int nst0, ncf, nef, setup_done, force_setup, tried_fresh, newstep, last, retry;
+  int nref, nref_fb, fp64mode;   // mixed precision: refinement sweeps, FP64 fallbacks, M in FP64
+  double mnorm;                  // |M|_inf of the current setup (mixed precision)
 };
 
 template <int G, int NMAX>
@@ -117,9 +120,9 @@ __device__ __forceinline__ void set_ewt(const Grp<G>& g, const Params& P, int n,
 // initial step and history (reading shared with the oracle: h0 from a
 // difference estimate of ||y''|| within [100 eps t, min(0.1 |tout - t|,
 // 0.1 (|y| + atol) / |f|)]).  Returns 0 or an error code.
-template <int G, int NMAX>
-__device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, const CellDesc& cd, CellSmem<NMAX>& S,
-                          Cell<G, NMAX>& C) {
+template <int G, int NMAX, int PREC>
+__device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, const CellDesc& cd,
+                                          CellSmem<NMAX, PREC>& S, Cell<G, NMAX>& C) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   const int n = cd.n;
   set_ewt(g, P, n, C);
@@ -239,8 +242,8 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
   C.qwait = C.q + 1;
 }
 
-template <int G, int NMAX>
-__device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem<NMAX>& S,
+template <int G, int NMAX, int PREC>
+__device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem<NMAX, PREC>& S,
                                           Cell<G, NMAX>& C) {
 #pragma unroll
   for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
@@ -254,9 +257,9 @@ __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem
 
 // One step attempt.  Returns true when the cell is finished (tout reached or
 // a failure status set).
-template <int G, int NMAX>
-__device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const CellDesc& cd, CellSmem<NMAX>& S,
-                        Cell<G, NMAX>& C) {
+template <int G, int NMAX, int PREC>
+__device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const CellDesc& cd,
+                                        CellSmem<NMAX, PREC>& S, Cell<G, NMAX>& C) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   const int n = cd.n;
   if (!(C.flags & F_STARTED)) {
@@ -313,8 +316,18 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     double y[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
-    form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
-    const int info = lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n);
+    int info;
+    if constexpr (PREC == 1) {
+      // FP32 factors of M; FP64 reaction derivatives kept for the residual
+      reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
+      C.mnorm = form_M32<G, NPL, NMAX>(g, cd, S, C.gamma);
+      info = lu_factor<G, NMAX, float>(g, reinterpret_cast<float (*)[NMAX + 1]>(&S.M[0][0]),
+                                       reinterpret_cast<float*>(S.dinv), S.perm, n);
+      C.fp64mode = 0;
+    } else {
+      form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
+      info = lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n);
+    }
     C.nsetups++;
     C.gammap = C.gamma;
     C.crate = 1.0;
@@ -341,7 +354,33 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       if (!all_finite(g, n, C.f)) break;
 #pragma unroll
       for (int p = 0; p < NPL; ++p) C.b[p] = C.gamma * C.f[p] - C.z[1][p] * rl1 - C.acor[p];
-      lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+      if constexpr (PREC == 1) {
+        bool solved = false;
+        if (!C.fp64mode) {
+          double bs[NPL];
+#pragma unroll
+          for (int p = 0; p < NPL; ++p) bs[p] = C.b[p];
+          const int sw = refined_solve<G, NPL, NMAX>(g, cd, S, C.gammap, C.mnorm, C.b);
+          C.nref += sw > 0 ? sw : MAXREF;
+          if (sw > 0) {
+            solved = true;
+          } else {
+            // refinement stalled: factor this setup's M in FP64 instead
+            C.nref_fb++;
+            form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap);
+            if (lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n)) {
+              C.setup_done = 0;
+              break;                      // singular: counts as a Newton failure
+            }
+            C.fp64mode = 1;
+#pragma unroll
+            for (int p = 0; p < NPL; ++p) C.b[p] = bs[p];
+          }
+        }
+        if (!solved) lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+      } else {
+        lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+      }
       if (C.gamma != C.gammap) {
         const double sc = 2.0 / (1.0 + C.gamma / C.gammap);
 #pragma unroll
@@ -434,12 +473,12 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   return false;
 }
 
-template <int G, int NMAX>
+template <int G, int NMAX, int PREC>
 __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
-  CellSmem<NMAX>& S = reinterpret_cast<CellSmem<NMAX>*>(smem)[gid];
+  CellSmem<NMAX, PREC>& S = reinterpret_cast<CellSmem<NMAX, PREC>*>(smem)[gid];
   bool active = gid < td.count;
   int64_t c = 0;
   CellDesc cd;
@@ -473,6 +512,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
     C.netf = s.netf; C.flags = s.flags; C.status = 0; C.qlast = s.qlast;
     C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
     C.rn = 1.0 / (double)cd.n;
+    C.nref = s.nrefine; C.nref_fb = s.nrefine_fb; C.fp64mode = 0; C.mnorm = 0.0;
     C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
@@ -487,7 +527,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   }
   while (__any_sync(FULL_MASK, active)) {
     if (active) {
-      if (attempt<G, NMAX>(g, P, cd, S, C)) {
+      if (attempt<G, NMAX, PREC>(g, P, cd, S, C)) {
         active = false;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
@@ -504,7 +544,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
           s.q = C.q; s.qwait = C.qwait; s.nst = C.nst; s.nstlp = C.nstlp;
           s.nfe = C.nfe; s.nsetups = C.nsetups; s.nni = C.nni; s.ncfn = C.ncfn;
           s.netf = C.netf; s.flags = C.flags; s.status = C.status; s.qlast = C.qlast;
-          s.nrefine = 0; s.nrefine_fb = 0; s.pad0 = 0; s.pad1 = 0;
+          s.nrefine = C.nref; s.nrefine_fb = C.nref_fb; s.pad0 = 0; s.pad1 = 0;
           P.st[c] = s;
           if (P.status) P.status[c] = C.status;
           if (C.status < 0) atomicMin(P.worst, C.status);
@@ -514,14 +554,15 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   }
 }
 
-template <int CLS>
+template <int CLS, int PREC>
 struct ClassSmem {
-  static constexpr int bytes = (32 / CLS_G[CLS]) * (int)sizeof(CellSmem<CLS_NMAX[CLS]>);
+  static constexpr int bytes = (32 / CLS_G[CLS]) * (int)sizeof(CellSmem<CLS_NMAX[CLS], PREC>);
 };
 
 // Persistent kernel of one size class: each warp takes the next tile of the
-// class range [t0, t1) from `counter` until none is left.
-template <int CLS>
+// class range [t0, t1) from `counter` until none is left.  PREC 0: FP64
+// factorisation; PREC 1: FP32 factorisation with FP64 refinement.
+template <int CLS, int PREC>
 __global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, int t0, int t1,
                                               unsigned* counter) {
   extern __shared__ __align__(16) char smem[];
@@ -531,16 +572,20 @@ __global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, 
     if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
     t = __shfl_sync(FULL_MASK, t, 0);
     if (t >= t1) break;
-    run_tile<CLS_G[CLS], CLS_NMAX[CLS]>(P, P.tiles[t], smem);
+    run_tile<CLS_G[CLS], CLS_NMAX[CLS], PREC>(P, P.tiles[t], smem);
     __syncwarp();
   }
 }
 
 typedef void (*cells_kernel_t)(const Params, int, int, unsigned*);
-static const cells_kernel_t CELLS_KERNELS[NCLASS] = {k_cells<0>, k_cells<1>, k_cells<2>, k_cells<3>,
-                                                     k_cells<4>};
-static const int CELLS_SMEM[NCLASS] = {ClassSmem<0>::bytes, ClassSmem<1>::bytes, ClassSmem<2>::bytes,
-                                       ClassSmem<3>::bytes, ClassSmem<4>::bytes};
+static const cells_kernel_t CELLS_KERNELS[2][NCLASS] = {
+    {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>},
+    {k_cells<0, 1>, k_cells<1, 1>, k_cells<2, 1>, k_cells<3, 1>, k_cells<4, 1>}};
+static const int CELLS_SMEM[2][NCLASS] = {
+    {ClassSmem<0, 0>::bytes, ClassSmem<1, 0>::bytes, ClassSmem<2, 0>::bytes, ClassSmem<3, 0>::bytes,
+     ClassSmem<4, 0>::bytes},
+    {ClassSmem<0, 1>::bytes, ClassSmem<1, 1>::bytes, ClassSmem<2, 1>::bytes, ClassSmem<3, 1>::bytes,
+     ClassSmem<4, 1>::bytes}};
 
 // ------------------------------------------------- standalone batched LU
 constexpr int LU_NMAX = 64;
@@ -597,6 +642,89 @@ __global__ void __launch_bounds__(32) k_lu_solve(int64_t nb, int n, const double
       const int i = g.rank + 32 * p;
       if (i < n) bvec[b * n + i] = x[p];
     }
+    g.sync();
+  }
+}
+
+// Mixed-precision solve of dense blocks: FP32 LU of each block, FP64 dense
+// residual r = b - A x, x += (LU32)^{-1} r until |r|/(|A| |x| + |b|) <= 1e-12
+// (at most MAXREF sweeps; sweeps[b] = -1 if not reached).
+__global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const double* a,
+                                                   const double* bvec, double* xout, int32_t* sweeps) {
+  extern __shared__ __align__(16) char smem[];
+  auto& S = *reinterpret_cast<CellSmem<LU_NMAX, 1>*>(smem);
+  double (*A)[LU_NMAX + 1] = reinterpret_cast<double (*)[LU_NMAX + 1]>(smem + sizeof(CellSmem<LU_NMAX, 1>));
+  float (*M32)[LU_NMAX + 1] = reinterpret_cast<float (*)[LU_NMAX + 1]>(&S.M[0][0]);
+  Grp<32> g;
+  constexpr int NPL = 2;
+  for (int64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+    const double* Ab = a + blk * n * n;
+    for (int e = g.rank; e < n * n; e += 32) {
+      const double v = Ab[e];
+      A[e / n][e % n] = v;
+      M32[e / n][e % n] = (float)v;
+    }
+    g.sync();
+    double anorm = 0.0;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + 32 * p;
+      if (i < n) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += fabs(A[i][j]);
+        anorm = fmax(anorm, s);
+      }
+    }
+    anorm = gmaxd(g, anorm);
+    const int info = lu_factor<32, LU_NMAX, float>(g, M32, reinterpret_cast<float*>(S.dinv), S.perm, n);
+    double b[NPL], x[NPL], r[NPL];
+    double bn = 0.0;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + 32 * p;
+      b[p] = i < n ? bvec[blk * n + i] : 0.0;
+      x[p] = 0.0;
+      r[p] = b[p];
+      bn = fmax(bn, fabs(b[p]));
+    }
+    bn = gmaxd(g, bn);
+    int sw = -1;
+    for (int it = 1; it <= MAXREF && !info; ++it) {
+      float c32[NPL];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) c32[p] = (float)r[p];
+      lu_solve32<32, NPL, LU_NMAX>(g, S, n, c32);
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
+      g.sync();
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        const int i = g.rank + 32 * p;
+        if (i < n) S.rates[i] = x[p];
+      }
+      g.sync();
+      double rn = 0.0, xn = 0.0;
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        const int i = g.rank + 32 * p;
+        if (i < n) {
+          double s = b[p];
+          for (int j = 0; j < n; ++j) s = fma(-A[i][j], S.rates[j], s);
+          r[p] = s;
+          rn = fmax(rn, fabs(s));
+          xn = fmax(xn, fabs(x[p]));
+        }
+      }
+      rn = gmaxd(g, rn);
+      xn = gmaxd(g, xn);
+      if (rn <= BERR_TOL * (anorm * xn + bn)) { sw = it; break; }
+    }
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + 32 * p;
+      if (i < n) xout[blk * n + i] = x[p];
+    }
+    if (g.rank == 0) sweeps[blk] = info ? -2 : sw;
     g.sync();
   }
 }
@@ -664,7 +792,7 @@ struct bdfb_ctx {
   cudaEvent_t evjoin[NCLASS] = {};
   cudaStream_t cstream[NCLASS] = {};  // one per size class, forked from `stream`
   float last_ms = 0.f;
-  int grid[NCLASS] = {};
+  int grid[2][NCLASS] = {};   // [precision][class]
 };
 
 static void free_ctx(bdfb_ctx* c) {
@@ -718,11 +846,14 @@ static int setup_launch(bdfb_ctx* c) {
   for (int k = 0; k < NCLASS; ++k) {
     BDFB_CUDA(cudaEventCreateWithFlags(&c->evjoin[k], cudaEventDisableTiming));
     BDFB_CUDA(cudaStreamCreateWithFlags(&c->cstream[k], cudaStreamNonBlocking));
-    BDFB_CUDA(cudaFuncSetAttribute(CELLS_KERNELS[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   CELLS_SMEM[k]));
-    int per_sm = 0;
-    BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CELLS_KERNELS[k], 32, CELLS_SMEM[k]));
-    c->grid[k] = std::max(1, per_sm) * sm_count();
+    for (int pr = 0; pr < 2; ++pr) {
+      BDFB_CUDA(cudaFuncSetAttribute(CELLS_KERNELS[pr][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     CELLS_SMEM[pr][k]));
+      int per_sm = 0;
+      BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CELLS_KERNELS[pr][k], 32,
+                                                              CELLS_SMEM[pr][k]));
+      c->grid[pr][k] = std::max(1, per_sm) * sm_count();
+    }
   }
   return 0;
 }
@@ -914,7 +1045,8 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
     if (v != 0 && v != 32) return BDFB_ILL_INPUT;
     ctx->mapping = (int)v;
   } else if (!std::strcmp(key, "precision")) {
-    if (v != 0) return BDFB_ILL_INPUT;   // FP32 factorisation not available in this build
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && ctx->kind != BDFB_MASSACTION) return BDFB_ILL_INPUT;  // residual needs reaction data
     ctx->precision = (int)v;
   } else if (!std::strcmp(key, "graph")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
@@ -992,8 +1124,9 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
     if (t1 <= t0) continue;
     cudaStream_t cs = ctx->cstream[cl];
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
-    const int grid = std::min(ctx->grid[cl], t1 - t0);
-    CELLS_KERNELS[cl]<<<grid, 32, CELLS_SMEM[cl], cs>>>(P, t0, t1, ctx->d_counter + cl);
+    const int pr = ctx->precision;
+    const int grid = std::min(ctx->grid[pr][cl], t1 - t0);
+    CELLS_KERNELS[pr][cl]<<<grid, 32, CELLS_SMEM[pr][cl], cs>>>(P, t0, t1, ctx->d_counter + cl);
     BDFB_CUDA(cudaGetLastError());
     BDFB_CUDA(cudaEventRecord(ctx->evjoin[cl], cs));
     BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[cl], 0));
@@ -1079,6 +1212,18 @@ extern "C" int bdfb_batched_lu_factor(int64_t nb, int n, double* a, int32_t* piv
   BDFB_CUDA(cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int64_t grid = std::min<int64_t>(nb, (int64_t)sm_count() * 6);
   k_lu_factor<<<(int)grid, 32, smem, as_stream(stream)>>>(nb, n, a, piv, info);
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b,
+                                        double* x, int32_t* sweeps, void* stream) {
+  if (nb < 0 || n < 1 || n > LU_NMAX || (nb > 0 && (!a || !b || !x || !sweeps))) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  const int smem = (int)sizeof(CellSmem<LU_NMAX, 1>) + LU_NMAX * (LU_NMAX + 1) * (int)sizeof(double);
+  BDFB_CUDA(cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int64_t grid = std::min<int64_t>(nb, (int64_t)sm_count() * 4);
+  k_solve_mixed<<<(int)grid, 32, smem, as_stream(stream)>>>(nb, n, a, b, x, sweeps);
   BDFB_CUDA(cudaGetLastError());
   return BDFB_SUCCESS;
 }

@@ -1,0 +1,82 @@
+"""Mixed precision (FP32 factorisation, FP64 iterative refinement).
+
+* The dense-block solve reaches normwise backward error <= 1e-12 in FP64 on
+  blocks M = I - gamma J shaped like the integrator's, and agrees with the
+  oracle's FP64 LU solve to the conditioning the backward error allows.
+* The integrator with FP32 factors meets the same final-state bar as the FP64
+  form on n = 54 mass-action cells, with the FP64 history, error test and
+  convergence test unchanged.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2011_12984_b300 import bdfb, gen
+
+from test_gpu_cells import check_against_oracle, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def blocks(nb, n, seed, scale=1e-3):
+    rng = np.random.default_rng(seed)
+    J = rng.standard_normal((nb, n, n)) * 10.0 ** rng.uniform(-2, 4, size=(nb, n, n))
+    return np.eye(n)[None] - scale * J
+
+
+@pytest.mark.parametrize("n", [1, 3, 10, 32, 54, 64])
+def test_refined_solve_backward_error(n):
+    nb = 300
+    M = blocks(nb, n, seed=7 * n)
+    rhs = np.random.default_rng(n).standard_normal((nb, n))
+    x = torch.zeros((nb, n), dtype=torch.float64, device="cuda")
+    sw = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    bdfb.batched_solve_mixed(torch.from_numpy(M).cuda(), torch.from_numpy(rhs).cuda(), x, sw)
+    xs, sws = x.cpu().numpy(), sw.cpu().numpy()
+    ok = sws > 0
+    assert ok.mean() > 0.95, np.unique(sws, return_counts=True)
+    for b in range(nb):
+        r = M[b] @ xs[b] - rhs[b]
+        eta = np.max(np.abs(r)) / (np.max(np.sum(np.abs(M[b]), axis=1)) * np.max(np.abs(xs[b]))
+                                   + np.max(np.abs(rhs[b])))
+        if ok[b]:
+            assert eta <= 1.05e-12, (b, eta, sws[b])
+        lu, piv, _ = oracle.lu_factor(M[b])
+        xo = oracle.lu_solve(lu, piv, rhs[b])
+        cond = np.linalg.cond(M[b], np.inf)
+        if ok[b]:
+            assert np.max(np.abs(xs[b] - xo)) <= 1e-11 * cond * np.max(np.abs(xo)) + 1e-300
+
+
+def test_refinement_gives_up_on_ill_conditioned_blocks():
+    """FP32 factors cannot refine a block with condition ~1e12: the solve
+    reports -1 (the integrator then refactors that cell in FP64)."""
+    n = 8
+    U, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((n, n)))
+    V, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((n, n)))
+    M = (U @ np.diag(np.logspace(0, -12, n)) @ V.T)[None]
+    rhs = np.ones((1, n))
+    x = torch.zeros((1, n), dtype=torch.float64, device="cuda")
+    sw = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bdfb.batched_solve_mixed(torch.from_numpy(M).cuda(), torch.from_numpy(rhs).cuda(), x, sw)
+    assert sw.item() in (-1, -2)
+
+
+def test_mixed_integrator_n54():
+    p = gen.mass_action(2048, sizes=(54,), seed=21).subset(np.arange(384))
+    ret, y, st, cs, stats = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10, precision=1)
+    assert ret == 0 and np.all(st == 0)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    s1 = np.add.reduceat(y, p.y_off[:-1])
+    assert np.max(np.abs(s1 - s0)) <= 5e-11
+    check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs)
+    assert stats["nrefine"] >= stats["nniters"]          # at least one sweep per solve
+    assert stats["nrefine_fallback"] <= 0.05 * stats["nlinsetups"]
+
+
+def test_mixed_rejected_for_robertson():
+    p = gen.robertson(4)
+    with bdfb.Integrator(p) as I:
+        with pytest.raises(bdfb.BdfbError):
+            I.set_option("precision", 1)
