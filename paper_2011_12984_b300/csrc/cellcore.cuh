@@ -10,6 +10,8 @@
 // same scalars and all control flow is uniform inside a group.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bdfb {
@@ -53,11 +55,12 @@ struct LaneGrid {
 
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
 
-// per-cell shared memory (PREC = 1 adds the reaction derivatives that the
-// mixed-precision solve needs for its FP64 residual)
+// per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
+// (mixed precision): M and its Gauss-Jordan inverse in FP32, plus the FP64
+// reaction derivatives the refinement residual needs.
 template <int NMAX, int PREC = 0>
 struct CellSmem {
-  double M[NMAX][NMAX + 1];   // M = I - gamma J, then its LU factors (FP64, or FP32 packed)
+  typename std::conditional<PREC == 1, float, double>::type M[NMAX][NMAX + 1];
   double zs[ZCOLS][NMAX];     // history saved before a step attempt
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side

@@ -259,7 +259,8 @@ __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem
 // a failure status set).
 template <int G, int NMAX, int PREC>
 __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const CellDesc& cd,
-                                        CellSmem<NMAX, PREC>& S, Cell<G, NMAX>& C) {
+                                        CellSmem<NMAX, PREC>& S, Cell<G, NMAX>& C,
+                                        double (*Mg)[NMAX + 1]) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   const int n = cd.n;
   if (!(C.flags & F_STARTED)) {
@@ -318,11 +319,11 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
     int info;
     if constexpr (PREC == 1) {
-      // FP32 factors of M; FP64 reaction derivatives kept for the residual
+      // FP32 Gauss-Jordan inverse of M; FP64 reaction derivatives kept for
+      // the refinement residual
       reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
       C.mnorm = form_M32<G, NPL, NMAX>(g, cd, S, C.gamma);
-      info = lu_factor<G, NMAX, float>(g, reinterpret_cast<float (*)[NMAX + 1]>(&S.M[0][0]),
-                                       reinterpret_cast<float*>(S.dinv), S.perm, n);
+      info = gj_inverse<G, NMAX>(g, S.M, S.perm, reinterpret_cast<float*>(S.ybuf), n);
       C.fp64mode = 0;
     } else {
       form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
@@ -365,10 +366,11 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
           if (sw > 0) {
             solved = true;
           } else {
-            // refinement stalled: factor this setup's M in FP64 instead
+            // refinement stalled: factor this setup's M in FP64 instead (in
+            // the cell's global workspace) until the next setup
             C.nref_fb++;
-            form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap);
-            if (lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n)) {
+            form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
+            if (lu_factor<G, NMAX, double>(g, Mg, S.dinv, S.perm, n)) {
               C.setup_done = 0;
               break;                      // singular: counts as a Newton failure
             }
@@ -377,7 +379,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
             for (int p = 0; p < NPL; ++p) C.b[p] = bs[p];
           }
         }
-        if (!solved) lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+        if (!solved) lu_solve<G, NPL, NMAX, double>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
       } else {
         lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
       }
@@ -473,12 +475,16 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   return false;
 }
 
+// fb: this warp's slice of the FP64 fallback workspace (mixed precision;
+// (32 / G) matrices of NMAX x (NMAX + 1) doubles), else null
 template <int G, int NMAX, int PREC>
-__device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem) {
+__device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem, double* fb) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
   CellSmem<NMAX, PREC>& S = reinterpret_cast<CellSmem<NMAX, PREC>*>(smem)[gid];
+  double (*Mg)[NMAX + 1] =
+      fb ? reinterpret_cast<double (*)[NMAX + 1]>(fb + (int64_t)gid * NMAX * (NMAX + 1)) : nullptr;
   bool active = gid < td.count;
   int64_t c = 0;
   CellDesc cd;
@@ -527,7 +533,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   }
   while (__any_sync(FULL_MASK, active)) {
     if (active) {
-      if (attempt<G, NMAX, PREC>(g, P, cd, S, C)) {
+      if (attempt<G, NMAX, PREC>(g, P, cd, S, C, Mg)) {
         active = false;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
@@ -564,20 +570,27 @@ struct ClassSmem {
 // factorisation; PREC 1: FP32 factorisation with FP64 refinement.
 template <int CLS, int PREC>
 __global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, int t0, int t1,
-                                              unsigned* counter) {
+                                              unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
+  constexpr int64_t FB = (int64_t)(32 / CLS_G[CLS]) * CLS_NMAX[CLS] * (CLS_NMAX[CLS] + 1);
+  double* fb = fbws ? fbws + (int64_t)blockIdx.x * FB : nullptr;
   for (;;) {
     int t = 0;
     if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
     t = __shfl_sync(FULL_MASK, t, 0);
     if (t >= t1) break;
-    run_tile<CLS_G[CLS], CLS_NMAX[CLS], PREC>(P, P.tiles[t], smem);
+    run_tile<CLS_G[CLS], CLS_NMAX[CLS], PREC>(P, P.tiles[t], smem, fb);
     __syncwarp();
   }
 }
 
-typedef void (*cells_kernel_t)(const Params, int, int, unsigned*);
+// doubles of FP64 fallback workspace one warp of class c needs
+static int64_t fallback_doubles_per_warp(int c) {
+  return (int64_t)(32 / CLS_G[c]) * CLS_NMAX[c] * (CLS_NMAX[c] + 1);
+}
+
+typedef void (*cells_kernel_t)(const Params, int, int, unsigned*, double*);
 static const cells_kernel_t CELLS_KERNELS[2][NCLASS] = {
     {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>},
     {k_cells<0, 1>, k_cells<1, 1>, k_cells<2, 1>, k_cells<3, 1>, k_cells<4, 1>}};
@@ -646,9 +659,10 @@ __global__ void __launch_bounds__(32) k_lu_solve(int64_t nb, int n, const double
   }
 }
 
-// Mixed-precision solve of dense blocks: FP32 LU of each block, FP64 dense
-// residual r = b - A x, x += (LU32)^{-1} r until |r|/(|A| |x| + |b|) <= 1e-12
-// (at most MAXREF sweeps; sweeps[b] = -1 if not reached).
+// Mixed-precision solve of dense blocks, the same scheme as the integrator's:
+// FP32 Gauss-Jordan inverse of each block, FP64 dense residual r = b - A x,
+// x += inv32 r until |r|/(|A| |x| + |b|) <= 1e-12 (at most MAXREF sweeps;
+// sweeps[b] = -1 if not reached).
 __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const double* a,
                                                    const double* bvec, double* xout, int32_t* sweeps) {
   extern __shared__ __align__(16) char smem[];
@@ -676,7 +690,7 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
       }
     }
     anorm = gmaxd(g, anorm);
-    const int info = lu_factor<32, LU_NMAX, float>(g, M32, reinterpret_cast<float*>(S.dinv), S.perm, n);
+    const int info = gj_inverse<32, LU_NMAX>(g, M32, S.perm, reinterpret_cast<float*>(S.ybuf), n);
     double b[NPL], x[NPL], r[NPL];
     double bn = 0.0;
 #pragma unroll
@@ -690,10 +704,10 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
     bn = gmaxd(g, bn);
     int sw = -1;
     for (int it = 1; it <= MAXREF && !info; ++it) {
-      float c32[NPL];
+      float r32[NPL], c32[NPL];
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) c32[p] = (float)r[p];
-      lu_solve32<32, NPL, LU_NMAX>(g, S, n, c32);
+      for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
+      apply_inverse32<32, NPL, LU_NMAX>(g, M32, reinterpret_cast<float*>(S.ybuf), n, r32, c32);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
       g.sync();
@@ -790,6 +804,7 @@ struct bdfb_ctx {
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
   cudaEvent_t evjoin[NCLASS] = {};
+  double* d_fbws[NCLASS] = {};      // FP64 fallback workspace per class (mixed precision, lazy)
   cudaStream_t cstream[NCLASS] = {};  // one per size class, forked from `stream`
   float last_ms = 0.f;
   int grid[2][NCLASS] = {};   // [precision][class]
@@ -803,6 +818,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
+  for (int k = 0; k < NCLASS; ++k) cudaFree(c->d_fbws[k]);
   for (int m = 0; m < 2; ++m) { cudaFree(c->d_tiles[m]); cudaFree(c->d_tcells[m]); }
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1114,6 +1130,16 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.mxstep = (int32_t)std::min<int64_t>(ctx->mxstep, 0x7fffffff);
   static const Consts K = make_consts();
   P.K = K;
+  if (ctx->precision == 1) {   // FP64 fallback workspace: one slice per resident warp
+    for (int cl = 0; cl < NCLASS; ++cl)
+      if (!ctx->d_fbws[cl] && ctx->cls_end[m][cl] > ctx->cls_begin[m][cl]) {
+        const size_t bytes = (size_t)ctx->grid[1][cl] * fallback_doubles_per_warp(cl) * sizeof(double);
+        if (cudaMalloc(&ctx->d_fbws[cl], bytes) != cudaSuccess) {
+          ctx->d_fbws[cl] = nullptr;
+          return BDFB_MEM_FAIL;
+        }
+      }
+  }
   BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NCLASS + 1) * sizeof(unsigned), s));
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
   // fork: one persistent launch per size class, largest cells first, each on
@@ -1126,7 +1152,8 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
     const int pr = ctx->precision;
     const int grid = std::min(ctx->grid[pr][cl], t1 - t0);
-    CELLS_KERNELS[pr][cl]<<<grid, 32, CELLS_SMEM[pr][cl], cs>>>(P, t0, t1, ctx->d_counter + cl);
+    CELLS_KERNELS[pr][cl]<<<grid, 32, CELLS_SMEM[pr][cl], cs>>>(P, t0, t1, ctx->d_counter + cl,
+                                                                pr == 1 ? ctx->d_fbws[cl] : nullptr);
     BDFB_CUDA(cudaGetLastError());
     BDFB_CUDA(cudaEventRecord(ctx->evjoin[cl], cs));
     BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[cl], 0));

@@ -1,15 +1,17 @@
 // mixed.cuh - FP32 factorisation of M = I - gamma J with FP64 iterative
 // refinement, per cell (mass-action cells).
 //
-// B300 runs FP32 FMAs 64x faster than FP64 ones, so the block LU and the
-// triangular solves run in FP32 and only the refinement residual r = b - M x
-// is FP64.  The residual does not store the FP64 matrix: M x = x - gamma J x
-// with J x assembled from the reaction derivatives d rate_r / d y_s kept
-// (FP64) from the setup point, reaction by reaction and species by species
-// in the same incidence order as the right-hand side.  A solve is accepted at
-// normwise backward error |r|_inf / (|M|_inf |x|_inf + |b|_inf) <= 1e-12;
-// after MAXREF sweeps without that, the cell falls back to an FP64 LU of the
-// same M until its next setup.
+// B300 runs FP32 FMAs 64x faster than FP64 ones, so the block is factored in
+// FP32 - as an explicit Gauss-Jordan inverse, which turns every correction
+// into a fully parallel matrix-vector product instead of two dependent
+// triangular sweeps - and only the refinement residual r = b - M x is FP64.
+// The residual does not store the FP64 matrix: M x = x - gamma J x with J x
+// assembled from the reaction derivatives d rate_r / d y_s kept (FP64) from
+// the setup point, reaction by reaction and species by species in the same
+// incidence order as the right-hand side.  A solve is accepted at normwise
+// backward error |r|_inf / (|M|_inf |x|_inf + |b|_inf) <= 1e-12; after
+// MAXREF sweeps without that, the cell falls back to an FP64 LU of the same
+// M (in a global-memory workspace) until its next setup.
 #pragma once
 
 #include "cellcore.cuh"
@@ -97,17 +99,19 @@ __device__ __forceinline__ double form_M32(const Grp<G>& g, const CellDesc& c, C
   return gmaxd(g, mnorm);
 }
 
-// FP64 M = I - gamma J from S.dr into S.M (the fallback factorisation)
+// FP64 M = I - gamma J from S.dr into Mg (the fallback factorisation's
+// matrix, in the cell's global-memory workspace)
 template <int G, int NPL, int NMAX>
 __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc& c,
-                                                 CellSmem<NMAX, 1>& S, double gamma) {
+                                                 CellSmem<NMAX, 1>& S, double gamma,
+                                                 double (*Mg)[NMAX + 1]) {
   const int n = c.n;
   g.sync();
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     const int i = g.rank + G * p;
     if (i >= n) continue;
-    double* row = S.M[i];
+    double* row = Mg[i];
     for (int j = 0; j < n; ++j) row[j] = 0.0;
     const int e1 = __ldg(c.inc_off + i + 1);
     for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
@@ -125,45 +129,6 @@ __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc
     for (int j = 0; j < n; ++j) row[j] = __dsub_rn(i == j ? 1.0 : 0.0, __dmul_rn(gamma, row[j]));
   }
   g.sync();
-}
-
-// x <- (P M32)^{-1} P x in FP32 (factors in the packed float view of S.M)
-template <int G, int NPL, int NMAX>
-__device__ __forceinline__ void lu_solve32(const Grp<G>& g, CellSmem<NMAX, 1>& S, int n,
-                                           float (&x)[NPL]) {
-  const float (*M)[NMAX + 1] = reinterpret_cast<const float (*)[NMAX + 1]>(&S.M[0][0]);
-  const float* dinv = reinterpret_cast<const float*>(S.dinv);
-  float* buf = reinterpret_cast<float*>(S.ybuf);
-#pragma unroll
-  for (int p = 0; p < NPL; ++p) {
-    const int i = g.rank + G * p;
-    if (i < n) buf[i] = x[p];
-  }
-  g.sync();
-#pragma unroll
-  for (int p = 0; p < NPL; ++p) {
-    const int i = g.rank + G * p;
-    if (i < n) x[p] = buf[S.perm[i]];
-  }
-  g.sync();
-  for (int j = 0; j < n; ++j) {
-    const float xj = bcastf(g, pick(x, j / G), j % G);
-#pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      const int i = g.rank + G * p;
-      if (i > j && i < n) x[p] = fmaf(-M[i][j], xj, x[p]);
-    }
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const int owner = j % G, slot = j / G;
-    const float xj = bcastf(g, pick(x, slot), owner) * dinv[j];
-    if (g.rank == owner) place(x, slot, xj);
-#pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      const int i = g.rank + G * p;
-      if (i < j) x[p] = fmaf(-M[i][j], xj, x[p]);
-    }
-  }
 }
 
 // jx = J x (FP64) from the stored reaction derivatives
@@ -199,13 +164,109 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
   g.sync();
 }
 
+// In-place Gauss-Jordan inverse with partial pivoting (ties to the lowest
+// row) of the n x n FP32 matrix A; the block inverse the paper applies to
+// its 3x3 reaction blocks (Sec. 6), here for any block size.  Returns 0 or
+// k + 1 when no nonzero pivot exists in column k.  piv (n entries) and colk
+// (n floats): scratch.
+template <int G, int NMAX>
+__device__ __forceinline__ int gj_inverse(const Grp<G>& g, float (*A)[NMAX + 1], int16_t* piv,
+                                          float* colk, int n) {
+  constexpr int R = LaneGrid<G>::R, C = LaneGrid<G>::C;
+  constexpr int NJ = (NMAX + C - 1) / C;
+  const int li = g.rank / C, lj = g.rank % C;
+  for (int k = 0; k < n; ++k) {
+    float best = -1.0f;
+    int p = n;
+    for (int i = k + g.rank; i < n; i += G) {
+      const float v = fabsf(A[i][k]);
+      if (v > best) { best = v; p = i; }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(g.mask, best, o, G);
+      const int op = __shfl_xor_sync(g.mask, p, o, G);
+      if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+    }
+    if (!(best > 0.0f) || p >= n) return k + 1;
+    if (g.rank == 0) piv[k] = (int16_t)p;
+    if (p != k)
+      for (int j = g.rank; j < n; j += G) {
+        const float t = A[k][j];
+        A[k][j] = A[p][j];
+        A[p][j] = t;
+      }
+    g.sync();
+    const float pinv = 1.0f / A[k][k];
+    g.sync();
+    // row k <- row k / pivot, with the pivot slot becoming 1 / pivot; keep
+    // column k (the elimination factors) before it is overwritten
+    for (int j = g.rank; j < n; j += G) A[k][j] = (j == k) ? pinv : A[k][j] * pinv;
+    for (int i = g.rank; i < n; i += G) colk[i] = A[i][k];
+    g.sync();
+    // eliminate column k from every other row (lanes on an R x C grid)
+    float u[NJ];
+#pragma unroll
+    for (int b = 0; b < NJ; ++b) {
+      const int j = lj + C * b;
+      u[b] = j < n ? A[k][j] : 0.0f;
+    }
+    for (int i = li; i < n; i += R) {
+      if (i == k) continue;
+      const float f = colk[i];
+#pragma unroll
+      for (int b = 0; b < NJ; ++b) {
+        const int j = lj + C * b;
+        if (j < n) A[i][j] = (j == k) ? -f * u[b] : fmaf(-f, u[b], A[i][j]);
+      }
+    }
+    g.sync();
+  }
+  // undo the row exchanges as column exchanges, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = g.rank; i < n; i += G) {
+        const float t = A[i][k];
+        A[i][k] = A[i][p];
+        A[i][p] = t;
+      }
+    g.sync();
+  }
+  return 0;
+}
+
+// x = Ainv r in FP32 (lanes own rows; r gathered through shared memory)
+template <int G, int NPL, int NMAX>
+__device__ __forceinline__ void apply_inverse32(const Grp<G>& g, const float (*Ainv)[NMAX + 1], float* buf,
+                                                int n, const float (&r)[NPL], float (&x)[NPL]) {
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) buf[i] = r[p];
+  }
+  g.sync();
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    float s = 0.0f;
+    if (i < n) {
+      const float* row = Ainv[i];
+      for (int j = 0; j < n; ++j) s = fmaf(row[j], buf[j], s);
+    }
+    x[p] = s;
+  }
+  g.sync();
+}
+
 // Solve M x = b (M = I - gammap J at the setup point) to backward error
-// <= 1e-12 by FP32 LU solves and FP64 residuals; b is replaced by x.
-// Returns the number of sweeps, or -1 when the tolerance was not reached
-// (b then holds the last iterate).
+// <= 1e-12 by corrections with the FP32 inverse in S.M and FP64 residuals;
+// b is replaced by x.  Returns the number of sweeps, or -1 when the tolerance
+// was not reached (b then holds the last iterate).
 template <int G, int NPL, int NMAX>
 __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, 1>& S,
                                              double gammap, double mnorm, double (&b)[NPL]) {
+  float* buf = reinterpret_cast<float*>(S.ybuf);
   const int n = c.n;
   double x[NPL], r[NPL], jx[NPL];
   double bn = 0.0;
@@ -218,10 +279,10 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
   bn = gmaxd(g, bn);
   int sweeps = -1;
   for (int it = 1; it <= MAXREF; ++it) {
-    float c32[NPL];
+    float r32[NPL], c32[NPL];
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) c32[p] = (float)r[p];
-    lu_solve32<G, NPL, NMAX>(g, S, n, c32);
+    for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
+    apply_inverse32<G, NPL, NMAX>(g, S.M, buf, n, r32, c32);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
     jac_vec<G, NPL, NMAX>(g, c, S, x, jx);
