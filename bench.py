@@ -313,6 +313,28 @@ def run_ours(args):
     flops = algorithmic_flops(prob, cs)
     achieved = flops / t_kern / 1e12
     nv = nvector_bandwidth(torch, bdfb)
+    variants = {"batched_fp64": value}
+    for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}), ("batched_mixed_fp32_lu", {"precision": 1})):
+        with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, **opts) as vi:
+            ts = []
+            for i in range(2 + max(1, min(args.steps, 3))):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                vi.init(0.0, y0)
+                r = vi.integrate(TOUT, y, st)
+                e1.record(s)
+                e1.synchronize()
+                if r != 0:
+                    raise RuntimeError(f"{name}: integrate returned {r}")
+                if i >= 2:
+                    ts.append(e0.elapsed_time(e1) * 1e-3)
+            variants[name] = ws * NCELL / (sum(ts) / len(ts))
+            if name == "batched_mixed_fp32_lu":
+                variants["mixed_accuracy"] = accuracy(prob, y.cpu().numpy())
+                mst = vi.stats()
+                variants["mixed_refine_sweeps_per_solve"] = mst["nrefine"] / max(1, mst["nniters"])
+                variants["mixed_fp64_fallbacks"] = mst["nrefine_fallback"]
     traffic = None
     acc = accuracy(prob, yh)
     cpu_v, cpu_threads, cpu_ns, cpu_dt, cpu_fail = cpu_oracle_rate(prob)
@@ -332,6 +354,7 @@ def run_ours(args):
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "kernel_ms": t_kern * 1e3, "algorithmic_fp64_flops": flops,
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)"},
+        "variants_cells_per_s": variants,
         "nvector_gbs": nv,
         "nvector_roofline": {"bound": "hbm", "achieved": nv["linear_sum"], "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": nv["linear_sum"] / pk["hbm_gbs"],

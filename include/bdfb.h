@@ -52,7 +52,7 @@ enum {
 };
 
 typedef enum { BDFB_MEM_HOST = 0, BDFB_MEM_DEVICE = 1 } bdfb_mem;
-typedef enum { BDFB_ROBERTSON = 0, BDFB_MASSACTION = 1 } bdfb_kind;
+typedef enum { BDFB_ROBERTSON = 0, BDFB_MASSACTION = 1, BDFB_BRUSSELATOR3D = 2 } bdfb_kind;
 
 const char* bdfb_strerror(int code);
 /* library version as an integer (major * 10000 + minor * 100 + patch) */
@@ -136,6 +136,13 @@ int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b
  *   (at most 2 * 56 per cell); reaction r consumes the distinct local species
  *   reactants[4 r .. 4 r + 3] and produces products[4 r .. 4 r + 3]
  *   (255 = empty slot) at rate k[r] * prod(y[reactants]).
+ * kind BDFB_BRUSSELATOR3D: one coupled system (the Sec. 2 "full model" case):
+ *   the Brusselator reaction terms of Sec. 6 with diffusion D lap() on a
+ *   periodic nx^3 grid over [0,1)^3 (7-point Laplacian); k = {A, B, eps, D,
+ *   nx} (5 doubles); ncell = nx^3; y is species-major, y[s nx^3 + (i nx + j)
+ *   nx + l] for species s = u, v, w.  Integrated with one shared step size,
+ *   global WRMS norms, Newton + GMRES (option "maxl", default 5, at most 16)
+ *   left-preconditioned by the 3x3 reaction blocks; control on the host.
  * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
  * arrays live; bdfb_create copies everything it needs, so the caller may
  * free its arrays when bdfb_create returns. */
@@ -186,7 +193,9 @@ int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem);
  * continue from tout (each call starts from a fresh Jacobian). */
 int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem);
 int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
-/* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits */
+/* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits.
+ * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
+ * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl. */
 int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
 
 #ifdef __cplusplus

@@ -36,6 +36,7 @@ MEM_HOST = 0
 MEM_DEVICE = 1
 ROBERTSON = 0
 MASSACTION = 1
+BRUSSELATOR3D = 2
 
 _vp = C.c_void_p
 _i64 = C.c_int64
@@ -191,7 +192,7 @@ class Integrator:
         self._keep = []
         p = Problem()
         p.mem = MEM_HOST
-        p.ncell = problem.ncell
+        p.ncell = problem.npts if problem.kind == "brusselator3d" else problem.ncell
 
         def host(a, dt):
             a = np.ascontiguousarray(a, dtype=dt)
@@ -201,6 +202,10 @@ class Integrator:
         if problem.kind == "robertson":
             p.kind = ROBERTSON
             p.k = host(problem.k, np.float64)
+        elif problem.kind == "brusselator3d":
+            p.kind = BRUSSELATOR3D
+            p.ncell = problem.npts
+            p.k = host([problem.A, problem.B, problem.eps, problem.D, float(problem.nx)], np.float64)
         else:
             p.kind = MASSACTION
             p.n = host(problem.n, np.int32)
@@ -213,8 +218,11 @@ class Integrator:
         check(lib.bdfb_create(C.byref(p), C.byref(h)), "bdfb_create")
         self._keep = []
         self.h = h
-        self.ncell = problem.ncell
-        self.ny = int(problem.y_off[-1])
+        if problem.kind == "brusselator3d":
+            self.ncell, self.ny = 1, 3 * problem.npts    # one coupled system
+        else:
+            self.ncell = problem.ncell
+            self.ny = int(problem.y_off[-1])
         self.set_stream(stream)
         check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")
         for k, v in options.items():

@@ -21,6 +21,7 @@
 
 #include "cellcore.cuh"
 #include "mixed.cuh"
+#include "grid.cuh"
 
 namespace bdfb {
 
@@ -807,7 +808,8 @@ struct bdfb_ctx {
   double* d_fbws[NCLASS] = {};      // FP64 fallback workspace per class (mixed precision, lazy)
   cudaStream_t cstream[NCLASS] = {};  // one per size class, forked from `stream`
   float last_ms = 0.f;
-  int grid[2][NCLASS] = {};   // [precision][class]
+  int pgrid[2][NCLASS] = {};  // persistent grid size [precision][class]
+  GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
 };
 
 static void free_ctx(bdfb_ctx* c) {
@@ -815,6 +817,7 @@ static void free_ctx(bdfb_ctx* c) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
+  grid_destroy(c->grid);
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
@@ -868,7 +871,7 @@ static int setup_launch(bdfb_ctx* c) {
       int per_sm = 0;
       BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CELLS_KERNELS[pr][k], 32,
                                                               CELLS_SMEM[pr][k]));
-      c->grid[pr][k] = std::max(1, per_sm) * sm_count();
+      c->pgrid[pr][k] = std::max(1, per_sm) * sm_count();
     }
   }
   return 0;
@@ -890,7 +893,8 @@ static int class_of(int n, int nr) {
 extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   if (!prob || !out) return BDFB_ILL_INPUT;
   *out = nullptr;
-  if (prob->ncell < 0 || (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION) ||
+  if (prob->ncell < 0 ||
+      (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION && prob->kind != BDFB_BRUSSELATOR3D) ||
       (prob->mem != BDFB_MEM_HOST && prob->mem != BDFB_MEM_DEVICE) || !prob->k)
     return BDFB_ILL_INPUT;
   bdfb_ctx* c = new (std::nothrow) bdfb_ctx();
@@ -898,6 +902,18 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   cudaGetDevice(&c->device);
   c->kind = prob->kind;
   c->ncell = prob->ncell;
+  if (prob->kind == BDFB_BRUSSELATOR3D) {   // one coupled system on a grid
+    std::vector<double> par;
+    TRY(fetch(par, prob->k, 5, prob->mem));
+    const int nx = (int)par[4];
+    if ((double)nx != par[4] || (int64_t)nx * nx * nx != prob->ncell) { free_ctx(c); return BDFB_ILL_INPUT; }
+    TRY(grid_create(nx, par[0], par[1], par[2], par[3], &c->grid));
+    c->ny = 3 * prob->ncell;
+    BDFB_CUDA(cudaEventCreate(&c->ev0));
+    BDFB_CUDA(cudaEventCreate(&c->ev1));
+    *out = c;
+    return BDFB_SUCCESS;
+  }
   const int64_t C = prob->ncell;
   std::vector<int32_t> n;
   std::vector<int64_t> yoff, roff;
@@ -1041,6 +1057,7 @@ extern "C" void bdfb_destroy(bdfb_ctx* ctx) { free_ctx(ctx); }
 extern "C" int bdfb_set_stream(bdfb_ctx* ctx, void* stream) {
   if (!ctx) return BDFB_ILL_INPUT;
   ctx->stream = as_stream(stream);
+  if (ctx->grid) grid_set_stream(ctx->grid, ctx->stream);
   return BDFB_SUCCESS;
 }
 
@@ -1049,11 +1066,13 @@ extern "C" int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol) {
     return BDFB_ILL_INPUT;
   ctx->rtol = rtol;
   ctx->atol = atol;
+  if (ctx->grid) grid_set_tolerances(ctx->grid, rtol, atol);
   return BDFB_SUCCESS;
 }
 
 extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   if (!ctx || !key) return BDFB_ILL_INPUT;
+  if (ctx->grid) return grid_set_option(ctx->grid, key, v);
   if (!std::strcmp(key, "mxstep")) {
     if (v < 1 || v > 1000000000) return BDFB_ILL_INPUT;
     ctx->mxstep = v;
@@ -1079,6 +1098,11 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
 extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem) {
   if (!ctx || !std::isfinite(t0) || (ctx->ny > 0 && !y0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->grid) {
+    const int r = grid_init(ctx->grid, t0, y0, mem);
+    ctx->initialized = r == 0;
+    return r;
+  }
   std::vector<CellState> st(std::max<int64_t>(ctx->ncell, 1));
   std::memset(st.data(), 0, st.size() * sizeof(CellState));
   for (auto& s : st) { s.t = t0; s.q = 1; s.crate = 1.0; }
@@ -1100,6 +1124,15 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
 extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
   if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->grid) {
+    const int r = grid_integrate(ctx->grid, tout, y, mem);
+    if (status) {
+      const int32_t sv = r;
+      if (mem == BDFB_MEM_HOST) *status = sv;
+      else BDFB_CUDA(cudaMemcpy(status, &sv, sizeof sv, cudaMemcpyHostToDevice));
+    }
+    return r;
+  }
   if (ctx->ncell == 0) return BDFB_SUCCESS;
   cudaStream_t s = ctx->stream;
   const int m = ctx->mapping == 32 ? 1 : 0;
@@ -1133,7 +1166,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   if (ctx->precision == 1) {   // FP64 fallback workspace: one slice per resident warp
     for (int cl = 0; cl < NCLASS; ++cl)
       if (!ctx->d_fbws[cl] && ctx->cls_end[m][cl] > ctx->cls_begin[m][cl]) {
-        const size_t bytes = (size_t)ctx->grid[1][cl] * fallback_doubles_per_warp(cl) * sizeof(double);
+        const size_t bytes = (size_t)ctx->pgrid[1][cl] * fallback_doubles_per_warp(cl) * sizeof(double);
         if (cudaMalloc(&ctx->d_fbws[cl], bytes) != cudaSuccess) {
           ctx->d_fbws[cl] = nullptr;
           return BDFB_MEM_FAIL;
@@ -1151,7 +1184,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
     cudaStream_t cs = ctx->cstream[cl];
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
     const int pr = ctx->precision;
-    const int grid = std::min(ctx->grid[pr][cl], t1 - t0);
+    const int grid = std::min(ctx->pgrid[pr][cl], t1 - t0);
     CELLS_KERNELS[pr][cl]<<<grid, 32, CELLS_SMEM[pr][cl], cs>>>(P, t0, t1, ctx->d_counter + cl,
                                                                 pr == 1 ? ctx->d_fbws[cl] : nullptr);
     BDFB_CUDA(cudaGetLastError());
@@ -1185,6 +1218,18 @@ static int fetch_states(bdfb_ctx* ctx, std::vector<CellState>& st) {
 
 extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
   if (!ctx || !out) return BDFB_ILL_INPUT;
+  if (ctx->grid) {
+    int64_t g[8];
+    double ms = 0.0;
+    grid_stats(ctx->grid, g, &ms);
+    std::memset(out, 0, sizeof *out);
+    out->ncell = ctx->ncell;
+    out->nsteps = g[0]; out->nfevals = g[1]; out->nlinsetups = g[2]; out->nniters = g[3];
+    out->nncfails = g[4]; out->netfails = g[5];
+    out->max_steps = out->min_steps = g[0];
+    out->last_kernel_ms = ms;
+    return BDFB_SUCCESS;
+  }
   std::vector<CellState> st;
   int r = fetch_states(ctx, st);
   if (r) return r;
@@ -1212,6 +1257,14 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
 extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (!ctx || (!out && ctx->ncell > 0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->grid) {
+    int64_t g[8];
+    double ms = 0.0;
+    grid_stats(ctx->grid, g, &ms);
+    if (mem == BDFB_MEM_HOST) std::memcpy(out, g, sizeof g);
+    else BDFB_CUDA(cudaMemcpy(out, g, sizeof g, cudaMemcpyHostToDevice));
+    return BDFB_SUCCESS;
+  }
   std::vector<CellState> st;
   int r = fetch_states(ctx, st);
   if (r) return r;

@@ -1,0 +1,79 @@
+"""GPU parity of the grouped grid integrator (Brusselator reaction-diffusion,
+one coupled system, Newton + left-preconditioned GMRES) against the oracle's
+grouped integrator: same method, same readings, so final states agree with an
+rtol = 1e-10 oracle truth as well as the oracle at the same tolerance does,
+and step counts agree."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2011_12984_b300 import bdfb, gen
+
+pytestmark = pytest.mark.gpu
+
+
+def run_grid(p, tout, rtol, atol, y0=None, maxl=5, device_io=True):
+    y0 = p.y0 if y0 is None else y0
+    with bdfb.Integrator(p, rtol=rtol, atol=atol, maxl=maxl) as I:
+        if device_io:
+            I.init(0.0, torch.from_numpy(np.ascontiguousarray(y0)).cuda())
+            y = torch.empty(y0.size, dtype=torch.float64, device="cuda")
+            ret = I.integrate(tout, y)
+            y = y.cpu().numpy()
+        else:
+            I.init(0.0, y0.copy())
+            y = np.empty(y0.size)
+            ret = I.integrate(tout, y)
+        return ret, y, I.cell_stats()[0], I.stats()
+
+
+@pytest.mark.parametrize("nx,tout", [(6, 0.05), (10, 0.02)])
+def test_grid_matches_oracle(nx, tout):
+    p = gen.brusselator3d(nx, seed=nx)
+    rtol, atol = 1e-6, 1e-10
+    ret, y, gs, _ = run_grid(p, tout, rtol, atol)
+    assert ret == 0
+    ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
+    rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
+    assert ro == 0 and rt == 0
+    w = rtol * np.abs(yt) + atol
+    eg = np.max(np.abs(y - yt) / w)
+    eo = np.max(np.abs(yo - yt) / w)
+    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
+    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)        # steps
+    assert gs[6] > 0                                         # GMRES iterations
+
+
+def test_grid_steady_state_stays():
+    p = gen.brusselator3d(8, noise=0.0)
+    ret, y, _, _ = run_grid(p, 0.1, 1e-6, 1e-10)
+    assert ret == 0
+    assert np.max(np.abs(y - p.y0) / np.abs(p.y0)) <= 1e-12
+
+
+def test_grid_fourier_mode_decay_and_host_io():
+    nx, k = 8, (1, 2, 0)
+    npts = nx ** 3
+    i, j, l = np.meshgrid(np.arange(nx), np.arange(nx), np.arange(nx), indexing="ij")
+    mode = np.cos(2 * np.pi * (k[0] * i + k[1] * j + k[2] * l) / nx).reshape(-1)
+    y0 = np.zeros(3 * npts)
+    y0[npts:2 * npts] = mode
+    p = gen.Brusselator3D(nx=nx, A=0.0, B=0.0, eps=5e-6, D=1e-2, y0=y0)
+    lam = -(4.0 * nx * nx) * sum(np.sin(np.pi * kd / nx) ** 2 for kd in k)
+    L = p.D * lam
+    tout = 0.5 / abs(L)
+    ret, y, _, _ = run_grid(p, tout, 1e-8, 1e-12, device_io=False)
+    assert ret == 0
+    assert np.max(np.abs(y[npts:2 * npts] - np.exp(L * tout) * mode)) <= 20 * 1e-8
+
+
+def test_grid_64_cubed_properties():
+    """A mid-size grid in the benchmark's launch configuration: finite, the
+    fast species on its slow manifold w = B / (1 + eps u)."""
+    p = gen.brusselator3d(64, seed=3)
+    ret, y, gs, st = run_grid(p, 0.05, 1e-6, 1e-10)
+    assert ret == 0 and np.all(np.isfinite(y))
+    u, v, w = y.reshape(3, -1)
+    assert np.max(np.abs(w - p.B / (1.0 + p.eps * u)) / w) < 1e-5
+    assert gs[0] > 0 and st["nsteps"] == gs[0]
