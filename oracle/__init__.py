@@ -292,5 +292,32 @@ def bruss_integrate(p, t0, tout, rtol, atol, maxl=5, mxstep=100000, y0=None):
     return ret, y, st
 
 
+# ---------------------------------------------------------------- MLP
+MLP_NPARAM = 5642
+
+
+def mlp_forward(params, X):
+    params, X = _f64(params), _f64(np.atleast_2d(X))
+    Y = np.empty((X.shape[0], 10))
+    lib().or_mlp_forward(_p(params), _i64(X.shape[0]), _p(X), _p(Y))
+    return Y
+
+
+def mlp_loss_grad(params, X, T):
+    params, X, T = _f64(params), _f64(np.atleast_2d(X)), _f64(np.atleast_2d(T))
+    g = np.empty(MLP_NPARAM)
+    L = lib()
+    L.or_mlp_loss_grad.restype = _d
+    loss = L.or_mlp_loss_grad(_p(params), _i64(X.shape[0]), _p(X), _p(T), _p(g))
+    return loss, g
+
+
+def adam_step(params, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """in place on float64 arrays"""
+    L = lib()
+    L.or_adam_step.argtypes = [_i64, _pd, _pd, _pd, _pd, _i64, _d, _d, _d, _d]
+    L.or_adam_step(params.size, _p(params), _p(_f64(g)), _p(m), _p(v), t, lr, b1, b2, eps)
+
+
 def host_threads() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)

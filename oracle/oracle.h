@@ -148,4 +148,11 @@ int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double to
 int or_bruss_gmres(const or_bruss* p, const double* y, double gamma, const double* ewt,
                    double tol, int maxl, double* b, double* resnorm);
 
+/* ---------------- learned Newton initial guess (12 -> 64 -> 64 -> 10 MLP) ---- */
+int or_mlp_nparam(void);
+void or_mlp_forward(const double* p, int64_t nrows, const double* X, double* Y);
+double or_mlp_loss_grad(const double* p, int64_t nrows, const double* X, const double* T, double* grad);
+void or_adam_step(int64_t n, double* p, const double* g, double* m, double* v, int64_t t, double lr,
+                  double b1, double b2, double eps);
+
 #endif
