@@ -165,6 +165,7 @@ typedef struct {
   int64_t ncells_failed;                                            /* status != 0 */
   int64_t nrefine, nrefine_fallback;  /* mixed precision: refinement sweeps, FP64 refactorisations */
   double last_kernel_ms;              /* device time of the last integrate's kernels */
+  int64_t nguess, nguess_fallback;    /* learned guesses taken; of those, Newton solves redone from 0 */
 } bdfb_stats;
 
 typedef struct bdfb_ctx bdfb_ctx;
@@ -182,7 +183,16 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *  "precision" 0 = FP64 factorisation (default), 1 = FP32 factorisation with
  *              FP64 iterative refinement to 1e-12 backward error
  *  "graph"     1 = replay integrate's launches from a captured CUDA graph
- *  "qmax"      maximum BDF order, 1..5 (default 5) */
+ *  "qmax"      maximum BDF order, 1..5 (default 5)
+ *  "predictor" 0 = Newton starts from a zero correction (default), 1 = from
+ *              the learned guess of bdfb_load_mlp (every cell n <= 10, FP64
+ *              factorisation; runs one warp per cell).  The unchanged Newton
+ *              convergence test judges the guess; when the Newton solve from
+ *              it fails, or converges to a correction that fails the local
+ *              error test, it is repeated from zero and counted in
+ *              nguess_fallback, not as a step failure.
+ * With "mapping" 32 and every cell n <= 16 the one-warp-per-cell kernel of
+ * the predictor runs (with or without the guess). */
 int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);
 /* set t0 and copy the initial state (packed by y_off); mem: where y0 lives */
 int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem);
@@ -197,6 +207,50 @@ int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
  * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
  * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl. */
 int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
+
+/* ------------------------------------- learned Newton initial guess (MLP)
+ * Not part of the paper: a 12 -> 64 -> 64 -> 10 ReLU network predicts the
+ * Newton correction Delta of a step, in error-weight units (Delta_i ewt_i),
+ * from the features x = (y_pred_0..9 (zero past n), (log10|h| + 8) / 4,
+ * gamma / h).  Parameters: 5642 FP32 values, W1[64][12], b1[64], W2[64][64],
+ * b2[64], W3[10][64], b3[10] (W[out][in]).  Evaluation and training run
+ * on BF16 tensor-core MMAs with FP32 accumulation; the master weights and
+ * Adam moments stay FP32.  X is [rows][12], T and Y [rows][10], row-major
+ * FP32; every pointer is device memory owned by the caller. */
+int64_t bdfb_mlp_nparam(void);        /* 5642 */
+int64_t bdfb_mlp_packed_bytes(void);  /* size of the packed BF16 operand form */
+/* FP32 parameters -> packed form (BF16 weights in MMA layouts, FP32 biases) */
+int bdfb_mlp_pack(const float* params, void* packed, void* stream);
+/* Y = net(X) for nrows rows (nrows >= 0) */
+int bdfb_mlp_forward(int64_t nrows, const float* X, const void* packed, float* Y, void* stream);
+/* grad += d loss / d params and *loss += loss over nrows >= 1 rows, with
+ * loss = mean over rows and the 10 outputs of (net(X) - T)^2; the caller
+ * zeroes grad and *loss first */
+int bdfb_mlp_loss_grad(int64_t nrows, const float* X, const float* T, const void* packed, float* grad,
+                       float* loss, void* stream);
+/* one Adam step (Kingma & Ba; b1 0.9, b2 0.999, eps 1e-8, bias-corrected
+ * with step number t >= 1) on params with gradient grad; grad is zeroed */
+int bdfb_mlp_adam(float* params, float* grad, float* m, float* v, int64_t t, float lr, void* stream);
+/* nsteps Adam steps (b1 0.9, b2 0.999, eps 1e-8, learning rate lr) on
+ * minibatches of `batch` consecutive rows, batch k = (t0 + step) mod
+ * max(1, nrows / batch); t0 = Adam steps already taken (bias correction).
+ * params, m, v (nparam FP32 each) are updated, packed is refreshed after
+ * every step, grad (nparam FP32) is workspace, loss_hist[step] receives
+ * each minibatch's loss. */
+int bdfb_mlp_train(int64_t nrows, const float* X, const float* T, float* params, float* m, float* v,
+                   void* packed, float* grad, float* loss_hist, int batch, int nsteps, int64_t t0,
+                   float lr, void* stream);
+/* use the packed network (device memory, 16-byte aligned, bytes ==
+ * bdfb_mlp_packed_bytes(); must stay valid while the context uses it) for
+ * the option "predictor"; NULL detaches it */
+int bdfb_load_mlp(bdfb_ctx* ctx, const void* packed, int64_t bytes);
+/* Recording for training: every accepted step of every cell (each cell
+ * n <= 10, FP64 factorisation) appends its features x (12 floats) to x and
+ * its converged correction Delta_i ewt_i (10 floats) to t at index
+ * atomicAdd(count, 1) while that index is < cap; *count keeps counting past
+ * cap.  x == NULL stops recording.  Recording runs the one-warp-per-cell
+ * kernel. */
+int bdfb_set_record(bdfb_ctx* ctx, float* x, float* t, int64_t cap, unsigned long long* count);
 
 #ifdef __cplusplus
 }

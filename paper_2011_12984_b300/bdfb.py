@@ -53,7 +53,8 @@ class Stats(C.Structure):
     _fields_ = [("ncell", _i64), ("nsteps", _i64), ("nfevals", _i64), ("nlinsetups", _i64),
                 ("nniters", _i64), ("nncfails", _i64), ("netfails", _i64), ("max_steps", _i64),
                 ("min_steps", _i64), ("ncells_failed", _i64), ("nrefine", _i64),
-                ("nrefine_fallback", _i64), ("last_kernel_ms", _d)]
+                ("nrefine_fallback", _i64), ("last_kernel_ms", _d), ("nguess", _i64),
+                ("nguess_fallback", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +87,16 @@ _sig("bdfb_init", C.c_int, [_vp, _d, _vp, _i32])
 _sig("bdfb_integrate", C.c_int, [_vp, _d, _vp, _vp, _i32])
 _sig("bdfb_get_stats", C.c_int, [_vp, C.POINTER(Stats)])
 _sig("bdfb_get_cell_stats", C.c_int, [_vp, _vp, _i32])
+_sig("bdfb_mlp_nparam", _i64, [])
+_sig("bdfb_mlp_packed_bytes", _i64, [])
+_sig("bdfb_mlp_pack", C.c_int, [_vp, _vp, _vp])
+_sig("bdfb_mlp_forward", C.c_int, [_i64, _vp, _vp, _vp, _vp])
+_sig("bdfb_mlp_loss_grad", C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp])
+_sig("bdfb_mlp_train", C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _i64,
+                                 C.c_float, _vp])
+_sig("bdfb_mlp_adam", C.c_int, [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp])
+_sig("bdfb_load_mlp", C.c_int, [_vp, _vp, _i64])
+_sig("bdfb_set_record", C.c_int, [_vp, _vp, _vp, _i64, _vp])
 
 
 class BdfbError(RuntimeError):
@@ -184,6 +195,47 @@ def batched_solve_mixed(a, b, x, sweeps, stream=None):
                                               _stream(stream)), "batched_solve_mixed")
 
 
+# ---------------------------------------------------- learned Newton guess
+MLP_NI, MLP_NO = 12, 10
+MLP_NPARAM = lib.bdfb_mlp_nparam()
+MLP_PACKED_BYTES = lib.bdfb_mlp_packed_bytes()
+
+
+def mlp_packed(device="cuda"):
+    """uninitialised packed-network buffer (uint8 CUDA tensor, 16-byte aligned)"""
+    return _torch().empty(MLP_PACKED_BYTES, dtype=_torch().uint8, device=device)
+
+
+def mlp_pack(params, packed, stream=None):
+    """FP32 parameters (CUDA, 5642) -> packed BF16 operand form"""
+    return check(lib.bdfb_mlp_pack(_dptr(params), _dptr(packed), _stream(stream)), "mlp_pack")
+
+
+def mlp_forward(X, packed, Y, stream=None):
+    """Y (rows, 10) = net(X (rows, 12)), FP32 CUDA tensors"""
+    return check(lib.bdfb_mlp_forward(X.shape[0], _dptr(X), _dptr(packed), _dptr(Y), _stream(stream)),
+                 "mlp_forward")
+
+
+def mlp_loss_grad(X, T, packed, grad, loss, stream=None):
+    """grad (5642) += d loss / d params, loss (1) += mean squared error"""
+    return check(lib.bdfb_mlp_loss_grad(X.shape[0], _dptr(X), _dptr(T), _dptr(packed), _dptr(grad),
+                                        _dptr(loss), _stream(stream)), "mlp_loss_grad")
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, stream=None):
+    """one Adam step (step number t >= 1); grad is zeroed"""
+    return check(lib.bdfb_mlp_adam(_dptr(params), _dptr(grad), _dptr(m), _dptr(v), int(t), float(lr),
+                                   _stream(stream)), "mlp_adam")
+
+
+def mlp_train(X, T, params, m, v, packed, grad, loss_hist, batch, nsteps, t0=0, lr=1e-3, stream=None):
+    """nsteps Adam steps on minibatches of X, T (see bdfb_mlp_train)"""
+    return check(lib.bdfb_mlp_train(X.shape[0], _dptr(X), _dptr(T), _dptr(params), _dptr(m), _dptr(v),
+                                    _dptr(packed), _dptr(grad), _dptr(loss_hist), int(batch), int(nsteps),
+                                    int(t0), float(lr), _stream(stream)), "mlp_train")
+
+
 # ------------------------------------------------------------- integrator
 class Integrator:
     """Owns a ``bdfb_ctx``.  ``problem`` is a generator problem (host arrays)."""
@@ -265,6 +317,22 @@ class Integrator:
         s = Stats()
         check(lib.bdfb_get_stats(self.h, C.byref(s)), "bdfb_get_stats")
         return s.as_dict()
+
+    def load_mlp(self, packed):
+        """use a packed network (CUDA uint8 tensor; None detaches) for option predictor=1"""
+        self._mlp = packed
+        ptr = None if packed is None else _dptr(packed)
+        n = 0 if packed is None else packed.numel() * packed.element_size()
+        check(lib.bdfb_load_mlp(self.h, ptr, n), "bdfb_load_mlp")
+
+    def set_record(self, x=None, t=None, count=None):
+        """record accepted steps' (features, correction) pairs into x (cap, 12)
+        and t (cap, 10) FP32 CUDA tensors; count: int64 CUDA tensor (1); x=None stops"""
+        self._rec = (x, t, count)
+        if x is None:
+            return check(lib.bdfb_set_record(self.h, None, None, 0, None), "bdfb_set_record")
+        return check(lib.bdfb_set_record(self.h, _dptr(x), _dptr(t), x.shape[0], _dptr(count)),
+                     "bdfb_set_record")
 
     def cell_stats(self):
         out = np.zeros((self.ncell, 8), np.int64)

@@ -15,6 +15,7 @@
 // Nothing in the kernel waits on another warp; every loop is bounded.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -22,6 +23,7 @@
 #include "cellcore.cuh"
 #include "mixed.cuh"
 #include "grid.cuh"
+#include "mlp.cuh"
 
 namespace bdfb {
 
@@ -43,7 +45,7 @@ struct CellState {
   int32_t q, qwait, nst, nstlp;
   int32_t nfe, nsetups, nni, ncfn;
   int32_t netf, flags, status, qlast;
-  int32_t nrefine, nrefine_fb, pad0, pad1;
+  int32_t nrefine, nrefine_fb, nguess, nguess_fb;
 };
 enum { F_STARTED = 1, F_GROWN = 2 };
 
@@ -74,6 +76,12 @@ struct Params {
   double tout, rtol, atol;
   int32_t mxstep;
   Consts K;
+  // learned Newton initial guess (one-warp-per-cell kernel only)
+  const void* mlp;            // packed network, or null: Newton starts from 0
+  float* rec_x;               // recording of (features, converged correction)
+  float* rec_t;               //   pairs of accepted steps, or null
+  int64_t rec_cap;
+  unsigned long long* rec_count;
 };
 
 template <int G>
@@ -93,6 +101,7 @@ struct Cell {
   int nst0, ncf, nef, setup_done, force_setup, tried_fresh, newstep, last, retry;
   int nref, nref_fb, fp64mode;   // mixed precision: refinement sweeps, FP64 fallbacks, M in FP64
   double mnorm;                  // |M|_inf of the current setup (mixed precision)
+  int nguess, nguess_fb;         // learned guesses taken, guesses abandoned for a zero start
 };
 
 template <int G, int NMAX>
@@ -256,13 +265,46 @@ __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem
   }
 }
 
+// Input feature of the learned guess held by this lane (one warp per cell,
+// species i on lane i): lanes 0..9 the predicted state y_pred (zero past n),
+// lane 10 (log10 |h| + 8) / 4, lane 11 gamma / h = 1 / l_1.
+__device__ __forceinline__ float mlp_feature(int lane, int n, double ypred, double h, double rl1) {
+  if (lane < MLP_NO) return lane < n ? (float)ypred : 0.f;
+  if (lane == MLP_NO) return (log10f(fabsf((float)h)) + 8.f) * 0.25f;
+  if (lane == MLP_NO + 1) return (float)rl1;
+  return 0.f;
+}
+
+// Newton initial correction from the network: row 0 of a 16-row MMA tile
+// holds this cell's features; the output (Delta in error-weight units) is
+// un-scaled by ewt.  A non-finite output starts that component from zero.
+__device__ __forceinline__ double mlp_guess(const void* mlp, float feat, int n, double ewt) {
+  const int lane = threadIdx.x & 31, c = lane & 3;
+  const float x0 = __shfl_sync(FULL_MASK, feat, 2 * c), x1 = __shfl_sync(FULL_MASK, feat, 2 * c + 1);
+  const float x8 = __shfl_sync(FULL_MASK, feat, 2 * c + 8), x9 = __shfl_sync(FULL_MASK, feat, 2 * c + 9);
+  uint32_t a[4] = {0u, 0u, 0u, 0u};
+  if (lane < 4) { a[0] = pack_bf16(x0, x1); a[2] = pack_bf16(x8, x9); }
+  float out[2][4];
+  mlp_tile_forward(mlp_view(mlp), a, out);
+  // row 0, column i sits on lane (i mod 8) / 2 of n-tile i / 8, element i & 1
+  const int src = (lane & 7) >> 1;
+  const float s00 = __shfl_sync(FULL_MASK, out[0][0], src), s01 = __shfl_sync(FULL_MASK, out[0][1], src);
+  const float s10 = __shfl_sync(FULL_MASK, out[1][0], src), s11 = __shfl_sync(FULL_MASK, out[1][1], src);
+  const float v = lane < 8 ? ((lane & 1) ? s01 : s00) : ((lane & 1) ? s11 : s10);
+  const double d = lane < n && lane < MLP_NO ? (double)v / ewt : 0.0;
+  return isfinite(d) ? d : 0.0;
+}
+
 // One step attempt.  Returns true when the cell is finished (tout reached or
-// a failure status set).
-template <int G, int NMAX, int PREC>
+// a failure status set).  LEARN (one warp per cell, n <= 10): Newton may
+// start from the network's guess and a recording of the accepted steps'
+// (features, converged correction) pairs may be kept.
+template <int G, int NMAX, int PREC, int LEARN = 0>
 __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const CellDesc& cd,
                                         CellSmem<NMAX, PREC>& S, Cell<G, NMAX>& C,
                                         double (*Mg)[NMAX + 1]) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
+  static_assert(!LEARN || (G == 32 && NPL == 1 && PREC == 0), "learned guess: one warp per cell, FP64");
   const int n = cd.n;
   if (!(C.flags & F_STARTED)) {
     if (P.tout == C.t) { C.status = 0; return true; }   // first step waits for tout != t0
@@ -342,9 +384,31 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   // ---- Newton iteration (norms compared squared, in FP64)
   double acnrm2 = 0.0;
   bool conv = false;
+  float feat = 0.f;
+  if constexpr (LEARN) feat = mlp_feature(g.rank, n, C.z[0][0], C.h, rl1);
   if (!fail) {
+    // pass 0 starts from the network's guess when one is loaded; if that
+    // Newton solve fails, pass 1 repeats it from zero (not a step failure)
+    bool guess = false;
+    if constexpr (LEARN) guess = P.mlp != nullptr;
+    const double crate0 = C.crate;
+    for (int pass = 0; pass < 2 && !conv; ++pass) {
+    if (pass == 1) {
+      if (!guess) break;
+      guess = false;
+      C.nguess_fb++;
+      C.crate = crate0;
+    }
+    if constexpr (LEARN) {
+      if (guess) {
+        C.nguess++;
+        C.acor[0] = mlp_guess(P.mlp, feat, n, C.ewt[0]);
+      }
+    }
+    if (!guess) {
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
+      for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
+    }
     double delp2 = 0.0;
     const double eq2 = Eq * Eq * 100.0;   // (E_q / 0.1)^2
     for (int it = 1; it <= 3; ++it) {
@@ -396,12 +460,16 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       if (it > 1) C.crate = fmax(0.3 * C.crate, (double)sqrtf((float)(del2 / delp2)));
       const double cr = fmin(1.0, C.crate);
       if (del2 * cr * cr * eq2 <= 1.0) {       // |del| min(1, rate) E_q / 0.1 <= 1
-        acnrm2 = (it == 1) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
+        acnrm2 = (it == 1 && !guess) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
         conv = true;
         break;
       }
       if (it >= 2 && del2 > 4.0 * delp2) break;  // |del| > 2 |del_prev|: diverging
       delp2 = del2;
+    }
+    // a guessed start whose converged correction fails the local error
+    // test is redone from zero too: the test then judges the plain solve
+    if (conv && guess && !(acnrm2 * Eq * Eq <= 1.0)) conv = false;
     }
     if (!conv) fail = true;
   }
@@ -457,6 +525,17 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     return false;
   }
   // ---- accept
+  if constexpr (LEARN) {
+    if (P.rec_x) {
+      unsigned long long idx = 0;
+      if (g.rank == 0) idx = atomicAdd(P.rec_count, 1ull);
+      idx = __shfl_sync(FULL_MASK, idx, 0);
+      if (idx < (unsigned long long)P.rec_cap) {
+        if (g.rank < MLP_NI) P.rec_x[idx * MLP_NI + g.rank] = feat;
+        if (g.rank < MLP_NO) P.rec_t[idx * MLP_NO + g.rank] = g.rank < n ? (float)(C.acor[0] * C.ewt[0]) : 0.f;
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j <= QMAX; ++j)
     if (j <= q) {
@@ -478,7 +557,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
 
 // fb: this warp's slice of the FP64 fallback workspace (mixed precision;
 // (32 / G) matrices of NMAX x (NMAX + 1) doubles), else null
-template <int G, int NMAX, int PREC>
+template <int G, int NMAX, int PREC, int LEARN = 0>
 __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem, double* fb) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   Grp<G> g;
@@ -520,6 +599,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
     C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
     C.rn = 1.0 / (double)cd.n;
     C.nref = s.nrefine; C.nref_fb = s.nrefine_fb; C.fp64mode = 0; C.mnorm = 0.0;
+    C.nguess = s.nguess; C.nguess_fb = s.nguess_fb;
     C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
@@ -534,7 +614,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   }
   while (__any_sync(FULL_MASK, active)) {
     if (active) {
-      if (attempt<G, NMAX, PREC>(g, P, cd, S, C, Mg)) {
+      if (attempt<G, NMAX, PREC, LEARN>(g, P, cd, S, C, Mg)) {
         active = false;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
@@ -551,7 +631,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
           s.q = C.q; s.qwait = C.qwait; s.nst = C.nst; s.nstlp = C.nstlp;
           s.nfe = C.nfe; s.nsetups = C.nsetups; s.nni = C.nni; s.ncfn = C.ncfn;
           s.netf = C.netf; s.flags = C.flags; s.status = C.status; s.qlast = C.qlast;
-          s.nrefine = C.nref; s.nrefine_fb = C.nref_fb; s.pad0 = 0; s.pad1 = 0;
+          s.nrefine = C.nref; s.nrefine_fb = C.nref_fb; s.nguess = C.nguess; s.nguess_fb = C.nguess_fb;
           P.st[c] = s;
           if (P.status) P.status[c] = C.status;
           if (C.status < 0) atomicMin(P.worst, C.status);
@@ -585,6 +665,25 @@ __global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, 
     __syncwarp();
   }
 }
+
+// One warp per cell for cells of at most 16 species, in input order (the
+// schedule of mapping 32); LEARN adds the learned guess and the recording.
+constexpr int W16_NMAX = 16;
+static_assert(CLS_NMAX[2] == W16_NMAX, "cells of classes 0..2 fit the one-warp NMAX 16 layout");
+__global__ void __launch_bounds__(32) k_cells_w16(const __grid_constant__ Params P, int t0, int t1,
+                                                  unsigned* counter) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    if (t >= t1) break;
+    run_tile<32, W16_NMAX, 0, 1>(P, P.tiles[t], smem, nullptr);
+    __syncwarp();
+  }
+}
+constexpr int W16_SMEM = (int)sizeof(CellSmem<W16_NMAX, 0>);
 
 // doubles of FP64 fallback workspace one warp of class c needs
 static int64_t fallback_doubles_per_warp(int c) {
@@ -810,6 +909,15 @@ struct bdfb_ctx {
   float last_ms = 0.f;
   int pgrid[2][NCLASS] = {};  // persistent grid size [precision][class]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
+  int maxn = 0;               // largest cell
+  bool fits_w16 = false;      // every cell fits the NMAX 16 shared-memory layout
+  int pgrid_w16 = 0;          // persistent grid of the one-warp-per-cell small-cell kernel
+  int predictor = 0;          // 1: Newton starts from the learned guess
+  const void* mlp = nullptr;  // packed network (caller-owned device memory)
+  float* rec_x = nullptr;     // recording buffers (caller-owned device memory)
+  float* rec_t = nullptr;
+  int64_t rec_cap = 0;
+  unsigned long long* rec_count = nullptr;
 };
 
 static void free_ctx(bdfb_ctx* c) {
@@ -874,6 +982,10 @@ static int setup_launch(bdfb_ctx* c) {
       c->pgrid[pr][k] = std::max(1, per_sm) * sm_count();
     }
   }
+  BDFB_CUDA(cudaFuncSetAttribute(k_cells_w16, cudaFuncAttributeMaxDynamicSharedMemorySize, W16_SMEM));
+  int per_sm = 0;
+  BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells_w16, 32, W16_SMEM));
+  c->pgrid_w16 = std::max(1, per_sm) * sm_count();
   return 0;
 }
 
@@ -951,6 +1063,10 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
     c->nrxn = nrxn;
   }
   c->ny = yoff[C];
+  for (int64_t i = 0; i < C; ++i) c->maxn = std::max(c->maxn, n[i]);
+  c->fits_w16 = true;
+  for (int64_t i = 0; i < C; ++i)
+    if (cls[i] > 2) c->fits_w16 = false;    // class 2 has NMAX 16
   c->h_n = n;
   c->h_yoff = yoff;
   if (prob->kind == BDFB_MASSACTION) {
@@ -1082,6 +1198,7 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "precision")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     if (v == 1 && ctx->kind != BDFB_MASSACTION) return BDFB_ILL_INPUT;  // residual needs reaction data
+    if (v == 1 && (ctx->predictor || ctx->rec_x)) return BDFB_ILL_INPUT;
     ctx->precision = (int)v;
   } else if (!std::strcmp(key, "graph")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
@@ -1089,6 +1206,10 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "qmax")) {
     if (v < 1 || v > QMAX) return BDFB_ILL_INPUT;
     ctx->qmax = (int)v;
+  } else if (!std::strcmp(key, "predictor")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && (ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)) return BDFB_ILL_INPUT;
+    ctx->predictor = (int)v;
   } else {
     return BDFB_ILL_INPUT;
   }
@@ -1134,8 +1255,12 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
     return r;
   }
   if (ctx->ncell == 0) return BDFB_SUCCESS;
+  if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
   cudaStream_t s = ctx->stream;
-  const int m = ctx->mapping == 32 ? 1 : 0;
+  const bool learn = ctx->predictor || ctx->rec_x;
+  // one warp per cell: the NMAX 16 kernel when every cell fits it
+  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && ctx->precision == 0);
+  const int m = (ctx->mapping == 32 || w16) ? 1 : 0;
   Params P;
   std::memset(&P, 0, sizeof P);
   P.kind = ctx->kind;
@@ -1163,6 +1288,11 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.mxstep = (int32_t)std::min<int64_t>(ctx->mxstep, 0x7fffffff);
   static const Consts K = make_consts();
   P.K = K;
+  P.mlp = ctx->predictor ? ctx->mlp : nullptr;
+  P.rec_x = ctx->rec_x;
+  P.rec_t = ctx->rec_t;
+  P.rec_cap = ctx->rec_cap;
+  P.rec_count = ctx->rec_count;
   if (ctx->precision == 1) {   // FP64 fallback workspace: one slice per resident warp
     for (int cl = 0; cl < NCLASS; ++cl)
       if (!ctx->d_fbws[cl] && ctx->cls_end[m][cl] > ctx->cls_begin[m][cl]) {
@@ -1178,7 +1308,12 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   // fork: one persistent launch per size class, largest cells first, each on
   // its own stream so smaller classes fill the SMs the larger ones release
   BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
-  for (int cl = NCLASS - 1; cl >= 0; --cl) {
+  if (w16) {
+    const int grid = std::min(ctx->pgrid_w16, ctx->ntiles[1]);
+    k_cells_w16<<<grid, 32, W16_SMEM, s>>>(P, 0, ctx->ntiles[1], ctx->d_counter);
+    BDFB_CUDA(cudaGetLastError());
+  }
+  for (int cl = NCLASS - 1; cl >= 0 && !w16; --cl) {
     const int t0 = ctx->cls_begin[m][cl], t1 = ctx->cls_end[m][cl];
     if (t1 <= t0) continue;
     cudaStream_t cs = ctx->cstream[cl];
@@ -1249,6 +1384,8 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
     out->ncells_failed += s.status != 0;
     out->nrefine += s.nrefine;
     out->nrefine_fallback += s.nrefine_fb;
+    out->nguess += s.nguess;
+    out->nguess_fallback += s.nguess_fb;
   }
   out->last_kernel_ms = ctx->last_ms;
   return BDFB_SUCCESS;
@@ -1280,6 +1417,25 @@ extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (ctx->ncell == 0) return BDFB_SUCCESS;
   if (mem == BDFB_MEM_HOST) std::memcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t));
   else BDFB_CUDA(cudaMemcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_load_mlp(bdfb_ctx* ctx, const void* packed, int64_t bytes) {
+  if (!ctx || ctx->grid || (packed && bytes != PACKED_BYTES)) return BDFB_ILL_INPUT;
+  if (packed && (reinterpret_cast<uintptr_t>(packed) & 15u)) return BDFB_ILL_INPUT;
+  ctx->mlp = packed;
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_set_record(bdfb_ctx* ctx, float* x, float* t, int64_t cap, unsigned long long* count) {
+  if (!ctx || ctx->grid) return BDFB_ILL_INPUT;
+  if (!x) {
+    ctx->rec_x = nullptr; ctx->rec_t = nullptr; ctx->rec_cap = 0; ctx->rec_count = nullptr;
+    return BDFB_SUCCESS;
+  }
+  if (!t || !count || cap < 0 || ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)
+    return BDFB_ILL_INPUT;
+  ctx->rec_x = x; ctx->rec_t = t; ctx->rec_cap = cap; ctx->rec_count = count;
   return BDFB_SUCCESS;
 }
 

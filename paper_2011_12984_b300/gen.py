@@ -245,6 +245,29 @@ def mass_action(ncell: int, sizes=(3, 10, 32, 54), seed: int = DEFAULT_SEED,
                              reactants=reactants, products=products, k=k, y0=y0)
 
 
+def mass_action_shared(ncell: int, n: int = 10, seed: int = DEFAULT_SEED, network: int = 0,
+                       **kw) -> MassActionProblem:
+    """``ncell`` cells that all carry one random ``n``-species network (the
+    network of cell ``network`` of ``mass_action(.., sizes=(n,), seed + 1)``)
+    and differ in their initial states: cell c's Dirichlet(1, ..., 1) state
+    uses draws 1 + 10 R + i of its stream under ``seed`` (the draws an
+    unshared cell of this size would use for it)."""
+    base = mass_action(network + 1, sizes=(n,), seed=seed + 1, **kw).subset([network])
+    R = int(base.rxn_off[1])
+    keys = stream_keys(seed, np.arange(ncell, dtype=np.uint64))
+    y0 = np.empty((ncell, n), np.float64)
+    for c0 in range(0, ncell, 65536):
+        kc = keys[c0:c0 + 65536][:, None]
+        e = -np.log1p(-uniform(kc, 1 + DRAWS_PER_RXN * R + np.arange(n)[None, :]))
+        y0[c0:c0 + 65536] = e / e.sum(axis=1, keepdims=True)
+    return MassActionProblem(n=np.full(ncell, n, np.int32),
+                             y_off=np.arange(ncell + 1, dtype=np.int64) * n,
+                             rxn_off=np.arange(ncell + 1, dtype=np.int64) * R,
+                             reactants=np.tile(base.reactants, (ncell, 1)),
+                             products=np.tile(base.products, (ncell, 1)),
+                             k=np.tile(base.k, ncell), y0=y0.reshape(-1))
+
+
 # --------------------------------------------------------------------------
 # Brusselator reaction-diffusion on a periodic 3-D grid
 # --------------------------------------------------------------------------

@@ -63,6 +63,21 @@ def test_bad_arguments_rejected_without_gpu(lib):
     assert L.bdfb_create(None, None) == ILL
     L.bdfb_set_option.argtypes = [C.c_void_p, C.c_char_p, C.c_int64]
     assert L.bdfb_set_option(None, b"mxstep", 5) == ILL
+    L.bdfb_mlp_nparam.restype = C.c_int64
+    assert L.bdfb_mlp_nparam() == 5642
+    L.bdfb_mlp_packed_bytes.restype = C.c_int64
+    assert L.bdfb_mlp_packed_bytes() % 16 == 0
+    L.bdfb_mlp_forward.argtypes = [C.c_int64] + [C.c_void_p] * 4
+    assert L.bdfb_mlp_forward(-1, None, None, None, None) == ILL
+    assert L.bdfb_mlp_forward(0, None, None, None, None) == 0
+    L.bdfb_mlp_loss_grad.argtypes = [C.c_int64] + [C.c_void_p] * 6
+    assert L.bdfb_mlp_loss_grad(0, None, None, None, None, None, None) == ILL
+    L.bdfb_mlp_pack.argtypes = [C.c_void_p] * 3
+    assert L.bdfb_mlp_pack(None, None, None) == ILL
+    L.bdfb_load_mlp.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    assert L.bdfb_load_mlp(None, None, 0) == ILL
+    L.bdfb_set_record.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    assert L.bdfb_set_record(None, None, None, 0, None) == ILL
 
 
 def test_binding_imports_and_fails_loudly_without_library(tmp_path):

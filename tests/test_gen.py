@@ -58,3 +58,18 @@ def test_brusselator_noise():
     ss = np.repeat(np.array(gen.brusselator_steady_state(b.A, b.B, b.eps)), b.npts)
     rel = b.y0 / ss - 1.0
     assert np.max(np.abs(rel)) <= 0.01 and abs(rel.mean()) < 1e-3
+
+
+def test_mass_action_shared_network():
+    p = gen.mass_action_shared(50, n=10, seed=11)
+    R = int(p.rxn_off[1])
+    assert R == 20 and p.ncell == 50 and np.all(p.n == 10)
+    for c in range(1, 50):        # one network for every cell
+        sl = slice(p.rxn_off[c], p.rxn_off[c + 1])
+        assert np.array_equal(p.reactants[sl], p.reactants[:R])
+        assert np.array_equal(p.products[sl], p.products[:R])
+        assert np.array_equal(p.k[sl], p.k[:R])
+    # the initial states are those of unshared cells of the same size and seed
+    q = gen.mass_action(50, sizes=(10,), seed=11)
+    assert np.array_equal(p.y0, q.y0)
+    assert np.allclose(np.add.reduceat(p.y0, p.y_off[:-1]), 1.0, rtol=0, atol=1e-14)

@@ -1,0 +1,266 @@
+"""GPU parity of the learned Newton initial guess.
+
+* forward pass and loss gradient of the BF16 tensor-core kernels against the
+  FP64 oracle network (tolerances from BF16 rounding: inputs, weights and
+  hidden activations each carry a relative error up to 2^-9, and the output
+  gradient too, so outputs and gradients agree to a few 1e-3 of their scale;
+  the bars are 3e-2 on the worst element and 1e-2 in RMS);
+* exact results where BF16 is exact: a network of permutation matrices
+  returns permuted inputs bit for bit (catches any transposed operand);
+* Adam against the oracle's step, training against its own loss;
+* the integrator with the guess: a zero network reproduces the plain run bit
+  for bit, a garbage network still meets the accuracy bar (the unchanged
+  Newton test judges every guess), a trained one too; the recording holds
+  one row per accepted step.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2011_12984_b300 import bdfb, gen
+
+pytestmark = pytest.mark.gpu
+
+NI, NH, NO = 12, 64, 10
+OFF_W1, OFF_B1 = 0, NH * NI
+OFF_W2 = OFF_B1 + NH
+OFF_B2 = OFF_W2 + NH * NH
+OFF_W3 = OFF_B2 + NH
+OFF_B3 = OFF_W3 + NO * NH
+NP = oracle.MLP_NPARAM
+
+
+def rand_params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(NP)
+    p[OFF_W1:OFF_B1] = rng.standard_normal(NH * NI) * np.sqrt(2.0 / NI)
+    p[OFF_B1:OFF_W2] = rng.standard_normal(NH) * 0.1
+    p[OFF_W2:OFF_B2] = rng.standard_normal(NH * NH) * np.sqrt(2.0 / NH)
+    p[OFF_B2:OFF_W3] = rng.standard_normal(NH) * 0.1
+    p[OFF_W3:OFF_B3] = rng.standard_normal(NO * NH) * np.sqrt(1.0 / NH)
+    p[OFF_B3:] = rng.standard_normal(NO) * 0.1
+    return (p * scale).astype(np.float32).astype(np.float64)   # FP32-exact
+
+
+def cuda32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def packed_of(p):
+    pk = bdfb.mlp_packed()
+    bdfb.mlp_pack(cuda32(p), pk)
+    return pk
+
+
+def gpu_forward(p, X):
+    Y = torch.empty((X.shape[0], NO), dtype=torch.float32, device="cuda")
+    bdfb.mlp_forward(cuda32(X), packed_of(p), Y)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy().astype(np.float64)
+
+
+def gpu_loss_grad(p, X, T):
+    g = torch.zeros(NP, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    bdfb.mlp_loss_grad(cuda32(X), cuda32(T), packed_of(p), g, loss)
+    torch.cuda.synchronize()
+    return float(loss.item()), g.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("rows", [1, 15, 16, 1037, 70001])
+def test_forward_matches_oracle(rows):
+    rng = np.random.default_rng(rows)
+    p = rand_params(5)
+    X = rng.uniform(-1, 1, (rows, NI)).astype(np.float32).astype(np.float64)
+    Y = gpu_forward(p, X)
+    Yo = oracle.mlp_forward(p, X)
+    scale = np.abs(Yo).max()
+    assert np.abs(Y - Yo).max() <= 3e-2 * scale
+    assert np.sqrt(np.mean((Y - Yo) ** 2)) <= 1e-2 * np.sqrt(np.mean(Yo ** 2))
+
+
+def test_forward_permutation_network_exact():
+    """y_i = x_{pi(i)} through three permutation layers: exact in BF16."""
+    rng = np.random.default_rng(9)
+    p1, p2, p3 = rng.permutation(NH), rng.permutation(NH), rng.permutation(NO)
+    p = np.zeros(NP)
+    # layer 1: h1[p1[i]] = x[i] for i < 12; layer 2: h2[p2[j]] = h1[j];
+    # layer 3: y[o] = h2[p2[p1[p3[o]]]] -> x[p3[o]] for p3[o] < 10 < 12
+    for i in range(NI):
+        p[OFF_W1 + p1[i] * NI + i] = 1.0
+    for j in range(NH):
+        p[OFF_W2 + p2[j] * NH + j] = 1.0
+    for o in range(NO):
+        p[OFF_W3 + o * NH + p2[p1[p3[o]]]] = 1.0
+    X = rng.integers(0, 17, (100, NI)) / 4.0           # exact in BF16, >= 0
+    Y = gpu_forward(p, X)
+    assert np.array_equal(Y, X[:, p3])
+    assert np.array_equal(oracle.mlp_forward(p, X), X[:, p3])
+
+
+@pytest.mark.parametrize("rows", [7, 300, 4096 + 5])
+def test_loss_grad_matches_oracle(rows):
+    rng = np.random.default_rng(100 + rows)
+    p = rand_params(6)
+    X = rng.uniform(-1, 1, (rows, NI)).astype(np.float32).astype(np.float64)
+    T = rng.standard_normal((rows, NO)).astype(np.float32).astype(np.float64)
+    loss, g = gpu_loss_grad(p, X, T)
+    lo, go = oracle.mlp_loss_grad(p, X, T)
+    assert abs(loss - lo) <= 1e-2 * lo
+    for a, b in [(OFF_W1, OFF_B1), (OFF_B1, OFF_W2), (OFF_W2, OFF_B2), (OFF_B2, OFF_W3),
+                 (OFF_W3, OFF_B3), (OFF_B3, NP)]:
+        d = g[a:b] - go[a:b]
+        assert np.linalg.norm(d) <= 3e-2 * np.linalg.norm(go[a:b]), (a, b)
+        assert np.abs(d).max() <= 6e-2 * np.abs(go[a:b]).max(), (a, b)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(3)
+    p = rand_params(7)
+    m = np.zeros(NP)
+    v = np.zeros(NP)
+    pd, md, vd = cuda32(p), cuda32(m), cuda32(v)
+    po, mo, vo = p.copy(), m.copy(), v.copy()
+    for t in range(1, 6):
+        g = (rng.standard_normal(NP) * 10.0 ** rng.uniform(-4, 0, NP)).astype(np.float32).astype(np.float64)
+        gd = cuda32(g)
+        bdfb.mlp_adam(pd, gd, md, vd, t, lr=1e-3)
+        oracle.adam_step(po, g, mo, vo, t, lr=1e-3)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(gd).item() == 0          # gradient consumed
+    assert np.abs(pd.cpu().numpy() - po).max() <= 1e-6
+    assert np.abs(md.cpu().numpy() - mo).max() <= 1e-6 * np.abs(mo).max()
+
+
+def test_training_reduces_loss():
+    """Fit a teacher network's outputs; the loss the kernels report is the
+    oracle's loss of the trained parameters (within BF16 rounding)."""
+    rng = np.random.default_rng(11)
+    teacher = rand_params(12)
+    X = rng.uniform(-1, 1, (16384, NI)).astype(np.float32).astype(np.float64)
+    T = oracle.mlp_forward(teacher, X)
+    p0 = rand_params(13)
+    params, m, v = cuda32(p0), torch.zeros(NP, device="cuda"), torch.zeros(NP, device="cuda")
+    pk, grad = bdfb.mlp_packed(), torch.zeros(NP, device="cuda")
+    hist = torch.zeros(1500, device="cuda")
+    bdfb.mlp_train(cuda32(X), cuda32(T), params, m, v, pk, grad, hist, batch=1024, nsteps=1500, lr=2e-3)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    l0 = oracle.mlp_loss_grad(p0, X, T)[0]
+    p1 = params.cpu().numpy().astype(np.float64)
+    l1 = oracle.mlp_loss_grad(p1, X, T)[0]
+    assert np.all(np.isfinite(h))
+    assert l1 < 0.1 * l0, (l0, l1)
+    assert h[-50:].mean() < 0.15 * h[:10].mean()
+    assert abs(h[-50:].mean() - l1) <= 0.3 * l1 + 3e-4
+
+
+# ------------------------------------------------------- integrator hooks
+RTOL, ATOL, TEND = 1e-6, 1e-10, 1e-3
+
+
+def run(prob, mlp=None, predictor=0, mapping=32, record=None):
+    with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=mapping) as I:
+        if mlp is not None:
+            I.load_mlp(mlp)
+        if predictor:
+            I.set_option("predictor", 1)
+        if record is not None:
+            I.set_record(*record)
+        I.init(0.0, torch.from_numpy(prob.y0).cuda())
+        y = torch.empty(int(prob.y_off[-1]), dtype=torch.float64, device="cuda")
+        st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
+        ret = I.integrate(TEND, y, st)
+        torch.cuda.synchronize()
+        return ret, y.cpu().numpy(), st.cpu().numpy(), I.cell_stats(), I.stats()
+
+
+def test_zero_network_reproduces_plain_run():
+    p = gen.mass_action_shared(2000, seed=21)
+    r0, y0, s0, c0, _ = run(p)
+    r1, y1, s1, c1, st = run(p, mlp=packed_of(np.zeros(NP)), predictor=1)
+    assert r0 == r1 == 0 and np.all(s0 == 0) and np.all(s1 == 0)
+    assert np.array_equal(y0, y1)
+    assert np.array_equal(c0[:, 0], c1[:, 0])
+    assert st["nguess"] > 0
+
+
+def test_garbage_network_still_accurate():
+    from test_gpu_cells import check_against_oracle
+    p = gen.mass_action_shared(512, seed=22)
+    ret, y, st, cs, stats = run(p, mlp=packed_of(rand_params(1, scale=30.0)), predictor=1)
+    assert ret == 0 and np.all(st == 0)
+    assert stats["nguess"] > 0 and stats["nguess_fallback"] > 0
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
+    eg, eo = check_against_oracle(p, TEND, RTOL, ATOL, y, cs)
+
+
+def test_predictor_argument_checks():
+    big = gen.mass_action(100000).subset(np.arange(64))            # cells with n > 10
+    with bdfb.Integrator(big, rtol=RTOL, atol=ATOL) as I:
+        with pytest.raises(bdfb.BdfbError):
+            I.set_option("predictor", 1)
+        x = torch.zeros((4, NI), device="cuda")
+        with pytest.raises(bdfb.BdfbError):
+            I.set_record(x, torch.zeros((4, NO), device="cuda"), torch.zeros(1, dtype=torch.int64, device="cuda"))
+    small = gen.mass_action_shared(8)
+    with bdfb.Integrator(small, rtol=RTOL, atol=ATOL) as I:
+        I.set_option("predictor", 1)
+        I.init(0.0, small.y0.copy())
+        with pytest.raises(bdfb.BdfbError):                       # no network loaded
+            I.integrate(TEND, np.empty(small.y0.size))
+        with pytest.raises(bdfb.BdfbError):
+            I.load_mlp(torch.zeros(17, dtype=torch.uint8, device="cuda"))
+
+
+def record(prob, cap):
+    x = torch.zeros((cap, NI), device="cuda")
+    t = torch.zeros((cap, NO), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ret, y, st, cs, stats = run(prob, record=(x, t, cnt))
+    n = int(cnt.item())
+    return ret, cs, n, x[:min(n, cap)].cpu().numpy(), t[:min(n, cap)].cpu().numpy()
+
+
+def test_recording_one_row_per_accepted_step():
+    p = gen.mass_action_shared(300, seed=23)
+    ret, cs, n, X, T = record(p, 10 ** 6)
+    assert ret == 0 and n == cs[:, 0].sum()
+    assert np.all(np.isfinite(X)) and np.all(np.isfinite(T))
+    assert np.all(X[:, :10] >= -1e-3) and np.all(X[:, :10] <= 1 + 1e-3)
+    inv_l1 = {1.0, 2 / 3, 6 / 11, 12 / 25, 60 / 137}
+    assert all(min(abs(v - w) for w in inv_l1) < 1e-6 for v in np.unique(X[:, 11]))
+    # the capped recording keeps the first cap rows and still counts them all
+    ret2, cs2, n2, X2, _ = record(p, 1000)
+    assert n2 == n and X2.shape[0] == 1000
+
+
+def test_trained_network_guess():
+    """Record the plain run's pairs, train, integrate other cells of the
+    same network with the guess: accuracy bar met; Newton iterations per
+    step reported next to the plain run's."""
+    from test_gpu_cells import check_against_oracle
+    train = gen.mass_action_shared(4000, seed=24)
+    _, cs, n, X, T = record(train, 2 * 10 ** 6)
+    params = cuda32(rand_params(2))
+    m, v = torch.zeros(NP, device="cuda"), torch.zeros(NP, device="cuda")
+    pk, grad = bdfb.mlp_packed(), torch.zeros(NP, device="cuda")
+    hist = torch.zeros(3000, device="cuda")
+    perm = np.random.default_rng(0).permutation(X.shape[0])
+    bdfb.mlp_train(cuda32(X[perm]), cuda32(T[perm]), params, m, v, pk, grad, hist,
+                   batch=4096, nsteps=3000, lr=1e-3)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    assert h[-100:].mean() < h[:20].mean()
+    test = gen.mass_action_shared(4000 + 512, seed=24).subset(np.arange(4000, 4512))
+    r0, y0, s0, c0, st0 = run(test)
+    r1, y1, s1, c1, st1 = run(test, mlp=pk, predictor=1)
+    assert r0 == r1 == 0 and np.all(s1 == 0)
+    check_against_oracle(test, TEND, RTOL, ATOL, y1, c1)
+    it0 = st0["nniters"] / st0["nsteps"]
+    it1 = st1["nniters"] / st1["nsteps"]
+    print(f"Newton iterations per step: plain {it0:.3f}, learned {it1:.3f}; "
+          f"guesses {st1['nguess']}, redone from zero {st1['nguess_fallback']}; "
+          f"train loss {h[:20].mean():.3g} -> {h[-100:].mean():.3g}")
