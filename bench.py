@@ -215,6 +215,107 @@ def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
             "jacobian_setups": int(gs[2])}
 
 
+def learned_workload(torch, bdfb, gen, ncell=1_000_000, ntrain_pairs=10_000_000, train_steps=6000,
+                     reps=1):
+    """The learned-guess workload: one 10-species network shared by ncell
+    cells (initial states differ), t in [0, 1e-3], rtol 1e-6.  Training pairs
+    come from recorded plain runs of other cells of the same network (seed + 1;
+    cells with index % 10 == 0 held out for validation); the network trains
+    on the GPU (Adam, batch 4096); then the ncell cells are integrated with
+    the plain zero start and with the guess, both one warp per cell."""
+    NI, NO, NP = bdfb.MLP_NI, bdfb.MLP_NO, bdfb.MLP_NPARAM
+    t_rec = time.perf_counter()
+    src_cells = max(1000, int(ntrain_pairs / 200))
+    src = gen.mass_action_shared(src_cells, seed=gen.DEFAULT_SEED + 1)
+    cap = int(ntrain_pairs * 1.3)
+    X = torch.zeros((cap, NI), device="cuda")
+    T = torch.zeros((cap, NO), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with bdfb.Integrator(src, rtol=RTOL, atol=ATOL, mapping=32) as ri:
+        ri.set_record(X, T, cnt)
+        ri.init(0.0, torch.from_numpy(src.y0).cuda())
+        ri.integrate(TOUT, torch.empty(src.y0.size, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    npairs = min(int(cnt.item()), cap)
+    t_rec = time.perf_counter() - t_rec
+    # shuffle; hold out 10% for validation
+    g = torch.Generator(device="cuda").manual_seed(5)
+    perm = torch.randperm(npairs, device="cuda", generator=g)
+    nval = npairs // 10
+    Xv, Tv = X[perm[:nval]].contiguous(), T[perm[:nval]].contiguous()
+    Xt, Tt = X[perm[nval:]].contiguous(), T[perm[nval:]].contiguous()
+    del X, T
+    rng = np.random.default_rng(7)
+    p0 = np.zeros(NP, np.float32)
+    sizes = [(64, 12), (64,), (64, 64), (64,), (10, 64), (10,)]
+    o = 0
+    for s in sizes:
+        k = int(np.prod(s))
+        fan_in = s[1] if len(s) == 2 else 1
+        p0[o:o + k] = rng.standard_normal(k) * (np.sqrt(2.0 / fan_in) if len(s) == 2 else 0.0)
+        o += k
+    params = torch.from_numpy(p0).cuda()
+    m, v = torch.zeros(NP, device="cuda"), torch.zeros(NP, device="cuda")
+    pk, grad = bdfb.mlp_packed(), torch.zeros(NP, device="cuda")
+    hist = torch.zeros(train_steps, device="cuda")
+
+    def val_loss():
+        vg = torch.zeros(NP, device="cuda")
+        vl = torch.zeros(1, device="cuda")
+        bdfb.mlp_loss_grad(Xv, Tv, pk, vg, vl)
+        return float(vl.item())
+
+    bdfb.mlp_pack(params, pk)
+    v0 = val_loss()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter()
+    bdfb.mlp_train(Xt, Tt, params, m, v, pk, grad, hist, batch=4096, nsteps=train_steps, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    v1 = val_loss()
+    var_t = float(Tv.var().item())
+    del Xt, Tt
+    prob = gen.mass_action_shared(ncell, seed=gen.DEFAULT_SEED)
+    y0 = torch.from_numpy(prob.y0).cuda()
+    y = torch.empty_like(y0)
+    out = {}
+    for name, opts in (("plain_auto_tiles", {}), ("plain_warp_per_cell", {"mapping": 32}),
+                       ("learned_warp_per_cell", {"mapping": 32, "predictor": 1})):
+        with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=opts.get("mapping", 0)) as li:
+            if opts.get("predictor"):
+                li.load_mlp(pk)
+                li.set_option("predictor", 1)
+            ts = []
+            for i in range(1 + reps):
+                li.init(0.0, y0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                r = li.integrate(TOUT, y)
+                e1.record()
+                e1.synchronize()
+                if r != 0:
+                    raise RuntimeError(f"{name}: integrate returned {r}")
+                if i >= 1:
+                    ts.append(e0.elapsed_time(e1) * 1e-3)
+            s = li.stats()
+            out[name] = {"cells_per_s": ncell / (sum(ts) / len(ts)),
+                         "newton_iters_per_step": s["nniters"] / max(1, s["nsteps"]),
+                         "rhs_per_step": s["nfevals"] / max(1, s["nsteps"]),
+                         "steps_per_cell": s["nsteps"] / ncell,
+                         "setups_per_cell": s["nlinsetups"] / ncell,
+                         "accuracy": accuracy(prob, y.cpu().numpy(), ncheck=512)}
+            if opts.get("predictor"):
+                out[name]["guesses"] = s["nguess"]
+                out[name]["guesses_redone_from_zero"] = s["nguess_fallback"]
+    return {"workload": f"mass-action shared 10-species network, {ncell} cells, Dirichlet y0, t in [0,1e-3], "
+                        "rtol 1e-6, atol 1e-10; MLP 12-64-64-10 BF16 MMA, FP32 accumulate",
+            "training": {"pairs": npairs, "pairs_offered": int(cnt.item()), "source_cells": src_cells,
+                         "record_s": t_rec, "train_s": t_train, "adam_steps": train_steps, "batch": 4096,
+                         "val_loss_init": v0, "val_loss_final": v1, "target_variance": var_t},
+            **out}
+
+
 def run_reference(args):
     """reference arm: the CPU oracle as it stands, on the host cores"""
     ws, rank, _ = dist_env()

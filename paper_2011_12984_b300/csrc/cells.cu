@@ -266,10 +266,11 @@ __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem
 }
 
 // Input feature of the learned guess held by this lane (one warp per cell,
-// species i on lane i): lanes 0..9 the predicted state y_pred (zero past n),
-// lane 10 (log10 |h| + 8) / 4, lane 11 gamma / h = 1 / l_1.
+// species i on lane i): lanes 0..9 the predicted state on a log scale,
+// (log10 max(y_pred, 1e-20) + 10) / 10 (zero past n), lane 10
+// (log10 |h| + 8) / 4, lane 11 gamma / h = 1 / l_1.
 __device__ __forceinline__ float mlp_feature(int lane, int n, double ypred, double h, double rl1) {
-  if (lane < MLP_NO) return lane < n ? (float)ypred : 0.f;
+  if (lane < MLP_NO) return lane < n ? (log10f(fmaxf((float)ypred, 1e-20f)) + 10.f) * 0.1f : 0.f;
   if (lane == MLP_NO) return (log10f(fabsf((float)h)) + 8.f) * 0.25f;
   if (lane == MLP_NO + 1) return (float)rl1;
   return 0.f;
@@ -393,83 +394,102 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     if constexpr (LEARN) guess = P.mlp != nullptr;
     const double crate0 = C.crate;
     for (int pass = 0; pass < 2 && !conv; ++pass) {
-    if (pass == 1) {
-      if (!guess) break;
-      guess = false;
-      C.nguess_fb++;
-      C.crate = crate0;
-    }
-    if constexpr (LEARN) {
-      if (guess) {
-        C.nguess++;
-        C.acor[0] = mlp_guess(P.mlp, feat, n, C.ewt[0]);
+      bool nzguess = false;     // this pass starts from a nonzero guess
+      if (pass == 1) {
+        if (!guess) break;
+        guess = false;
+        C.nguess_fb++;
+        C.crate = crate0;
       }
-    }
-    if (!guess) {
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
-    }
-    double delp2 = 0.0;
-    const double eq2 = Eq * Eq * 100.0;   // (E_q / 0.1)^2
-    for (int it = 1; it <= 3; ++it) {
-      double y[NPL];
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p] + C.acor[p];
-      rhs<G, NPL, NMAX>(g, cd, S, y, C.f);
-      C.nfe++;
-      if (!all_finite(g, n, C.f)) break;
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) C.b[p] = C.gamma * C.f[p] - C.z[1][p] * rl1 - C.acor[p];
-      if constexpr (PREC == 1) {
-        bool solved = false;
-        if (!C.fp64mode) {
-          double bs[NPL];
-#pragma unroll
-          for (int p = 0; p < NPL; ++p) bs[p] = C.b[p];
-          const int sw = refined_solve<G, NPL, NMAX>(g, cd, S, C.gammap, C.mnorm, C.b);
-          C.nref += sw > 0 ? sw : MAXREF;
-          if (sw > 0) {
-            solved = true;
-          } else {
-            // refinement stalled: factor this setup's M in FP64 instead (in
-            // the cell's global workspace) until the next setup
-            C.nref_fb++;
-            form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
-            if (lu_factor<G, NMAX, double>(g, Mg, S.dinv, S.perm, n)) {
-              C.setup_done = 0;
-              break;                      // singular: counts as a Newton failure
-            }
-            C.fp64mode = 1;
-#pragma unroll
-            for (int p = 0; p < NPL; ++p) C.b[p] = bs[p];
+      if constexpr (LEARN) {
+        if (guess) {
+          C.nguess++;
+          C.acor[0] = mlp_guess(P.mlp, feat, n, C.ewt[0]);
+          // trust region: a correction that would fail the local error test
+          // (E_q |Delta| > 1) cannot be the accepted one; such a guess is dropped
+          if (!(wrms2(g, n, C.rn, C.acor, C.ewt) * Eq * Eq <= 1.0)) {
+            C.acor[0] = 0.0;
+            guess = false;
+            C.nguess_fb++;
           }
+          nzguess = __any_sync(FULL_MASK, C.acor[0] != 0.0);
         }
-        if (!solved) lu_solve<G, NPL, NMAX, double>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
-      } else {
-        lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
       }
-      if (C.gamma != C.gammap) {
-        const double sc = 2.0 / (1.0 + C.gamma / C.gammap);
+      if (!guess) {
 #pragma unroll
-        for (int p = 0; p < NPL; ++p) C.b[p] *= sc;
+        for (int p = 0; p < NPL; ++p) C.acor[p] = 0.0;
       }
-      const double del2 = wrms2(g, n, C.rn, C.b, C.ewt);
+      double delp2 = 0.0;
+      const double eq2 = Eq * Eq * 100.0;   // (E_q / 0.1)^2
+      for (int it = 1; it <= 3; ++it) {
+        double y[NPL];
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) C.acor[p] += C.b[p];
-      C.nni++;
-      if (it > 1) C.crate = fmax(0.3 * C.crate, (double)sqrtf((float)(del2 / delp2)));
-      const double cr = fmin(1.0, C.crate);
-      if (del2 * cr * cr * eq2 <= 1.0) {       // |del| min(1, rate) E_q / 0.1 <= 1
-        acnrm2 = (it == 1 && !guess) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
-        conv = true;
-        break;
+        for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p] + C.acor[p];
+        rhs<G, NPL, NMAX>(g, cd, S, y, C.f);
+        C.nfe++;
+        if (!all_finite(g, n, C.f)) break;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.b[p] = C.gamma * C.f[p] - C.z[1][p] * rl1 - C.acor[p];
+        if constexpr (PREC == 1) {
+          bool solved = false;
+          if (!C.fp64mode) {
+            double bs[NPL];
+#pragma unroll
+            for (int p = 0; p < NPL; ++p) bs[p] = C.b[p];
+            const int sw = refined_solve<G, NPL, NMAX>(g, cd, S, C.gammap, C.mnorm, C.b);
+            C.nref += sw > 0 ? sw : MAXREF;
+            if (sw > 0) {
+              solved = true;
+            } else {
+              // refinement stalled: factor this setup's M in FP64 instead (in
+              // the cell's global workspace) until the next setup
+              C.nref_fb++;
+              form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
+              if (lu_factor<G, NMAX, double>(g, Mg, S.dinv, S.perm, n)) {
+                C.setup_done = 0;
+                break;                      // singular: counts as a Newton failure
+              }
+              C.fp64mode = 1;
+#pragma unroll
+              for (int p = 0; p < NPL; ++p) C.b[p] = bs[p];
+            }
+          }
+          if (!solved) lu_solve<G, NPL, NMAX, double>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
+        } else {
+          lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+        }
+        // a stale M's step scaling, except on the first step from a nonzero
+        // guess: unscaled, that step gives w.Delta = -w.z1 / l1 for every w
+        // with w^T J = 0 (w^T M = w^T), so the linear invariants of the ODE
+        // come out as from a zero start; a scaled one would keep a share of
+        // the guess's error in them
+        if (C.gamma != C.gammap && !(nzguess && it == 1)) {
+          const double sc = 2.0 / (1.0 + C.gamma / C.gammap);
+#pragma unroll
+          for (int p = 0; p < NPL; ++p) C.b[p] *= sc;
+        }
+        const double del2 = wrms2(g, n, C.rn, C.b, C.ewt);
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) C.acor[p] += C.b[p];
+        C.nni++;
+        if (it > 1) C.crate = fmax(0.3 * C.crate, (double)sqrtf((float)(del2 / delp2)));
+        // the rate carried over from earlier solves holds between the zero
+        // start and the solution; a guessed start is tested with it only when
+        // the guess lies closer to the new iterate than zero does
+        // (|del| <= |Delta|), else with rate 1
+        double cr = fmin(1.0, C.crate);
+        if (nzguess && it == 1 && !(del2 <= wrms2(g, n, C.rn, C.acor, C.ewt))) cr = 1.0;
+        if (del2 * cr * cr * eq2 <= 1.0) {       // |del| min(1, rate) E_q / 0.1 <= 1
+          acnrm2 = (it == 1 && !guess) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
+          conv = true;
+          break;
+        }
+        if (it >= 2 && del2 > 4.0 * delp2) break;  // |del| > 2 |del_prev|: diverging
+        delp2 = del2;
       }
-      if (it >= 2 && del2 > 4.0 * delp2) break;  // |del| > 2 |del_prev|: diverging
-      delp2 = del2;
-    }
-    // a guessed start whose converged correction fails the local error
-    // test is redone from zero too: the test then judges the plain solve
-    if (conv && guess && !(acnrm2 * Eq * Eq <= 1.0)) conv = false;
+      // a guessed start whose converged correction fails the local error
+      // test is redone from zero too: the test then judges the plain solve
+      if (conv && guess && !(acnrm2 * Eq * Eq <= 1.0)) conv = false;
     }
     if (!conv) fail = true;
   }
