@@ -215,6 +215,71 @@ def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
             "jacobian_setups": int(gs[2])}
 
 
+def timed_integrations(torch, integ, y0, y, tout, reps, flush=None):
+    """event-timed seconds of `reps` integrations from t = 0 (one untimed first)"""
+    ts = []
+    for i in range(reps + 1):
+        if flush is not None:
+            flush.fill_(float(i))
+        integ.init(0.0, y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = integ.integrate(tout, y)
+        e1.record()
+        e1.synchronize()
+        if r != 0:
+            raise RuntimeError(f"integrate returned {r}")
+        if i >= 1:
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+    return sum(ts) / len(ts)
+
+
+def robertson_workload(torch, bdfb, gen, reps=3):
+    """1000 Robertson cells (per-cell log-uniform rate factors in [0.5, 2]),
+    t in [0, 40], rtol 1e-4, atol 1e-8; every cell checked against the oracle
+    at rtol 1e-10, atol 1e-14; the oracle timed at the run's tolerances."""
+    import oracle
+    p = gen.robertson(1000)
+    y0 = torch.from_numpy(p.y0).cuda()
+    y = torch.empty_like(y0)
+    with bdfb.Integrator(p, rtol=1e-4, atol=1e-8, autotune=1) as I:
+        t = timed_integrations(torch, I, y0, y, 40.0, reps)
+        st = I.stats()
+    yh = y.cpu().numpy()
+    yt, _, _ = oracle.integrate_cells(p, 0.0, 40.0, 1e-10, 1e-14, threads=oracle.host_threads())
+    e = (np.abs(yh - yt) / (1e-4 * np.abs(yt) + 1e-8)).reshape(-1, 3).max(axis=1)
+    t0 = time.perf_counter()
+    oracle.integrate_cells(p, 0.0, 40.0, 1e-4, 1e-8, threads=oracle.host_threads())
+    tc = time.perf_counter() - t0
+    return {"workload": "Robertson 1000 cells, k scaled by log-U[0.5,2] per cell, t in [0,40], rtol 1e-4, atol 1e-8",
+            "cells_per_s": 1000 / t, "ms": t * 1e3, "steps_per_cell": st["nsteps"] / 1000,
+            "sum_y_max_dev": float(np.abs(yh.reshape(-1, 3).sum(axis=1) - 1.0).max()),
+            "accuracy": {"cells_checked": 1000, "err_median": float(np.median(e)),
+                         "err_p99": float(np.percentile(e, 99)), "err_max": float(e.max()),
+                         "frac_within_10": float((e <= 10).mean())},
+            "oracle_cells_per_s": 1000 / tc, "oracle_cores": oracle.host_threads()}
+
+
+def mixed54_workload(torch, bdfb, gen, ncell=262_144, reps=1, flush=None):
+    """262 144 mass-action cells of 54 species: FP64 factorisation against
+    FP32 factorisation with FP64 refinement, same GPU, same inputs."""
+    p = gen.mass_action(ncell, sizes=(54,), seed=gen.DEFAULT_SEED + 7)
+    y0 = torch.from_numpy(p.y0).cuda()
+    y = torch.empty_like(y0)
+    out = {"workload": f"mass-action {ncell} cells, n = 54, 108 reactions, t in [0,1e-3], rtol 1e-6, atol 1e-10"}
+    for name, prec in (("fp64_lu", 0), ("fp32_lu_fp64_refinement", 1)):
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, precision=prec) as I:
+            t = timed_integrations(torch, I, y0, y, TOUT, reps, flush)
+            st = I.stats()
+        out[name] = {"cells_per_s": ncell / t, "s": t, "steps_per_cell": st["nsteps"] / ncell,
+                     "accuracy": accuracy(p, y.cpu().numpy(), ncheck=256)}
+        if prec:
+            out[name]["refinement_sweeps_per_solve"] = st["nrefine"] / max(1, st["nniters"])
+            out[name]["fp64_fallbacks"] = st["nrefine_fallback"]
+    out["speedup_mixed_over_fp64"] = out["fp32_lu_fp64_refinement"]["cells_per_s"] / out["fp64_lu"]["cells_per_s"]
+    return out
+
+
 def learned_workload(torch, bdfb, gen, ncell=1_000_000, ntrain_pairs=10_000_000, train_steps=6000,
                      reps=1):
     """The learned-guess workload: one 10-species network shared by ncell
@@ -360,10 +425,8 @@ def run_ours(args):
     y = torch.empty_like(y0)
     st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping, precision=args.precision)
-    # one persistent launch per non-empty size class (bounds 4, 8, 16, 32, 56)
-    need = np.maximum(prob.n, (np.diff(prob.rxn_off) + 1) // 2)
-    launches_per_step = len(set(np.searchsorted([4, 8, 16, 32, 56], need).tolist())) if args.mapping == 0 else 1
+    integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping, precision=args.precision,
+                            autotune=0 if args.no_autotune or args.mapping else 1)
 
     def step():
         integ.init(0.0, y0)
@@ -375,6 +438,10 @@ def run_ours(args):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
+    # one persistent launch per kernel variant in use (the autotuner may put
+    # two size classes on one variant)
+    mp, trial_ms = integ.mapping()
+    launches_per_step = len({(int(g), int(nm)) for g, nm, c in mp if c})
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -408,6 +475,7 @@ def run_ours(args):
                               "kernel_ms": 1e3 * sum(kern_s) / len(kern_s), "ncell": NCELL,
                               "mapping": args.mapping, "sizes": list(SIZES), "quick": True,
                               "precision": args.precision, "stats": integ.stats(),
+                              "mapping_by_class": mp.tolist(), "autotune_trial_ms": trial_ms.tolist(),
                               "steps_per_cell": float(cs[:, 0].mean()),
                               "fp64_tflops_algorithmic": algorithmic_flops(prob, cs) / (sum(kern_s) / len(kern_s)) / 1e12}))
         integ.close()
@@ -442,6 +510,11 @@ def run_ours(args):
     achieved = flops / t_kern / 1e12
     nv = nvector_bandwidth(torch, bdfb)
     grid = grid_workload(torch, bdfb, gen)
+    learned = learned_workload(torch, bdfb, gen, train_steps=20000) if not args.no_learned else None
+    configs = None
+    if not args.no_configs:
+        configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
+                   "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush)}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}), ("batched_mixed_fp32_lu", {"precision": 1})):
         with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, **opts) as vi:
@@ -472,7 +545,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": WORKLOAD, "ncell": NCELL, "mapping": "size-class tiles (auto)" if args.mapping == 0 else "one warp per cell",
+        "config": {"workload": WORKLOAD, "ncell": NCELL,
+                   "mapping": ("one warp per cell" if args.mapping else
+                               "size-class tiles" + ("" if args.no_autotune else ", autotuned")),
+                   "lanes_per_cell_and_nmax_by_class": [[int(g), int(nm)] if c else None for g, nm, c in mp],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "accuracy": acc,
         "integrator_stats": {"steps_per_cell": st_sum["nsteps"] / NCELL,
@@ -485,6 +561,8 @@ def run_ours(args):
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)"},
         "variants_cells_per_s": variants,
         "coupled_grid": grid,
+        "learned_guess": learned,
+        "other_workloads": configs,
         "nvector_gbs": nv,
         "nvector_roofline": {"bound": "hbm", "achieved": nv["linear_sum"], "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": nv["linear_sum"] / pk["hbm_gbs"],
@@ -515,6 +593,12 @@ def main():
                     help="time the device path only (no e2e, accuracy, CPU or vector legs)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP64 factorisation; 1: FP32 factorisation + FP64 refinement")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run each size class on its own tiling instead of the autotuned one")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the Robertson and 262144 x 54 mixed-precision legs")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-guess leg (1M-cell shared network, training on the GPU)")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     args = ap.parse_args()

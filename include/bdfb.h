@@ -166,6 +166,7 @@ typedef struct {
   int64_t nrefine, nrefine_fallback;  /* mixed precision: refinement sweeps, FP64 refactorisations */
   double last_kernel_ms;              /* device time of the last integrate's kernels */
   int64_t nguess, nguess_fallback;    /* learned guesses taken; of those, Newton solves redone from 0 */
+  int64_t graph_captures, graph_launches;  /* option "graph": captures made, replays launched */
 } bdfb_stats;
 
 typedef struct bdfb_ctx bdfb_ctx;
@@ -182,7 +183,19 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              cell for every cell in input order (the plain form)
  *  "precision" 0 = FP64 factorisation (default), 1 = FP32 factorisation with
  *              FP64 iterative refinement to 1e-12 backward error
- *  "graph"     1 = replay integrate's launches from a captured CUDA graph
+ *  "graph"     1 = capture integrate's launch sequence (counter reset, one
+ *              persistent launch per kernel variant on forked streams, join)
+ *              into a CUDA graph once and replay it; a call that differs only
+ *              in tout patches tout into the graph, any other change
+ *              (tolerances, options, schedule) recaptures
+ *  "autotune"  1 = on the next integrate, and again after a precision change,
+ *              time every kernel variant that can run a size class on a
+ *              sample of that class (first 16384 cells, current state to
+ *              tout, on scratch copies: the context's state is untouched)
+ *              and run each class on the fastest (another variant must beat
+ *              the class's own by 3%); mapping 0 only.  Variants differ in
+ *              rounding order, so tuned runs agree with untuned ones to
+ *              rounding, not bitwise.
  *  "qmax"      maximum BDF order, 1..5 (default 5)
  *  "predictor" 0 = Newton starts from a zero correction (default), 1 = from
  *              the learned guess of bdfb_load_mlp (every cell n <= 10, FP64
@@ -213,6 +226,16 @@ int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
  * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
  * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl. */
 int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
+/* Cell-to-lane mapping in use.  Size classes c = 0..4 hold cells with
+ * max(n, ceil(reactions / 2)) <= 4, 8, 16, 32, 56.  Kernel variants v =
+ * 0..5 are (lanes per cell G, largest cell NMAX) = (1, 4), (4, 8), (8, 16),
+ * (16, 32), (32, 56) and the one-warp (32, 16).  out (host, 15 int32):
+ * out[3c] = G, out[3c + 1] = NMAX of the variant class c runs on (under the
+ * current options; the tuned one after autotuning), out[3c + 2] = cells in
+ * class c (0: class empty, G = NMAX = 0).  trial_ms (host, 5 x 6 floats, or
+ * NULL): the autotuner's trial time of variant v on class c at [6c + v]
+ * (0: not tried). */
+int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms);
 
 /* ------------------------------------- learned Newton initial guess (MLP)
  * Not part of the paper: a 12 -> 64 -> 64 -> 10 ReLU network predicts the

@@ -54,7 +54,7 @@ class Stats(C.Structure):
                 ("nniters", _i64), ("nncfails", _i64), ("netfails", _i64), ("max_steps", _i64),
                 ("min_steps", _i64), ("ncells_failed", _i64), ("nrefine", _i64),
                 ("nrefine_fallback", _i64), ("last_kernel_ms", _d), ("nguess", _i64),
-                ("nguess_fallback", _i64)]
+                ("nguess_fallback", _i64), ("graph_captures", _i64), ("graph_launches", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +87,7 @@ _sig("bdfb_init", C.c_int, [_vp, _d, _vp, _i32])
 _sig("bdfb_integrate", C.c_int, [_vp, _d, _vp, _vp, _i32])
 _sig("bdfb_get_stats", C.c_int, [_vp, C.POINTER(Stats)])
 _sig("bdfb_get_cell_stats", C.c_int, [_vp, _vp, _i32])
+_sig("bdfb_get_mapping", C.c_int, [_vp, _vp, _vp])
 _sig("bdfb_mlp_nparam", _i64, [])
 _sig("bdfb_mlp_packed_bytes", _i64, [])
 _sig("bdfb_mlp_pack", C.c_int, [_vp, _vp, _vp])
@@ -317,6 +318,13 @@ class Integrator:
         s = Stats()
         check(lib.bdfb_get_stats(self.h, C.byref(s)), "bdfb_get_stats")
         return s.as_dict()
+
+    def mapping(self):
+        """(per size class (G, NMAX, cells) int32 [5, 3], autotune trial ms [5, 6])"""
+        out = np.zeros((5, 3), np.int32)
+        ms = np.zeros((5, 6), np.float32)
+        check(lib.bdfb_get_mapping(self.h, out.ctypes.data, ms.ctypes.data), "bdfb_get_mapping")
+        return out, ms
 
     def load_mlp(self, packed):
         """use a packed network (CUDA uint8 tensor; None detaches) for option predictor=1"""

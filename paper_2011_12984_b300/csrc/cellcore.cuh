@@ -297,9 +297,13 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
       constexpr int R = LaneGrid<G>::R, C = LaneGrid<G>::C;
       constexpr int NJ = (NMAX + C - 1) / C;
       const int li = g.rank / C, lj = g.rank % C;
+      // column slots that still hold trailing columns (the same for the
+      // whole group): slots past it would issue predicated-off FP64 work
+      const int nbu = (n - k - 1 + C - 1) / C;
       T u[NJ];
 #pragma unroll
       for (int b = 0; b < NJ; ++b) {
+        if (b >= nbu) break;
         const int j = k + 1 + lj + C * b;
         u[b] = j < n ? M[k][j] : (T)0;
       }
@@ -307,6 +311,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
         const T lik = M[i][k];
 #pragma unroll
         for (int b = 0; b < NJ; ++b) {
+          if (b >= nbu) break;
           const int j = k + 1 + lj + C * b;
           if (j < n) M[i][j] = fma(-lik, u[b], M[i][j]);
         }
@@ -337,6 +342,7 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
     const double xj = g.bcast(pick(x, j / G), j % G);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
+      if (G * (p + 1) - 1 <= j) continue;      // no row of this slot is below j
       const int i = g.rank + G * p;
       if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
     }
@@ -347,6 +353,7 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
     if (g.rank == owner) place(x, slot, xj);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
+      if (G * p >= j) continue;                 // no row of this slot is above j
       const int i = g.rank + G * p;
       if (i < j) x[p] = fma(-(double)M[i][j], xj, x[p]);
     }

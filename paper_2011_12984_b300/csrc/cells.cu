@@ -669,9 +669,12 @@ struct ClassSmem {
 // Persistent kernel of one size class: each warp takes the next tile of the
 // class range [t0, t1) from `counter` until none is left.  PREC 0: FP64
 // factorisation; PREC 1: FP32 factorisation with FP64 refinement.
+// warps per SM each class kernel should keep resident (its shared-memory
+// limit for the two largest classes): bounds the registers ptxas may use
+constexpr int CLS_MINB[NCLASS] = {12, 12, 12, 8, 7};
 template <int CLS, int PREC>
-__global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, int t0, int t1,
-                                              unsigned* counter, double* fbws) {
+__global__ void __launch_bounds__(32, CLS_MINB[CLS]) k_cells(const __grid_constant__ Params P, int t0, int t1,
+                                                             unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
   constexpr int64_t FB = (int64_t)(32 / CLS_G[CLS]) * CLS_NMAX[CLS] * (CLS_NMAX[CLS] + 1);
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(32) k_cells(const __grid_constant__ Params P, 
 constexpr int W16_NMAX = 16;
 static_assert(CLS_NMAX[2] == W16_NMAX, "cells of classes 0..2 fit the one-warp NMAX 16 layout");
 __global__ void __launch_bounds__(32) k_cells_w16(const __grid_constant__ Params P, int t0, int t1,
-                                                  unsigned* counter) {
+                                                  unsigned* counter, double*) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -719,6 +722,20 @@ static const int CELLS_SMEM[2][NCLASS] = {
      ClassSmem<4, 0>::bytes},
     {ClassSmem<0, 1>::bytes, ClassSmem<1, 1>::bytes, ClassSmem<2, 1>::bytes, ClassSmem<3, 1>::bytes,
      ClassSmem<4, 1>::bytes}};
+
+// Kernel variants (cell-to-lane mappings): the five size-class tilings and
+// the one-warp-per-cell NMAX 16 kernel.  A cell can run on any variant whose
+// NMAX covers it; launches go largest NMAX first.
+constexpr int NVAR = NCLASS + 1;
+constexpr int VAR_W16 = NCLASS;
+constexpr int VAR_G[NVAR] = {1, 4, 8, 16, 32, 32};
+constexpr int VAR_NMAX[NVAR] = {4, 8, 16, 32, 56, 16};
+constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W16, 2, 1, 0};
+static cells_kernel_t var_kernel(int pr, int v) {
+  if (v < NCLASS) return CELLS_KERNELS[pr][v];
+  return pr == 0 ? k_cells_w16 : nullptr;
+}
+static int var_smem(int pr, int v) { return v < NCLASS ? CELLS_SMEM[pr][v] : W16_SMEM; }
 
 // ------------------------------------------------- standalone batched LU
 constexpr int LU_NMAX = 64;
@@ -894,6 +911,13 @@ static Consts make_consts() {
 using namespace bdfb;
 
 // ---------------------------------------------------------------- context
+struct Sched {
+  TileDesc* d_tiles = nullptr;
+  int32_t* d_tcells = nullptr;
+  int ntiles = 0;
+  int vbeg[NVAR] = {}, vend[NVAR] = {};   // tile range of each variant
+};
+
 struct bdfb_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -911,11 +935,23 @@ struct bdfb_ctx {
   CellState* d_state = nullptr;
   double* d_z = nullptr;
   double* d_acorp = nullptr;
-  TileDesc* d_tiles[2] = {nullptr, nullptr};
-  int32_t* d_tcells[2] = {nullptr, nullptr};
-  int ntiles[2] = {0, 0};
-  int cls_begin[2][NCLASS] = {}, cls_end[2][NCLASS] = {};  // tile range of each class
-  unsigned* d_counter = nullptr;   // [c] tile counter of class c, [NCLASS] worst status (int)
+  // schedules: [0] size-class tiles, [1] one cell per warp in input order,
+  // [2] size classes on the variants the autotuner picked
+  Sched sched[3];
+  int sched_gen = 0;               // bumped whenever a schedule is rebuilt
+  std::vector<int8_t> h_cls;       // size class of every cell
+  unsigned* d_counter = nullptr;   // [v] tile counter of variant v, [NVAR] worst status (int)
+  int autotune = 0;                // option "autotune"
+  int tuned_prec = -1;             // precision the tuned schedule was made for (-1: none)
+  int tuned_var[NCLASS] = {};      // variant picked for each size class
+  float tune_ms[NCLASS][NVAR] = {};  // trial times, 0 = not tried
+  // CUDA graph of the launch sequence (option "graph")
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cgraph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  Params gkey;                     // Params of the capture with tout = 0
+  int gkey_gen = -1, gkey_m = -1, gkey_w16 = -1;
+  int64_t graph_launches = 0, graph_captures = 0;
   int32_t* d_status = nullptr;
   double rtol = 1e-6, atol = 1e-10;
   int64_t mxstep = 100000;
@@ -923,15 +959,14 @@ struct bdfb_ctx {
   double t0 = 0.0;
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
-  cudaEvent_t evjoin[NCLASS] = {};
+  cudaEvent_t evjoin[NVAR] = {};
   double* d_fbws[NCLASS] = {};      // FP64 fallback workspace per class (mixed precision, lazy)
-  cudaStream_t cstream[NCLASS] = {};  // one per size class, forked from `stream`
+  cudaStream_t cstream[NVAR] = {};  // one per variant, forked from `stream`
   float last_ms = 0.f;
-  int pgrid[2][NCLASS] = {};  // persistent grid size [precision][class]
+  int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
   int maxn = 0;               // largest cell
   bool fits_w16 = false;      // every cell fits the NMAX 16 shared-memory layout
-  int pgrid_w16 = 0;          // persistent grid of the one-warp-per-cell small-cell kernel
   int predictor = 0;          // 1: Newton starts from the learned guess
   const void* mlp = nullptr;  // packed network (caller-owned device memory)
   float* rec_x = nullptr;     // recording buffers (caller-owned device memory)
@@ -950,11 +985,14 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
   for (int k = 0; k < NCLASS; ++k) cudaFree(c->d_fbws[k]);
-  for (int m = 0; m < 2; ++m) { cudaFree(c->d_tiles[m]); cudaFree(c->d_tcells[m]); }
+  for (int m = 0; m < 3; ++m) { cudaFree(c->sched[m].d_tiles); cudaFree(c->sched[m].d_tcells); }
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cgraph) cudaGraphDestroy(c->cgraph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evfork) cudaEventDestroy(c->evfork);
-  for (int k = 0; k < NCLASS; ++k) {
+  for (int k = 0; k < NVAR; ++k) {
     if (c->evjoin[k]) cudaEventDestroy(c->evjoin[k]);
     if (c->cstream[k]) cudaStreamDestroy(c->cstream[k]);
   }
@@ -990,23 +1028,79 @@ static int setup_launch(bdfb_ctx* c) {
   BDFB_CUDA(cudaEventCreate(&c->ev0));
   BDFB_CUDA(cudaEventCreate(&c->ev1));
   BDFB_CUDA(cudaEventCreateWithFlags(&c->evfork, cudaEventDisableTiming));
-  for (int k = 0; k < NCLASS; ++k) {
+  BDFB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < NVAR; ++k) {
     BDFB_CUDA(cudaEventCreateWithFlags(&c->evjoin[k], cudaEventDisableTiming));
     BDFB_CUDA(cudaStreamCreateWithFlags(&c->cstream[k], cudaStreamNonBlocking));
     for (int pr = 0; pr < 2; ++pr) {
-      BDFB_CUDA(cudaFuncSetAttribute(CELLS_KERNELS[pr][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     CELLS_SMEM[pr][k]));
+      const cells_kernel_t kf = var_kernel(pr, k);
+      if (!kf) continue;
+      BDFB_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, var_smem(pr, k)));
       int per_sm = 0;
-      BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, CELLS_KERNELS[pr][k], 32,
-                                                              CELLS_SMEM[pr][k]));
+      BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 32, var_smem(pr, k)));
       c->pgrid[pr][k] = std::max(1, per_sm) * sm_count();
     }
   }
-  BDFB_CUDA(cudaFuncSetAttribute(k_cells_w16, cudaFuncAttributeMaxDynamicSharedMemorySize, W16_SMEM));
-  int per_sm = 0;
-  BDFB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells_w16, 32, W16_SMEM));
-  c->pgrid_w16 = std::max(1, per_sm) * sm_count();
   return 0;
+}
+
+// Tiles of the cells in `order`, grouped by variant in launch order (the
+// caller sorts `order` so that each variant's cells are contiguous): 32 / G
+// cells of one variant per tile, or one cell per tile when `single`.
+static void make_tiles(const std::vector<int32_t>& order, const std::vector<int8_t>& var, bool single,
+                       std::vector<TileDesc>& tiles, std::vector<int32_t>& tcells, int* vbeg, int* vend) {
+  tiles.clear();
+  tcells.clear();
+  for (int v = 0; v < NVAR; ++v) { vbeg[v] = 0; vend[v] = 0; }
+  size_t i = 0;
+  while (i < order.size()) {
+    const int v = var[order[i]];
+    const int cpt = single ? 1 : 32 / VAR_G[v];
+    TileDesc td;
+    td.cls = v;
+    td.first = (int32_t)tcells.size();
+    td.count = 0;
+    td.pad = 0;
+    while (i < order.size() && var[order[i]] == v && td.count < cpt) {
+      tcells.push_back(order[i]);
+      ++td.count;
+      ++i;
+    }
+    const int t = (int)tiles.size();
+    if (vend[v] == 0) vbeg[v] = t;
+    vend[v] = t + 1;
+    tiles.push_back(td);
+  }
+}
+
+// cells grouped by variant in launch order, larger cells first within one
+static std::vector<int32_t> launch_order(const std::vector<int8_t>& var, const std::vector<int32_t>& n,
+                                         const std::vector<int32_t>& cells) {
+  int rank[NVAR];
+  for (int k = 0; k < NVAR; ++k) rank[VAR_ORDER[k]] = k;
+  std::vector<int32_t> order(cells);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    if (var[a] != var[b]) return rank[var[a]] < rank[var[b]];
+    return n[a] > n[b];
+  });
+  return order;
+}
+
+static int upload_sched(bdfb_ctx* c, int m, const std::vector<int32_t>& order, const std::vector<int8_t>& var,
+                        bool single) {
+  std::vector<TileDesc> tiles;
+  std::vector<int32_t> tcells;
+  Sched& S = c->sched[m];
+  make_tiles(order, var, single, tiles, tcells, S.vbeg, S.vend);
+  cudaFree(S.d_tiles);
+  cudaFree(S.d_tcells);
+  S.d_tiles = nullptr;
+  S.d_tcells = nullptr;
+  S.ntiles = (int)tiles.size();
+  c->sched_gen++;
+  int r = dev_alloc_copy(&S.d_tiles, tiles.data(), tiles.size());
+  if (r) return r;
+  return dev_alloc_copy(&S.d_tcells, tcells.data(), tcells.size());
 }
 
 static int class_of(int n, int nr) {
@@ -1134,54 +1228,22 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
     TRY(dev_alloc_copy(&c->d_inc, inc.data(), inc.size()));
   }
   TRY(dev_alloc_copy(&c->d_k, k.data(), k.size()));
-  // schedules: [0] tiles by size class, largest class first; [1] one cell per warp, input order
-  for (int m = 0; m < 2; ++m) {
-    std::vector<TileDesc> tiles;
-    std::vector<int32_t> tcells;
-    if (m == 0) {
-      std::vector<int32_t> order(C);
-      for (int64_t i = 0; i < C; ++i) order[i] = (int32_t)i;
-      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        if (cls[a] != cls[b]) return cls[a] > cls[b];
-        return n[a] > n[b];
-      });
-      int64_t i = 0;
-      while (i < C) {
-        const int cl = cls[order[i]];
-        const int cpt = 32 / CLS_G[cl];
-        TileDesc td;
-        td.cls = cl;
-        td.first = (int32_t)tcells.size();
-        td.count = 0;
-        td.pad = 0;
-        while (i < C && cls[order[i]] == cl && td.count < cpt) { tcells.push_back(order[i]); ++td.count; ++i; }
-        tiles.push_back(td);
-      }
-    } else {
-      for (int64_t i = 0; i < C; ++i) {
-        TileDesc td;
-        td.cls = 4;
-        td.first = (int32_t)i;
-        td.count = 1;
-        td.pad = 0;
-        tiles.push_back(td);
-        tcells.push_back((int32_t)i);
-      }
-    }
-    c->ntiles[m] = (int)tiles.size();
-    for (int k2 = 0; k2 < NCLASS; ++k2) { c->cls_begin[m][k2] = 0; c->cls_end[m][k2] = 0; }
-    for (int t = 0; t < (int)tiles.size(); ++t) {   // tiles of a class are contiguous
-      const int cl = tiles[t].cls;
-      if (c->cls_end[m][cl] == 0) c->cls_begin[m][cl] = t;
-      c->cls_end[m][cl] = t + 1;
-    }
-    TRY(dev_alloc_copy(&c->d_tiles[m], tiles.data(), tiles.size()));
-    TRY(dev_alloc_copy(&c->d_tcells[m], tcells.data(), tcells.size()));
+  // schedules: [0] tiles by size class, largest class first; [1] one cell
+  // per warp in input order (all on the NMAX 56 variant; launched on the
+  // NMAX 16 one-warp kernel when every cell fits it)
+  c->h_cls.assign(C, 0);
+  for (int64_t i = 0; i < C; ++i) c->h_cls[i] = (int8_t)cls[i];
+  {
+    std::vector<int32_t> all(C);
+    for (int64_t i = 0; i < C; ++i) all[i] = (int32_t)i;
+    TRY(upload_sched(c, 0, launch_order(c->h_cls, n, all), c->h_cls, false));
+    std::vector<int8_t> v4(C, 4);
+    TRY(upload_sched(c, 1, all, v4, true));
   }
   TRY(dev_alloc_copy<CellState>(&c->d_state, nullptr, C));
   TRY(dev_alloc_copy<double>(&c->d_z, nullptr, 6 * std::max<int64_t>(c->ny, 1)));
   TRY(dev_alloc_copy<double>(&c->d_acorp, nullptr, c->ny));
-  TRY(dev_alloc_copy<unsigned>(&c->d_counter, nullptr, NCLASS + 1));
+  TRY(dev_alloc_copy<unsigned>(&c->d_counter, nullptr, NVAR + 1));
   TRY(dev_alloc_copy<int32_t>(&c->d_status, nullptr, C));
   TRY(setup_launch(c));
   *out = c;
@@ -1223,6 +1285,10 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "graph")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     ctx->graph = (int)v;
+  } else if (!std::strcmp(key, "autotune")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    ctx->autotune = (int)v;
+    ctx->tuned_prec = -1;     // tune again on the next integrate
   } else if (!std::strcmp(key, "qmax")) {
     if (v < 1 || v > QMAX) return BDFB_ILL_INPUT;
     ctx->qmax = (int)v;
@@ -1262,27 +1328,10 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
   return BDFB_SUCCESS;
 }
 
-extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
-  if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
-  if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
-  if (ctx->grid) {
-    const int r = grid_integrate(ctx->grid, tout, y, mem);
-    if (status) {
-      const int32_t sv = r;
-      if (mem == BDFB_MEM_HOST) *status = sv;
-      else BDFB_CUDA(cudaMemcpy(status, &sv, sizeof sv, cudaMemcpyHostToDevice));
-    }
-    return r;
-  }
-  if (ctx->ncell == 0) return BDFB_SUCCESS;
-  if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
-  cudaStream_t s = ctx->stream;
-  const bool learn = ctx->predictor || ctx->rec_x;
-  // one warp per cell: the NMAX 16 kernel when every cell fits it
-  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && ctx->precision == 0);
-  const int m = (ctx->mapping == 32 || w16) ? 1 : 0;
+// Params of an integrate call (schedule fields filled by the caller)
+static Params base_params(bdfb_ctx* ctx, double tout) {
   Params P;
-  std::memset(&P, 0, sizeof P);
+  std::memset(&P, 0, sizeof P);   // padding too: Params are compared bytewise
   P.kind = ctx->kind;
   P.qmax = ctx->qmax;
   P.ny = ctx->ny;
@@ -1293,11 +1342,8 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.k = ctx->d_k;
   P.inc_off = ctx->d_incoff;
   P.inc = ctx->d_inc;
-  P.tiles = ctx->d_tiles[m];
-  P.tile_cells = ctx->d_tcells[m];
-  P.ntiles = ctx->ntiles[m];
   P.tile_counter = ctx->d_counter;
-  P.worst = reinterpret_cast<int*>(ctx->d_counter + NCLASS);
+  P.worst = reinterpret_cast<int*>(ctx->d_counter + NVAR);
   P.st = ctx->d_state;
   P.z = ctx->d_z;
   P.acorp = ctx->d_acorp;
@@ -1313,38 +1359,253 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.rec_t = ctx->rec_t;
   P.rec_cap = ctx->rec_cap;
   P.rec_count = ctx->rec_count;
-  if (ctx->precision == 1) {   // FP64 fallback workspace: one slice per resident warp
-    for (int cl = 0; cl < NCLASS; ++cl)
-      if (!ctx->d_fbws[cl] && ctx->cls_end[m][cl] > ctx->cls_begin[m][cl]) {
-        const size_t bytes = (size_t)ctx->pgrid[1][cl] * fallback_doubles_per_warp(cl) * sizeof(double);
-        if (cudaMalloc(&ctx->d_fbws[cl], bytes) != cudaSuccess) {
-          ctx->d_fbws[cl] = nullptr;
-          return BDFB_MEM_FAIL;
-        }
+  return P;
+}
+
+// FP64 fallback workspace of a size-class variant (mixed precision): one
+// slice per resident warp, allocated on first use
+static int ensure_fbws(bdfb_ctx* ctx, int v) {
+  if (ctx->d_fbws[v]) return 0;
+  const size_t bytes = (size_t)ctx->pgrid[1][v] * fallback_doubles_per_warp(v) * sizeof(double);
+  if (cudaMalloc(&ctx->d_fbws[v], bytes) != cudaSuccess) {
+    ctx->d_fbws[v] = nullptr;
+    return BDFB_MEM_FAIL;
+  }
+  return 0;
+}
+
+// The launch sequence of one integrate call on stream s: clear the tile
+// counters, then fork one persistent launch per variant of the schedule,
+// largest cells first, each on its own stream so that smaller cells fill
+// the SMs the larger ones release, and join.  `single_w16`: the one-cell
+// tiles of the NMAX 56 range run on the NMAX 16 one-warp kernel.
+static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, bool single_w16,
+                      cudaStream_t s) {
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NVAR + 1) * sizeof(unsigned), s));
+  BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
+  for (int k = 0; k < NVAR; ++k) {
+    const int v = VAR_ORDER[k];
+    const int t0 = S.vbeg[v], t1 = S.vend[v];
+    if (t1 <= t0) continue;
+    const int kv = (v == 4 && single_w16) ? VAR_W16 : v;
+    const cells_kernel_t kf = var_kernel(pr, kv);
+    if (!kf) return BDFB_ILL_INPUT;
+    cudaStream_t cs = ctx->cstream[v];
+    BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
+    const int grid = std::min(ctx->pgrid[pr][kv], t1 - t0);
+    kf<<<grid, 32, var_smem(pr, kv), cs>>>(P, t0, t1, ctx->d_counter + v,
+                                           (pr == 1 && kv < NCLASS) ? ctx->d_fbws[kv] : nullptr);
+    BDFB_CUDA(cudaGetLastError());
+    BDFB_CUDA(cudaEventRecord(ctx->evjoin[v], cs));
+    BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[v], 0));
+  }
+  return 0;
+}
+
+// Option "graph": the launch sequence is captured once into a CUDA graph
+// and replayed; a later call with the same parameters but another tout
+// patches tout into the kernel nodes; anything else recaptures.
+static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, bool single_w16, cudaStream_t s) {
+  Params key = P;
+  key.tout = 0.0;
+  const bool same = ctx->gexec && ctx->gkey_gen == ctx->sched_gen && ctx->gkey_m == m &&
+                    ctx->gkey_w16 == (int)single_w16 && !std::memcmp(&key, &ctx->gkey, sizeof key);
+  if (!same) {
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    if (ctx->cgraph) { cudaGraphDestroy(ctx->cgraph); ctx->cgraph = nullptr; }
+    // captured on a stream of the context (the legacy default stream cannot
+    // be captured); the graph is launched on s
+    BDFB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int r = launch_all(ctx, P, ctx->sched[m], pr, single_w16, ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (r || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return r ? r : BDFB_CUDA_FAIL;
+    }
+    ctx->cgraph = g;
+    BDFB_CUDA(cudaGraphInstantiate(&ctx->gexec, g, 0));
+    ctx->gkey = key;
+    ctx->gkey_gen = ctx->sched_gen;
+    ctx->gkey_m = m;
+    ctx->gkey_w16 = (int)single_w16;
+    ctx->graph_captures++;
+  } else {
+    size_t nn = 0;
+    BDFB_CUDA(cudaGraphGetNodes(ctx->cgraph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    BDFB_CUDA(cudaGraphGetNodes(ctx->cgraph, nodes.data(), &nn));
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType ty;
+      BDFB_CUDA(cudaGraphNodeGetType(nodes[i], &ty));
+      if (ty != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp;
+      BDFB_CUDA(cudaGraphKernelNodeGetParams(nodes[i], &kp));
+      Params pn = *static_cast<Params*>(kp.kernelParams[0]);
+      pn.tout = P.tout;
+      int t0 = *static_cast<int*>(kp.kernelParams[1]);
+      int t1 = *static_cast<int*>(kp.kernelParams[2]);
+      unsigned* cnt = *static_cast<unsigned**>(kp.kernelParams[3]);
+      double* fb = *static_cast<double**>(kp.kernelParams[4]);
+      void* args[5] = {&pn, &t0, &t1, &cnt, &fb};
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      BDFB_CUDA(cudaGraphExecKernelNodeSetParams(ctx->gexec, nodes[i], &kp));
+    }
+  }
+  BDFB_CUDA(cudaGraphLaunch(ctx->gexec, s));
+  ctx->graph_launches++;
+  return 0;
+}
+
+// Autotuner: for every size class with more than one variant that can run
+// its cells (its own tiling, the next larger one, and for cells of at most
+// 16 species the one-warp NMAX 16 kernel), integrate a sample of the class
+// (its first 16384 cells) from the current state to tout once per variant
+// on scratch copies of the state, time each launch with events, and keep
+// the fastest (another variant must beat the class's own by 3%).  The
+// context's state is not touched.  Builds schedule 2.
+static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s) {
+  const int64_t C = ctx->ncell;
+  constexpr int64_t SAMPLE = 16384;
+  std::vector<std::vector<int32_t>> members(NCLASS);
+  for (int64_t i = 0; i < C; ++i)
+    if ((int64_t)members[ctx->h_cls[i]].size() < SAMPLE) members[ctx->h_cls[i]].push_back((int32_t)i);
+  CellState* st2 = nullptr;
+  double *z2 = nullptr, *acorp2 = nullptr;
+  TileDesc* tiles2 = nullptr;
+  int32_t* tcells2 = nullptr;
+  unsigned* cnt2 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = 0;
+  auto fail = [&](int r) { if (!rc) rc = r; };
+  const size_t zbytes = 6 * (size_t)std::max<int64_t>(ctx->ny, 1) * sizeof(double);
+  if (cudaMalloc(&st2, C * sizeof(CellState)) != cudaSuccess || cudaMalloc(&z2, zbytes) != cudaSuccess ||
+      cudaMalloc(&acorp2, std::max<int64_t>(ctx->ny, 1) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&tiles2, SAMPLE * sizeof(TileDesc)) != cudaSuccess ||
+      cudaMalloc(&tcells2, SAMPLE * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cnt2, (NVAR + 1) * sizeof(unsigned)) != cudaSuccess)
+    fail(BDFB_MEM_FAIL);
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) fail(BDFB_CUDA_FAIL);
+  std::vector<int8_t> var(C, 0);
+  for (int cl = 0; cl < NCLASS && !rc; ++cl) {
+    ctx->tuned_var[cl] = cl;
+    for (int v = 0; v < NVAR; ++v) ctx->tune_ms[cl][v] = 0.f;
+    if (members[cl].empty()) continue;
+    std::vector<int> cand = {cl};
+    if (cl + 1 < NCLASS) cand.push_back(cl + 1);
+    if (cl <= 2 && pr == 0) cand.push_back(VAR_W16);
+    float best = 0.f;
+    for (int v : cand) {
+      if (v < NCLASS && pr == 1 && ensure_fbws(ctx, v)) { fail(BDFB_MEM_FAIL); break; }
+      for (int32_t c : members[cl]) var[c] = (int8_t)v;
+      std::vector<TileDesc> tiles;
+      std::vector<int32_t> tcells;
+      int vb[NVAR], ve[NVAR];
+      make_tiles(launch_order(var, ctx->h_n, members[cl]), var, v == VAR_W16, tiles, tcells, vb, ve);
+      const int nt = (int)tiles.size();
+      Params Pt = P0;
+      Pt.st = st2;
+      Pt.z = z2;
+      Pt.acorp = acorp2;
+      Pt.tiles = tiles2;
+      Pt.tile_cells = tcells2;
+      Pt.ntiles = nt;
+      Pt.tile_counter = cnt2;
+      Pt.worst = reinterpret_cast<int*>(cnt2 + NVAR);
+      Pt.status = nullptr;
+      Pt.rec_x = nullptr;
+      Pt.mlp = nullptr;
+      if (cudaMemcpyAsync(tiles2, tiles.data(), nt * sizeof(TileDesc), cudaMemcpyHostToDevice, s) ||
+          cudaMemcpyAsync(tcells2, tcells.data(), tcells.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s) ||
+          cudaMemcpyAsync(st2, ctx->d_state, C * sizeof(CellState), cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(z2, ctx->d_z, zbytes, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(acorp2, ctx->d_acorp, std::max<int64_t>(ctx->ny, 1) * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s) ||
+          cudaMemsetAsync(cnt2, 0, (NVAR + 1) * sizeof(unsigned), s)) {
+        fail(BDFB_CUDA_FAIL);
+        break;
+      }
+      const cells_kernel_t kf = var_kernel(pr, v);
+      cudaEventRecord(e0, s);
+      kf<<<std::min(ctx->pgrid[pr][v], nt), 32, var_smem(pr, v), s>>>(
+          Pt, 0, nt, cnt2, (pr == 1 && v < NCLASS) ? ctx->d_fbws[v] : nullptr);
+      cudaEventRecord(e1, s);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        fail(BDFB_CUDA_FAIL);
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ctx->tune_ms[cl][v] = ms;
+      if (v == cl) best = ms;
+      else if (ms < 0.97f * best) { best = ms; ctx->tuned_var[cl] = v; }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(st2); cudaFree(z2); cudaFree(acorp2); cudaFree(tiles2); cudaFree(tcells2); cudaFree(cnt2);
+  if (rc) return rc;
+  std::vector<int32_t> all(C);
+  for (int64_t i = 0; i < C; ++i) {
+    all[i] = (int32_t)i;
+    var[i] = (int8_t)ctx->tuned_var[ctx->h_cls[i]];
+  }
+  const int r = upload_sched(ctx, 2, launch_order(var, ctx->h_n, all), var, false);
+  if (r) return r;
+  ctx->tuned_prec = pr;
+  return 0;
+}
+
+extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
+  if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
+  if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->grid) {
+    const int r = grid_integrate(ctx->grid, tout, y, mem);
+    if (status) {
+      const int32_t sv = r;
+      if (mem == BDFB_MEM_HOST) *status = sv;
+      else BDFB_CUDA(cudaMemcpy(status, &sv, sizeof sv, cudaMemcpyHostToDevice));
+    }
+    return r;
+  }
+  if (ctx->ncell == 0) return BDFB_SUCCESS;
+  if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
+  cudaStream_t s = ctx->stream;
+  const int pr = ctx->precision;
+  const bool learn = ctx->predictor || ctx->rec_x;
+  // one warp per cell: the NMAX 16 kernel when every cell fits it
+  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && pr == 0);
+  int m = (ctx->mapping == 32 || w16) ? 1 : 0;
+  Params P = base_params(ctx, tout);
+  if (m == 0 && ctx->autotune) {
+    if (ctx->tuned_prec != pr) {
+      P.tiles = ctx->sched[0].d_tiles;
+      P.tile_cells = ctx->sched[0].d_tcells;
+      P.ntiles = ctx->sched[0].ntiles;
+      int r = run_autotune(ctx, P, pr, s);
+      if (r) return r;
+    }
+    m = 2;
+  }
+  const Sched& S = ctx->sched[m];
+  P.tiles = S.d_tiles;
+  P.tile_cells = S.d_tcells;
+  P.ntiles = S.ntiles;
+  if (pr == 1) {
+    for (int v = 0; v < NCLASS; ++v)
+      if (S.vend[v] > S.vbeg[v]) {
+        const int r = ensure_fbws(ctx, v);
+        if (r) return r;
       }
   }
-  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NCLASS + 1) * sizeof(unsigned), s));
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
-  // fork: one persistent launch per size class, largest cells first, each on
-  // its own stream so smaller classes fill the SMs the larger ones release
-  BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
-  if (w16) {
-    const int grid = std::min(ctx->pgrid_w16, ctx->ntiles[1]);
-    k_cells_w16<<<grid, 32, W16_SMEM, s>>>(P, 0, ctx->ntiles[1], ctx->d_counter);
-    BDFB_CUDA(cudaGetLastError());
-  }
-  for (int cl = NCLASS - 1; cl >= 0 && !w16; --cl) {
-    const int t0 = ctx->cls_begin[m][cl], t1 = ctx->cls_end[m][cl];
-    if (t1 <= t0) continue;
-    cudaStream_t cs = ctx->cstream[cl];
-    BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
-    const int pr = ctx->precision;
-    const int grid = std::min(ctx->pgrid[pr][cl], t1 - t0);
-    CELLS_KERNELS[pr][cl]<<<grid, 32, CELLS_SMEM[pr][cl], cs>>>(P, t0, t1, ctx->d_counter + cl,
-                                                                pr == 1 ? ctx->d_fbws[cl] : nullptr);
-    BDFB_CUDA(cudaGetLastError());
-    BDFB_CUDA(cudaEventRecord(ctx->evjoin[cl], cs));
-    BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[cl], 0));
+  if (ctx->graph) {
+    const int r = launch_graph(ctx, P, m, pr, w16, s);
+    if (r) return r;
+  } else {
+    const int r = launch_all(ctx, P, S, pr, w16, s);
+    if (r) return r;
   }
   BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
   if (y) {
@@ -1356,7 +1617,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
                               mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   }
   int worst = 0;
-  BDFB_CUDA(cudaMemcpyAsync(&worst, ctx->d_counter + NCLASS, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaMemcpyAsync(&worst, ctx->d_counter + NVAR, sizeof(int), cudaMemcpyDeviceToHost, s));
   BDFB_CUDA(cudaStreamSynchronize(s));
   cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
   return worst;
@@ -1407,6 +1668,8 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
     out->nguess += s.nguess;
     out->nguess_fallback += s.nguess_fb;
   }
+  out->graph_captures = ctx->graph_captures;
+  out->graph_launches = ctx->graph_launches;
   out->last_kernel_ms = ctx->last_ms;
   return BDFB_SUCCESS;
 }
@@ -1437,6 +1700,28 @@ extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (ctx->ncell == 0) return BDFB_SUCCESS;
   if (mem == BDFB_MEM_HOST) std::memcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t));
   else BDFB_CUDA(cudaMemcpy(out, v.data(), 8 * ctx->ncell * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
+  if (!ctx || !out) return BDFB_ILL_INPUT;
+  std::memset(out, 0, 3 * NCLASS * sizeof(int32_t));
+  if (trial_ms) std::memset(trial_ms, 0, NCLASS * NVAR * sizeof(float));
+  if (ctx->grid) return BDFB_SUCCESS;
+  const bool learn = ctx->predictor || ctx->rec_x;
+  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && ctx->precision == 0);
+  for (int64_t i = 0; i < ctx->ncell; ++i) out[3 * ctx->h_cls[i] + 2]++;
+  for (int cl = 0; cl < NCLASS; ++cl) {
+    if (!out[3 * cl + 2]) continue;
+    int v = cl;
+    if (w16) v = VAR_W16;
+    else if (ctx->mapping == 32) v = 4;
+    else if (ctx->autotune && ctx->tuned_prec == ctx->precision) v = ctx->tuned_var[cl];
+    out[3 * cl] = VAR_G[v];
+    out[3 * cl + 1] = VAR_NMAX[v];
+    if (trial_ms && ctx->autotune && ctx->tuned_prec >= 0)
+      for (int k = 0; k < NVAR; ++k) trial_ms[cl * NVAR + k] = ctx->tune_ms[cl][k];
+  }
   return BDFB_SUCCESS;
 }
 
