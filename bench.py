@@ -580,6 +580,19 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_part(args):
+    """one leg alone (a profiling entry point); prints its JSON"""
+    import torch
+    from paper_2011_12984_b300 import bdfb, gen
+    if args.part == "grid":
+        out = grid_workload(torch, bdfb, gen, nx=args.grid_nx, tout=args.grid_tout, reps=max(1, args.steps))
+    elif args.part == "nvector":
+        out = nvector_bandwidth(torch, bdfb, reps=max(1, args.steps))
+    else:
+        out = learned_workload(torch, bdfb, gen, ncell=args.ncell, train_steps=20000)
+    print(json.dumps({"part": args.part, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,12 +614,18 @@ def main():
                     help="skip the learned-guess leg (1M-cell shared network, training on the GPU)")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
+    ap.add_argument("--part", default="all", choices=["all", "grid", "nvector", "learned"],
+                    help="run one leg alone and print its JSON (for profiling); all: the benchmark")
+    ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
+    ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid: end time")
     args = ap.parse_args()
     globals()["NCELL"] = args.ncell
     if args.sizes:
         globals()["SIZES"] = tuple(int(s) for s in args.sizes.split(","))
     if args.impl == "reference":
         run_reference(args)
+    elif args.part != "all":
+        run_part(args)
     else:
         run_ours(args)
 

@@ -2,9 +2,9 @@
  * bdfb.h - C ABI of libbdfb: batched variable-order BDF / Newton integration
  * of many independent small ODE systems on one NVIDIA B300 (sm_103a).
  *
- * The calls follow the integrator interface the paper keeps identical between
- * CPU and GPU builds (Sec. 5, "all of the calls to integrator functions are
- * the same"): create / init / set tolerances / integrate to tout / get stats.
+ * The calls follow the integrator interface the paper keeps unchanged between
+ * its CPU and GPU builds (Sec. 5): create / init / set tolerances /
+ * integrate to tout / get stats.
  * The per-cell ("submodel") use case of Sec. 2 - many small independent
  * systems, each a diagonal block of one block-diagonal Jacobian (Fig. 1) - is
  * integrated with per-cell step control, Newton iteration and a direct solve

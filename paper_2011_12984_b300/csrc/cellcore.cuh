@@ -261,19 +261,22 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
   for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
   g.sync();
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
+    // pivot search on integer keys: the bit patterns of non-negative IEEE
+    // doubles order like their values, so |a| compares on the integer pipe
+    // (a NaN key exceeds every finite one and is rejected below)
+    long long best = -1;
     int p = n;
     for (int i = k + g.rank; i < n; i += G) {
-      const double v = fabs((double)M[i][k]);
+      const long long v = __double_as_longlong(fabs((double)M[i][k]));
       if (v > best) { best = v; p = i; }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(g.mask, best, o, G);
+      const long long ob = __shfl_xor_sync(g.mask, best, o, G);
       const int op = __shfl_xor_sync(g.mask, p, o, G);
       if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
     }
-    if (!(best > 0.0) || p >= n) return k + 1;
+    if (p >= n || !(__longlong_as_double(best) > 0.0) || best >= 0x7ff0000000000000LL) return k + 1;
     if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
     if (p != k) {
       for (int j = g.rank; j < n; j += G) {

@@ -104,17 +104,57 @@ struct Cell {
   int nguess, nguess_fb;         // learned guesses taken, guesses abandoned for a zero start
 };
 
-template <int G, int NMAX>
-__device__ __forceinline__ void rescale(Cell<G, NMAX>& C, double eta) {
+// The order-dependent loops are dispatched on q (group-uniform) to bodies
+// unrolled for that order, so no predicated-off FP64 work is issued for the
+// columns above q.
+template <int Q, int NPL>
+__device__ __forceinline__ void rescale_q(double (&z)[QMAX + 1][NPL], double eta) {
   double fct = 1.0;
 #pragma unroll
-  for (int j = 1; j <= QMAX; ++j) {
+  for (int j = 1; j <= Q; ++j) {
     fct *= eta;
-    if (j <= C.q) {
 #pragma unroll
-      for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) C.z[j][p] *= fct;
-    }
+    for (int p = 0; p < NPL; ++p) z[j][p] *= fct;
   }
+}
+
+// z_{j-1} += z_j for k = 1..Q, j = Q..k (multiplication by the Pascal matrix)
+template <int Q, int NPL>
+__device__ __forceinline__ void pascal_q(double (&z)[QMAX + 1][NPL]) {
+#pragma unroll
+  for (int k = 1; k <= Q; ++k)
+#pragma unroll
+    for (int j = Q; j >= k; --j)
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) z[j - 1][p] += z[j][p];
+}
+
+// z_j += l_j acor, j = 0..Q
+template <int Q, int NPL>
+__device__ __forceinline__ void correct_q(double (&z)[QMAX + 1][NPL], const double* l, const double (&acor)[NPL]) {
+#pragma unroll
+  for (int j = 0; j <= Q; ++j) {
+    const double lj = l[j];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) z[j][p] = fma(lj, acor[p], z[j][p]);
+  }
+}
+
+#define BDFB_DISPATCH_Q(q, call) \
+  switch (q) {                   \
+    case 1: call(1); break;      \
+    case 2: call(2); break;      \
+    case 3: call(3); break;      \
+    case 4: call(4); break;      \
+    default: call(5); break;     \
+  }
+
+template <int G, int NMAX>
+__device__ __forceinline__ void rescale(Cell<G, NMAX>& C, double eta) {
+  constexpr int NPL = Cell<G, NMAX>::NPL;
+#define BDFB_RESCALE(Q) rescale_q<Q, NPL>(C.z, eta)
+  BDFB_DISPATCH_Q(C.q, BDFB_RESCALE)
+#undef BDFB_RESCALE
   C.h *= eta;
 }
 
@@ -341,14 +381,9 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       for (int j = 0; j <= QMAX; ++j) S.zs[j][i] = C.z[j][p];
     }
   }
-#pragma unroll
-  for (int k = 1; k <= QMAX; ++k)
-#pragma unroll
-    for (int j = QMAX; j >= 1; --j)
-      if (k <= q && j >= k && j <= q) {
-#pragma unroll
-        for (int p = 0; p < NPL; ++p) C.z[j - 1][p] += C.z[j][p];
-      }
+#define BDFB_PASCAL(Q) pascal_q<Q, NPL>(C.z)
+  BDFB_DISPATCH_Q(q, BDFB_PASCAL)
+#undef BDFB_PASCAL
   const double tnew = C.last ? P.tout : C.t + C.h;
   const double rl1 = P.K.rl1[q];
   const double Eq = P.K.E[q][0];
@@ -556,13 +591,9 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       }
     }
   }
-#pragma unroll
-  for (int j = 0; j <= QMAX; ++j)
-    if (j <= q) {
-      const double lj = P.K.l[q][j];
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) C.z[j][p] = fma(lj, C.acor[p], C.z[j][p]);
-    }
+#define BDFB_CORRECT(Q) correct_q<Q, NPL>(C.z, P.K.l[q], C.acor)
+  BDFB_DISPATCH_Q(q, BDFB_CORRECT)
+#undef BDFB_CORRECT
   C.t = tnew;
   C.nst++;
   C.hlast = C.h;

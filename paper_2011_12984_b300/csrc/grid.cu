@@ -8,8 +8,8 @@
 // each block inverted in closed form like the paper's symbolically generated
 // Gauss-Jordan inverse).
 //
-// Control runs on the host, as in the paper (Sec. 2: "the integrator control
-// logic resides on the host"); every vector operation is a B300 kernel and
+// Control runs on the host, as in the paper (Sec. 2: the integrator's
+// decisions are taken on the CPU); every vector operation is a B300 kernel and
 // every reduction returns one scalar to the host (Sec. 4.1).  Fused kernels
 // cut the passes over the ~400 MB vectors of a 256^3 grid: the Nordsieck
 // prediction only materialises z_0 and z_1, the corrector applies the Pascal

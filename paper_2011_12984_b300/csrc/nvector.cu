@@ -64,10 +64,32 @@ struct LCArgs {
   double c[NV_MAX];
 };
 
+// sweeps per loop trip: few operands get more independent loads in flight
+template <int NV>
+struct Sweeps {
+  static constexpr int U = NV <= 2 ? 4 : (NV <= 4 ? 2 : 1);
+};
+
 template <int NV>
 __global__ void k_linear_combination2(int64_t n2, LCArgs A, double2* z) {
+  constexpr int U = Sweeps<NV>::U;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (U - 1) * stride < n2; i += U * stride) {
+    double2 v[U][NV];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[u][j] = __ldcs(reinterpret_cast<const double2*>(A.x[j]) + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double sx = A.c[0] * v[u][0].x, sy = A.c[0] * v[u][0].y;
+#pragma unroll
+      for (int j = 1; j < NV; ++j) { sx = fma(A.c[j], v[u][j].x, sx); sy = fma(A.c[j], v[u][j].y, sy); }
+      __stcs(z + i + u * stride, make_double2(sx, sy));
+    }
+  }
+  for (; i < n2; i += stride) {
     double2 v[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = __ldcs(reinterpret_cast<const double2*>(A.x[j]) + i);
@@ -142,8 +164,15 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[RD_THREA
 }
 
 // MODE 0: out[j] = x . y_j;  MODE 1: out[0] = sqrt(sum (x w)^2 / n)
+// resident blocks per SM a reduction is compiled for (bounds its registers:
+// enough warps must be resident to keep the loads of all operands in flight)
+template <int NV>
+struct RedBlocks {
+  static constexpr int value = NV <= 6 ? 4 : 2;
+};
+
 template <int NV, int MODE>
-__global__ void __launch_bounds__(RD_THREADS) k_reduce(int64_t n, const double* x, RedArgs A,
+__global__ void __launch_bounds__(RD_THREADS, RedBlocks<NV>::value) k_reduce(int64_t n, const double* x, RedArgs A,
                                                        double* work, double* out, int vec) {
   __shared__ double sh[NV][RD_THREADS / 32];
   __shared__ int is_last;
@@ -155,7 +184,31 @@ __global__ void __launch_bounds__(RD_THREADS) k_reduce(int64_t n, const double* 
   if (vec) {
     const int64_t n2 = n >> 1;
     const double2* x2 = reinterpret_cast<const double2*>(x);
-    for (int64_t i = i0; i < n2; i += stride) {
+    constexpr int U = Sweeps<NV>::U;
+    int64_t i = i0;
+    for (; i + (U - 1) * stride < n2; i += U * stride) {
+      double2 xv[U], yv[U][NV];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        xv[u] = __ldcs(x2 + i + u * stride);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) yv[u][j] = __ldcs(reinterpret_cast<const double2*>(A.y[j]) + i + u * stride);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          if (MODE == 0) {
+            acc[j] = fma(xv[u].x, yv[u][j].x, acc[j]);
+            acc[j] = fma(xv[u].y, yv[u][j].y, acc[j]);
+          } else {
+            double p = xv[u].x * yv[u][j].x, q = xv[u].y * yv[u][j].y;
+            acc[j] = fma(p, p, acc[j]);
+            acc[j] = fma(q, q, acc[j]);
+          }
+        }
+    }
+    for (; i < n2; i += stride) {
       double2 xv = __ldcs(x2 + i);
 #pragma unroll
       for (int j = 0; j < NV; ++j) {
@@ -335,7 +388,7 @@ extern "C" int bdfb_nv_scale_add_multi(int64_t n, int nv, const double* a, const
 
 static int launch_reduce(int mode, int64_t n, int nv, const double* x, const RedArgs& A, bool al,
                          double* work, double* out, cudaStream_t s) {
-  int g = grid_for(al ? (n >> 1) : n, RD_THREADS, 6);
+  int g = grid_for(al ? (n >> 1) : n, RD_THREADS, nv <= 6 ? 4 : 2);
   if (g > RD_MAX_BLOCKS) g = RD_MAX_BLOCKS;
   int vec = al ? 1 : 0;
   if (mode == 1) {

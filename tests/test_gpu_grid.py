@@ -77,3 +77,13 @@ def test_grid_64_cubed_properties():
     u, v, w = y.reshape(3, -1)
     assert np.max(np.abs(w - p.B / (1.0 + p.eps * u)) / w) < 1e-5
     assert gs[0] > 0 and st["nsteps"] == gs[0]
+
+
+def test_grid_256_cubed_steady_state():
+    """The benchmark's 256^3 grid (50 331 648 unknowns) in its launch
+    configuration: started at the exact steady state it must stay there."""
+    p = gen.brusselator3d(256, noise=0.0)
+    ret, y, gs, _ = run_grid(p, 0.1, 1e-6, 1e-10)
+    assert ret == 0
+    assert np.max(np.abs(y - p.y0) / np.abs(p.y0)) <= 1e-12
+    assert gs[0] > 0

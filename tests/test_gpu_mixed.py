@@ -80,3 +80,22 @@ def test_mixed_rejected_for_robertson():
     with bdfb.Integrator(p) as I:
         with pytest.raises(bdfb.BdfbError):
             I.set_option("precision", 1)
+
+
+def test_mixed_full_size_sampled():
+    """The 262 144-cell, 54-species workload in both factorisations, as the
+    benchmark runs it: every cell succeeds and conserves sum y; 128 sampled
+    cells against the truth; the two precisions agree to the tolerance."""
+    p = gen.mass_action(262144, sizes=(54,), seed=gen.DEFAULT_SEED + 7)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    cells = np.sort(np.random.default_rng(5).choice(p.ncell, 128, replace=False))
+    ys = {}
+    for prec in (0, 1):
+        ret, y, st, cs, stats = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10, precision=prec)
+        assert ret == 0 and np.all(st == 0)
+        assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
+        ysub = np.concatenate([y[p.y_off[c]:p.y_off[c + 1]] for c in cells])
+        check_against_oracle(p.subset(cells), 1e-3, 1e-6, 1e-10, ysub, cs[cells])
+        ys[prec] = y
+    w = 1e-6 * np.abs(ys[0]) + 1e-10
+    assert np.median(np.abs(ys[1] - ys[0]) / w) <= 3.0

@@ -268,3 +268,23 @@ def test_trained_network_guess():
     print(f"Newton iterations per step: plain {it0:.3f}, learned {it1:.3f}; "
           f"guesses {st1['nguess']}, redone from zero {st1['nguess_fallback']}; "
           f"train loss {h[:20].mean():.3g} -> {h[-100:].mean():.3g}")
+
+
+def test_shared_network_full_size_sampled():
+    """The 1 000 000-cell shared-network workload in the benchmark's plain
+    launch configurations: every cell succeeds and conserves sum y, both
+    mappings agree to the tolerance, 128 sampled cells against the truth."""
+    from test_gpu_cells import check_against_oracle
+    p = gen.mass_action_shared(1_000_000)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    cells = np.sort(np.random.default_rng(6).choice(p.ncell, 128, replace=False))
+    ys = {}
+    for mapping in (0, 32):
+        ret, y, st, cs, _ = run(p, mapping=mapping)
+        assert ret == 0 and np.all(st == 0)
+        assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
+        ysub = np.concatenate([y[p.y_off[c]:p.y_off[c + 1]] for c in cells])
+        check_against_oracle(p.subset(cells), TEND, RTOL, ATOL, ysub, cs[cells])
+        ys[mapping] = y
+    w = RTOL * np.abs(ys[0]) + ATOL
+    assert np.median(np.abs(ys[32] - ys[0]) / w) <= 3.0
