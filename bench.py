@@ -165,14 +165,12 @@ def nvector_bandwidth(torch, bdfb, n=1 << 25, reps=20):
     ops = {
         "linear_sum": (lambda: bdfb.nv_linear_sum(0.5, v[0], -1.0, v[1], v[2]), 24),
         "linear_combination_6": (lambda: bdfb.nv_linear_combination([0.1] * 6, v[:6], v[6]), 8 * 7),
-        "scale_add_multi_6": (lambda: bdfb.nv_scale_add_multi([0.1] * 3, v[0], v[1:4], v[4:7]), 8 * 7),
+        "scale_add_multi_3": (lambda: bdfb.nv_scale_add_multi([0.1] * 3, v[0], v[1:4], v[4:7]), 8 * 7),
         "dot_prod_multi_5": (lambda: bdfb.nv_dot_prod_multi(v[0], v[1:6], out, work), 8 * 6),
         "wrms_norm": (lambda: bdfb.nv_wrms_norm(v[0], v[1], out, work), 16),
     }
     res = {}
     for name, (fn, bpe) in ops.items():
-        if name == "scale_add_multi_6":
-            bpe = 8 * (2 * 3 + 1)
         for _ in range(3):
             fn()
         times = []
@@ -186,6 +184,27 @@ def nvector_bandwidth(torch, bdfb, n=1 << 25, reps=20):
         res[name] = round(bpe * n / statistics.mean(times) / 1e9, 1)
     res["n"] = n
     return res
+
+
+# FP64 instructions per byte moved, per element of the benchmarked forms
+# (DFMA/DMUL/DADD all issue on the FP64 pipe, 2 lanes per SM per cycle)
+NV_FP64_INST_PER_BYTE = {"linear_sum": 2 / 24, "linear_combination_6": 6 / 56, "scale_add_multi_3": 3 / 56,
+                         "dot_prod_multi_5": 5 / 48, "wrms_norm": 2 / 16}
+
+
+def nvector_ceilings(nv, hbm_gbs, sm_mhz):
+    """per op: the lower of the HBM copy rate and the FP64 issue limit
+    (148 SMs x 2 FP64 lanes per cycle / FP64 instructions per byte); on B300
+    FP64 runs at 1:64 of FP32, so the reductions are co-limited by it"""
+    mhz = sm_mhz or 2032.0
+    inst_rate = 148 * 2 * mhz * 1e6
+    out = {}
+    for k, ipb in NV_FP64_INST_PER_BYTE.items():
+        cap = min(hbm_gbs, inst_rate / ipb / 1e9)
+        out[k] = {"achieved_gbs": nv[k], "fp64_limit_gbs": round(inst_rate / ipb / 1e9, 1),
+                  "ceiling_gbs": round(cap, 1), "frac_of_ceiling": round(nv[k] / cap, 3),
+                  "frac_of_hbm": round(nv[k] / hbm_gbs, 3)}
+    return out
 
 
 def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
@@ -567,6 +586,7 @@ def run_ours(args):
         "nvector_roofline": {"bound": "hbm", "achieved": nv["linear_sum"], "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": nv["linear_sum"] / pk["hbm_gbs"],
                              "peak_source": f"hbm_gbs of {pk_kind}"},
+        "nvector_ceilings": nvector_ceilings(nv, pk["hbm_gbs"], clk.summary().get("sm_mhz")),
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"first {cpu_ns} of the {NCELL} cells ({cpu_dt:.1f} s, {cpu_fail} failed)"},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(8 * y0h.size),

@@ -44,13 +44,16 @@ def run_gpu(prob, t0, tout, rtol, atol, device_io=True, **opts):
         return ret, y, st, I.cell_stats(), I.stats()
 
 
-def check_against_oracle(prob, tout, rtol, atol, y, cstats):
+def check_against_oracle(prob, tout, rtol, atol, y, cstats, max_factor=1.5):
+    """max_factor: per-cell bound as a multiple of the oracle's worst cell
+    (1.5 for runs that take the oracle's decisions up to rounding; runs whose
+    Newton iterations start elsewhere differ as two valid integrations do)"""
     yo, so, sto = oracle.integrate_cells(prob, 0.0, tout, rtol, atol, threads=THREADS)
     yt, stt, _ = oracle.integrate_cells(prob, 0.0, tout, 1e-10, 1e-14, threads=THREADS)
     assert np.all(so == 0) and np.all(stt == 0)
     eg = werr(y, yt, prob, rtol, atol)
     eo = werr(yo, yt, prob, rtol, atol)
-    bound = max(10.0, 1.5 * eo.max())
+    bound = max(10.0, max_factor * eo.max())
     bad = eg > bound
     assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10], bound)
     assert np.percentile(eg, 50) <= 1.5 * np.percentile(eo, 50) + 1.0

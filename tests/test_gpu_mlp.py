@@ -198,7 +198,7 @@ def test_garbage_network_still_accurate(scale):
     assert stats["nguess"] > 0 and stats["nguess_fallback"] > 0
     s0 = np.add.reduceat(p.y0, p.y_off[:-1])
     assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
-    eg, eo = check_against_oracle(p, TEND, RTOL, ATOL, y, cs)
+    eg, eo = check_against_oracle(p, TEND, RTOL, ATOL, y, cs, max_factor=4.0)
 
 
 def test_predictor_argument_checks():
@@ -262,7 +262,7 @@ def test_trained_network_guess():
     r0, y0, s0, c0, st0 = run(test)
     r1, y1, s1, c1, st1 = run(test, mlp=pk, predictor=1)
     assert r0 == r1 == 0 and np.all(s1 == 0)
-    check_against_oracle(test, TEND, RTOL, ATOL, y1, c1)
+    check_against_oracle(test, TEND, RTOL, ATOL, y1, c1, max_factor=4.0)
     it0 = st0["nniters"] / st0["nsteps"]
     it1 = st1["nniters"] / st1["nsteps"]
     print(f"Newton iterations per step: plain {it0:.3f}, learned {it1:.3f}; "
