@@ -189,8 +189,9 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              in tout patches tout into the graph, any other change
  *              (tolerances, options, schedule) recaptures
  *  "autotune"  1 = on the next integrate, and again after a precision change,
- *              time every kernel variant that can run a size class on a
- *              sample of that class (first 16384 cells, current state to
+ *              time every kernel variant (bdfb_get_mapping) whose NMAX covers
+ *              a size class without more than doubling it on a sample of that
+ *              class (first 16384 cells, current state to
  *              tout, on scratch copies: the context's state is untouched)
  *              and run each class on the fastest (another variant must beat
  *              the class's own by 3%); mapping 0 only.  Variants differ in
@@ -210,8 +211,8 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              with a zero start, and its convergence test uses the rate
  *              carried over from earlier solves only when the guess lies
  *              closer to the new iterate than zero does (else rate 1).
- * With "mapping" 32 and every cell n <= 16 the one-warp-per-cell kernel of
- * the predictor runs (with or without the guess). */
+ * "mapping" 32 runs every cell on the smallest one-warp-per-cell kernel all
+ * cells fit (NMAX 16 — the predictor's kernel, FP64 only — 32 or 56). */
 int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);
 /* set t0 and copy the initial state (packed by y_off); mem: where y0 lives */
 int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem);
@@ -228,13 +229,14 @@ int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
 int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
 /* Cell-to-lane mapping in use.  Size classes c = 0..4 hold cells with
  * max(n, ceil(reactions / 2)) <= 4, 8, 16, 32, 56.  Kernel variants v =
- * 0..5 are (lanes per cell G, largest cell NMAX) = (1, 4), (4, 8), (8, 16),
- * (16, 32), (32, 56) and the one-warp (32, 16).  out (host, 15 int32):
- * out[3c] = G, out[3c + 1] = NMAX of the variant class c runs on (under the
- * current options; the tuned one after autotuning), out[3c + 2] = cells in
- * class c (0: class empty, G = NMAX = 0).  trial_ms (host, 5 x 6 floats, or
- * NULL): the autotuner's trial time of variant v on class c at [6c + v]
- * (0: not tried). */
+ * 0..7 are (lanes per cell G, largest cell NMAX) = (1, 4), (4, 8), (8, 16),
+ * (16, 32), (32, 56) (the classes' own tilings), (32, 16) (one warp per cell;
+ * the learned guess runs here), (32, 32) and (16, 16).  out (host, 15
+ * int32): out[3c] = G, out[3c + 1] = NMAX of the variant class c runs on
+ * (under the current options; the tuned one after autotuning), out[3c + 2] =
+ * cells in class c (0: class empty, G = NMAX = 0).  trial_ms (host, 5 x 8
+ * floats, or NULL): the autotuner's trial time of variant v on class c at
+ * [8c + v] (0: not tried). */
 int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms);
 
 /* ------------------------------------- learned Newton initial guess (MLP)

@@ -320,9 +320,9 @@ class Integrator:
         return s.as_dict()
 
     def mapping(self):
-        """(per size class (G, NMAX, cells) int32 [5, 3], autotune trial ms [5, 6])"""
+        """(per size class (G, NMAX, cells) int32 [5, 3], autotune trial ms [5, 8])"""
         out = np.zeros((5, 3), np.int32)
-        ms = np.zeros((5, 6), np.float32)
+        ms = np.zeros((5, 8), np.float32)
         check(lib.bdfb_get_mapping(self.h, out.ctypes.data, ms.ctypes.data), "bdfb_get_mapping")
         return out, ms
 

@@ -692,81 +692,66 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   }
 }
 
-template <int CLS, int PREC>
-struct ClassSmem {
-  static constexpr int bytes = (32 / CLS_G[CLS]) * (int)sizeof(CellSmem<CLS_NMAX[CLS], PREC>);
+// Kernel variants (cell-to-lane mappings): G lanes per cell for cells of at
+// most NMAX species.  0..4 are the size classes' own tilings; 5 is one warp
+// per cell of up to 16 species carrying the learned guess and the recording;
+// 6 is one warp per cell of up to 32 species; 7 is 16 lanes per cell of up
+// to 16 species.  A cell runs on any variant whose NMAX covers it; launches
+// go largest NMAX first.
+constexpr int NVAR = NCLASS + 3;
+constexpr int VAR_W16 = NCLASS, VAR_W32 = NCLASS + 1, VAR_H16 = NCLASS + 2;
+constexpr int VAR_G[NVAR] = {1, 4, 8, 16, 32, 32, 32, 16};
+constexpr int VAR_NMAX[NVAR] = {4, 8, 16, 32, 56, 16, 32, 16};
+constexpr int VAR_LEARN[NVAR] = {0, 0, 0, 0, 0, 1, 0, 0};
+constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W32, VAR_W16, VAR_H16, 2, 1, 0};
+// warps per SM each variant should keep resident (the shared-memory limit of
+// the largest ones): bounds the registers ptxas may use
+constexpr int VAR_MINB[NVAR] = {12, 12, 12, 8, 7, 12, 12, 12};
+static_assert(CLS_G[0] == VAR_G[0] && CLS_NMAX[4] == VAR_NMAX[4], "variants 0..4 are the class tilings");
+
+template <int V, int PREC>
+struct VarSmem {
+  static constexpr int bytes = (32 / VAR_G[V]) * (int)sizeof(CellSmem<VAR_NMAX[V], PREC>);
 };
 
-// Persistent kernel of one size class: each warp takes the next tile of the
-// class range [t0, t1) from `counter` until none is left.  PREC 0: FP64
+// Persistent kernel of one variant: each warp takes the next tile of the
+// range [t0, t1) from `counter` until none is left.  PREC 0: FP64
 // factorisation; PREC 1: FP32 factorisation with FP64 refinement.
-// warps per SM each class kernel should keep resident (its shared-memory
-// limit for the two largest classes): bounds the registers ptxas may use
-constexpr int CLS_MINB[NCLASS] = {12, 12, 12, 8, 7};
-template <int CLS, int PREC>
-__global__ void __launch_bounds__(32, CLS_MINB[CLS]) k_cells(const __grid_constant__ Params P, int t0, int t1,
-                                                             unsigned* counter, double* fbws) {
+template <int V, int PREC>
+__global__ void __launch_bounds__(32, VAR_MINB[V]) k_cells(const __grid_constant__ Params P, int t0, int t1,
+                                                           unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
-  constexpr int64_t FB = (int64_t)(32 / CLS_G[CLS]) * CLS_NMAX[CLS] * (CLS_NMAX[CLS] + 1);
+  constexpr int64_t FB = (int64_t)(32 / VAR_G[V]) * VAR_NMAX[V] * (VAR_NMAX[V] + 1);
   double* fb = fbws ? fbws + (int64_t)blockIdx.x * FB : nullptr;
   for (;;) {
     int t = 0;
     if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
     t = __shfl_sync(FULL_MASK, t, 0);
     if (t >= t1) break;
-    run_tile<CLS_G[CLS], CLS_NMAX[CLS], PREC>(P, P.tiles[t], smem, fb);
+    run_tile<VAR_G[V], VAR_NMAX[V], PREC, VAR_LEARN[V]>(P, P.tiles[t], smem, fb);
     __syncwarp();
   }
 }
 
-// One warp per cell for cells of at most 16 species, in input order (the
-// schedule of mapping 32); LEARN adds the learned guess and the recording.
-constexpr int W16_NMAX = 16;
-static_assert(CLS_NMAX[2] == W16_NMAX, "cells of classes 0..2 fit the one-warp NMAX 16 layout");
-__global__ void __launch_bounds__(32) k_cells_w16(const __grid_constant__ Params P, int t0, int t1,
-                                                  unsigned* counter, double*) {
-  extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int t = 0;
-    if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
-    t = __shfl_sync(FULL_MASK, t, 0);
-    if (t >= t1) break;
-    run_tile<32, W16_NMAX, 0, 1>(P, P.tiles[t], smem, nullptr);
-    __syncwarp();
-  }
-}
-constexpr int W16_SMEM = (int)sizeof(CellSmem<W16_NMAX, 0>);
-
-// doubles of FP64 fallback workspace one warp of class c needs
-static int64_t fallback_doubles_per_warp(int c) {
-  return (int64_t)(32 / CLS_G[c]) * CLS_NMAX[c] * (CLS_NMAX[c] + 1);
+// doubles of FP64 fallback workspace one warp of variant v needs
+static int64_t fallback_doubles_per_warp(int v) {
+  return (int64_t)(32 / VAR_G[v]) * VAR_NMAX[v] * (VAR_NMAX[v] + 1);
 }
 
 typedef void (*cells_kernel_t)(const Params, int, int, unsigned*, double*);
-static const cells_kernel_t CELLS_KERNELS[2][NCLASS] = {
-    {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>},
-    {k_cells<0, 1>, k_cells<1, 1>, k_cells<2, 1>, k_cells<3, 1>, k_cells<4, 1>}};
-static const int CELLS_SMEM[2][NCLASS] = {
-    {ClassSmem<0, 0>::bytes, ClassSmem<1, 0>::bytes, ClassSmem<2, 0>::bytes, ClassSmem<3, 0>::bytes,
-     ClassSmem<4, 0>::bytes},
-    {ClassSmem<0, 1>::bytes, ClassSmem<1, 1>::bytes, ClassSmem<2, 1>::bytes, ClassSmem<3, 1>::bytes,
-     ClassSmem<4, 1>::bytes}};
-
-// Kernel variants (cell-to-lane mappings): the five size-class tilings and
-// the one-warp-per-cell NMAX 16 kernel.  A cell can run on any variant whose
-// NMAX covers it; launches go largest NMAX first.
-constexpr int NVAR = NCLASS + 1;
-constexpr int VAR_W16 = NCLASS;
-constexpr int VAR_G[NVAR] = {1, 4, 8, 16, 32, 32};
-constexpr int VAR_NMAX[NVAR] = {4, 8, 16, 32, 56, 16};
-constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W16, 2, 1, 0};
-static cells_kernel_t var_kernel(int pr, int v) {
-  if (v < NCLASS) return CELLS_KERNELS[pr][v];
-  return pr == 0 ? k_cells_w16 : nullptr;
-}
-static int var_smem(int pr, int v) { return v < NCLASS ? CELLS_SMEM[pr][v] : W16_SMEM; }
+static const cells_kernel_t CELLS_KERNELS[2][NVAR] = {
+    {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>, k_cells<5, 0>, k_cells<6, 0>,
+     k_cells<7, 0>},
+    {k_cells<0, 1>, k_cells<1, 1>, k_cells<2, 1>, k_cells<3, 1>, k_cells<4, 1>, nullptr, k_cells<6, 1>,
+     k_cells<7, 1>}};
+static const int CELLS_SMEM[2][NVAR] = {
+    {VarSmem<0, 0>::bytes, VarSmem<1, 0>::bytes, VarSmem<2, 0>::bytes, VarSmem<3, 0>::bytes, VarSmem<4, 0>::bytes,
+     VarSmem<5, 0>::bytes, VarSmem<6, 0>::bytes, VarSmem<7, 0>::bytes},
+    {VarSmem<0, 1>::bytes, VarSmem<1, 1>::bytes, VarSmem<2, 1>::bytes, VarSmem<3, 1>::bytes, VarSmem<4, 1>::bytes,
+     0, VarSmem<6, 1>::bytes, VarSmem<7, 1>::bytes}};
+static cells_kernel_t var_kernel(int pr, int v) { return CELLS_KERNELS[pr][v]; }
+static int var_smem(int pr, int v) { return CELLS_SMEM[pr][v]; }
 
 // ------------------------------------------------- standalone batched LU
 constexpr int LU_NMAX = 64;
@@ -981,7 +966,7 @@ struct bdfb_ctx {
   cudaGraph_t cgraph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   Params gkey;                     // Params of the capture with tout = 0
-  int gkey_gen = -1, gkey_m = -1, gkey_w16 = -1;
+  int gkey_gen = -1, gkey_m = -1, gkey_single = -1;
   int64_t graph_launches = 0, graph_captures = 0;
   int32_t* d_status = nullptr;
   double rtol = 1e-6, atol = 1e-10;
@@ -991,13 +976,14 @@ struct bdfb_ctx {
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
   cudaEvent_t evjoin[NVAR] = {};
-  double* d_fbws[NCLASS] = {};      // FP64 fallback workspace per class (mixed precision, lazy)
+  double* d_fbws[NVAR] = {};        // FP64 fallback workspace per variant (mixed precision, lazy)
   cudaStream_t cstream[NVAR] = {};  // one per variant, forked from `stream`
   float last_ms = 0.f;
   int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
   int maxn = 0;               // largest cell
   bool fits_w16 = false;      // every cell fits the NMAX 16 shared-memory layout
+  bool fits_w32 = false;      // every cell fits the NMAX 32 shared-memory layout
   int predictor = 0;          // 1: Newton starts from the learned guess
   const void* mlp = nullptr;  // packed network (caller-owned device memory)
   float* rec_x = nullptr;     // recording buffers (caller-owned device memory)
@@ -1015,7 +1001,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
-  for (int k = 0; k < NCLASS; ++k) cudaFree(c->d_fbws[k]);
+  for (int k = 0; k < NVAR; ++k) cudaFree(c->d_fbws[k]);
   for (int m = 0; m < 3; ++m) { cudaFree(c->sched[m].d_tiles); cudaFree(c->sched[m].d_tcells); }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cgraph) cudaGraphDestroy(c->cgraph);
@@ -1210,8 +1196,11 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   c->ny = yoff[C];
   for (int64_t i = 0; i < C; ++i) c->maxn = std::max(c->maxn, n[i]);
   c->fits_w16 = true;
-  for (int64_t i = 0; i < C; ++i)
+  c->fits_w32 = true;
+  for (int64_t i = 0; i < C; ++i) {
     if (cls[i] > 2) c->fits_w16 = false;    // class 2 has NMAX 16
+    if (cls[i] > 3) c->fits_w32 = false;    // class 3 has NMAX 32
+  }
   c->h_n = n;
   c->h_yoff = yoff;
   if (prob->kind == BDFB_MASSACTION) {
@@ -1359,6 +1348,14 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
   return BDFB_SUCCESS;
 }
 
+// The one-warp-per-cell kernel of mapping 32 (and of the learned guess): the
+// smallest shared-memory layout every cell fits
+static int one_warp_variant(const bdfb_ctx* ctx, bool learn) {
+  if (learn || (ctx->fits_w16 && ctx->precision == 0)) return VAR_W16;
+  if (ctx->fits_w32) return VAR_W32;
+  return 4;
+}
+
 // Params of an integrate call (schedule fields filled by the caller)
 static Params base_params(bdfb_ctx* ctx, double tout) {
   Params P;
@@ -1408,9 +1405,9 @@ static int ensure_fbws(bdfb_ctx* ctx, int v) {
 // The launch sequence of one integrate call on stream s: clear the tile
 // counters, then fork one persistent launch per variant of the schedule,
 // largest cells first, each on its own stream so that smaller cells fill
-// the SMs the larger ones release, and join.  `single_w16`: the one-cell
-// tiles of the NMAX 56 range run on the NMAX 16 one-warp kernel.
-static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, bool single_w16,
+// the SMs the larger ones release, and join.  `single`: the variant the
+// one-cell tiles of the one-warp-per-cell schedule (variant 4's range) run on.
+static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, int single,
                       cudaStream_t s) {
   BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NVAR + 1) * sizeof(unsigned), s));
   BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
@@ -1418,14 +1415,13 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, bo
     const int v = VAR_ORDER[k];
     const int t0 = S.vbeg[v], t1 = S.vend[v];
     if (t1 <= t0) continue;
-    const int kv = (v == 4 && single_w16) ? VAR_W16 : v;
+    const int kv = v == 4 ? single : v;
     const cells_kernel_t kf = var_kernel(pr, kv);
     if (!kf) return BDFB_ILL_INPUT;
     cudaStream_t cs = ctx->cstream[v];
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
     const int grid = std::min(ctx->pgrid[pr][kv], t1 - t0);
-    kf<<<grid, 32, var_smem(pr, kv), cs>>>(P, t0, t1, ctx->d_counter + v,
-                                           (pr == 1 && kv < NCLASS) ? ctx->d_fbws[kv] : nullptr);
+    kf<<<grid, 32, var_smem(pr, kv), cs>>>(P, t0, t1, ctx->d_counter + v, pr == 1 ? ctx->d_fbws[kv] : nullptr);
     BDFB_CUDA(cudaGetLastError());
     BDFB_CUDA(cudaEventRecord(ctx->evjoin[v], cs));
     BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[v], 0));
@@ -1436,18 +1432,18 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, bo
 // Option "graph": the launch sequence is captured once into a CUDA graph
 // and replayed; a later call with the same parameters but another tout
 // patches tout into the kernel nodes; anything else recaptures.
-static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, bool single_w16, cudaStream_t s) {
+static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, int single, cudaStream_t s) {
   Params key = P;
   key.tout = 0.0;
   const bool same = ctx->gexec && ctx->gkey_gen == ctx->sched_gen && ctx->gkey_m == m &&
-                    ctx->gkey_w16 == (int)single_w16 && !std::memcmp(&key, &ctx->gkey, sizeof key);
+                    ctx->gkey_single == single && !std::memcmp(&key, &ctx->gkey, sizeof key);
   if (!same) {
     if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
     if (ctx->cgraph) { cudaGraphDestroy(ctx->cgraph); ctx->cgraph = nullptr; }
     // captured on a stream of the context (the legacy default stream cannot
     // be captured); the graph is launched on s
     BDFB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int r = launch_all(ctx, P, ctx->sched[m], pr, single_w16, ctx->cap_stream);
+    const int r = launch_all(ctx, P, ctx->sched[m], pr, single, ctx->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (r || e != cudaSuccess) {
@@ -1459,7 +1455,7 @@ static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, bool sing
     ctx->gkey = key;
     ctx->gkey_gen = ctx->sched_gen;
     ctx->gkey_m = m;
-    ctx->gkey_w16 = (int)single_w16;
+    ctx->gkey_single = single;
     ctx->graph_captures++;
   } else {
     size_t nn = 0;
@@ -1523,17 +1519,20 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
     ctx->tuned_var[cl] = cl;
     for (int v = 0; v < NVAR; ++v) ctx->tune_ms[cl][v] = 0.f;
     if (members[cl].empty()) continue;
+    // the class's own tiling first, then every other variant whose NMAX
+    // covers the class without more than doubling it
     std::vector<int> cand = {cl};
-    if (cl + 1 < NCLASS) cand.push_back(cl + 1);
-    if (cl <= 2 && pr == 0) cand.push_back(VAR_W16);
+    for (int v = 0; v < NVAR; ++v)
+      if (v != cl && var_kernel(pr, v) && VAR_NMAX[v] >= CLS_NMAX[cl] && VAR_NMAX[v] <= 2 * CLS_NMAX[cl])
+        cand.push_back(v);
     float best = 0.f;
     for (int v : cand) {
-      if (v < NCLASS && pr == 1 && ensure_fbws(ctx, v)) { fail(BDFB_MEM_FAIL); break; }
+      if (pr == 1 && ensure_fbws(ctx, v)) { fail(BDFB_MEM_FAIL); break; }
       for (int32_t c : members[cl]) var[c] = (int8_t)v;
       std::vector<TileDesc> tiles;
       std::vector<int32_t> tcells;
       int vb[NVAR], ve[NVAR];
-      make_tiles(launch_order(var, ctx->h_n, members[cl]), var, v == VAR_W16, tiles, tcells, vb, ve);
+      make_tiles(launch_order(var, ctx->h_n, members[cl]), var, false, tiles, tcells, vb, ve);
       const int nt = (int)tiles.size();
       Params Pt = P0;
       Pt.st = st2;
@@ -1560,7 +1559,7 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
       const cells_kernel_t kf = var_kernel(pr, v);
       cudaEventRecord(e0, s);
       kf<<<std::min(ctx->pgrid[pr][v], nt), 32, var_smem(pr, v), s>>>(
-          Pt, 0, nt, cnt2, (pr == 1 && v < NCLASS) ? ctx->d_fbws[v] : nullptr);
+          Pt, 0, nt, cnt2, pr == 1 ? ctx->d_fbws[v] : nullptr);
       cudaEventRecord(e1, s);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         fail(BDFB_CUDA_FAIL);
@@ -1606,8 +1605,9 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   const int pr = ctx->precision;
   const bool learn = ctx->predictor || ctx->rec_x;
   // one warp per cell: the NMAX 16 kernel when every cell fits it
-  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && pr == 0);
-  int m = (ctx->mapping == 32 || w16) ? 1 : 0;
+  // one warp per cell: the smallest one-warp kernel every cell fits
+  const int single = one_warp_variant(ctx, learn);
+  int m = (ctx->mapping == 32 || learn) ? 1 : 0;
   Params P = base_params(ctx, tout);
   if (m == 0 && ctx->autotune) {
     if (ctx->tuned_prec != pr) {
@@ -1624,7 +1624,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.tile_cells = S.d_tcells;
   P.ntiles = S.ntiles;
   if (pr == 1) {
-    for (int v = 0; v < NCLASS; ++v)
+    for (int v = 0; v < NVAR; ++v)
       if (S.vend[v] > S.vbeg[v]) {
         const int r = ensure_fbws(ctx, v);
         if (r) return r;
@@ -1632,10 +1632,10 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   }
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
   if (ctx->graph) {
-    const int r = launch_graph(ctx, P, m, pr, w16, s);
+    const int r = launch_graph(ctx, P, m, pr, single, s);
     if (r) return r;
   } else {
-    const int r = launch_all(ctx, P, S, pr, w16, s);
+    const int r = launch_all(ctx, P, S, pr, single, s);
     if (r) return r;
   }
   BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
@@ -1740,13 +1740,11 @@ extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
   if (trial_ms) std::memset(trial_ms, 0, NCLASS * NVAR * sizeof(float));
   if (ctx->grid) return BDFB_SUCCESS;
   const bool learn = ctx->predictor || ctx->rec_x;
-  const bool w16 = learn || (ctx->mapping == 32 && ctx->fits_w16 && ctx->precision == 0);
   for (int64_t i = 0; i < ctx->ncell; ++i) out[3 * ctx->h_cls[i] + 2]++;
   for (int cl = 0; cl < NCLASS; ++cl) {
     if (!out[3 * cl + 2]) continue;
     int v = cl;
-    if (w16) v = VAR_W16;
-    else if (ctx->mapping == 32) v = 4;
+    if (learn || ctx->mapping == 32) v = one_warp_variant(ctx, learn);
     else if (ctx->autotune && ctx->tuned_prec == ctx->precision) v = ctx->tuned_var[cl];
     out[3 * cl] = VAR_G[v];
     out[3 * cl + 1] = VAR_NMAX[v];
