@@ -255,7 +255,10 @@ __device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellS
 // Right-looking LU with partial pivoting of the n x n matrix in S.M (ties in
 // |pivot| go to the lowest row).  Returns 0 or k + 1 when pivot k is zero (or
 // no finite pivot exists).  pivk (optional) records the pivot row of each step.
-template <int G, int NMAX, typename T>
+// UNITU: the strictly upper part is stored divided by its row's pivot (P M =
+// L D U' with U' unit upper, D = diag(1 / dinv)), so that a solve needs one
+// vector scaling by dinv instead of a multiply per back-substitution column.
+template <int G, int NMAX, typename T, bool UNITU = false>
 __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* dinv, int16_t* perm, int n,
                          int16_t* pivk = nullptr) {
   for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
@@ -319,6 +322,10 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
           if (j < n) M[i][j] = fma(-lik, u[b], M[i][j]);
         }
       }
+      if constexpr (UNITU) {
+        g.sync();                     // every lane has read row k
+        for (int j = k + 1 + g.rank; j < n; j += G) M[k][j] *= rinv;
+      }
     }
     g.sync();
   }
@@ -326,7 +333,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
 }
 
 // x <- (P M)^{-1} P x with the factors above; x distributed over the group.
-template <int G, int NPL, int NMAX, typename T>
+template <int G, int NPL, int NMAX, typename T, bool UNITU = false>
 __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1], const T* dinv,
                          const int16_t* perm, double* buf, int n, double (&x)[NPL]) {
 #pragma unroll
@@ -350,10 +357,20 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
       if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
     }
   }
-  for (int j = n - 1; j >= 0; --j) {            // U x = y
+  if constexpr (UNITU) {                         // y <- D^{-1} y
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) x[p] *= (double)dinv[i];
+    }
+  }
+  for (int j = n - 1; j >= 0; --j) {            // U x = y (U' x = y when UNITU)
     const int owner = j % G, slot = j / G;
-    const double xj = g.bcast(pick(x, slot), owner) * (double)dinv[j];
-    if (g.rank == owner) place(x, slot, xj);
+    double xj = g.bcast(pick(x, slot), owner);
+    if constexpr (!UNITU) {
+      xj *= (double)dinv[j];
+      if (g.rank == owner) place(x, slot, xj);
+    }
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
       if (G * p >= j) continue;                 // no row of this slot is above j

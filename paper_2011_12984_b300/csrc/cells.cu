@@ -406,7 +406,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       C.fp64mode = 0;
     } else {
       form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
-      info = lu_factor<G, NMAX, double>(g, S.M, S.dinv, S.perm, n);
+      info = lu_factor<G, NMAX, double, true>(g, S.M, S.dinv, S.perm, n);
     }
     C.nsetups++;
     C.gammap = C.gamma;
@@ -480,7 +480,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
               // the cell's global workspace) until the next setup
               C.nref_fb++;
               form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
-              if (lu_factor<G, NMAX, double>(g, Mg, S.dinv, S.perm, n)) {
+              if (lu_factor<G, NMAX, double, true>(g, Mg, S.dinv, S.perm, n)) {
                 C.setup_done = 0;
                 break;                      // singular: counts as a Newton failure
               }
@@ -489,9 +489,9 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
               for (int p = 0; p < NPL; ++p) C.b[p] = bs[p];
             }
           }
-          if (!solved) lu_solve<G, NPL, NMAX, double>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
+          if (!solved) lu_solve<G, NPL, NMAX, double, true>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
         } else {
-          lu_solve<G, NPL, NMAX, double>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
+          lu_solve<G, NPL, NMAX, double, true>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
         }
         // a stale M's step scaling, except on the first step from a nonzero
         // guess: unscaled, that step gives w.Delta = -w.z1 / l1 for every w
