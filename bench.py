@@ -400,6 +400,21 @@ def learned_workload(torch, bdfb, gen, ncell=1_000_000, ntrain_pairs=10_000_000,
             **out}
 
 
+def shard_seed(seed, rank):
+    """weak scaling: rank r integrates its own cells, drawn with seed + r (the
+    ranks' workloads are disjoint and equally sized; no data-path exchange)"""
+    return seed + rank
+
+
+def slowest_rank_time(torch, dist, t, device):
+    """the job's step time: the maximum over ranks (t itself on one rank)"""
+    if not dist:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def run_reference(args):
     """reference arm: the CPU oracle as it stands, on the host cores"""
     ws, rank, _ = dist_env()
@@ -439,7 +454,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2011_12984_b300 import bdfb, gen
     # weak scaling: every rank integrates its own 100 000 cells (seed per rank)
-    prob = gen.mass_action(NCELL, sizes=SIZES, seed=gen.DEFAULT_SEED + rank)
+    prob = gen.mass_action(NCELL, sizes=SIZES, seed=shard_seed(gen.DEFAULT_SEED, rank))
     y0 = torch.from_numpy(prob.y0).cuda()
     y = torch.empty_like(y0)
     st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
@@ -479,11 +494,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t_step = sum(step_s) / len(step_s)
-    if dist:
-        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = slowest_rank_time(torch, dist, sum(step_s) / len(step_s), "cuda")
     value = ws * NCELL / t_step
     cs = integ.cell_stats()
     yh = y.cpu().numpy()

@@ -391,8 +391,8 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   // ---- linear setup
   int jcur = 0;
   bool fail = false;
-  if (!C.setup_done || C.force_setup || fabs(C.gamma / C.gammap - 1.0) > 0.3 ||
-      C.nst >= C.nstlp + 20) {
+  const double gratio = C.gamma / C.gammap;   // (not used before the first setup)
+  if (!C.setup_done || C.force_setup || fabs(gratio - 1.0) > 0.3 || C.nst >= C.nstlp + 20) {
     double y[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
@@ -418,6 +418,8 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     if (info) { fail = true; C.setup_done = 0; }
   }
   // ---- Newton iteration (norms compared squared, in FP64)
+  // a stale M's step scaling 2 / (1 + gamma / gamma_setup), once per attempt
+  const double scst = C.gamma != C.gammap ? 2.0 / (1.0 + gratio) : 1.0;
   double acnrm2 = 0.0;
   bool conv = false;
   float feat = 0.f;
@@ -499,9 +501,8 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         // come out as from a zero start; a scaled one would keep a share of
         // the guess's error in them
         if (C.gamma != C.gammap && !(nzguess && it == 1)) {
-          const double sc = 2.0 / (1.0 + C.gamma / C.gammap);
 #pragma unroll
-          for (int p = 0; p < NPL; ++p) C.b[p] *= sc;
+          for (int p = 0; p < NPL; ++p) C.b[p] *= scst;
         }
         const double del2 = wrms2(g, n, C.rn, C.b, C.ewt);
 #pragma unroll
