@@ -56,16 +56,44 @@ struct LaneGrid {
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
 
 // per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
-// (mixed precision): M and its Gauss-Jordan inverse in FP32, plus the FP64
-// reaction derivatives the refinement residual needs.
+// (mixed precision): M and its Gauss-Jordan inverse in FP32.  Both keep the
+// FP64 reaction derivatives of the last setup (computed once per reaction, then
+// gathered into the rows of J; mixed precision reuses them in the refinement
+// residual).
+// reaction rates (RHS scratch) and d rate_r / d y_(reactant a) at the setup
+// point (mass action).  FP64 path: the rates live only inside a RHS call and
+// the derivatives only inside a setup, so they share storage; the mixed path
+// keeps the derivatives for the refinement residual of every Newton step.
+template <int NMAX, bool SHARE, bool DR>
+struct RateBufs {
+  double rates[2 * NMAX];
+  double dr[DR ? 2 * NMAX : 1][4];
+};
+template <int NMAX>
+struct RateBufs<NMAX, true, true> {
+  union {
+    double rates[2 * NMAX];
+    double dr[2 * NMAX][4];
+  };
+};
+
+// the per-reaction derivatives pay off from 16 species up (below, a tile
+// holds many small cells and the shared memory goes to residency)
+template <int NMAX, int PREC>
+struct UsesDr {
+  static constexpr bool value = PREC == 1 || NMAX >= 16;
+};
+
 template <int NMAX, int PREC = 0>
-struct CellSmem {
+struct CellSmem : RateBufs<NMAX, PREC == 0, UsesDr<NMAX, PREC>::value> {
+  static constexpr bool DR = UsesDr<NMAX, PREC>::value;
   typename std::conditional<PREC == 1, float, double>::type M[NMAX][NMAX + 1];
-  double zs[ZCOLS][NMAX];     // history saved before a step attempt
+  // history saved before a step attempt; the FP64 kernel of the largest
+  // cells keeps it in registers instead (its shared memory bounds residency)
+  static constexpr bool ZREG = PREC == 0 && NMAX >= 56;
+  double zs[ZREG ? 1 : ZCOLS][NMAX];
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side
-  double rates[2 * NMAX];     // reaction rates (mass action)
-  double dr[PREC ? 2 * NMAX : 1][4];  // d rate_r / d y_(reactant a) at the setup point
   int16_t perm[NMAX];         // row i of P M is row perm[i] of M
 };
 

@@ -95,6 +95,7 @@ template <int G, int NMAX>
 struct Cell {
   static constexpr int NPL = (NMAX + G - 1) / G;
   double z[QMAX + 1][NPL];
+  double zsave[NMAX >= 56 ? QMAX + 1 : 1][NPL];   // saved history (CellSmem::ZREG kernels)
   double acor[NPL], acorp[NPL], ewt[NPL], f[NPL], b[NPL];
   double t, h, gamma, gammap, crate, hlast, rn;   // rn = 1/n
   int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
@@ -295,12 +296,19 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
 template <int G, int NMAX, int PREC>
 __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem<NMAX, PREC>& S,
                                           Cell<G, NMAX>& C) {
+  if constexpr (CellSmem<NMAX, PREC>::ZREG) {
 #pragma unroll
-  for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
-    const int i = g.rank + G * p;
-    if (i < n) {
+    for (int p = 0; p < Cell<G, NMAX>::NPL; ++p)
 #pragma unroll
-      for (int j = 0; j <= QMAX; ++j) C.z[j][p] = S.zs[j][i];
+      for (int j = 0; j <= QMAX; ++j) C.z[j][p] = C.zsave[j][p];
+  } else {
+#pragma unroll
+    for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j <= QMAX; ++j) C.z[j][p] = S.zs[j][i];
+      }
     }
   }
 }
@@ -373,12 +381,19 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   if (C.t + C.h == C.t) { C.status = BDFB_ERR_FAILURE; return true; }
   const int q = C.q;
   // save and predict: z_{j-1} += z_j repeatedly (Pascal triangle)
+  if constexpr (CellSmem<NMAX, PREC>::ZREG) {
 #pragma unroll
-  for (int p = 0; p < NPL; ++p) {
-    const int i = g.rank + G * p;
-    if (i < n) {
+    for (int p = 0; p < NPL; ++p)
 #pragma unroll
-      for (int j = 0; j <= QMAX; ++j) S.zs[j][i] = C.z[j][p];
+      for (int j = 0; j <= QMAX; ++j) C.zsave[j][p] = C.z[j][p];
+  } else {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j <= QMAX; ++j) S.zs[j][i] = C.z[j][p];
+      }
     }
   }
 #define BDFB_PASCAL(Q) pascal_q<Q, NPL>(C.z)
@@ -405,7 +420,16 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       info = gj_inverse<G, NMAX>(g, S.M, S.perm, reinterpret_cast<float*>(S.ybuf), n);
       C.fp64mode = 0;
     } else {
-      form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
+      bool direct = true;
+      if constexpr (CellSmem<NMAX, PREC>::DR) {
+        if (cd.kind == BDFB_MASSACTION) {
+          // each reaction's derivatives once, then gathered into the rows
+          reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
+          form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gamma, S.M);
+          direct = false;
+        }
+      }
+      if (direct) form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
       info = lu_factor<G, NMAX, double, true>(g, S.M, S.dinv, S.perm, n);
     }
     C.nsetups++;

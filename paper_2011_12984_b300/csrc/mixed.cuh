@@ -35,9 +35,9 @@ __device__ __forceinline__ float bcastf(const Grp<G>& g, float v, int src) {
 
 // d rate_r / d y_{s_a} for every reaction r and reactant slot a at y (FP64),
 // into S.dr; lanes over reactions.
-template <int G, int NPL, int NMAX>
+template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void reaction_derivs(const Grp<G>& g, const CellDesc& c,
-                                                CellSmem<NMAX, 1>& S, const double (&y)[NPL]) {
+                                                CellSmem<NMAX, PREC>& S, const double (&y)[NPL]) {
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   for (int r = g.rank; r < c.nr; r += G) {
     const uint32_t rc = __ldg(c.reac + r);
@@ -99,11 +99,13 @@ __device__ __forceinline__ double form_M32(const Grp<G>& g, const CellDesc& c, C
   return gmaxd(g, mnorm);
 }
 
-// FP64 M = I - gamma J from S.dr into Mg (the fallback factorisation's
-// matrix, in the cell's global-memory workspace)
-template <int G, int NPL, int NMAX>
+// FP64 M = I - gamma J from S.dr into Mg: the FP64 path's M in shared
+// memory, or the mixed path's fallback matrix in the cell's global-memory
+// workspace.  Rows are summed in the order of the direct definition (the
+// incidence lists' reaction order), so M equals the entry-by-entry formation.
+template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc& c,
-                                                 CellSmem<NMAX, 1>& S, double gamma,
+                                                 CellSmem<NMAX, PREC>& S, double gamma,
                                                  double (*Mg)[NMAX + 1]) {
   const int n = c.n;
   g.sync();
