@@ -55,11 +55,6 @@ struct LaneGrid {
 
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
 
-// per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
-// (mixed precision): M and its Gauss-Jordan inverse in FP32.  Both keep the
-// FP64 reaction derivatives of the last setup (computed once per reaction, then
-// gathered into the rows of J; mixed precision reuses them in the refinement
-// residual).
 // reaction rates (RHS scratch) and d rate_r / d y_(reactant a) at the setup
 // point (mass action).  FP64 path: the rates live only inside a RHS call and
 // the derivatives only inside a setup, so they share storage; the mixed path
@@ -84,6 +79,11 @@ struct UsesDr {
   static constexpr bool value = PREC == 1 || NMAX >= 16;
 };
 
+// per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
+// (mixed precision): M and its Gauss-Jordan inverse in FP32.  Both keep the
+// FP64 reaction derivatives of the last setup (computed once per reaction, then
+// gathered into the rows of J; mixed precision reuses them in the refinement
+// residual).
 template <int NMAX, int PREC = 0>
 struct CellSmem : RateBufs<NMAX, PREC == 0, UsesDr<NMAX, PREC>::value> {
   static constexpr bool DR = UsesDr<NMAX, PREC>::value;
@@ -161,13 +161,19 @@ __device__ __forceinline__ double eta_from(double d2, float safety2, float e) {
   return (double)(1.0f / (exp2f(e * __log2f(x)) + 1.0e-6f));
 }
 
+// finiteness on the integer pipe: an IEEE double is inf or NaN exactly when
+// its exponent bits are all ones
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 template <int G, int NPL>
 __device__ __forceinline__ bool all_finite(const Grp<G>& g, int n, const double (&x)[NPL]) {
   bool bad = false;
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     const int i = g.rank + G * p;
-    if (i < n && !isfinite(x[p])) bad = true;
+    if (i < n && !finite_bits(x[p])) bad = true;
   }
   return !g.any(bad);
 }
@@ -215,19 +221,29 @@ __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem
       S.rates[r] = rate;
     }
     g.sync();
+    // one pass over the lane's species' incidence lists back to back (a
+    // running sum flushed at each species), so that the group waits for the
+    // longest total instead of the longest list of every slot
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      const int i = g.rank + G * p;
-      double acc = 0.0;
-      if (i < c.n) {
-        const int e1 = __ldg(c.inc_off + i + 1);
-        for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
-          const uint32_t v = __ldg(c.inc + e);
-          const double rt = S.rates[v >> 1];
-          acc = (v & 1u) ? acc + rt : acc - rt;
-        }
+    for (int p = 0; p < NPL; ++p) f[p] = 0.0;
+    int p = 0, e = 0, e1 = 0;
+    double acc = 0.0;
+    if (g.rank < c.n) { e = __ldg(c.inc_off + g.rank); e1 = __ldg(c.inc_off + g.rank + 1); }
+    else p = NPL;
+    while (p < NPL) {
+      if (e < e1) {
+        const uint32_t v = __ldg(c.inc + e);
+        const double rt = S.rates[v >> 1];
+        acc = (v & 1u) ? acc + rt : acc - rt;
+        ++e;
+      } else {
+        place(f, p, acc);
+        acc = 0.0;
+        ++p;
+        const int i = g.rank + G * p;
+        if (p < NPL && i < c.n) { e = __ldg(c.inc_off + i); e1 = __ldg(c.inc_off + i + 1); }
+        else p = NPL;
       }
-      f[p] = acc;
     }
   }
   g.sync();
