@@ -55,20 +55,20 @@ struct LaneGrid {
 
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
 
-// reaction rates (RHS scratch) and d rate_r / d y_(reactant a) at the setup
-// point (mass action).  FP64 path: the rates live only inside a RHS call and
+// reaction rates (RHS scratch) and dr[a][r] = d rate_r / d y_(reactant a) at
+// the setup point (mass action).  FP64 path: the rates live only inside a RHS call and
 // the derivatives only inside a setup, so they share storage; the mixed path
 // keeps the derivatives for the refinement residual of every Newton step.
 template <int NMAX, bool SHARE, bool DR>
 struct RateBufs {
   double rates[2 * NMAX];
-  double dr[DR ? 2 * NMAX : 1][4];
+  double dr[4][DR ? 2 * NMAX : 1];   // [reactant slot][reaction]: lanes over reactions hit distinct banks
 };
 template <int NMAX>
 struct RateBufs<NMAX, true, true> {
   union {
     double rates[2 * NMAX];
-    double dr[2 * NMAX][4];
+    double dr[4][2 * NMAX];
   };
 };
 

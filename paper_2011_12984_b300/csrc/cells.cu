@@ -732,6 +732,9 @@ constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W32, VAR_W16, VAR_H16, 2, 1, 0};
 // warps per SM each variant should keep resident (the shared-memory limit of
 // the largest ones): bounds the registers ptxas may use
 constexpr int VAR_MINB[NVAR] = {12, 12, 12, 8, 7, 12, 12, 12};
+// mixed precision: M in FP32 halves the shared memory, so registers bound the
+// residency of the two largest tilings
+constexpr int var_minb(int v, int prec) { return prec == 1 && (v == 3 || v == 4) ? 10 : VAR_MINB[v]; }
 static_assert(CLS_G[0] == VAR_G[0] && CLS_NMAX[4] == VAR_NMAX[4], "variants 0..4 are the class tilings");
 
 template <int V, int PREC>
@@ -743,7 +746,7 @@ struct VarSmem {
 // range [t0, t1) from `counter` until none is left.  PREC 0: FP64
 // factorisation; PREC 1: FP32 factorisation with FP64 refinement.
 template <int V, int PREC>
-__global__ void __launch_bounds__(32, VAR_MINB[V]) k_cells(const __grid_constant__ Params P, int t0, int t1,
+__global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_constant__ Params P, int t0, int t1,
                                                            unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;

@@ -53,7 +53,7 @@ __device__ __forceinline__ void reaction_derivs(const Grp<G>& g, const CellDesc&
           if (b != a && sb != 255u) d *= S.ybuf[sb];
         }
       }
-      S.dr[r][a] = d;
+      S.dr[a][r] = d;
     }
   }
   g.sync();
@@ -83,7 +83,7 @@ __device__ __forceinline__ double form_M32(const Grp<G>& g, const CellDesc& c, C
       for (int a = 0; a < 4; ++a) {
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
-        const float d = (float)S.dr[r][a];
+        const float d = (float)S.dr[a][r];
         row[s] = (v & 1u) ? row[s] + d : row[s] - d;
       }
     }
@@ -124,7 +124,7 @@ __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc
       for (int a = 0; a < 4; ++a) {
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
-        const double d = S.dr[r][a];
+        const double d = S.dr[a][r];
         row[s] = (v & 1u) ? row[s] + d : row[s] - d;
       }
     }
@@ -144,7 +144,7 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const uint32_t sp = (rc >> (8 * a)) & 255u;
-      if (sp != 255u) s = fma(S.dr[r][a], S.ybuf[sp], s);
+      if (sp != 255u) s = fma(S.dr[a][r], S.ybuf[sp], s);
     }
     S.rates[r] = s;
   }
