@@ -189,6 +189,37 @@ __device__ __forceinline__ void scatter_y(const Grp<G>& g, CellSmem<NMAX, PREC>&
   g.sync();
 }
 
+// out_i = sum of +vals[r] over the reactions r producing species i and -vals[r]
+// over those consuming it, in incidence-list (reaction) order.  One pass over
+// the lane's species' lists back to back (a running sum flushed at each
+// species), so that the group waits for the longest total, not for the
+// longest list of every slot.
+template <int G, int NPL>
+__device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& c, const double* vals,
+                                               double (&out)[NPL]) {
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) out[p] = 0.0;
+  int p = 0, e = 0, e1 = 0;
+  double acc = 0.0;
+  if (g.rank < c.n) { e = __ldg(c.inc_off + g.rank); e1 = __ldg(c.inc_off + g.rank + 1); }
+  else p = NPL;
+  while (p < NPL) {
+    if (e < e1) {
+      const uint32_t v = __ldg(c.inc + e);
+      const double rt = vals[v >> 1];
+      acc = (v & 1u) ? acc + rt : acc - rt;
+      ++e;
+    } else {
+      place(out, p, acc);
+      acc = 0.0;
+      ++p;
+      const int i = g.rank + G * p;
+      if (p < NPL && i < c.n) { e = __ldg(c.inc_off + i); e1 = __ldg(c.inc_off + i + 1); }
+      else p = NPL;
+    }
+  }
+}
+
 // ------------------------------------------------------------ right-hand side
 // f = f(y).  Mass action: rate_r = k_r prod_{s in R(r)} y_s, then each species
 // sums -rate over reactions consuming it and +rate over reactions producing
@@ -221,30 +252,7 @@ __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem
       S.rates[r] = rate;
     }
     g.sync();
-    // one pass over the lane's species' incidence lists back to back (a
-    // running sum flushed at each species), so that the group waits for the
-    // longest total instead of the longest list of every slot
-#pragma unroll
-    for (int p = 0; p < NPL; ++p) f[p] = 0.0;
-    int p = 0, e = 0, e1 = 0;
-    double acc = 0.0;
-    if (g.rank < c.n) { e = __ldg(c.inc_off + g.rank); e1 = __ldg(c.inc_off + g.rank + 1); }
-    else p = NPL;
-    while (p < NPL) {
-      if (e < e1) {
-        const uint32_t v = __ldg(c.inc + e);
-        const double rt = S.rates[v >> 1];
-        acc = (v & 1u) ? acc + rt : acc - rt;
-        ++e;
-      } else {
-        place(f, p, acc);
-        acc = 0.0;
-        ++p;
-        const int i = g.rank + G * p;
-        if (p < NPL && i < c.n) { e = __ldg(c.inc_off + i); e1 = __ldg(c.inc_off + i + 1); }
-        else p = NPL;
-      }
-    }
+    gather_species<G, NPL>(g, c, S.rates, f);
   }
   g.sync();
 }

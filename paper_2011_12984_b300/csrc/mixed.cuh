@@ -149,20 +149,7 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
     S.rates[r] = s;
   }
   g.sync();
-#pragma unroll
-  for (int p = 0; p < NPL; ++p) {
-    const int i = g.rank + G * p;
-    double acc = 0.0;
-    if (i < c.n) {
-      const int e1 = __ldg(c.inc_off + i + 1);
-      for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
-        const uint32_t v = __ldg(c.inc + e);
-        const double rt = S.rates[v >> 1];
-        acc = (v & 1u) ? acc + rt : acc - rt;
-      }
-    }
-    jx[p] = acc;
-  }
+  gather_species<G, NPL>(g, c, S.rates, jx);
   g.sync();
 }
 
