@@ -264,6 +264,7 @@ def robertson_workload(torch, bdfb, gen, reps=3):
     with bdfb.Integrator(p, rtol=1e-4, atol=1e-8, autotune=1) as I:
         t = timed_integrations(torch, I, y0, y, 40.0, reps)
         st = I.stats()
+        mp, _ = I.mapping()
     yh = y.cpu().numpy()
     yt, _, _ = oracle.integrate_cells(p, 0.0, 40.0, 1e-10, 1e-14, threads=oracle.host_threads())
     e = (np.abs(yh - yt) / (1e-4 * np.abs(yt) + 1e-8)).reshape(-1, 3).max(axis=1)
@@ -272,6 +273,7 @@ def robertson_workload(torch, bdfb, gen, reps=3):
     tc = time.perf_counter() - t0
     return {"workload": "Robertson 1000 cells, k scaled by log-U[0.5,2] per cell, t in [0,40], rtol 1e-4, atol 1e-8",
             "cells_per_s": 1000 / t, "ms": t * 1e3, "steps_per_cell": st["nsteps"] / 1000,
+            "lanes_per_cell_and_nmax": [int(mp[0][0]), int(mp[0][1])],
             "sum_y_max_dev": float(np.abs(yh.reshape(-1, 3).sum(axis=1) - 1.0).max()),
             "accuracy": {"cells_checked": 1000, "err_median": float(np.median(e)),
                          "err_p99": float(np.percentile(e, 99)), "err_max": float(e.max()),
@@ -363,9 +365,10 @@ def learned_workload(torch, bdfb, gen, ncell=1_000_000, ntrain_pairs=10_000_000,
     y0 = torch.from_numpy(prob.y0).cuda()
     y = torch.empty_like(y0)
     out = {}
-    for name, opts in (("plain_auto_tiles", {}), ("plain_warp_per_cell", {"mapping": 32}),
+    for name, opts in (("plain_autotuned_tiles", {}), ("plain_warp_per_cell", {"mapping": 32}),
                        ("learned_warp_per_cell", {"mapping": 32, "predictor": 1})):
-        with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=opts.get("mapping", 0)) as li:
+        with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=opts.get("mapping", 0),
+                             autotune=0 if opts.get("mapping") else 1) as li:
             if opts.get("predictor"):
                 li.load_mlp(pk)
                 li.set_option("predictor", 1)
@@ -546,7 +549,8 @@ def run_ours(args):
         configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
                    "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush)}
     variants = {"batched_fp64": value}
-    for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}), ("batched_mixed_fp32_lu", {"precision": 1})):
+    for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
+                       ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):
         with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, **opts) as vi:
             ts = []
             for i in range(2 + max(1, min(args.steps, 3))):
@@ -619,6 +623,10 @@ def run_part(args):
         out = grid_workload(torch, bdfb, gen, nx=args.grid_nx, tout=args.grid_tout, reps=max(1, args.steps))
     elif args.part == "nvector":
         out = nvector_bandwidth(torch, bdfb, reps=max(1, args.steps))
+    elif args.part == "robertson":
+        out = robertson_workload(torch, bdfb, gen, reps=max(1, args.steps))
+    elif args.part == "mixed54":
+        out = mixed54_workload(torch, bdfb, gen, reps=max(1, args.steps))
     else:
         out = learned_workload(torch, bdfb, gen, ncell=args.ncell, train_steps=20000)
     print(json.dumps({"part": args.part, **out}))
@@ -645,7 +653,7 @@ def main():
                     help="skip the learned-guess leg (1M-cell shared network, training on the GPU)")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
-    ap.add_argument("--part", default="all", choices=["all", "grid", "nvector", "learned"],
+    ap.add_argument("--part", default="all", choices=["all", "grid", "nvector", "learned", "robertson", "mixed54"],
                     help="run one leg alone and print its JSON (for profiling); all: the benchmark")
     ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
     ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid: end time")

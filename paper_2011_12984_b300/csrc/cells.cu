@@ -1575,26 +1575,36 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
       Pt.rec_x = nullptr;
       Pt.mlp = nullptr;
       if (cudaMemcpyAsync(tiles2, tiles.data(), nt * sizeof(TileDesc), cudaMemcpyHostToDevice, s) ||
-          cudaMemcpyAsync(tcells2, tcells.data(), tcells.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s) ||
-          cudaMemcpyAsync(st2, ctx->d_state, C * sizeof(CellState), cudaMemcpyDeviceToDevice, s) ||
-          cudaMemcpyAsync(z2, ctx->d_z, zbytes, cudaMemcpyDeviceToDevice, s) ||
-          cudaMemcpyAsync(acorp2, ctx->d_acorp, std::max<int64_t>(ctx->ny, 1) * sizeof(double),
-                          cudaMemcpyDeviceToDevice, s) ||
-          cudaMemsetAsync(cnt2, 0, (NVAR + 1) * sizeof(unsigned), s)) {
+          cudaMemcpyAsync(tcells2, tcells.data(), tcells.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) {
         fail(BDFB_CUDA_FAIL);
         break;
       }
       const cells_kernel_t kf = var_kernel(pr, v);
-      cudaEventRecord(e0, s);
-      kf<<<std::min(ctx->pgrid[pr][v], nt), 32, var_smem(pr, v), s>>>(
-          Pt, 0, nt, cnt2, pr == 1 ? ctx->d_fbws[v] : nullptr);
-      cudaEventRecord(e1, s);
-      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-        fail(BDFB_CUDA_FAIL);
-        break;
-      }
+      // short trials (small classes) are repeated and the fastest kept
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        if (cudaMemcpyAsync(st2, ctx->d_state, C * sizeof(CellState), cudaMemcpyDeviceToDevice, s) ||
+            cudaMemcpyAsync(z2, ctx->d_z, zbytes, cudaMemcpyDeviceToDevice, s) ||
+            cudaMemcpyAsync(acorp2, ctx->d_acorp, std::max<int64_t>(ctx->ny, 1) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s) ||
+            cudaMemsetAsync(cnt2, 0, (NVAR + 1) * sizeof(unsigned), s)) {
+          fail(BDFB_CUDA_FAIL);
+          break;
+        }
+        cudaEventRecord(e0, s);
+        kf<<<std::min(ctx->pgrid[pr][v], nt), 32, var_smem(pr, v), s>>>(
+            Pt, 0, nt, cnt2, pr == 1 ? ctx->d_fbws[v] : nullptr);
+        cudaEventRecord(e1, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+          fail(BDFB_CUDA_FAIL);
+          break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = rep == 0 ? t : std::min(ms, t);
+        if (ms >= 20.f) break;
+      }
+      if (rc) break;
       ctx->tune_ms[cl][v] = ms;
       if (v == cl) best = ms;
       else if (ms < 0.97f * best) { best = ms; ctx->tuned_var[cl] = v; }
