@@ -190,8 +190,8 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              (tolerances, options, schedule) recaptures
  *  "autotune"  1 = on the next integrate, and again after a precision change,
  *              time every kernel variant (bdfb_get_mapping) whose NMAX covers
- *              a size class without more than doubling it on a sample of that
- *              class (first 16384 cells, current state to
+ *              a size class (classes with one such variant are not timed) on
+ *              a sample of that class (first 16384 cells, current state to
  *              tout, on scratch copies: the context's state is untouched)
  *              and run each class on the fastest (another variant must beat
  *              the class's own by 3%); mapping 0 only.  Variants differ in

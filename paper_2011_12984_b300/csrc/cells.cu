@@ -1548,11 +1548,12 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
     for (int v = 0; v < NVAR; ++v) ctx->tune_ms[cl][v] = 0.f;
     if (members[cl].empty()) continue;
     // the class's own tiling first, then every other variant whose NMAX
-    // covers the class without more than doubling it
+    // covers the class (small workloads can favour more lanes per cell:
+    // more warps in flight); nothing to time when there is no alternative
     std::vector<int> cand = {cl};
     for (int v = 0; v < NVAR; ++v)
-      if (v != cl && var_kernel(pr, v) && VAR_NMAX[v] >= CLS_NMAX[cl] && VAR_NMAX[v] <= 2 * CLS_NMAX[cl])
-        cand.push_back(v);
+      if (v != cl && var_kernel(pr, v) && VAR_NMAX[v] >= CLS_NMAX[cl]) cand.push_back(v);
+    if (cand.size() == 1) continue;
     float best = 0.f;
     for (int v : cand) {
       if (pr == 1 && ensure_fbws(ctx, v)) { fail(BDFB_MEM_FAIL); break; }

@@ -36,7 +36,9 @@ def test_autotuned_mapping_accuracy(precision):
             continue
         assert NMAX >= nmax[c] or (NMAX == 16 and c <= 2)
         assert G in (1, 4, 8, 16, 32)
-        assert ms[c, c] > 0                     # the class's own variant was timed
+        # the class's own variant was timed, unless it is the only one that
+        # holds the class (the 56-species tiling)
+        assert ms[c, c] > 0 or c == 4
     assert mp[:, 2].sum() == p.ncell
     s0 = np.add.reduceat(p.y0, p.y_off[:-1])
     assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
