@@ -205,12 +205,13 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              the local error test itself (E_q |guess| > 1) is dropped;
  *              when the Newton solve from a guess fails, or converges to a
  *              correction that fails the local error test, it is repeated
- *              from zero.  Both count in nguess_fallback, not as failures.  The first Newton
- *              step from a nonzero guess skips the stale-matrix scaling so
- *              that linear invariants (sum y for mass action) are kept as
- *              with a zero start, and its convergence test uses the rate
- *              carried over from earlier solves only when the guess lies
- *              closer to the new iterate than zero does (else rate 1).
+ *              from zero.  Both count in nguess_fallback, not as failures.
+ *              The first Newton step from a nonzero guess skips the
+ *              stale-matrix scaling so that linear invariants (sum y for
+ *              mass action) are kept as with a zero start, and its
+ *              convergence test uses the rate carried over from earlier
+ *              solves only when the guess lies closer to the new iterate
+ *              than zero does (else rate 1).
  * "mapping" 32 runs every cell on the smallest one-warp-per-cell kernel all
  * cells fit (NMAX 16 — the predictor's kernel, FP64 only — 32 or 56). */
 int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);
@@ -243,8 +244,9 @@ int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms);
  * Not part of the paper: a 12 -> 64 -> 64 -> 10 ReLU network predicts the
  * Newton correction Delta of a step, in error-weight units (Delta_i ewt_i),
  * from the features x = ((log10 max(y_pred_i, 1e-20) + 10) / 10 for
- * i = 0..9 (zero past n), (log10|h| + 8) / 4, gamma / h).  Parameters: 5642 FP32 values, W1[64][12], b1[64], W2[64][64],
- * b2[64], W3[10][64], b3[10] (W[out][in]).  Evaluation and training run
+ * i = 0..9 (zero past n), (log10|h| + 8) / 4, gamma / h).  Parameters:
+ * 5642 FP32 values, W1[64][12], b1[64], W2[64][64], b2[64], W3[10][64],
+ * b3[10] (W[out][in]).  Evaluation and training run
  * on BF16 tensor-core MMAs with FP32 accumulation; the master weights and
  * Adam moments stay FP32.  X is [rows][12], T and Y [rows][10], row-major
  * FP32; every pointer is device memory owned by the caller. */
