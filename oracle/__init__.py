@@ -47,7 +47,8 @@ class Cells(C.Structure):
 
 
 class Bruss(C.Structure):
-    _fields_ = [("nx", C.c_int), ("A", _d), ("B", _d), ("eps", _d), ("D", _d)]
+    _fields_ = [("nx", C.c_int), ("A", _d), ("B", _d), ("eps", _d), ("D", _d), ("dim", C.c_int),
+                ("c", _d), ("len", _d)]
 
 
 def lib():
@@ -79,6 +80,47 @@ def _ptrs(vs):
 
 
 # ---------------------------------------------------------------- vectors
+def scale(c, x):
+    x = _f64(x)
+    z = np.empty_like(x)
+    lib().or_scale(_i64(x.size), _d(c), _p(x), _p(z))
+    return z
+
+
+def const(c, n):
+    z = np.empty(n)
+    lib().or_const(_i64(n), _d(c), _p(z))
+    return z
+
+
+def abs_(x):
+    x = _f64(x)
+    z = np.empty_like(x)
+    lib().or_abs(_i64(x.size), _p(x), _p(z))
+    return z
+
+
+def inv(x):
+    x = _f64(x)
+    z = np.empty_like(x)
+    lib().or_inv(_i64(x.size), _p(x), _p(z))
+    return z
+
+
+def add_const(x, b):
+    x = _f64(x)
+    z = np.empty_like(x)
+    lib().or_add_const(_i64(x.size), _p(x), _d(b), _p(z))
+    return z
+
+
+def error_weights(rtol, atol, y):
+    y = _f64(y)
+    w = np.empty_like(y)
+    lib().or_error_weights(_i64(y.size), _d(rtol), _d(atol), _p(y), _p(w))
+    return w
+
+
 def linear_sum(a, x, b, y):
     x, y = _f64(x), _f64(y)
     z = np.empty_like(x)
@@ -254,7 +296,11 @@ def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threa
 
 
 def bruss_struct(p):
-    return Bruss(p.nx, p.A, p.B, p.eps, p.D)
+    """the 3-D reaction-diffusion grid, or the 1-D advection line (p.kind ==
+    "brusselator1d": speed p.c on [0, p.length))"""
+    if getattr(p, "kind", "") == "brusselator1d":
+        return Bruss(p.nx, p.A, p.B, p.eps, 0.0, 1, p.c, p.length)
+    return Bruss(p.nx, p.A, p.B, p.eps, p.D, 3, 0.0, 1.0)
 
 
 def bruss_rhs(p, y):

@@ -23,6 +23,28 @@ static void nadd(nsum* a, double x) {
 static double nget(const nsum* a) { return a->s + a->c; }
 
 /* z = a x + b y */
+/* the elementwise support operations of the vector class (Sec. 4): one
+ * correctly rounded IEEE operation per element (two for the error weights) */
+void or_scale(int64_t n, double c, const double* x, double* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = c * x[i];
+}
+void or_const(int64_t n, double c, double* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = c;
+}
+void or_abs(int64_t n, const double* x, double* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = fabs(x[i]);
+}
+void or_inv(int64_t n, const double* x, double* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = 1.0 / x[i];
+}
+void or_add_const(int64_t n, const double* x, double b, double* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = x[i] + b;
+}
+/* error weights ewt_i = 1 / (rtol |y_i| + atol) */
+void or_error_weights(int64_t n, double rtol, double atol, const double* y, double* w) {
+  for (int64_t i = 0; i < n; ++i) w[i] = 1.0 / (rtol * fabs(y[i]) + atol);
+}
+
 void or_linear_sum(int64_t n, double a, const double* x, double b, const double* y, double* z) {
   for (int64_t i = 0; i < n; ++i) z[i] = a * x[i] + b * y[i];
 }

@@ -33,6 +33,12 @@ enum {
 #define OR_QMAX 5
 
 /* ---------------- vector operations (Sec. 4: streaming / reduction) ---- */
+void or_scale(int64_t n, double c, const double* x, double* z);
+void or_const(int64_t n, double c, double* z);
+void or_abs(int64_t n, const double* x, double* z);
+void or_inv(int64_t n, const double* x, double* z);
+void or_add_const(int64_t n, const double* x, double b, double* z);
+void or_error_weights(int64_t n, double rtol, double atol, const double* y, double* w);
 void or_linear_sum(int64_t n, double a, const double* x, double b, const double* y, double* z);
 void or_linear_combination(int64_t n, int nv, const double* c, const double* const* x, double* z);
 void or_scale_add_multi(int64_t n, int nv, const double* a, const double* x,
@@ -131,10 +137,16 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
                         const double* y0, double tout, const or_options* opt, double* yout,
                         int64_t* stats, int64_t* ntrace);
 
-/* ---------------- Brusselator reaction-diffusion (grouped, GMRES) -------- */
+/* ---------------- Brusselator grids (grouped, GMRES) -------------------- */
+/* dim 3: reaction-diffusion on a periodic nx^3 grid over [0,1)^3, 7-point
+ * Laplacian with coefficient D.  dim 1: the paper's demo (Sec. 6),
+ * advection-reaction on a periodic line of nx points over [0, len) with
+ * first-order upwind differences for speed c.  Species-major u | v | w. */
 typedef struct {
   int nx;
   double A, B, eps, D;
+  int dim;
+  double c, len;
 } or_bruss;
 void or_bruss_rhs(const or_bruss* p, const double* y, double* f);
 void or_bruss_jv(const or_bruss* p, const double* y, const double* v, double* jv);

@@ -223,10 +223,13 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Brusselator reaction-diffusion on a periodic nx^3 grid (species-major)    */
-/* u' = D lap u + A - (w+1) u + v u^2                                        */
-/* v' = D lap v + w u - v u^2                                                */
-/* w' = D lap w + (B - w)/eps - w u                                          */
+/* Brusselator grids (species-major u | v | w), reaction terms of Sec. 6     */
+/* u' = T u + A - (w+1) u + v u^2                                            */
+/* v' = T v + w u - v u^2                                                    */
+/* w' = T w + (B - w)/eps - w u                                              */
+/* with the transport T = D lap on the periodic nx^3 grid (dim 3), or the    */
+/* demo's advection T = -c d/dx by first-order upwind differences on the     */
+/* periodic line of nx points (dim 1, Sec. 6)                                */
 /* ------------------------------------------------------------------------ */
 static int64_t wrapi(int64_t i, int64_t n) { return (i + n) % n; }
 
@@ -240,6 +243,27 @@ static double lap(const or_bruss* p, const double* a, int64_t i, int64_t j, int6
   return (s - 6.0 * c) / (dx * dx);
 }
 
+static int64_t bruss_npts(const or_bruss* p) {
+  return p->dim == 1 ? (int64_t)p->nx : (int64_t)p->nx * p->nx * p->nx;
+}
+
+/* -c da/dx at point q of the line, upwind: backward difference for c >= 0,
+ * forward difference for c < 0; dx = len / nx */
+static double advect(const or_bruss* p, const double* a, int64_t q) {
+  int64_t n = p->nx;
+  double dx = p->len / (double)n;
+  if (p->c >= 0.0) return -p->c * (a[q] - a[wrapi(q - 1, n)]) / dx;
+  return -p->c * (a[wrapi(q + 1, n)] - a[q]) / dx;
+}
+
+/* the transport term of one species' field a at point q */
+static double transport(const or_bruss* p, const double* a, int64_t q) {
+  if (p->dim == 1) return advect(p, a, q);
+  int64_t n = p->nx;
+  int64_t i = q / (n * n), j = (q / n) % n, k = q % n;
+  return p->D * lap(p, a, i, j, k);
+}
+
 /* reaction Jacobian of one point, row-major 3x3 */
 static void bruss_jr(const or_bruss* p, double u, double v, double w, double* J) {
   J[0] = -(w + 1.0) + 2.0 * u * v;  J[1] = u * u;   J[2] = -u;
@@ -248,33 +272,27 @@ static void bruss_jr(const or_bruss* p, double u, double v, double w, double* J)
 }
 
 void or_bruss_rhs(const or_bruss* p, const double* y, double* f) {
-  int64_t n = p->nx, np = n * n * n;
+  int64_t np = bruss_npts(p);
   const double *U = y, *V = y + np, *W = y + 2 * np;
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = 0; j < n; ++j)
-      for (int64_t k = 0; k < n; ++k) {
-        int64_t q = (i * n + j) * n + k;
-        double u = U[q], v = V[q], w = W[q];
-        f[q] = p->D * lap(p, U, i, j, k) + p->A - (w + 1.0) * u + v * u * u;
-        f[np + q] = p->D * lap(p, V, i, j, k) + w * u - v * u * u;
-        f[2 * np + q] = p->D * lap(p, W, i, j, k) + (p->B - w) / p->eps - w * u;
-      }
+  for (int64_t q = 0; q < np; ++q) {
+    double u = U[q], v = V[q], w = W[q];
+    f[q] = transport(p, U, q) + p->A - (w + 1.0) * u + v * u * u;
+    f[np + q] = transport(p, V, q) + w * u - v * u * u;
+    f[2 * np + q] = transport(p, W, q) + (p->B - w) / p->eps - w * u;
+  }
 }
 
 void or_bruss_jv(const or_bruss* p, const double* y, const double* v, double* jv) {
-  int64_t n = p->nx, np = n * n * n;
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = 0; j < n; ++j)
-      for (int64_t k = 0; k < n; ++k) {
-        int64_t q = (i * n + j) * n + k;
-        double J[9];
-        bruss_jr(p, y[q], y[np + q], y[2 * np + q], J);
-        for (int s = 0; s < 3; ++s) {
-          double acc = p->D * lap(p, v + s * np, i, j, k);
-          for (int t = 0; t < 3; ++t) acc += J[s * 3 + t] * v[t * np + q];
-          jv[s * np + q] = acc;
-        }
-      }
+  int64_t np = bruss_npts(p);
+  for (int64_t q = 0; q < np; ++q) {
+    double J[9];
+    bruss_jr(p, y[q], y[np + q], y[2 * np + q], J);
+    for (int s = 0; s < 3; ++s) {
+      double acc = transport(p, v + s * np, q);
+      for (int t = 0; t < 3; ++t) acc += J[s * 3 + t] * v[t * np + q];
+      jv[s * np + q] = acc;
+    }
+  }
 }
 
 #define GM_MAX 32
@@ -289,7 +307,7 @@ typedef struct {
 } bruss_user;
 
 static void bruss_psolve(bruss_user* B, double* v) {
-  int64_t np = (int64_t)B->p->nx * B->p->nx * B->p->nx;
+  int64_t np = bruss_npts(B->p);
   for (int64_t q = 0; q < np; ++q) {
     double x[3] = {v[q], v[np + q], v[2 * np + q]};
     or_lu_solve(3, B->plu + 9 * q, B->ppiv + 3 * q, x);
@@ -307,7 +325,7 @@ static int bruss_rhs_cb(void* u, double t, const double* y, double* f) {
 static int bruss_lsetup_cb(void* u, double t, const double* y, double gamma) {
   (void)t;
   bruss_user* B = (bruss_user*)u;
-  int64_t np = (int64_t)B->p->nx * B->p->nx * B->p->nx;
+  int64_t np = bruss_npts(B->p);
   for (int64_t q = 0; q < np; ++q) {
     double J[9];
     bruss_jr(B->p, y[q], y[np + q], y[2 * np + q], J);
@@ -325,7 +343,7 @@ static int bruss_lsetup_cb(void* u, double t, const double* y, double gamma) {
 static int gmres_core(bruss_user* B, const double* y, double gamma, const double* ewt,
                       double tol, double* b, double* resnorm, int* converged) {
   const or_bruss* p = B->p;
-  int64_t np = (int64_t)p->nx * p->nx * p->nx, N = 3 * np;
+  int64_t np = bruss_npts(p), N = 3 * np;
   int maxl = B->maxl;
   double sqrtN = sqrt((double)N);
   double* V = B->V;        /* (maxl+1) x N */
@@ -421,7 +439,7 @@ static int bruss_lsolve_cb(void* u, double t, const double* ycur, double gamma,
 }
 
 static int bruss_alloc(bruss_user* B, const or_bruss* p, int maxl) {
-  int64_t np = (int64_t)p->nx * p->nx * p->nx, N = 3 * np;
+  int64_t np = bruss_npts(p), N = 3 * np;
   memset(B, 0, sizeof *B);
   B->p = p;
   B->maxl = maxl;
@@ -451,7 +469,7 @@ int or_bruss_gmres(const or_bruss* p, const double* y, double gamma, const doubl
 int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double tout,
                        double rtol, double atol, int maxl, int64_t mxstep,
                        double* yout, int64_t* stats) {
-  int64_t N = 3 * (int64_t)p->nx * p->nx * p->nx;
+  int64_t N = 3 * bruss_npts(p);
   bruss_user B;
   if (maxl < 1 || maxl > GM_MAX) return OR_ILL_INPUT;
   if (bruss_alloc(&B, p, maxl)) { bruss_free(&B); return OR_MEM_FAIL; }

@@ -24,8 +24,12 @@ Sec. 6):
   species (all stoichiometric coefficients 1, so the total concentration is
   conserved), rate constants log-uniform in [1e-2, 1e8], initial
   concentrations Dirichlet(1, ..., 1).
+* ``mass_action_shared`` - one random network shared by all cells, initial
+  states drawn per cell.
 * ``brusselator3d`` - u, v, w on a periodic n^3 grid, initial state the
   reaction steady state times (1 + 0.01 U[-1, 1]).
+* ``brusselator1d`` - the demonstration problem itself: u, v, w advected on a
+  periodic line, the paper's Gaussian-bump initial state (no random draws).
 """
 from __future__ import annotations
 
@@ -311,3 +315,34 @@ def brusselator3d(nx: int, seed: int = DEFAULT_SEED, A: float = 1.0, B: float = 
         for s in range(3):
             y0[s * npts + p0: s * npts + p0 + len(p)] = ss[s] * (1.0 + noise * (2.0 * uniform(keys, s) - 1.0))
     return Brusselator3D(nx=nx, A=A, B=B, eps=eps, D=D, y0=y0)
+
+
+@dataclass
+class Brusselator1D:
+    """The paper's demonstration problem (Sec. 6): u, v, w advected with speed
+    ``c`` on a periodic line of ``nx`` points over [0, length), stored
+    species-major (``y0[s * nx + i]``, point i at x = i length / nx)."""
+    nx: int
+    A: float
+    B: float
+    eps: float
+    c: float
+    length: float
+    y0: np.ndarray = field(repr=False)
+    kind: str = "brusselator1d"
+
+    @property
+    def npts(self) -> int:
+        return self.nx
+
+
+def brusselator1d(nx: int, length: float = 10.0, A: float = 1.0, B: float = 3.5, eps: float = 5.0e-6,
+                  c: float = 0.01, alpha: float = 0.1) -> Brusselator1D:
+    """The demo's initial state (Sec. 6): u = A + p, v = B / A + p, w = 3 + p
+    with the Gaussian bump p(x) = alpha exp(-(x - mu)^2 / (2 sigma^2)),
+    mu = length / 2, sigma = length / 4 (no random draws)."""
+    x = np.arange(nx, dtype=np.float64) * (length / nx)
+    mu, sigma = 0.5 * length, 0.25 * length
+    p = alpha * np.exp(-((x - mu) ** 2) / (2.0 * sigma * sigma))
+    y0 = np.concatenate([A + p, B / A + p, 3.0 + p])
+    return Brusselator1D(nx=nx, A=A, B=B, eps=eps, c=c, length=length, y0=y0)

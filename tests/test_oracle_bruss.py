@@ -1,4 +1,5 @@
-"""Pins of the oracle's Brusselator reaction-diffusion system and GMRES.
+"""Pins of the oracle's Brusselator systems (the 3-D reaction-diffusion grid
+and the 1-D advection-reaction demo of Sec. 6) and GMRES.
 
 * the reaction steady state u* = A, w* = B/(1 + eps A), v* = w*/A stays put;
 * with u = w = 0 and A = B = 0 the v field diffuses freely: a single Fourier
@@ -6,7 +7,11 @@
   -(4/dx^2) sum_d sin^2(pi k_d / n), so f, J v and the integrated decay
   exp(D lambda t) are known in closed form;
 * J v agrees with central differences of f;
-* GMRES with as many Krylov vectors as unknowns equals the dense solve.
+* GMRES with as many Krylov vectors as unknowns equals the dense solve;
+* 1-D demo: the paper's initial state, a uniform steady state stays put
+  (upwind differences of a constant vanish), a Fourier mode of v under pure
+  advection follows the exact solution of the upwind-discretised system for
+  either sign of c, J v and full-Krylov GMRES as above.
 """
 import numpy as np
 
@@ -100,3 +105,71 @@ def test_fast_species_reaches_its_slow_manifold():
     w0 = p.y0.reshape(3, -1)[2]
     assert np.max(np.abs(w0 - p.B / (1.0 + p.eps * p.y0.reshape(3, -1)[0])) / w0) > 1e-3
     assert st[6] > 0        # GMRES iterations were used
+
+
+# ------------------------------------------------ the 1-D advection demo (Sec. 6)
+def advect_mode(nx, k, c, length, t):
+    """exact solution of the upwind-discretised advection v' = -c D v on the
+    periodic line for v(0) = cos(theta j): Re(exp(lambda t) exp(i theta j))
+    with theta = 2 pi k / nx and lambda = -(c/dx)(1 - e^{-i theta}) for
+    c >= 0 (backward difference), -(c/dx)(e^{i theta} - 1) for c < 0"""
+    dx = length / nx
+    th = 2 * np.pi * k / nx
+    lam1 = -(c / dx) * (1 - np.exp(-1j * th)) if c >= 0 else -(c / dx) * (np.exp(1j * th) - 1)
+    j = np.arange(nx)
+    return np.real(np.exp(lam1 * t) * np.exp(1j * th * j)), lam1
+
+
+def test_1d_demo_initial_state():
+    p = gen.brusselator1d(40, length=10.0)
+    x = np.arange(40) * 0.25
+    bump = 0.1 * np.exp(-((x - 5.0) ** 2) / (2 * 2.5 ** 2))
+    assert np.allclose(p.y0[:40], 1.0 + bump, rtol=0, atol=1e-15)
+    assert np.allclose(p.y0[40:80], 3.5 + bump, rtol=0, atol=1e-15)
+    assert np.allclose(p.y0[80:], 3.0 + bump, rtol=0, atol=1e-15)
+
+
+def test_1d_uniform_steady_state_stays():
+    nx = 64
+    u, v, w = gen.brusselator_steady_state(1.0, 3.5, 5e-6)
+    y0 = np.concatenate([np.full(nx, u), np.full(nx, v), np.full(nx, w)])
+    p = gen.Brusselator1D(nx=nx, A=1.0, B=3.5, eps=5e-6, c=0.01, length=10.0, y0=y0)
+    f = oracle.bruss_rhs(p, y0)
+    assert np.max(np.abs(f[:2 * nx])) <= 1e-13          # advection of a uniform field is exactly 0
+    ret, y, st = oracle.bruss_integrate(p, 0.0, 1.0, 1e-6, 1e-10)
+    assert ret == 0 and np.max(np.abs(y - y0) / y0) <= 1e-12
+
+
+def test_1d_fourier_mode_of_pure_advection():
+    for c in (0.01, -0.02):
+        nx, k, length = 32, 3, 10.0
+        y0 = np.zeros(3 * nx)
+        y0[nx:2 * nx] = np.cos(2 * np.pi * k * np.arange(nx) / nx)
+        p = gen.Brusselator1D(nx=nx, A=0.0, B=0.0, eps=5e-6, c=c, length=length, y0=y0)
+        f = oracle.bruss_rhs(p, y0)
+        dvdt, lam1 = advect_mode(nx, k, c, length, 0.0)
+        exact_f = np.real(lam1 * np.exp(2j * np.pi * k * np.arange(nx) / nx))
+        assert np.max(np.abs(f[nx:2 * nx] - exact_f)) <= 1e-13 * abs(lam1)
+        assert np.max(np.abs(f[:nx])) == 0.0 and np.max(np.abs(f[2 * nx:])) == 0.0
+        tout = 1.0 / abs(lam1)
+        ret, y, st = oracle.bruss_integrate(p, 0.0, tout, 1e-8, 1e-12, y0=y0)
+        assert ret == 0
+        exact, _ = advect_mode(nx, k, c, length, tout)
+        assert np.max(np.abs(y[nx:2 * nx] - exact)) <= 20 * 1e-8
+
+
+def test_1d_jv_and_full_krylov_gmres():
+    p = gen.brusselator1d(10, length=10.0)             # 30 unknowns
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(p.y0.size)
+    h = 1e-6
+    fd = (oracle.bruss_rhs(p, p.y0 + h * v) - oracle.bruss_rhs(p, p.y0 - h * v)) / (2 * h)
+    jv = oracle.bruss_jv(p, p.y0, v)
+    assert np.max(np.abs(jv - fd)) <= 1e-6 * np.max(np.abs(jv))
+    N = p.y0.size
+    gamma = 2e-5
+    J = np.column_stack([oracle.bruss_jv(p, p.y0, e) for e in np.eye(N)])
+    M = np.eye(N) - gamma * J
+    b = rng.standard_normal(N)
+    x, it, rn = oracle.bruss_gmres(p, p.y0, gamma, np.ones(N), 0.0, N, b)
+    assert np.max(np.abs(M @ x - b)) <= 1e-10 * np.max(np.abs(b))

@@ -91,3 +91,21 @@ def test_lu_backward_error(n):
     r = M @ x - b
     eta = np.max(np.abs(r)) / (np.max(np.sum(np.abs(M), axis=1)) * np.max(np.abs(x)) + np.max(np.abs(b)))
     assert eta <= 1e-14
+
+
+def test_support_ops_fixed_points():
+    """Values the definitions fix exactly: scaling by 1 and 0, constants,
+    |x| of signed values, 1/x of powers of two, x + 0, and error weights of
+    y = 0 (1/atol) and of powers of two with atol = 0.5 ulp-free choices."""
+    x = np.array([-3.5, -0.0, 0.0, 2.0, 1e300, -1e-300])
+    assert np.array_equal(oracle.scale(1.0, x), x)
+    assert np.all(oracle.scale(0.0, x[np.isfinite(x)]) == 0.0)
+    assert np.array_equal(oracle.const(7.25, 5), np.full(5, 7.25))
+    assert np.array_equal(oracle.abs_(x), np.array([3.5, 0.0, 0.0, 2.0, 1e300, 1e-300]))
+    p2 = 2.0 ** np.arange(-20, 21)
+    assert np.array_equal(oracle.inv(p2), 2.0 ** -np.arange(-20, 21))
+    assert np.array_equal(oracle.inv(-p2), -(2.0 ** -np.arange(-20, 21)))
+    assert np.array_equal(oracle.add_const(x[:4], 0.0), x[:4] + 0.0)
+    assert np.array_equal(oracle.add_const(np.array([1.0, 2.0]), 0.5), np.array([1.5, 2.5]))
+    w = oracle.error_weights(0.25, 0.5, np.array([0.0, 2.0, -2.0, 6.0]))
+    assert np.array_equal(w, np.array([2.0, 1.0, 1.0, 0.5]))      # 1/(0.25*|y| + 0.5)
