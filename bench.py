@@ -418,6 +418,35 @@ def slowest_rank_time(torch, dist, t, device):
     return float(tt.item())
 
 
+def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps=1):
+    """The paper's demonstration problem (Sec. 6) as one coupled system:
+    Brusselator reactions (A = 1, B = 3.5, eps = 5e-6) advected with c = 0.01
+    on a periodic line of nx points over [0, length) by first-order upwind
+    differences, the paper's Gaussian-bump initial state, t in [0, tout];
+    BDF with Newton + GMRES(5), 3x3 reaction blocks as preconditioner
+    (advection implicit in the Newton operator)."""
+    p = gen.brusselator1d(nx, length=length)
+    y0 = torch.from_numpy(p.y0).cuda()
+    y = torch.empty_like(y0)
+    ts = []
+    with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5) as li:
+        for _ in range(reps + 1):
+            li.init(0.0, y0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = li.integrate(tout, y)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            if r != 0:
+                raise RuntimeError(f"line integrate returned {r}")
+        gs = li.cell_stats()[0]
+    t = min(ts[1:])
+    return {"workload": f"Brusselator 1-D advection-reaction (the paper's demo) {nx} points x 3, length {length}, "
+                        f"c 0.01, A 1, B 3.5, eps 5e-6, t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 blocks",
+            "points_per_s": nx / t, "seconds": t, "steps": int(gs[0]), "newton_iters": int(gs[3]),
+            "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
+
+
 def run_reference(args):
     """reference arm: the CPU oracle as it stands, on the host cores"""
     ws, rank, _ = dist_env()
@@ -547,7 +576,8 @@ def run_ours(args):
     configs = None
     if not args.no_configs:
         configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
-                   "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush)}
+                   "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush),
+                   "advection_line_1e7": line_workload(torch, bdfb, gen)}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
                        ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):
@@ -627,6 +657,8 @@ def run_part(args):
         out = robertson_workload(torch, bdfb, gen, reps=max(1, args.steps))
     elif args.part == "mixed54":
         out = mixed54_workload(torch, bdfb, gen, reps=max(1, args.steps))
+    elif args.part == "line":
+        out = line_workload(torch, bdfb, gen, nx=args.line_nx, tout=args.grid_tout, reps=max(1, args.steps))
     else:
         out = learned_workload(torch, bdfb, gen, ncell=args.ncell, train_steps=20000)
     print(json.dumps({"part": args.part, **out}))
@@ -648,15 +680,17 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="run each size class on its own tiling instead of the autotuned one")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the Robertson and 262144 x 54 mixed-precision legs")
+                    help="skip the Robertson, 262144 x 54 mixed-precision and 1-D demo legs")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-guess leg (1M-cell shared network, training on the GPU)")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
-    ap.add_argument("--part", default="all", choices=["all", "grid", "nvector", "learned", "robertson", "mixed54"],
+    ap.add_argument("--part", default="all",
+                    choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line"],
                     help="run one leg alone and print its JSON (for profiling); all: the benchmark")
     ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
-    ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid: end time")
+    ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid / line: end time")
+    ap.add_argument("--line-nx", type=int, default=10_000_000, help="--part line: points on the line")
     args = ap.parse_args()
     globals()["NCELL"] = args.ncell
     if args.sizes:

@@ -52,7 +52,12 @@ enum {
 };
 
 typedef enum { BDFB_MEM_HOST = 0, BDFB_MEM_DEVICE = 1 } bdfb_mem;
-typedef enum { BDFB_ROBERTSON = 0, BDFB_MASSACTION = 1, BDFB_BRUSSELATOR3D = 2 } bdfb_kind;
+typedef enum {
+  BDFB_ROBERTSON = 0,
+  BDFB_MASSACTION = 1,
+  BDFB_BRUSSELATOR3D = 2,
+  BDFB_BRUSSELATOR1D = 3
+} bdfb_kind;
 
 const char* bdfb_strerror(int code);
 /* library version as an integer (major * 10000 + minor * 100 + patch) */
@@ -69,6 +74,15 @@ int bdfb_version(void);
 /* z = a x + b y  (N_VLinearSum; z may alias x or y) */
 int bdfb_nv_linear_sum(int64_t n, double a, const double* x, double b, const double* y,
                        double* z, void* stream);
+/* the support operations: z = c x (N_VScale), z = c (N_VConst), z = |x|
+ * (N_VAbs), z = 1 / x (N_VInv), z = x + b (N_VAddConst), and the fused error
+ * weights w = 1 / (rtol |y| + atol) (rtol >= 0, atol > 0); z may alias x */
+int bdfb_nv_scale(int64_t n, double c, const double* x, double* z, void* stream);
+int bdfb_nv_const(int64_t n, double c, double* z, void* stream);
+int bdfb_nv_abs(int64_t n, const double* x, double* z, void* stream);
+int bdfb_nv_inv(int64_t n, const double* x, double* z, void* stream);
+int bdfb_nv_add_const(int64_t n, const double* x, double b, double* z, void* stream);
+int bdfb_nv_error_weights(int64_t n, double rtol, double atol, const double* y, double* w, void* stream);
 /* z = sum_{j<nv} c[j] x[j]; c is a host array, x a host array of nv device
  * pointers; 1 <= nv <= 16  (N_VLinearCombination; z may alias x[0]) */
 int bdfb_nv_linear_combination(int64_t n, int nv, const double* c, const double* const* x,
@@ -143,6 +157,12 @@ int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b
  *   nx + l] for species s = u, v, w.  Integrated with one shared step size,
  *   global WRMS norms, Newton + GMRES (option "maxl", default 5, at most 16)
  *   left-preconditioned by the 3x3 reaction blocks; control on the host.
+ * kind BDFB_BRUSSELATOR1D: the demonstration problem of Sec. 6 as one
+ *   coupled system: the same reaction terms with advection -c d/dx (first-
+ *   order upwind differences) on a periodic line of nx points over
+ *   [0, len); k = {A, B, eps, c, len, nx} (6 doubles); ncell = nx; y is
+ *   species-major, y[s nx + i] at x = i len / nx.  Integrated like
+ *   BDFB_BRUSSELATOR3D (advection implicit inside the Newton operator).
  * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
  * arrays live; bdfb_create copies everything it needs, so the caller may
  * free its arrays when bdfb_create returns. */

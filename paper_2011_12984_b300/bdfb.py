@@ -37,6 +37,7 @@ MEM_DEVICE = 1
 ROBERTSON = 0
 MASSACTION = 1
 BRUSSELATOR3D = 2
+BRUSSELATOR1D = 3
 
 _vp = C.c_void_p
 _i64 = C.c_int64
@@ -70,6 +71,12 @@ def _sig(name, res, args):
 _sig("bdfb_strerror", C.c_char_p, [C.c_int])
 _sig("bdfb_version", C.c_int, [])
 _sig("bdfb_nv_linear_sum", C.c_int, [_i64, _d, _vp, _d, _vp, _vp, _vp])
+_sig("bdfb_nv_scale", C.c_int, [_i64, _d, _vp, _vp, _vp])
+_sig("bdfb_nv_const", C.c_int, [_i64, _d, _vp, _vp])
+_sig("bdfb_nv_abs", C.c_int, [_i64, _vp, _vp, _vp])
+_sig("bdfb_nv_inv", C.c_int, [_i64, _vp, _vp, _vp])
+_sig("bdfb_nv_add_const", C.c_int, [_i64, _vp, _d, _vp, _vp])
+_sig("bdfb_nv_error_weights", C.c_int, [_i64, _d, _d, _vp, _vp, _vp])
 _sig("bdfb_nv_linear_combination", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
 _sig("bdfb_nv_scale_add_multi", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("bdfb_nv_dot_prod_multi", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
@@ -149,6 +156,31 @@ def _f64_array(v):
 def nv_linear_sum(a, x, b, y, z, stream=None):
     return check(lib.bdfb_nv_linear_sum(x.numel(), a, _dptr(x), b, _dptr(y), _dptr(z), _stream(stream)),
                  "nv_linear_sum")
+
+
+def nv_scale(c, x, z, stream=None):
+    return check(lib.bdfb_nv_scale(z.numel(), c, _dptr(x), _dptr(z), _stream(stream)), "nv_scale")
+
+
+def nv_const(c, z, stream=None):
+    return check(lib.bdfb_nv_const(z.numel(), c, _dptr(z), _stream(stream)), "nv_const")
+
+
+def nv_abs(x, z, stream=None):
+    return check(lib.bdfb_nv_abs(z.numel(), _dptr(x), _dptr(z), _stream(stream)), "nv_abs")
+
+
+def nv_inv(x, z, stream=None):
+    return check(lib.bdfb_nv_inv(z.numel(), _dptr(x), _dptr(z), _stream(stream)), "nv_inv")
+
+
+def nv_add_const(x, b, z, stream=None):
+    return check(lib.bdfb_nv_add_const(z.numel(), _dptr(x), b, _dptr(z), _stream(stream)), "nv_add_const")
+
+
+def nv_error_weights(rtol, atol, y, w, stream=None):
+    return check(lib.bdfb_nv_error_weights(w.numel(), rtol, atol, _dptr(y), _dptr(w), _stream(stream)),
+                 "nv_error_weights")
 
 
 def nv_linear_combination(c, xs, z, stream=None):
@@ -245,7 +277,7 @@ class Integrator:
         self._keep = []
         p = Problem()
         p.mem = MEM_HOST
-        p.ncell = problem.npts if problem.kind == "brusselator3d" else problem.ncell
+        p.ncell = problem.npts if problem.kind in ("brusselator3d", "brusselator1d") else problem.ncell
 
         def host(a, dt):
             a = np.ascontiguousarray(a, dtype=dt)
@@ -259,6 +291,10 @@ class Integrator:
             p.kind = BRUSSELATOR3D
             p.ncell = problem.npts
             p.k = host([problem.A, problem.B, problem.eps, problem.D, float(problem.nx)], np.float64)
+        elif problem.kind == "brusselator1d":
+            p.kind = BRUSSELATOR1D
+            p.k = host([problem.A, problem.B, problem.eps, problem.c, problem.length, float(problem.nx)],
+                       np.float64)
         else:
             p.kind = MASSACTION
             p.n = host(problem.n, np.int32)
@@ -271,7 +307,7 @@ class Integrator:
         check(lib.bdfb_create(C.byref(p), C.byref(h)), "bdfb_create")
         self._keep = []
         self.h = h
-        if problem.kind == "brusselator3d":
+        if problem.kind in ("brusselator3d", "brusselator1d"):
             self.ncell, self.ny = 1, 3 * problem.npts    # one coupled system
         else:
             self.ncell = problem.ncell

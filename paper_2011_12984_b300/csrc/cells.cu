@@ -1165,7 +1165,8 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   if (!prob || !out) return BDFB_ILL_INPUT;
   *out = nullptr;
   if (prob->ncell < 0 ||
-      (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION && prob->kind != BDFB_BRUSSELATOR3D) ||
+      (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION && prob->kind != BDFB_BRUSSELATOR3D &&
+       prob->kind != BDFB_BRUSSELATOR1D) ||
       (prob->mem != BDFB_MEM_HOST && prob->mem != BDFB_MEM_DEVICE) || !prob->k)
     return BDFB_ILL_INPUT;
   bdfb_ctx* c = new (std::nothrow) bdfb_ctx();
@@ -1179,6 +1180,18 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
     const int nx = (int)par[4];
     if ((double)nx != par[4] || (int64_t)nx * nx * nx != prob->ncell) { free_ctx(c); return BDFB_ILL_INPUT; }
     TRY(grid_create(nx, par[0], par[1], par[2], par[3], &c->grid));
+    c->ny = 3 * prob->ncell;
+    BDFB_CUDA(cudaEventCreate(&c->ev0));
+    BDFB_CUDA(cudaEventCreate(&c->ev1));
+    *out = c;
+    return BDFB_SUCCESS;
+  }
+  if (prob->kind == BDFB_BRUSSELATOR1D) {   // the demo's advection-reaction line
+    std::vector<double> par;
+    TRY(fetch(par, prob->k, 6, prob->mem));
+    const int64_t nx = (int64_t)par[5];
+    if ((double)nx != par[5] || nx != prob->ncell) { free_ctx(c); return BDFB_ILL_INPUT; }
+    TRY(grid_create_line_or_cube(1, nx, par[0], par[1], par[2], 0.0, par[3], par[4], &c->grid));
     c->ny = 3 * prob->ncell;
     BDFB_CUDA(cudaEventCreate(&c->ev0));
     BDFB_CUDA(cudaEventCreate(&c->ev1));

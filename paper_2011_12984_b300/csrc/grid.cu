@@ -84,6 +84,24 @@ __global__ void k_bruss_rhs(int nx, double A, double B, double reps, double D, c
   f[2 * np + p] = lap[2] + (B - w) * reps - w * u;
 }
 
+// 1-D advection-reaction line (the demo problem of Sec. 6): -c da/dx by
+// first-order upwind differences on a periodic line of np points; cdx = c / dx
+__device__ __forceinline__ double upwind(const double* a, int64_t q, int64_t np, double cdx) {
+  if (cdx >= 0.0) return -cdx * (a[q] - a[q == 0 ? np - 1 : q - 1]);
+  return -cdx * (a[q + 1 == np ? 0 : q + 1] - a[q]);
+}
+
+// f = -c da/dx + reaction(y), species-major u | v | w; reps = 1/eps
+__global__ void k_bruss1_rhs(int64_t np, double A, double B, double reps, double cdx, const double* __restrict__ y,
+                             double* __restrict__ f) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
+    const double u = y[q], v = y[np + q], w = y[2 * np + q];
+    f[q] = upwind(y, q, np, cdx) + A - (w + 1.0) * u + v * u * u;
+    f[np + q] = upwind(y + np, q, np, cdx) + w * u - v * u * u;
+    f[2 * np + q] = upwind(y + 2 * np, q, np, cdx) + (B - w) * reps - w * u;
+  }
+}
+
 // reaction Jacobian of one point (row-major 3x3); reps = 1/eps
 __device__ __forceinline__ void bruss_jr(double reps, double u, double v, double w, double* J) {
   J[0] = -(w + 1.0) + 2.0 * u * v; J[1] = u * u;   J[2] = -u;
@@ -143,6 +161,34 @@ __global__ void k_bruss_apply(int nx, double D, double reps, double gamma, const
 #pragma unroll
   for (int s = 0; s < 3; ++s)
     w[s * np + p] = ewt[s * np + p] * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+}
+
+// the same operator on the 1-D line, advection in place of diffusion
+__global__ void k_bruss1_apply(int64_t np, double cdx, double reps, double gamma, const double* __restrict__ v,
+                               const double* __restrict__ ewt, const double* __restrict__ sc,
+                               const double* __restrict__ y, const double* __restrict__ Pinv,
+                               double* __restrict__ w) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pl = p == 0 ? np - 1 : p - 1, pr = p + 1 == np ? 0 : p + 1;
+    double u[3], adv[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const double* vs = v + s * np;
+      const double* ss = sc + s * np;
+      u[s] = vs[p] * ss[p];
+      adv[s] = cdx >= 0.0 ? -cdx * (u[s] - vs[pl] * ss[pl]) : -cdx * (vs[pr] * ss[pr] - u[s]);
+    }
+    double J[9];
+    bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
+    double a[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+      a[s] = u[s] - gamma * (adv[s] + J[3 * s] * u[0] + J[3 * s + 1] * u[1] + J[3 * s + 2] * u[2]);
+    const double* P = Pinv + 9 * p;
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+      w[s * np + p] = ewt[s * np + p] * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+  }
 }
 
 // v = S P^{-1} b
@@ -237,8 +283,10 @@ __global__ void k_rescale(int64_t N, int q, GZ Z, double eta) {
 
 struct GridBDF {
   int nx = 0;
+  int dim = 3;                // 3: nx^3 diffusion grid; 1: nx-point advection line
   int64_t np = 0, N = 0;
   double A = 1, B = 3, eps = 5e-6, D = 1e-2;
+  double cdx = 0.0;           // dim 1: c / dx
   double rtol = 1e-6, atol = 1e-10;
   int maxl = 5;
   int64_t mxstep = 100000;
@@ -312,7 +360,10 @@ static int g_dots(GridBDF* g, const double* x, const double* const* ys, int nv, 
 }
 
 static int g_rhs(GridBDF* g, const double* y, double* f) {
-  k_bruss_rhs<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->A, g->B, g->reps, g->D, y, f);
+  if (g->dim == 1)
+    k_bruss1_rhs<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->A, g->B, g->reps, g->cdx, y, f);
+  else
+    k_bruss_rhs<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->A, g->B, g->reps, g->D, y, f);
   BDFB_CUDA(cudaGetLastError());
   g->nfe++;
   return 0;
@@ -360,8 +411,12 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   int k = 0;
   bool conv = false;
   for (int j = 0; j < maxl; ++j) {
-    k_bruss_apply<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j], g->ewt,
-                                                          g->sc, ycur, g->Pinv, g->w);
+    if (g->dim == 1)
+      k_bruss1_apply<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->cdx, g->reps, g->gamma, g->V[j], g->ewt, g->sc,
+                                                      ycur, g->Pinv, g->w);
+    else
+      k_bruss_apply<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j], g->ewt,
+                                                            g->sc, ycur, g->Pinv, g->w);
     BDFB_CUDA(cudaGetLastError());
     double hcol[MAXL_MAX + 1];
     GCHK(g_dots(g, g->w, g->V, j + 1, hcol));        // classical Gram-Schmidt
@@ -630,13 +685,22 @@ static int g_initial_step(GridBDF* g, double tout) {
 }
 
 int grid_create(int nx, double A, double B, double eps, double D, GridBDF** out) {
-  if (nx < 2 || nx > 2048 || !(eps > 0.0)) return BDFB_ILL_INPUT;
+  return grid_create_line_or_cube(3, nx, A, B, eps, D, 0.0, 1.0, out);
+}
+
+int grid_create_line_or_cube(int dim, int64_t nx, double A, double B, double eps, double D, double c,
+                             double len, GridBDF** out) {
+  if ((dim != 1 && dim != 3) || nx < 2 || (dim == 3 && nx > 2048) || (dim == 1 && nx > (int64_t)1 << 30) ||
+      !(eps > 0.0) || !std::isfinite(c) || !(len > 0.0))
+    return BDFB_ILL_INPUT;
   GridBDF* g = new (std::nothrow) GridBDF();
   if (!g) return BDFB_MEM_FAIL;
-  g->nx = nx;
-  g->np = (int64_t)nx * nx * nx;
+  g->nx = (int)nx;
+  g->dim = dim;
+  g->np = dim == 1 ? nx : nx * nx * nx;
   g->N = 3 * g->np;
   g->A = A; g->B = B; g->eps = eps; g->D = D;
+  g->cdx = dim == 1 ? c / (len / (double)nx) : 0.0;
   g->reps = 1.0 / eps;
   make_tables(g);
   const size_t vb = g->N * sizeof(double);

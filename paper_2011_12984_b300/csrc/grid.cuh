@@ -9,6 +9,10 @@ namespace bdfb {
 struct GridBDF;
 
 int grid_create(int nx, double A, double B, double eps, double D, GridBDF** out);
+// dim 3: the nx^3 reaction-diffusion grid (D); dim 1: the advection-reaction
+// line of nx points over [0, len) with speed c (first-order upwind)
+int grid_create_line_or_cube(int dim, int64_t nx, double A, double B, double eps, double D, double c,
+                             double len, GridBDF** out);
 void grid_destroy(GridBDF* g);
 void grid_set_stream(GridBDF* g, cudaStream_t s);
 void grid_set_tolerances(GridBDF* g, double rtol, double atol);

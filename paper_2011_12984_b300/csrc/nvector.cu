@@ -58,6 +58,61 @@ __global__ void k_linear_sum1(int64_t n, double a, const double* x, double b, co
     z[i] = a * x[i] + b * y[i];
 }
 
+// ------------------------------------------------------------ support ops
+// z = op(x) elementwise: Scale (a x), Const (a), Abs, Inv (1 / x), AddConst
+// (x + a), and the fused error weight 1 / (a |x| + b) (a = rtol, b = atol)
+enum { UOP_SCALE = 0, UOP_CONST, UOP_ABS, UOP_INV, UOP_ADDCONST, UOP_EWT };
+
+template <int OP>
+__device__ __forceinline__ double uop(double x, double a, double b) {
+  if (OP == UOP_SCALE) return a * x;
+  if (OP == UOP_CONST) return a;
+  if (OP == UOP_ABS) return fabs(x);
+  if (OP == UOP_INV) return 1.0 / x;
+  if (OP == UOP_ADDCONST) return x + a;
+  return 1.0 / (a * fabs(x) + b);
+}
+
+template <int OP>
+__global__ void k_unary2(int64_t n2, const double2* x, double a, double b, double2* z) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (UNROLL - 1) * stride < n2; i += UNROLL * stride) {
+    double2 v[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) v[u] = OP == UOP_CONST ? make_double2(0.0, 0.0) : __ldcs(x + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u)
+      __stcs(z + i + u * stride, make_double2(uop<OP>(v[u].x, a, b), uop<OP>(v[u].y, a, b)));
+  }
+  for (; i < n2; i += stride) {
+    const double2 v = OP == UOP_CONST ? make_double2(0.0, 0.0) : __ldcs(x + i);
+    __stcs(z + i, make_double2(uop<OP>(v.x, a, b), uop<OP>(v.y, a, b)));
+  }
+}
+
+template <int OP>
+__global__ void k_unary1(int64_t n, const double* x, double a, double b, double* z) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    z[i] = uop<OP>(OP == UOP_CONST ? 0.0 : x[i], a, b);
+}
+
+template <int OP>
+static int launch_unary(int64_t n, const double* x, double a, double b, double* z, cudaStream_t s) {
+  const bool al = aligned16(z) && (OP == UOP_CONST || aligned16(x));
+  const int64_t n2 = n >> 1;
+  if (al && n2) {
+    k_unary2<OP><<<grid_for(n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(
+        n2, reinterpret_cast<const double2*>(x), a, b, reinterpret_cast<double2*>(z));
+    if (n & 1) k_unary1<OP><<<1, 32, 0, s>>>(1, OP == UOP_CONST ? x : x + n - 1, a, b, z + n - 1);
+  } else {
+    k_unary1<OP><<<grid_for(n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, x, a, b, z);
+  }
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
 // ------------------------------------------------------------ LinearCombination
 struct LCArgs {
   const double* x[NV_MAX];
@@ -277,6 +332,37 @@ extern "C" int64_t bdfb_nv_work_doubles(int64_t n, int nv) {
   (void)n;
   (void)nv;
   return (int64_t)RD_MAX_BLOCKS * NV_MAX + 2;
+}
+
+extern "C" int bdfb_nv_scale(int64_t n, double c, const double* x, double* z, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !z))) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_SCALE>(n, x, c, 0.0, z, as_stream(stream)) : BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_nv_const(int64_t n, double c, double* z, void* stream) {
+  if (n < 0 || (n > 0 && !z)) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_CONST>(n, nullptr, c, 0.0, z, as_stream(stream)) : BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_nv_abs(int64_t n, const double* x, double* z, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !z))) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_ABS>(n, x, 0.0, 0.0, z, as_stream(stream)) : BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_nv_inv(int64_t n, const double* x, double* z, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !z))) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_INV>(n, x, 0.0, 0.0, z, as_stream(stream)) : BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_nv_add_const(int64_t n, const double* x, double b, double* z, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !z))) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_ADDCONST>(n, x, b, 0.0, z, as_stream(stream)) : BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_nv_error_weights(int64_t n, double rtol, double atol, const double* y, double* w,
+                                     void* stream) {
+  if (n < 0 || (n > 0 && (!y || !w)) || !(rtol >= 0.0) || !(atol > 0.0)) return BDFB_ILL_INPUT;
+  return n ? launch_unary<UOP_EWT>(n, y, rtol, atol, w, as_stream(stream)) : BDFB_SUCCESS;
 }
 
 extern "C" int bdfb_nv_linear_sum(int64_t n, double a, const double* x, double b, const double* y,

@@ -87,3 +87,52 @@ def test_grid_256_cubed_steady_state():
     assert ret == 0
     assert np.max(np.abs(y - p.y0) / np.abs(p.y0)) <= 1e-12
     assert gs[0] > 0
+
+
+# ------------------------------------------------ the 1-D advection demo (Sec. 6)
+@pytest.mark.parametrize("nx,length,tout", [(40, 10.0, 0.5), (200, 100.0, 1.0)])
+def test_line_matches_oracle(nx, length, tout):
+    """The demo problem (paper's initial state) against the oracle's grouped
+    integrator, as for the 3-D grid."""
+    p = gen.brusselator1d(nx, length=length)
+    rtol, atol = 1e-6, 1e-10
+    ret, y, gs, _ = run_grid(p, tout, rtol, atol)
+    assert ret == 0
+    ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
+    rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
+    assert ro == 0 and rt == 0
+    w = rtol * np.abs(yt) + atol
+    eg = np.max(np.abs(y - yt) / w)
+    eo = np.max(np.abs(yo - yt) / w)
+    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
+    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)
+    assert gs[6] > 0
+
+
+def test_line_uniform_steady_state_stays_at_1e6_points():
+    nx = 1_000_000
+    u, v, w = gen.brusselator_steady_state(1.0, 3.5, 5e-6)
+    y0 = np.concatenate([np.full(nx, u), np.full(nx, v), np.full(nx, w)])
+    p = gen.Brusselator1D(nx=nx, A=1.0, B=3.5, eps=5e-6, c=0.01, length=1000.0, y0=y0)
+    ret, y, gs, _ = run_grid(p, 1.0, 1e-6, 1e-10)
+    assert ret == 0
+    assert np.max(np.abs(y - y0) / y0) <= 1e-12
+
+
+@pytest.mark.parametrize("c", [0.01, -0.02])
+def test_line_fourier_mode_of_pure_advection(c):
+    """v advected alone (u = w = 0, A = B = 0): the exact solution of the
+    upwind-discretised system, for either direction of the wind."""
+    nx, k, length = 1000, 7, 10.0
+    y0 = np.zeros(3 * nx)
+    j = np.arange(nx)
+    th = 2 * np.pi * k / nx
+    y0[nx:2 * nx] = np.cos(th * j)
+    p = gen.Brusselator1D(nx=nx, A=0.0, B=0.0, eps=5e-6, c=c, length=length, y0=y0)
+    dx = length / nx
+    lam1 = -(c / dx) * (1 - np.exp(-1j * th)) if c >= 0 else -(c / dx) * (np.exp(1j * th) - 1)
+    tout = 1.0 / abs(lam1)
+    ret, y, gs, _ = run_grid(p, tout, 1e-8, 1e-12, device_io=False)
+    assert ret == 0
+    exact = np.real(np.exp(lam1 * tout) * np.exp(1j * th * j))
+    assert np.max(np.abs(y[nx:2 * nx] - exact)) <= 20 * 1e-8

@@ -106,3 +106,30 @@ def test_large_vectors_sampled():
     bdfb.nv_dot_prod_multi(dx, [dy, dx], out, bdfb.nv_work(n, 2))
     d, s = oracle.dot_prod_multi(x.numpy(), [y.numpy(), x.numpy()])
     assert np.all(np.abs(out.cpu().numpy() - d) <= 1e-14 * s)
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("off", [0, 1])
+def test_support_ops(n, off):
+    """Scale, Const, Abs, Inv, AddConst: one correctly rounded operation per
+    element, so bitwise equal to the oracle; error weights within 2 ulp (the
+    kernel may fuse rtol |y| + atol into one multiply-add)."""
+    (x,) = gen.uniform_vectors(n, 1, seed=n + 7)
+    x = x + np.sign(x) * 1e-3                      # keep 1/x finite
+    dx = to_dev(x, off)
+    dz = to_dev(np.zeros(n), off)
+    bdfb.nv_scale(-2.5, dx, dz)
+    assert np.array_equal(dz.cpu().numpy(), oracle.scale(-2.5, x))
+    bdfb.nv_const(3.25, dz)
+    assert np.array_equal(dz.cpu().numpy(), oracle.const(3.25, n))
+    bdfb.nv_abs(dx, dz)
+    assert np.array_equal(dz.cpu().numpy(), oracle.abs_(x))
+    bdfb.nv_inv(dx, dz)
+    assert np.array_equal(dz.cpu().numpy(), oracle.inv(x))
+    bdfb.nv_add_const(dx, 0.125, dz)
+    assert np.array_equal(dz.cpu().numpy(), oracle.add_const(x, 0.125))
+    bdfb.nv_error_weights(1e-6, 1e-10, dx, dz)
+    w = oracle.error_weights(1e-6, 1e-10, x)
+    assert np.all(np.abs(dz.cpu().numpy() - w) <= 4.5e-16 * w)
+    bdfb.nv_scale(0.5, dx, dx)                     # z aliases x
+    assert np.array_equal(dx.cpu().numpy(), oracle.scale(0.5, x))
