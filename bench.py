@@ -447,6 +447,27 @@ def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps
             "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
 
 
+def grouped_workload(torch, bdfb, gen, ncell=100_000, reps=1, flush=None):
+    """The mass-action workload integrated as ONE system (option "grouped":
+    one step size and order, error test over every species, task-local
+    Newton solves per cell; the grouping of Sec. 2) against per-cell step
+    control on the same cells: the cost of the stiffness caveat of Sec. 2."""
+    p = gen.mass_action(ncell, sizes=SIZES)
+    y0 = torch.from_numpy(p.y0).cuda()
+    y = torch.empty_like(y0)
+    out = {"workload": f"mass-action {ncell} cells (sizes {'/'.join(map(str, SIZES))}), t in [0,1e-3], "
+                       f"rtol 1e-6, atol 1e-10"}
+    for name, opts in (("per_cell", {}), ("grouped_task_local_newton", {"grouped": 1})):
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, **opts) as I:
+            t = timed_integrations(torch, I, y0, y, TOUT, reps, flush)
+            st = I.stats()
+        out[name] = {"cells_per_s": ncell / t, "s": t, "steps_per_cell": st["nsteps"] / ncell,
+                     "max_steps": st["max_steps"], "newton_iters_per_cell": st["nniters"] / ncell,
+                     "accuracy": accuracy(p, y.cpu().numpy(), ncheck=256)}
+    out["per_cell_over_grouped"] = out["per_cell"]["cells_per_s"] / out["grouped_task_local_newton"]["cells_per_s"]
+    return out
+
+
 def run_reference(args):
     """reference arm: the CPU oracle as it stands, on the host cores"""
     ws, rank, _ = dist_env()
@@ -577,7 +598,8 @@ def run_ours(args):
     if not args.no_configs:
         configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
                    "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush),
-                   "advection_line_1e7": line_workload(torch, bdfb, gen)}
+                   "advection_line_1e7": line_workload(torch, bdfb, gen),
+                   "grouped_vs_per_cell_100k": grouped_workload(torch, bdfb, gen, ncell=NCELL, flush=flush)}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
                        ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):
@@ -657,6 +679,8 @@ def run_part(args):
         out = robertson_workload(torch, bdfb, gen, reps=max(1, args.steps))
     elif args.part == "mixed54":
         out = mixed54_workload(torch, bdfb, gen, reps=max(1, args.steps))
+    elif args.part == "grouped":
+        out = grouped_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "line":
         out = line_workload(torch, bdfb, gen, nx=args.line_nx, tout=args.grid_tout, reps=max(1, args.steps))
     else:
@@ -680,13 +704,13 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="run each size class on its own tiling instead of the autotuned one")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the Robertson, 262144 x 54 mixed-precision and 1-D demo legs")
+                    help="skip the Robertson, 262144 x 54 mixed-precision, 1-D demo and grouped legs")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-guess leg (1M-cell shared network, training on the GPU)")
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     ap.add_argument("--part", default="all",
-                    choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line"],
+                    choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line", "grouped"],
                     help="run one leg alone and print its JSON (for profiling); all: the benchmark")
     ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
     ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid / line: end time")

@@ -232,6 +232,21 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              convergence test uses the rate carried over from earlier
  *              solves only when the guess lies closer to the new iterate
  *              than zero does (else rate 1).
+ *  "grouped"   1 = integrate all cells as ONE system (the grouping of many
+ *              small systems into one, Sec. 2, with the demonstration
+ *              problem's task-local Newton solver, Sec. 7): one step size
+ *              and order for every cell, the local
+ *              error test on the norm over all species, and a task-local
+ *              Newton solve — each cell's block of the Newton matrix is
+ *              factored and iterated to its own convergence test (the same
+ *              test as per-cell mode, in that cell's norm) and the step's
+ *              solve fails if any cell's does.  FP64 only, no predictor.
+ *              The Jacobian is refreshed for every cell at once (gamma
+ *              ratio 0.3 or 20 steps, as per-cell).  Setting it makes the
+ *              next integrate start from the state of the last bdfb_init.
+ *              Statistics: every cell counts every grouped step, RHS
+ *              evaluation, setup and failure; nniters sums the cells'
+ *              task-local iterations.
  * "mapping" 32 runs every cell on the smallest one-warp-per-cell kernel all
  * cells fit (NMAX 16 — the predictor's kernel, FP64 only — 32 or 56). */
 int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);
@@ -246,7 +261,10 @@ int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32
 int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
 /* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits.
  * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
- * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl. */
+ * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl.
+ * Option "grouped": every row holds the shared counters (nni: the mean over
+ * cells of the summed task-local iterations), the order and the step size
+ * the next step will try. */
 int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
 /* Cell-to-lane mapping in use.  Size classes c = 0..4 hold cells with
  * max(n, ceil(reactions / 2)) <= 4, 8, 16, 32, 56.  Kernel variants v =

@@ -60,6 +60,8 @@ def lib():
                                           C.POINTER(Options), _pd, _pi64, _pi64]
         L.or_cells_integrate.argtypes = [C.POINTER(Cells), _i64, _i64, _d, _pd, _d, _d, _d,
                                          _i64, _pd, _pi32, _pi64]
+        L.or_cells_integrate_grouped.argtypes = [C.POINTER(Cells), _d, _pd, _d, _d, _d, _i64,
+                                                 _pd, _pi64]
         L.or_bruss_gmres.argtypes = [C.POINTER(Bruss), _pd, _d, _pd, _d, C.c_int, _pd, _pd]
         L.or_bruss_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, C.c_int, _i64,
                                          _pd, _pi64]
@@ -293,6 +295,19 @@ def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threa
             list(ex.map(run, ranges))
     del keep
     return y, status, stats
+
+
+def integrate_cells_grouped(prob, t0, tout, rtol, atol, mxstep=100000, y0=None):
+    """All cells as one system with task-local Newton solves (one step size and
+    order, error test over every species); returns (y, ret, stats[8])."""
+    s, keep = _cells_struct(prob)
+    y0 = _f64(prob.y0 if y0 is None else y0)
+    y = y0.copy()
+    stats = np.zeros(8, np.int64)
+    ret = lib().or_cells_integrate_grouped(C.byref(s), t0, _p(y0), tout, rtol, atol, mxstep,
+                                           _p(y), _p(stats, _pi64))
+    del keep
+    return y, ret, stats
 
 
 def bruss_struct(p):

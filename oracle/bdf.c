@@ -43,6 +43,8 @@ struct or_bdf {
   int grown_once;        /* first step-size increase done (eta cap 1e4 before) */
   double *z, *zs, *ewt, *acor, *acor_prev, *y, *f, *b;
   double gamma, gammap, crate;
+  double *bcrate, *bdelp; /* task-local Newton: per block rate and last |delta| */
+  int8_t* bstate;         /* per block: 0 iterating, 1 converged, 2 failed */
   int64_t nst, nstlp;
   int force_setup, setup_done;
   or_stats st;
@@ -128,7 +130,12 @@ or_bdf* or_bdf_create(const or_system* sys, const or_options* opt, double t0, co
   m->y = (double*)calloc((size_t)N, sizeof(double));
   m->f = (double*)calloc((size_t)N, sizeof(double));
   m->b = (double*)calloc((size_t)N, sizeof(double));
-  if (!m->z || !m->zs || !m->ewt || !m->acor || !m->acor_prev || !m->y || !m->f || !m->b) {
+  const int64_t nb = sys->nblock > 0 ? sys->nblock : 0;
+  m->bcrate = (double*)calloc((size_t)(nb + 1), sizeof(double));
+  m->bdelp = (double*)calloc((size_t)(nb + 1), sizeof(double));
+  m->bstate = (int8_t*)calloc((size_t)(nb + 1), 1);
+  if (!m->z || !m->zs || !m->ewt || !m->acor || !m->acor_prev || !m->y || !m->f || !m->b ||
+      !m->bcrate || !m->bdelp || !m->bstate) {
     or_bdf_free(m);
     return NULL;
   }
@@ -142,6 +149,7 @@ void or_bdf_free(or_bdf* m) {
   if (!m) return;
   free(m->z); free(m->zs); free(m->ewt); free(m->acor); free(m->acor_prev);
   free(m->y); free(m->f); free(m->b);
+  free(m->bcrate); free(m->bdelp); free(m->bstate);
   free(m);
 }
 
@@ -206,7 +214,10 @@ static int initial_step(or_bdf* m, double tout, const double* f0) {
  * Convergence: with rate R = max(0.3 R_prev, |delta_m| / |delta_{m-1}|),
  * converged when |delta_m| min(1, R) E_q <= 0.1 (a tenth of the error-test
  * bound); diverged when |delta_m| > 2 |delta_{m-1}|. */
+static int newton_local(or_bdf* m, double tnew, double Eq, double* acnrm);
+
 static int newton(or_bdf* m, double tnew, double Eq, double* acnrm) {
+  if (m->sys.nblock > 0) return newton_local(m, tnew, Eq, acnrm);
   int64_t N = m->N;
   double l1 = ell1(m->q);
   const double* z0 = Z(m, 0);
@@ -261,6 +272,81 @@ static int newton(or_bdf* m, double tnew, double Eq, double* acnrm) {
       delp = del;
     }
     if (conv) return 0;
+    if (!jcur && !tried_fresh) { m->force_setup = 1; tried_fresh = 1; continue; }
+    return 1;
+  }
+}
+
+/* Task-local Newton (sys.nblock > 0).  The Jacobian refresh rule, gamma and
+ * the stale-M scaling are those of newton() and shared by all blocks; each
+ * block b then runs the iteration of newton() on its own entries: its own
+ * rate R_b, its own |delta| (WRMS over the block's n_b entries), its own
+ * convergence and divergence tests, and it stops changing once converged.  A
+ * block whose f is not finite fails.  The solve succeeds when every block
+ * has converged (then *acnrm = ||Delta|| over all N); otherwise a stale M is
+ * refreshed once, as in newton(), and the step fails after that. */
+static int newton_local(or_bdf* m, double tnew, double Eq, double* acnrm) {
+  const int64_t N = m->N, nb = m->sys.nblock;
+  const int64_t* off = m->sys.block_off;
+  double l1 = ell1(m->q);
+  const double* z0 = Z(m, 0);
+  const double* z1 = Z(m, 1);
+  int tried_fresh = 0;
+  for (;;) {
+    int jcur = 0;
+    if (!m->setup_done || m->force_setup || fabs(m->gamma / m->gammap - 1.0) > 0.3 ||
+        m->nst >= m->nstlp + 20) {
+      int r = m->sys.lsetup(m->sys.user, tnew, z0, m->gamma);
+      m->st.nsetups++;
+      m->gammap = m->gamma;
+      for (int64_t k = 0; k < nb; ++k) m->bcrate[k] = 1.0;
+      m->nstlp = m->nst;
+      m->force_setup = 0;
+      m->setup_done = 1;
+      jcur = 1;
+      if (r < 0) return OR_LSETUP_FAIL;
+      if (r > 0) return 1;
+    }
+    for (int64_t i = 0; i < N; ++i) { m->acor[i] = 0.0; m->y[i] = z0[i]; }
+    for (int64_t k = 0; k < nb; ++k) { m->bstate[k] = 0; m->bdelp[k] = 0.0; }
+    int64_t active = nb, failed = 0;
+    for (int it = 1; it <= 3 && active > 0; ++it) {
+      int r = m->sys.rhs(m->sys.user, tnew, m->y, m->f);
+      m->st.nfe++;
+      if (r < 0) return OR_RHSFUNC_FAIL;
+      for (int64_t i = 0; i < N; ++i) m->b[i] = m->gamma * m->f[i] - z1[i] / l1 - m->acor[i];
+      r = m->sys.lsolve(m->sys.user, tnew, m->y, m->gamma, m->ewt, 0.05 * 0.1 / Eq, m->b);
+      if (r < 0) return OR_LSOLVE_FAIL;
+      const double s = (m->sys.direct && m->gamma != m->gammap) ? 2.0 / (1.0 + m->gamma / m->gammap) : 1.0;
+      for (int64_t k = 0; k < nb; ++k) {
+        if (m->bstate[k] != 0) continue;
+        const int64_t i0 = off[k], i1 = off[k + 1];
+        int finite = r == 0;
+        for (int64_t i = i0; i < i1; ++i) finite = finite && isfinite(m->f[i]);
+        if (!finite) { m->bstate[k] = 2; --active; ++failed; continue; }
+        double ss = 0.0;
+        for (int64_t i = i0; i < i1; ++i) {
+          const double d = m->b[i] * s;
+          ss += (d * m->ewt[i]) * (d * m->ewt[i]);
+          m->acor[i] += d;
+          m->y[i] = z0[i] + m->acor[i];
+        }
+        const double del = sqrt(ss / (double)(i1 - i0));
+        m->st.nni++;
+        if (it > 1) {
+          double rate = del / m->bdelp[k];
+          m->bcrate[k] = (0.3 * m->bcrate[k] > rate) ? 0.3 * m->bcrate[k] : rate;
+        }
+        double dcon = del * (m->bcrate[k] < 1.0 ? m->bcrate[k] : 1.0) * Eq / 0.1;
+        if (dcon <= 1.0) { m->bstate[k] = 1; --active; continue; }
+        if ((it >= 2 && del > 2.0 * m->bdelp[k]) || it == 3) { m->bstate[k] = 2; --active; ++failed; continue; }
+        m->bdelp[k] = del;
+      }
+    }
+    if (!failed && active == 0) {
+      *acnrm = wrms(m, m->acor);
+      return 0;
+    }
     if (!jcur && !tried_fresh) { m->force_setup = 1; tried_fresh = 1; continue; }
     return 1;
   }

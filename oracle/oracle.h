@@ -70,6 +70,12 @@ typedef struct {
   int (*lsolve)(void* user, double t, const double* ycur, double gamma,
                 const double* ewt, double tol, double* b);
   int direct; /* 1: scale the correction by 2/(1+gamma/gamma_setup) */
+  /* task-local Newton (demonstration problem's solver, Sec. 7) when nblock > 0:
+   * the unknowns split into independent blocks [block_off[b], block_off[b+1])
+   * and each block iterates to its own convergence test in its own WRMS norm;
+   * the solve fails when any block's does.  lsolve must act block by block. */
+  int64_t nblock;
+  const int64_t* block_off;
 } or_system;
 
 typedef struct {
@@ -131,6 +137,14 @@ typedef struct {
 int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
                        const double* y0, double tout, double rtol, double atol,
                        int64_t mxstep, double* yout, int32_t* status, int64_t* stats);
+
+/* All cells [0, ncell) as ONE system (the grouping of Sec. 2): one step size,
+ * order and error test over every species, block-diagonal Newton matrix with
+ * one dense LU per cell, task-local Newton solves (or_system.nblock = ncell).
+ * stats = {nst, nfe, nsetups, nni (summed over cells), ncfn, netf, qlast, 0}. */
+int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y0, double tout,
+                               double rtol, double atol, int64_t mxstep, double* yout,
+                               int64_t* stats);
 
 /* y' = A y + sum_k C_k t^k, dense LU (pins of the BDF core) */
 int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, double t0,

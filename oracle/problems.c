@@ -108,30 +108,35 @@ static int cell_lsolve(void* u, double t, const double* ycur, double gamma,
   return 0;
 }
 
+/* the data of cell c (buffers J, M, piv left to the caller) */
+static void cell_user_of(const or_cells* cells, int64_t c, cell_user* u) {
+  memset(u, 0, sizeof *u);
+  u->kind = cells->kind;
+  if (cells->kind == 0) {
+    u->n = 3;
+    u->k = cells->k + 3 * c;
+  } else {
+    u->n = cells->n[c];
+    int64_t ro = cells->rxn_off[c];
+    u->nr = (int)(cells->rxn_off[c + 1] - ro);
+    u->k = cells->k + ro;
+    u->reac = cells->reac + 4 * ro;
+    u->prod = cells->prod + 4 * ro;
+  }
+}
+
 int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
                        const double* y0, double tout, double rtol, double atol,
                        int64_t mxstep, double* yout, int32_t* status, int64_t* stats) {
   int worst = 0;
   for (int64_t c = c0; c < c1; ++c) {
     cell_user u;
-    memset(&u, 0, sizeof u);
-    u.kind = cells->kind;
+    cell_user_of(cells, c, &u);
     int64_t yo = cells->y_off[c];
-    if (cells->kind == 0) {
-      u.n = 3;
-      u.k = cells->k + 3 * c;
-    } else {
-      u.n = cells->n[c];
-      int64_t ro = cells->rxn_off[c];
-      u.nr = (int)(cells->rxn_off[c + 1] - ro);
-      u.k = cells->k + ro;
-      u.reac = cells->reac + 4 * ro;
-      u.prod = cells->prod + 4 * ro;
-    }
     u.J = (double*)malloc(sizeof(double) * u.n * u.n);
     u.M = (double*)malloc(sizeof(double) * u.n * u.n);
     u.piv = (int*)malloc(sizeof(int) * u.n);
-    or_system sys = {u.n, &u, cell_rhs, cell_lsetup, cell_lsolve, 1};
+    or_system sys = {u.n, &u, cell_rhs, cell_lsetup, cell_lsolve, 1, 0, NULL};
     or_options opt;
     memset(&opt, 0, sizeof opt);
     opt.rtol = rtol;
@@ -157,6 +162,77 @@ int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
     if (ret < worst) worst = ret;
   }
   return worst;
+}
+
+/* ---- all cells as one system with task-local Newton solves -------------- */
+typedef struct {
+  int64_t ncell;
+  const int64_t* y_off;
+  cell_user* u;
+} group_user;
+
+static int group_rhs(void* p, double t, const double* y, double* f) {
+  group_user* g = (group_user*)p;
+  for (int64_t c = 0; c < g->ncell; ++c) cell_rhs(&g->u[c], t, y + g->y_off[c], f + g->y_off[c]);
+  return 0;   /* non-finite entries fail their own block in the Newton iteration */
+}
+
+static int group_lsetup(void* p, double t, const double* y, double gamma) {
+  group_user* g = (group_user*)p;
+  int bad = 0;
+  for (int64_t c = 0; c < g->ncell; ++c) bad |= cell_lsetup(&g->u[c], t, y + g->y_off[c], gamma);
+  return bad ? 1 : 0;
+}
+
+static int group_lsolve(void* p, double t, const double* ycur, double gamma,
+                        const double* ewt, double tol, double* b) {
+  (void)t; (void)ycur; (void)gamma; (void)ewt; (void)tol;
+  group_user* g = (group_user*)p;
+  for (int64_t c = 0; c < g->ncell; ++c) or_lu_solve(g->u[c].n, g->u[c].M, g->u[c].piv, b + g->y_off[c]);
+  return 0;
+}
+
+int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y0, double tout,
+                               double rtol, double atol, int64_t mxstep, double* yout,
+                               int64_t* stats) {
+  const int64_t C = cells->ncell;
+  if (C <= 0) return 0;
+  group_user g;
+  g.ncell = C;
+  g.y_off = cells->y_off;
+  g.u = (cell_user*)calloc((size_t)C, sizeof(cell_user));
+  int ok = g.u != NULL;
+  for (int64_t c = 0; ok && c < C; ++c) {
+    cell_user_of(cells, c, &g.u[c]);
+    const int n = g.u[c].n;
+    g.u[c].J = (double*)malloc(sizeof(double) * n * n);
+    g.u[c].M = (double*)malloc(sizeof(double) * n * n);
+    g.u[c].piv = (int*)malloc(sizeof(int) * n);
+    ok = g.u[c].J && g.u[c].M && g.u[c].piv;
+  }
+  int ret = OR_MEM_FAIL;
+  if (ok) {
+    or_system sys = {cells->y_off[C], &g, group_rhs, group_lsetup, group_lsolve, 1, C, cells->y_off};
+    or_options opt;
+    memset(&opt, 0, sizeof opt);
+    opt.rtol = rtol;
+    opt.atol = atol;
+    opt.mxstep = mxstep;
+    or_bdf* m = or_bdf_create(&sys, &opt, t0, y0);
+    if (m) {
+      ret = or_bdf_solve(m, tout, yout);
+      if (stats) {
+        or_stats st;
+        or_bdf_stats(m, &st);
+        stats[0] = st.nst; stats[1] = st.nfe; stats[2] = st.nsetups; stats[3] = st.nni;
+        stats[4] = st.ncfn; stats[5] = st.netf; stats[6] = st.qlast; stats[7] = 0;
+      }
+      or_bdf_free(m);
+    }
+  }
+  for (int64_t c = 0; g.u && c < C; ++c) { free(g.u[c].J); free(g.u[c].M); free(g.u[c].piv); }
+  free(g.u);
+  return ret;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -204,7 +280,7 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
                         const double* y0, double tout, const or_options* opt, double* yout,
                         int64_t* stats, int64_t* ntrace) {
   lin_user L = {N, A, ncoef, C, (double*)malloc(sizeof(double) * N * N), (int*)malloc(sizeof(int) * N)};
-  or_system sys = {N, &L, lin_rhs, lin_lsetup, lin_lsolve, 1};
+  or_system sys = {N, &L, lin_rhs, lin_lsetup, lin_lsolve, 1, 0, NULL};
   or_bdf* m = or_bdf_create(&sys, opt, t0, y0);
   int ret = OR_MEM_FAIL;
   if (m && L.M && L.piv) {
@@ -473,7 +549,7 @@ int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double to
   bruss_user B;
   if (maxl < 1 || maxl > GM_MAX) return OR_ILL_INPUT;
   if (bruss_alloc(&B, p, maxl)) { bruss_free(&B); return OR_MEM_FAIL; }
-  or_system sys = {N, &B, bruss_rhs_cb, bruss_lsetup_cb, bruss_lsolve_cb, 0};
+  or_system sys = {N, &B, bruss_rhs_cb, bruss_lsetup_cb, bruss_lsolve_cb, 0, 0, NULL};
   or_options opt;
   memset(&opt, 0, sizeof opt);
   opt.rtol = rtol;

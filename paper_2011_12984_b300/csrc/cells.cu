@@ -781,6 +781,167 @@ static const int CELLS_SMEM[2][NVAR] = {
 static cells_kernel_t var_kernel(int pr, int v) { return CELLS_KERNELS[pr][v]; }
 static int var_smem(int pr, int v) { return CELLS_SMEM[pr][v]; }
 
+// ------------------------------------------- grouped task-local Newton mode
+// The cells as ONE system (shared h and q, global error norms; the control of
+// the grid integrator drives it) solved the way of the paper's demo (Sec. 6):
+// every cell runs its own Newton iteration with its own convergence test and
+// a direct solve of its block, and if any cell fails the whole step is
+// retried with a smaller step size.  Jacobian LU factors persist between the
+// host-driven steps in global memory (lu: n x n per cell, row-major).
+struct GroupParams {
+  Params P;                      // cell data, tiles of the size-class schedule
+  int mode;                      // 0: Newton solve, 1: right-hand side
+  int setup;                     // fresh Jacobians at zp0 first
+  double gamma, gammap, rl1, Eq;
+  const double* zp0;             // predicted state / RHS input (mode 1)
+  const double* zp1;
+  const double* ewt;
+  double* out;                   // Newton: converged correction; RHS: f
+  double* lu;                    // per-cell factors, offsets lu_off
+  const int64_t* lu_off;
+  double* dinv;                  // per species
+  int16_t* perm;                 // per species
+  double* crate;                 // per cell
+  int* failed;
+  unsigned long long* iters;     // [0] completed iterations (sum), [1] RHS evaluations (max)
+};
+
+template <int G, int NMAX>
+__device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& GP, CellSmem<NMAX, 0>& S,
+                                           int64_t c) {
+  constexpr int NPL = (NMAX + G - 1) / G;
+  const Params& P = GP.P;
+  CellDesc cd;
+  int64_t yo;
+  if (P.kind == BDFB_ROBERTSON) {
+    cd.n = 3; cd.nr = 0; cd.k = P.k + 3 * c; cd.reac = nullptr; cd.inc_off = nullptr; cd.inc = nullptr;
+    yo = 3 * c;
+  } else {
+    cd.n = P.n[c];
+    yo = P.y_off[c];
+    const int64_t ro = P.rxn_off[c];
+    cd.nr = (int)(P.rxn_off[c + 1] - ro);
+    cd.k = P.k + ro;
+    cd.reac = P.reac + ro;
+    cd.inc_off = P.inc_off + yo;
+    cd.inc = P.inc;
+  }
+  cd.kind = P.kind;
+  const int n = cd.n;
+  double z0[NPL], z1[NPL], w[NPL];
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    const bool in = i < n;
+    z0[p] = in ? GP.zp0[yo + i] : 0.0;
+    z1[p] = in && GP.mode == 0 ? GP.zp1[yo + i] : 0.0;
+    w[p] = in && GP.mode == 0 ? GP.ewt[yo + i] : 0.0;
+  }
+  if (GP.mode == 1) {
+    double f[NPL];
+    rhs<G, NPL, NMAX>(g, cd, S, z0, f);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) GP.out[yo + i] = f[p];
+    }
+    return;
+  }
+  double* lu = GP.lu + GP.lu_off[c];
+  double crate = GP.crate[c];
+  if (GP.setup) {
+    bool direct = true;
+    if constexpr (CellSmem<NMAX, 0>::DR) {
+      if (cd.kind == BDFB_MASSACTION) {
+        reaction_derivs<G, NPL, NMAX>(g, cd, S, z0);
+        form_M64_from_dr<G, NPL, NMAX>(g, cd, S, GP.gamma, S.M);
+        direct = false;
+      }
+    }
+    if (direct) form_M<G, NPL, NMAX>(g, cd, S, z0, GP.gamma);
+    int info = lu_factor<G, NMAX, double, true>(g, S.M, S.dinv, S.perm, n);
+    crate = 1.0;
+    if (info) {                   // singular block: the step fails
+      if (g.rank == 0) atomicOr(GP.failed, 1);
+      if (g.rank == 0) GP.crate[c] = crate;
+      return;
+    }
+    for (int e = g.rank; e < n * n; e += G) lu[e] = S.M[e / n][e % n];
+    for (int i = g.rank; i < n; i += G) { GP.dinv[yo + i] = S.dinv[i]; GP.perm[yo + i] = S.perm[i]; }
+  } else {
+    for (int e = g.rank; e < n * n; e += G) S.M[e / n][e % n] = lu[e];
+    for (int i = g.rank; i < n; i += G) { S.dinv[i] = GP.dinv[yo + i]; S.perm[i] = GP.perm[yo + i]; }
+  }
+  g.sync();
+  const double rn = 1.0 / (double)n;
+  const double eq2 = GP.Eq * GP.Eq * 100.0;
+  const double scst = GP.gamma != GP.gammap ? 2.0 / (1.0 + GP.gamma / GP.gammap) : 1.0;
+  double acor[NPL], f[NPL], b[NPL];
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) acor[p] = 0.0;
+  double delp2 = 0.0;
+  bool conv = false;
+  int it = 1, nit = 0;
+  for (; it <= 3; ++it) {
+    double y[NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) y[p] = z0[p] + acor[p];
+    rhs<G, NPL, NMAX>(g, cd, S, y, f);
+    if (!all_finite(g, n, f)) break;
+    ++nit;
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) b[p] = GP.gamma * f[p] - z1[p] * GP.rl1 - acor[p];
+    lu_solve<G, NPL, NMAX, double, true>(g, S.M, S.dinv, S.perm, S.ybuf, n, b);
+    if (GP.gamma != GP.gammap) {
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) b[p] *= scst;
+    }
+    const double del2 = wrms2(g, n, rn, b, w);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) acor[p] += b[p];
+    if (it > 1) crate = fmax(0.3 * crate, (double)sqrtf((float)(del2 / delp2)));
+    const double cr = fmin(1.0, crate);
+    if (del2 * cr * cr * eq2 <= 1.0) { conv = true; break; }
+    if (it >= 2 && del2 > 4.0 * delp2) break;
+    delp2 = del2;
+  }
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i < n) GP.out[yo + i] = acor[p];
+  }
+  if (g.rank == 0) {
+    GP.crate[c] = crate;
+    atomicAdd(GP.iters, (unsigned long long)nit);
+    atomicMax(GP.iters + 1, (unsigned long long)(it > 3 ? 3 : it));
+    if (!conv) atomicOr(GP.failed, 1);
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(32, VAR_MINB[V]) k_group(const __grid_constant__ GroupParams GP, int t0, int t1,
+                                                           unsigned* counter) {
+  static_assert(V < NCLASS, "grouped mode runs on the size classes' own tilings");
+  constexpr int G = VAR_G[V], NMAX = VAR_NMAX[V];
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31;
+  Grp<G> g;
+  const int gid = lane / G;
+  CellSmem<NMAX, 0>& S = reinterpret_cast<CellSmem<NMAX, 0>*>(smem)[gid];
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    if (t >= t1) break;
+    const TileDesc td = GP.P.tiles[t];
+    if (gid < td.count) group_cell<G, NMAX>(g, GP, S, GP.P.tile_cells[td.first + gid]);
+    __syncwarp();
+  }
+}
+
+typedef void (*group_kernel_t)(const GroupParams, int, int, unsigned*);
+static const group_kernel_t GROUP_KERNELS[NCLASS] = {k_group<0>, k_group<1>, k_group<2>, k_group<3>, k_group<4>};
+
 // ------------------------------------------------- standalone batched LU
 constexpr int LU_NMAX = 64;
 
@@ -1009,6 +1170,18 @@ struct bdfb_ctx {
   float last_ms = 0.f;
   int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
+  // option "grouped": the cells as one system with task-local Newton solves
+  int grouped = 0;
+  bool gfresh = true;         // the grouped integrator needs the state of bdfb_init
+  GridBDF* gg = nullptr;
+  double* d_glu = nullptr;    // per-cell LU factors (n x n each)
+  int64_t* d_gluoff = nullptr;
+  double* d_gdinv = nullptr;
+  int16_t* d_gperm = nullptr;
+  double* d_gcrate = nullptr;
+  int* d_gflag = nullptr;
+  unsigned long long* d_giters = nullptr;
+  int gpgrid[NCLASS] = {};
   int maxn = 0;               // largest cell
   bool fits_w16 = false;      // every cell fits the NMAX 16 shared-memory layout
   bool fits_w32 = false;      // every cell fits the NMAX 32 shared-memory layout
@@ -1026,6 +1199,9 @@ static void free_ctx(bdfb_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   grid_destroy(c->grid);
+  grid_destroy(c->gg);
+  cudaFree(c->d_glu); cudaFree(c->d_gluoff); cudaFree(c->d_gdinv); cudaFree(c->d_gperm);
+  cudaFree(c->d_gcrate); cudaFree(c->d_gflag); cudaFree(c->d_giters);
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
@@ -1357,6 +1533,10 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     if (v == 1 && (ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)) return BDFB_ILL_INPUT;
     ctx->predictor = (int)v;
+  } else if (!std::strcmp(key, "grouped")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    ctx->grouped = (int)v;
+    ctx->gfresh = true;       // the next integrate starts from the state of bdfb_init
   } else {
     return BDFB_ILL_INPUT;
   }
@@ -1385,6 +1565,7 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
                               mem == BDFB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   BDFB_CUDA(cudaStreamSynchronize(s));   // the host staging vector goes out of scope
   ctx->t0 = t0;
+  ctx->gfresh = true;
   ctx->initialized = true;
   return BDFB_SUCCESS;
 }
@@ -1639,6 +1820,128 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
   return 0;
 }
 
+// ---- grouped task-local Newton mode (option "grouped")
+static int group_launch(bdfb_ctx* ctx, const GroupParams& GP, cudaStream_t s) {
+  const Sched& S = ctx->sched[0];
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NVAR + 1) * sizeof(unsigned), s));
+  for (int cl = NCLASS - 1; cl >= 0; --cl) {
+    const int t0 = S.vbeg[cl], t1 = S.vend[cl];
+    if (t1 <= t0) continue;
+    GROUP_KERNELS[cl]<<<std::min(ctx->gpgrid[cl], t1 - t0), 32, CELLS_SMEM[0][cl], s>>>(GP, t0, t1,
+                                                                                         ctx->d_counter + cl);
+    BDFB_CUDA(cudaGetLastError());
+  }
+  return 0;
+}
+
+static GroupParams group_params(bdfb_ctx* ctx) {
+  GroupParams GP;
+  std::memset(&GP, 0, sizeof GP);
+  GP.P = base_params(ctx, 0.0);
+  GP.P.tiles = ctx->sched[0].d_tiles;
+  GP.P.tile_cells = ctx->sched[0].d_tcells;
+  GP.P.ntiles = ctx->sched[0].ntiles;
+  GP.lu = ctx->d_glu;
+  GP.lu_off = ctx->d_gluoff;
+  GP.dinv = ctx->d_gdinv;
+  GP.perm = ctx->d_gperm;
+  GP.crate = ctx->d_gcrate;
+  GP.failed = ctx->d_gflag;
+  GP.iters = ctx->d_giters;
+  return GP;
+}
+
+static int group_rhs(void* user, const double* y, double* f, cudaStream_t s) {
+  bdfb_ctx* ctx = static_cast<bdfb_ctx*>(user);
+  GroupParams GP = group_params(ctx);
+  GP.mode = 1;
+  GP.zp0 = y;
+  GP.out = f;
+  return group_launch(ctx, GP, s);
+}
+
+static int group_solve(void* user, const double* zp0, const double* zp1, const double* ewt, double gamma,
+                       double gammap, double rl1, double Eq, int setup, double* acor, int* failed,
+                       int64_t* iters, int64_t* sweeps, cudaStream_t s) {
+  bdfb_ctx* ctx = static_cast<bdfb_ctx*>(user);
+  GroupParams GP = group_params(ctx);
+  GP.mode = 0;
+  GP.setup = setup;
+  GP.gamma = gamma;
+  GP.gammap = gammap;
+  GP.rl1 = rl1;
+  GP.Eq = Eq;
+  GP.zp0 = zp0;
+  GP.zp1 = zp1;
+  GP.ewt = ewt;
+  GP.out = acor;
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_gflag, 0, sizeof(int), s));
+  BDFB_CUDA(cudaMemsetAsync(ctx->d_giters, 0, 2 * sizeof(unsigned long long), s));
+  const int r = group_launch(ctx, GP, s);
+  if (r) return r;
+  int fl = 0;
+  unsigned long long it[2] = {0, 0};
+  BDFB_CUDA(cudaMemcpyAsync(&fl, ctx->d_gflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaMemcpyAsync(it, ctx->d_giters, sizeof it, cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaStreamSynchronize(s));
+  *failed = fl;
+  *iters = (int64_t)it[0];
+  *sweeps = (int64_t)it[1];
+  return 0;
+}
+
+static int grouped_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
+  if (ctx->precision != 0 || ctx->predictor || ctx->rec_x) return BDFB_ILL_INPUT;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->gg) {
+    const int64_t C = ctx->ncell;
+    std::vector<int64_t> off(C);
+    int64_t tot = 0;
+    for (int64_t i = 0; i < C; ++i) { off[i] = tot; tot += (int64_t)ctx->h_n[i] * ctx->h_n[i]; }
+    int r = dev_alloc_copy(&ctx->d_gluoff, off.data(), C);
+    if (!r) r = dev_alloc_copy<double>(&ctx->d_glu, nullptr, tot);
+    if (!r) r = dev_alloc_copy<double>(&ctx->d_gdinv, nullptr, ctx->ny);
+    if (!r) r = dev_alloc_copy<int16_t>(&ctx->d_gperm, nullptr, ctx->ny);
+    if (!r) r = dev_alloc_copy<double>(&ctx->d_gcrate, nullptr, C);
+    if (!r) r = dev_alloc_copy<int>(&ctx->d_gflag, nullptr, 1);
+    if (!r) r = dev_alloc_copy<unsigned long long>(&ctx->d_giters, nullptr, 2);
+    for (int cl = 0; cl < NCLASS && !r; ++cl) {
+      int per_sm = 0;
+      if (cudaFuncSetAttribute(GROUP_KERNELS[cl], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               CELLS_SMEM[0][cl]) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, GROUP_KERNELS[cl], 32, CELLS_SMEM[0][cl]) !=
+              cudaSuccess)
+        r = BDFB_CUDA_FAIL;
+      ctx->gpgrid[cl] = std::max(1, per_sm) * sm_count();
+    }
+    GridExternal ext;
+    ext.user = ctx;
+    ext.rhs = group_rhs;
+    ext.solve = group_solve;
+    if (!r) r = grid_create_external(ctx->ny, ext, &ctx->gg);
+    if (r) return r;
+  }
+  grid_set_stream(ctx->gg, s);
+  grid_set_tolerances(ctx->gg, ctx->rtol, ctx->atol);
+  {
+    int r = grid_set_option(ctx->gg, "mxstep", ctx->mxstep);
+    if (!r) r = grid_set_option(ctx->gg, "qmax", ctx->qmax);
+    if (r) return r;
+  }
+  if (ctx->gfresh) {
+    const int r = grid_init(ctx->gg, ctx->t0, ctx->d_z, BDFB_MEM_DEVICE);
+    if (r) return r;
+    ctx->gfresh = false;
+  }
+  const int r = grid_integrate(ctx->gg, tout, y, mem);
+  if (status) {
+    std::vector<int32_t> sv(ctx->ncell, r);
+    if (mem == BDFB_MEM_HOST) std::memcpy(status, sv.data(), ctx->ncell * sizeof(int32_t));
+    else BDFB_CUDA(cudaMemcpy(status, sv.data(), ctx->ncell * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  return r;
+}
+
 extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
   if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
@@ -1652,6 +1955,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
     return r;
   }
   if (ctx->ncell == 0) return BDFB_SUCCESS;
+  if (ctx->grouped) return grouped_integrate(ctx, tout, y, status, mem);
   if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
   cudaStream_t s = ctx->stream;
   const int pr = ctx->precision;
@@ -1717,6 +2021,19 @@ static int fetch_states(bdfb_ctx* ctx, std::vector<CellState>& st) {
 
 extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
   if (!ctx || !out) return BDFB_ILL_INPUT;
+  if (ctx->grouped && ctx->gg) {    // every cell takes every grouped step
+    int64_t g[8];
+    double ms = 0.0;
+    grid_stats(ctx->gg, g, &ms);
+    std::memset(out, 0, sizeof *out);
+    out->ncell = ctx->ncell;
+    const int64_t C = ctx->ncell;
+    out->nsteps = g[0] * C; out->nfevals = g[1] * C; out->nlinsetups = g[2] * C;
+    out->nniters = g[3]; out->nncfails = g[4] * C; out->netfails = g[5] * C;
+    out->max_steps = out->min_steps = g[0];
+    out->last_kernel_ms = ms;
+    return BDFB_SUCCESS;
+  }
   if (ctx->grid) {
     int64_t g[8];
     double ms = 0.0;
@@ -1766,6 +2083,22 @@ extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
     grid_stats(ctx->grid, g, &ms);
     if (mem == BDFB_MEM_HOST) std::memcpy(out, g, sizeof g);
     else BDFB_CUDA(cudaMemcpy(out, g, sizeof g, cudaMemcpyHostToDevice));
+    return BDFB_SUCCESS;
+  }
+  if (ctx->grouped && ctx->gg) {   // the shared counters in every row
+    int64_t g[8];
+    double ms = 0.0, h = 0.0;
+    int q = 0;
+    grid_stats(ctx->gg, g, &ms);
+    grid_next_step(ctx->gg, &q, &h);
+    int64_t hb;
+    std::memcpy(&hb, &h, sizeof hb);
+    const int64_t row[8] = {g[0], g[1], g[2], g[3] / std::max<int64_t>(ctx->ncell, 1), g[4], g[5], q, hb};
+    std::vector<int64_t> v(8 * ctx->ncell);
+    for (int64_t i = 0; i < ctx->ncell; ++i) std::memcpy(v.data() + 8 * i, row, sizeof row);
+    if (ctx->ncell == 0) return BDFB_SUCCESS;
+    if (mem == BDFB_MEM_HOST) std::memcpy(out, v.data(), v.size() * sizeof(int64_t));
+    else BDFB_CUDA(cudaMemcpy(out, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     return BDFB_SUCCESS;
   }
   std::vector<CellState> st;

@@ -287,6 +287,8 @@ struct GridBDF {
   int64_t np = 0, N = 0;
   double A = 1, B = 3, eps = 5e-6, D = 1e-2;
   double cdx = 0.0;           // dim 1: c / dx
+  bool external = false;      // rhs and Newton solve supplied from outside
+  GridExternal ext = {};
   double rtol = 1e-6, atol = 1e-10;
   int maxl = 5;
   int64_t mxstep = 100000;
@@ -360,7 +362,10 @@ static int g_dots(GridBDF* g, const double* x, const double* const* ys, int nv, 
 }
 
 static int g_rhs(GridBDF* g, const double* y, double* f) {
-  if (g->dim == 1)
+  if (g->external) {
+    const int r = g->ext.rhs(g->ext.user, y, f, g->s);
+    if (r) return r;
+  } else if (g->dim == 1)
     k_bruss1_rhs<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->A, g->B, g->reps, g->cdx, y, f);
   else
     k_bruss_rhs<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->A, g->B, g->reps, g->D, y, f);
@@ -479,7 +484,41 @@ static int g_psetup(GridBDF* g, const double* y) {
 }
 
 // Newton iteration; 0 converged (*acnrm = |acor|), 1 recoverable failure, <0 error
+// grouped task-local Newton: one global setup decision, the solves per part
+// outside; any part that fails fails the whole step (retried once with fresh
+// Jacobians when they were stale, then h / 4 by the caller)
+static int g_newton_external(GridBDF* g, double Eq, double* acnrm) {
+  bool tried_fresh = false;
+  for (;;) {
+    bool setup = false;
+    if (!g->setup_done || g->force_setup || std::fabs(g->gamma / g->gammap - 1.0) > 0.3 ||
+        g->nst >= g->nstlp + 20) {
+      setup = true;
+      g->nsetups++;
+      g->gammap = g->gamma;
+      g->nstlp = g->nst;
+      g->force_setup = false;
+      g->setup_done = true;
+    }
+    int failed = 0;
+    int64_t iters = 0, sweeps = 0;
+    const int r = g->ext.solve(g->ext.user, g->zp0, g->zp1, g->ewt, g->gamma, g->gammap, 1.0 / ell1(g, g->q), Eq,
+                               setup ? 1 : 0, g->acor, &failed, &iters, &sweeps, g->s);
+    if (r) return r;
+    g->nni += iters;
+    g->nfe += sweeps;
+    if (!failed) {
+      GCHK(g_wrms(g, g->acor, acnrm));
+      GCHK(bdfb_nv_linear_sum(g->N, 1.0, g->zp0, 1.0, g->acor, g->y, g->s));
+      return 0;
+    }
+    if (!setup && !tried_fresh) { g->force_setup = true; tried_fresh = true; continue; }
+    return 1;
+  }
+}
+
 static int g_newton(GridBDF* g, double Eq, double* acnrm) {
+  if (g->external) return g_newton_external(g, Eq, acnrm);
   const int64_t N = g->N;
   const double l1 = ell1(g, g->q);
   bool tried_fresh = false;
@@ -729,6 +768,40 @@ int grid_create_line_or_cube(int dim, int64_t nx, double A, double B, double eps
   return 0;
 }
 
+int grid_create_external(int64_t N, GridExternal ext, GridBDF** out) {
+  if (N < 1 || !ext.rhs || !ext.solve) return BDFB_ILL_INPUT;
+  GridBDF* g = new (std::nothrow) GridBDF();
+  if (!g) return BDFB_MEM_FAIL;
+  g->external = true;
+  g->ext = ext;
+  g->nx = 0;
+  g->dim = 0;
+  g->np = N;
+  g->N = N;
+  make_tables(g);
+  const size_t vb = g->N * sizeof(double);
+  bool ok = true;
+  auto alloc = [&](double** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; ok = false; }
+  };
+  for (int j = 0; j <= GQMAX + 1; ++j) alloc(&g->z[j], vb);
+  alloc(&g->ewt, vb); alloc(&g->sc, vb); alloc(&g->acor, vb); alloc(&g->acorp, vb); alloc(&g->y, vb); alloc(&g->f, vb);
+  alloc(&g->b, vb); alloc(&g->zp0, vb); alloc(&g->zp1, vb); alloc(&g->tmp, vb); alloc(&g->w, vb);
+  alloc(&g->work, bdfb_nv_work_doubles(g->N, MAXL_MAX) * sizeof(double));
+  alloc(&g->dres, (MAXL_MAX + 2) * sizeof(double));
+  alloc(&g->part, (size_t)sm_count() * 8 * sizeof(double));
+  if (ok && cudaMalloc(&g->dsing, sizeof(int)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost(&g->hres, (MAXL_MAX + 2) * sizeof(double)) != cudaSuccess) ok = false;
+  if (ok && cudaMemset(g->work, 0, bdfb_nv_work_doubles(g->N, MAXL_MAX) * sizeof(double)) != cudaSuccess) ok = false;
+  if (ok && (cudaEventCreate(&g->e0) != cudaSuccess || cudaEventCreate(&g->e1) != cudaSuccess)) ok = false;
+  if (!ok) {
+    grid_destroy(g);
+    return BDFB_MEM_FAIL;
+  }
+  *out = g;
+  return 0;
+}
+
 void grid_destroy(GridBDF* g) {
   if (!g) return;
   for (int j = 0; j <= GQMAX + 1; ++j) cudaFree(g->z[j]);
@@ -811,6 +884,11 @@ void grid_stats(GridBDF* g, int64_t out[8], double* last_ms) {
   out[0] = g->nst; out[1] = g->nfe; out[2] = g->nsetups; out[3] = g->nni;
   out[4] = g->ncfn; out[5] = g->netf; out[6] = g->nli; out[7] = g->nlfail;
   *last_ms = g->last_ms;
+}
+
+void grid_next_step(GridBDF* g, int* q, double* h) {
+  *q = g->q;
+  *h = g->h;
 }
 
 }  // namespace bdfb

@@ -13,6 +13,24 @@ int grid_create(int nx, double A, double B, double eps, double D, GridBDF** out)
 // line of nx points over [0, len) with speed c (first-order upwind)
 int grid_create_line_or_cube(int dim, int64_t nx, double A, double B, double eps, double D, double c,
                              double len, GridBDF** out);
+// A system whose right-hand side and Newton solve are supplied from outside
+// (the grouped "task-local Newton" mode of the per-cell problems): the grid
+// integrator's control (prediction, global error test, step and order
+// selection) drives them.  rhs: f = f(y).  solve: given the predicted z0, z1,
+// the error weights and gamma (gammap: gamma of the last setup; setup = 1
+// asks for fresh Jacobians at z0 first), run the Newton iterations and
+// leave the converged correction in acor; *failed = 1 when any part of the
+// system did not converge; *iters = Newton iterations it took (summed over
+// the parts), *sweeps = right-hand-side evaluations of the whole system they
+// amount to.  Both return 0 or a negative code.
+struct GridExternal {
+  void* user;
+  int (*rhs)(void* user, const double* y, double* f, cudaStream_t s);
+  int (*solve)(void* user, const double* zp0, const double* zp1, const double* ewt, double gamma,
+               double gammap, double rl1, double Eq, int setup, double* acor, int* failed, int64_t* iters,
+               int64_t* sweeps, cudaStream_t s);
+};
+int grid_create_external(int64_t N, GridExternal ext, GridBDF** out);
 void grid_destroy(GridBDF* g);
 void grid_set_stream(GridBDF* g, cudaStream_t s);
 void grid_set_tolerances(GridBDF* g, double rtol, double atol);
@@ -21,5 +39,7 @@ int grid_init(GridBDF* g, double t0, const double* y0, int mem);
 int grid_integrate(GridBDF* g, double tout, double* y, int mem);
 // stats: nst, nfe, nsetups, nni, ncfn, netf, nli (GMRES iterations), nlfail
 void grid_stats(GridBDF* g, int64_t out[8], double* last_ms);
+// order and step size the next step will try
+void grid_next_step(GridBDF* g, int* q, double* h);
 
 }  // namespace bdfb
