@@ -419,7 +419,7 @@ def slowest_rank_time(torch, dist, t, device):
 
 
 def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps=1):
-    """The paper's demonstration problem (Sec. 6) as one coupled system:
+    """The paper's demonstration problem (Sec. 7) as one coupled system:
     Brusselator reactions (A = 1, B = 3.5, eps = 5e-6) advected with c = 0.01
     on a periodic line of nx points over [0, length) by first-order upwind
     differences, the paper's Gaussian-bump initial state, t in [0, tout];

@@ -151,13 +151,13 @@ int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b
  *   reactants[4 r .. 4 r + 3] and produces products[4 r .. 4 r + 3]
  *   (255 = empty slot) at rate k[r] * prod(y[reactants]).
  * kind BDFB_BRUSSELATOR3D: one coupled system (the Sec. 2 "full model" case):
- *   the Brusselator reaction terms of Sec. 6 with diffusion D lap() on a
+ *   the Brusselator reaction terms of Sec. 7 with diffusion D lap() on a
  *   periodic nx^3 grid over [0,1)^3 (7-point Laplacian); k = {A, B, eps, D,
  *   nx} (5 doubles); ncell = nx^3; y is species-major, y[s nx^3 + (i nx + j)
  *   nx + l] for species s = u, v, w.  Integrated with one shared step size,
  *   global WRMS norms, Newton + GMRES (option "maxl", default 5, at most 16)
  *   left-preconditioned by the 3x3 reaction blocks; control on the host.
- * kind BDFB_BRUSSELATOR1D: the demonstration problem of Sec. 6 as one
+ * kind BDFB_BRUSSELATOR1D: the demonstration problem of Sec. 7 as one
  *   coupled system: the same reaction terms with advection -c d/dx (first-
  *   order upwind differences) on a periodic line of nx points over
  *   [0, len); k = {A, B, eps, c, len, nx} (6 doubles); ncell = nx; y is

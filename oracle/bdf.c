@@ -5,7 +5,7 @@
  * The paper names the method (CVODE, an adaptive-order, adaptive-step
  * implicit linear multistep method, Sec. 1), its Newton nonlinear solver and
  * direct / Krylov linear solvers (Sec. 5), and the per-system Newton solve with
- * whole-step retry on failure (Sec. 6), but defers every formula to the CVODE
+ * whole-step retry on failure (Sec. 7), but defers every formula to the CVODE
  * documentation.  The steps below are therefore the standard Nordsieck-form
  * BDF written from its mathematics, with these readings:
  *

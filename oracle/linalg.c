@@ -92,7 +92,7 @@ double or_wrms_norm(int64_t n, const double* x, const double* w) {
 
 /* Gaussian elimination with partial pivoting, P A = L U, row-major.
  * The paper factors the block-diagonal M = I - gamma J block by block
- * (Sec. 5, batched solver over blocks sharing one structure; Sec. 6, per-point
+ * (Sec. 5, batched solver over blocks sharing one structure; Sec. 7, per-point
  * 3x3 block solves); this is the textbook dense algorithm for one block. */
 int or_lu_factor(int n, double* a, int* piv) {
   for (int k = 0; k < n; ++k) {

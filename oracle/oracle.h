@@ -153,7 +153,7 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
 
 /* ---------------- Brusselator grids (grouped, GMRES) -------------------- */
 /* dim 3: reaction-diffusion on a periodic nx^3 grid over [0,1)^3, 7-point
- * Laplacian with coefficient D.  dim 1: the paper's demo (Sec. 6),
+ * Laplacian with coefficient D.  dim 1: the paper's demo (Sec. 7),
  * advection-reaction on a periodic line of nx points over [0, len) with
  * first-order upwind differences for speed c.  Species-major u | v | w. */
 typedef struct {

@@ -6,9 +6,9 @@
  * systems, e.g. chemistry in each grid cell) are integrated one cell at a time
  * with their own step control and a dense LU of the cell's block of
  * M = I - gamma J (the block-diagonal structure of Fig. 1).  The Brusselator
- * (reaction terms of Sec. 6, with diffusion in place of advection) is one
+ * (reaction terms of Sec. 7, with diffusion in place of advection) is one
  * coupled system integrated with Newton + GMRES, preconditioned by the 3x3
- * reaction blocks as in the Sec. 6 global-Newton configuration.
+ * reaction blocks as in the Sec. 7 global-Newton configuration.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -299,13 +299,13 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Brusselator grids (species-major u | v | w), reaction terms of Sec. 6     */
+/* Brusselator grids (species-major u | v | w), reaction terms of Sec. 7     */
 /* u' = T u + A - (w+1) u + v u^2                                            */
 /* v' = T v + w u - v u^2                                                    */
 /* w' = T w + (B - w)/eps - w u                                              */
 /* with the transport T = D lap on the periodic nx^3 grid (dim 3), or the    */
 /* demo's advection T = -c d/dx by first-order upwind differences on the     */
-/* periodic line of nx points (dim 1, Sec. 6)                                */
+/* periodic line of nx points (dim 1, Sec. 7)                                */
 /* ------------------------------------------------------------------------ */
 static int64_t wrapi(int64_t i, int64_t n) { return (i + n) % n; }
 

@@ -2,7 +2,7 @@
 //
 // The paper's submodel use case (Sec. 2): many small independent ODE systems,
 // one per grid cell, whose Jacobian is block diagonal (Fig. 1); each block is
-// solved directly (Sec. 5 batched block solver; Sec. 6 task-local Newton with
+// solved directly (Sec. 5 batched block solver; Sec. 7 task-local Newton with
 // per-block solves, a failed solve repeating the step with a smaller h).
 // Here every cell keeps its own step size and order, and one persistent launch
 // integrates all cells to tout: warps take tiles of cells from an atomic
@@ -783,7 +783,7 @@ static int var_smem(int pr, int v) { return CELLS_SMEM[pr][v]; }
 
 // ------------------------------------------- grouped task-local Newton mode
 // The cells as ONE system (shared h and q, global error norms; the control of
-// the grid integrator drives it) solved the way of the paper's demo (Sec. 6):
+// the grid integrator drives it) solved the way of the paper's demo (Sec. 7):
 // every cell runs its own Newton iteration with its own convergence test and
 // a direct solve of its block, and if any cell fails the whole step is
 // retried with a smaller step size.  Jacobian LU factors persist between the

@@ -1,10 +1,10 @@
 // grid.cu - the grouped ("full model", Sec. 2) integrator: the Brusselator
-// reaction terms of Sec. 6 with diffusion on a periodic nx^3 grid, integrated
+// reaction terms of Sec. 7 with diffusion on a periodic nx^3 grid, integrated
 // as ONE coupled system (shared step size, global FP64 WRMS norms) by
 // variable-order BDF with Newton, the linear systems solved by GMRES built
 // on the NVECTOR kernels (Sec. 5: Krylov solvers need only vector
 // operations) and left-preconditioned by the 3x3 reaction blocks (the
-// block-Jacobi preconditioner of the Sec. 6 global-Newton configuration,
+// block-Jacobi preconditioner of the Sec. 7 global-Newton configuration,
 // each block inverted in closed form like the paper's symbolically generated
 // Gauss-Jordan inverse).
 //
@@ -84,7 +84,7 @@ __global__ void k_bruss_rhs(int nx, double A, double B, double reps, double D, c
   f[2 * np + p] = lap[2] + (B - w) * reps - w * u;
 }
 
-// 1-D advection-reaction line (the demo problem of Sec. 6): -c da/dx by
+// 1-D advection-reaction line (the demo problem of Sec. 7): -c da/dx by
 // first-order upwind differences on a periodic line of np points; cdx = c / dx
 __device__ __forceinline__ double upwind(const double* a, int64_t q, int64_t np, double cdx) {
   if (cdx >= 0.0) return -cdx * (a[q] - a[q == 0 ? np - 1 : q - 1]);

@@ -155,7 +155,7 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
 
 // In-place Gauss-Jordan inverse with partial pivoting (ties to the lowest
 // row) of the n x n FP32 matrix A; the block inverse the paper applies to
-// its 3x3 reaction blocks (Sec. 6), here for any block size.  Returns 0 or
+// its 3x3 reaction blocks (Sec. 7), here for any block size.  Returns 0 or
 // k + 1 when no nonzero pivot exists in column k.  piv (n entries) and colk
 // (n floats): scratch.
 template <int G, int NMAX>

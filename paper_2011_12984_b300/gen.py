@@ -15,7 +15,7 @@ and the recipe is independent of vectorisation or chunking.
 Workloads (the problem statements follow the paper's two use cases, Sec. 2:
 many small independent systems, one per grid cell, and one large coupled
 system; the Brusselator reaction terms are the demonstration problem of
-Sec. 6):
+Sec. 7):
 
 * ``robertson``  - Robertson kinetics, 3 species per cell, rate constants
   scaled per cell by independent log-uniform factors in [0.5, 2].
@@ -297,7 +297,7 @@ class Brusselator3D:
 
 
 def brusselator_steady_state(A: float, B: float, eps: float):
-    """Reaction steady state of the Sec. 6 Brusselator terms:
+    """Reaction steady state of the Sec. 7 Brusselator terms:
     u* = A, w* = B / (1 + eps A), v* = w* / A."""
     w = B / (1.0 + eps * A)
     return A, w / A, w
@@ -319,7 +319,7 @@ def brusselator3d(nx: int, seed: int = DEFAULT_SEED, A: float = 1.0, B: float = 
 
 @dataclass
 class Brusselator1D:
-    """The paper's demonstration problem (Sec. 6): u, v, w advected with speed
+    """The paper's demonstration problem (Sec. 7): u, v, w advected with speed
     ``c`` on a periodic line of ``nx`` points over [0, length), stored
     species-major (``y0[s * nx + i]``, point i at x = i length / nx)."""
     nx: int
@@ -338,7 +338,7 @@ class Brusselator1D:
 
 def brusselator1d(nx: int, length: float = 10.0, A: float = 1.0, B: float = 3.5, eps: float = 5.0e-6,
                   c: float = 0.01, alpha: float = 0.1) -> Brusselator1D:
-    """The demo's initial state (Sec. 6): u = A + p, v = B / A + p, w = 3 + p
+    """The demo's initial state (Sec. 7): u = A + p, v = B / A + p, w = 3 + p
     with the Gaussian bump p(x) = alpha exp(-(x - mu)^2 / (2 sigma^2)),
     mu = length / 2, sigma = length / 4 (no random draws)."""
     x = np.arange(nx, dtype=np.float64) * (length / nx)

@@ -89,7 +89,7 @@ def test_grid_256_cubed_steady_state():
     assert gs[0] > 0
 
 
-# ------------------------------------------------ the 1-D advection demo (Sec. 6)
+# ------------------------------------------------ the 1-D advection demo (Sec. 7)
 @pytest.mark.parametrize("nx,length,tout", [(40, 10.0, 0.5), (200, 100.0, 1.0)])
 def test_line_matches_oracle(nx, length, tout):
     """The demo problem (paper's initial state) against the oracle's grouped

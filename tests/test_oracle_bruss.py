@@ -1,5 +1,5 @@
 """Pins of the oracle's Brusselator systems (the 3-D reaction-diffusion grid
-and the 1-D advection-reaction demo of Sec. 6) and GMRES.
+and the 1-D advection-reaction demo of Sec. 7) and GMRES.
 
 * the reaction steady state u* = A, w* = B/(1 + eps A), v* = w*/A stays put;
 * with u = w = 0 and A = B = 0 the v field diffuses freely: a single Fourier
@@ -107,7 +107,7 @@ def test_fast_species_reaches_its_slow_manifold():
     assert st[6] > 0        # GMRES iterations were used
 
 
-# ------------------------------------------------ the 1-D advection demo (Sec. 6)
+# ------------------------------------------------ the 1-D advection demo (Sec. 7)
 def advect_mode(nx, k, c, length, t):
     """exact solution of the upwind-discretised advection v' = -c D v on the
     periodic line for v(0) = cos(theta j): Re(exp(lambda t) exp(i theta j))
