@@ -51,6 +51,23 @@ class Bruss(C.Structure):
                 ("c", _d), ("len", _d)]
 
 
+_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, _d, _pd, _pd)
+_SOLVE = C.CFUNCTYPE(C.c_int, C.c_void_p, _d, _pd, _d, _pd)
+
+
+class ImexSystem(C.Structure):
+    _fields_ = [("N", _i64), ("user", C.c_void_p), ("fe", _FN), ("fi", _FN), ("isolve", _SOLVE)]
+
+
+class ArkOptions(C.Structure):
+    _fields_ = [("rtol", _d), ("atol", _d), ("mxstep", _i64), ("fixed_h", _d)]
+
+
+class ArkStats(C.Structure):
+    _fields_ = [("nst", _i64), ("nfe", _i64), ("nfi", _i64), ("nni", _i64), ("ncfn", _i64),
+                ("netf", _i64), ("hlast", _d), ("tcur", _d)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -62,6 +79,10 @@ def lib():
                                          _i64, _pd, _pi32, _pi64]
         L.or_cells_integrate_grouped.argtypes = [C.POINTER(Cells), _d, _pd, _d, _d, _d, _i64,
                                                  _pd, _pi64]
+        L.or_ark_table.argtypes = [_pd, _pd, _pd, _pd, _pd]
+        L.or_ark_integrate.argtypes = [C.POINTER(ImexSystem), C.POINTER(ArkOptions), _d, _pd, _d,
+                                       _pd, C.POINTER(ArkStats)]
+        L.or_bruss_ark_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, _i64, _pd, _pi64]
         L.or_bruss_gmres.argtypes = [C.POINTER(Bruss), _pd, _d, _pd, _d, C.c_int, _pd, _pd]
         L.or_bruss_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, C.c_int, _i64,
                                          _pd, _pi64]
@@ -350,6 +371,56 @@ def bruss_integrate(p, t0, tout, rtol, atol, maxl=5, mxstep=100000, y0=None):
     st = np.zeros(8, np.int64)
     ret = lib().or_bruss_integrate(C.byref(s), t0, _p(y0), tout, rtol, atol, maxl, mxstep,
                                    _p(y), _p(st, _pi64))
+    return ret, y, st
+
+
+# ---------------------------------------------------------------- IMEX ARK
+def ark_table():
+    """the ARK3(2)4L[2]SA tables as the oracle holds them: (c, AE, AI, b, bhat)"""
+    c, b, bh = np.zeros(4), np.zeros(4), np.zeros(4)
+    AE, AI = np.zeros((4, 4)), np.zeros((4, 4))
+    lib().or_ark_table(_p(c), _p(AE), _p(AI), _p(b), _p(bh))
+    return c, AE, AI, b, bh
+
+
+def ark_integrate(fe, fi, isolve, y0, t0, tout, rtol=1e-6, atol=1e-10, fixed_h=0.0, mxstep=100000):
+    """The oracle's IMEX ARK on Python callbacks (small systems only):
+    fe(t, y) and fi(t, y) return arrays; isolve(t, y, gamma, x) returns
+    (I - gamma J_I(t, y))^{-1} x.  Returns (y, ret, stats dict)."""
+    y0 = _f64(y0)
+    N = y0.size
+
+    def wrap(fun):
+        def cb(user, t, y, f):
+            out = fun(t, np.ctypeslib.as_array(y, (N,)).copy())
+            np.ctypeslib.as_array(f, (N,))[:] = out
+            return 0 if np.all(np.isfinite(out)) else 1
+        return _FN(cb)
+
+    def cbs(user, t, y, g, x):
+        xv = np.ctypeslib.as_array(x, (N,))
+        xv[:] = isolve(t, np.ctypeslib.as_array(y, (N,)).copy(), g, xv.copy())
+        return 0
+
+    cfe, cfi, csolve = wrap(fe), wrap(fi), _SOLVE(cbs)
+    sys_ = ImexSystem(N, None, cfe, cfi, csolve)
+    opt = ArkOptions(rtol, atol, mxstep, fixed_h)
+    st = ArkStats()
+    y = np.empty(N)
+    ret = lib().or_ark_integrate(C.byref(sys_), C.byref(opt), t0, _p(y0), tout, _p(y), C.byref(st))
+    stats = {k: getattr(st, k) for k, _ in ArkStats._fields_}
+    return y, ret, stats
+
+
+def bruss_ark_integrate(p, t0, tout, rtol, atol, mxstep=100000, y0=None):
+    """the 1-D demonstration problem by IMEX ARK (advection explicit, reaction
+    implicit); returns (ret, y, stats[8] = nst, nfe, nfi, nni, ncfn, netf)"""
+    s = bruss_struct(p)
+    y0 = _f64(p.y0 if y0 is None else y0)
+    y = np.empty_like(y0)
+    st = np.zeros(8, np.int64)
+    ret = lib().or_bruss_ark_integrate(C.byref(s), t0, _p(y0), tout, rtol, atol, mxstep, _p(y),
+                                       _p(st, _pi64))
     return ret, y, st
 
 

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["linalg.c", "bdf.c", "problems.c", "mlp.c"]
+SOURCES = ["linalg.c", "bdf.c", "ark.c", "problems.c", "mlp.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

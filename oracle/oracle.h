@@ -169,6 +169,11 @@ void or_bruss_jv(const or_bruss* p, const double* y, const double* v, double* jv
 int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double tout,
                        double rtol, double atol, int maxl, int64_t mxstep,
                        double* yout, int64_t* stats);
+/* the two parts of the right-hand side and the reaction Jacobian of one
+ * point (row-major 3x3): f = transport + reaction */
+void or_bruss_transport(const or_bruss* p, const double* y, double* f);
+void or_bruss_reaction(const or_bruss* p, const double* y, double* f);
+void or_bruss_reaction_jac(const or_bruss* p, double u, double v, double w, double* J);
 /* one GMRES solve of (I - gamma J(y)) x = b, preconditioner blocks at y,
  * as used inside the integrator; returns iterations; x overwrites b */
 int or_bruss_gmres(const or_bruss* p, const double* y, double gamma, const double* ewt,
@@ -180,5 +185,35 @@ void or_mlp_forward(const double* p, int64_t nrows, const double* X, double* Y);
 double or_mlp_loss_grad(const double* p, int64_t nrows, const double* X, const double* T, double* grad);
 void or_adam_step(int64_t n, double* p, const double* g, double* m, double* v, int64_t t, double lr,
                   double b1, double b2, double eps);
+
+/* ---------------- IMEX additive Runge-Kutta (ark.c) --------------------- */
+/* y' = f_E(t, y) + f_I(t, y): f_E explicit, f_I implicit (the demonstration
+ * problem's integrator, Sec. 7).  isolve: x <- (I - gamma J_I(t, y))^{-1} x. */
+typedef struct {
+  int64_t N;
+  void* user;
+  int (*fe)(void* user, double t, const double* y, double* f);
+  int (*fi)(void* user, double t, const double* y, double* f);
+  int (*isolve)(void* user, double t, const double* y, double gamma, double* x);
+} or_imex_system;
+typedef struct {
+  double rtol, atol;
+  int64_t mxstep;   /* steps per call (default 100000) */
+  double fixed_h;   /* > 0: constant steps (the last one clamped to tout), no error control */
+} or_ark_options;
+typedef struct {
+  int64_t nst, nfe, nfi, nni, ncfn, netf;
+  double hlast, tcur;
+} or_ark_stats;
+/* the ARK3(2)4L[2]SA tables: c[4], AE[4x4], AI[4x4] row-major, b[4], bhat[4] */
+void or_ark_table(double* c, double* AE, double* AI, double* b, double* bhat);
+int or_ark_integrate(const or_imex_system* sys, const or_ark_options* opt, double t0,
+                     const double* y0, double tout, double* yout, or_ark_stats* st);
+/* the 1-D demonstration problem (dim 1): advection explicit, reaction
+ * implicit with exact Newton on the 3x3 point blocks; stats = {nst, nfe,
+ * nfi, nni, ncfn, netf, 0, 0} */
+int or_bruss_ark_integrate(const or_bruss* p, double t0, const double* y0, double tout,
+                           double rtol, double atol, int64_t mxstep, double* yout,
+                           int64_t* stats);
 
 #endif

@@ -347,6 +347,27 @@ static void bruss_jr(const or_bruss* p, double u, double v, double w, double* J)
   J[6] = -w;                        J[7] = 0.0;     J[8] = -1.0 / p->eps - u;
 }
 
+void or_bruss_transport(const or_bruss* p, const double* y, double* f) {
+  int64_t np = bruss_npts(p);
+  for (int s = 0; s < 3; ++s)
+    for (int64_t q = 0; q < np; ++q) f[s * np + q] = transport(p, y + s * np, q);
+}
+
+void or_bruss_reaction(const or_bruss* p, const double* y, double* f) {
+  int64_t np = bruss_npts(p);
+  const double *U = y, *V = y + np, *W = y + 2 * np;
+  for (int64_t q = 0; q < np; ++q) {
+    double u = U[q], v = V[q], w = W[q];
+    f[q] = p->A - (w + 1.0) * u + v * u * u;
+    f[np + q] = w * u - v * u * u;
+    f[2 * np + q] = (p->B - w) / p->eps - w * u;
+  }
+}
+
+void or_bruss_reaction_jac(const or_bruss* p, double u, double v, double w, double* J) {
+  bruss_jr(p, u, v, w, J);
+}
+
 void or_bruss_rhs(const or_bruss* p, const double* y, double* f) {
   int64_t np = bruss_npts(p);
   const double *U = y, *V = y + np, *W = y + 2 * np;
