@@ -447,6 +447,39 @@ def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps
             "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
 
 
+def imex_workload(torch, bdfb, gen, nx, length, tout=10.0, precisions=(0, 1), reps=1):
+    """The paper's demonstration problem with its own integrator type (Sec. 7):
+    IMEX additive Runge-Kutta (ARK3(2)4L[2]SA), first-order upwind advection
+    explicit, Brusselator reactions implicit, every implicit stage solved by
+    Newton on the 3x3 point blocks (one task per GPU), rtol 1e-6,
+    atol 1e-10, t in [0, tout]."""
+    p = gen.brusselator1d(nx, length=length)
+    y0 = torch.from_numpy(p.y0).cuda()
+    y = torch.empty_like(y0)
+    out = {"workload": f"Brusselator 1-D advection-reaction {nx} points x 3, length {length}, c 0.01, "
+                       f"A 1, B 3.5, eps 5e-6, t in [0,{tout}], rtol 1e-6, atol 1e-10, IMEX ARK3(2)4 + "
+                       f"task-local Newton (3x3 blocks)"}
+    for prec in precisions:
+        ts = []
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, imex=1, precision=prec) as li:
+            for _ in range(reps + 1):
+                li.init(0.0, y0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = li.integrate(tout, y)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                if r != 0:
+                    raise RuntimeError(f"imex integrate returned {r}")
+            cs = li.cell_stats()[0]
+        t = min(ts[1:])
+        name = "fp64" if prec == 0 else "fp32_blocks_fp64_residual"
+        out[name] = {"seconds": t, "points_per_s": nx / t, "steps": int(cs[0]), "newton_iters": int(cs[3]),
+                     "error_test_failures": int(cs[5]), "newton_failures": int(cs[4]),
+                     "ms_per_step": 1e3 * t / max(1, int(cs[0]))}
+    return out
+
+
 def grouped_workload(torch, bdfb, gen, ncell=100_000, reps=1, flush=None):
     """The mass-action workload integrated as ONE system (option "grouped":
     one step size and order, error test over every species, task-local
@@ -599,7 +632,11 @@ def run_ours(args):
         configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
                    "mixed_precision_262144x54": mixed54_workload(torch, bdfb, gen, flush=flush),
                    "advection_line_1e7": line_workload(torch, bdfb, gen),
-                   "grouped_vs_per_cell_100k": grouped_workload(torch, bdfb, gen, ncell=NCELL, flush=flush)}
+                   "grouped_vs_per_cell_100k": grouped_workload(torch, bdfb, gen, ncell=NCELL, flush=flush),
+                   # the paper's single-GPU demo sizes (Sec. 7.2: n_x = 1e7, b = 1000, t_f = 10) and
+                   # its one-node Summit problem (Sec. 7.1: n_x = 6e5, b = 10, t_f = 10, run there on 6 GPUs)
+                   "imex_demo_1e7": imex_workload(torch, bdfb, gen, 10_000_000, 1000.0),
+                   "imex_demo_6e5_b10": imex_workload(torch, bdfb, gen, 600_000, 10.0, precisions=(1,))}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
                        ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):
@@ -679,6 +716,9 @@ def run_part(args):
         out = robertson_workload(torch, bdfb, gen, reps=max(1, args.steps))
     elif args.part == "mixed54":
         out = mixed54_workload(torch, bdfb, gen, reps=max(1, args.steps))
+    elif args.part == "imex":
+        out = imex_workload(torch, bdfb, gen, args.line_nx, args.line_length, tout=args.grid_tout,
+                            reps=max(1, args.steps))
     elif args.part == "grouped":
         out = grouped_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "line":
@@ -710,11 +750,13 @@ def main():
     ap.add_argument("--sizes", default=None,
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     ap.add_argument("--part", default="all",
-                    choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line", "grouped"],
+                    choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line", "grouped",
+                             "imex"],
                     help="run one leg alone and print its JSON (for profiling); all: the benchmark")
     ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
     ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid / line: end time")
-    ap.add_argument("--line-nx", type=int, default=10_000_000, help="--part line: points on the line")
+    ap.add_argument("--line-nx", type=int, default=10_000_000, help="--part line / imex: points on the line")
+    ap.add_argument("--line-length", type=float, default=1000.0, help="--part imex: length of the line")
     args = ap.parse_args()
     globals()["NCELL"] = args.ncell
     if args.sizes:

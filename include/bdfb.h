@@ -162,7 +162,20 @@ int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b
  *   order upwind differences) on a periodic line of nx points over
  *   [0, len); k = {A, B, eps, c, len, nx} (6 doubles); ncell = nx; y is
  *   species-major, y[s nx + i] at x = i len / nx.  Integrated like
- *   BDFB_BRUSSELATOR3D (advection implicit inside the Newton operator).
+ *   BDFB_BRUSSELATOR3D (advection implicit inside the Newton operator), or,
+ *   with option "imex" = 1 set before bdfb_init, by the paper's own
+ *   integrator type: an IMEX additive Runge-Kutta method (ARK3(2)4L[2]SA of
+ *   Kennedy and Carpenter) with the advection explicit and the reactions
+ *   implicit, every implicit stage solved by Newton on the 3x3 point blocks
+ *   (exact Jacobian at each iterate, one convergence test over the whole
+ *   vector: the demonstration's task-local solver with one task per GPU);
+ *   embedded error estimate, PID step control, last step clamped on tout.
+ *   An integrate with "imex" = 1 before an init that followed it fails
+ *   with BDFB_ILL_INPUT.  Option "precision" on this kind selects the IMEX
+ *   path's arithmetic: 0 (default) FP64 throughout; 1 forms and solves the
+ *   3x3 Newton blocks in FP32 and keeps FP32 norm weights, with the state,
+ *   stage sums, reaction terms and Newton residual in FP64 (the iteration
+ *   converges to the same FP64 residual test).
  * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
  * arrays live; bdfb_create copies everything it needs, so the caller may
  * free its arrays when bdfb_create returns. */
@@ -262,6 +275,10 @@ int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
 /* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits.
  * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
  * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl.
+ * Option "imex" (BDFB_BRUSSELATOR1D): one row nst, advection evaluations,
+ * reaction evaluations, Newton iterations, ncfn, netf, 0, 0 (bdfb_get_stats:
+ * nfevals = reaction evaluations, nlinsetups = nniters, since the 3x3 blocks
+ * are formed at every iteration).
  * Option "grouped": every row holds the shared counters (nni: the mean over
  * cells of the summed task-local iterations), the order and the step size
  * the next step will try. */

@@ -1,0 +1,682 @@
+// ark.cu - the demonstration problem's time integrator (Sec. 7): an IMEX
+// additive Runge-Kutta method with the advection terms explicit and the stiff
+// reaction terms implicit, on the periodic line of nx points (species-major
+// u | v | w).
+//
+// Method ARK3(2)4L[2]SA of Kennedy and Carpenter (Appl. Numer. Math. 44,
+// 2003): explicit 4-stage table AE, stiffly accurate ESDIRK table AI with
+// diagonal gamma, shared abscissae and weights b (order 3), embedded weights
+// bhat (order 2).  Stage i > 1 solves z = a_i + h gamma f_I(z),
+// a_i = y_n + h sum_{j<i} (AE_ij f_E(z_j) + AI_ij f_I(z_j)), by Newton from
+// the predictor z = a_i + h gamma f_I(y_n) with the reaction Jacobian of
+// every point at the current iterate:
+// the implicit part is pointwise, so (I - h gamma J_I) is block diagonal and
+// each point's 3x3 block is formed and inverted in registers (adjugate
+// formula, the counterpart of the paper's symbolically generated Gauss-Jordan
+// inverse) — nothing is stored between iterations.  The convergence test is
+// over the whole vector: on one GPU the demonstration's task-local solver has
+// one task.  Each stage keeps g_j = f_E(z_j) + f_I(z_j) and f_I(z_j) (so
+// a_i = y_n + h sum_j (AE_ij g_j + (AI_ij - AE_ij) f_I(z_j)) and the step's
+// solution and error estimate read the four g_j only).
+//
+// Precision 0 does everything in FP64 (3x3 blocks by the adjugate formula).
+// Precision 1 keeps FP64 for the state, the stage sums, the reaction terms
+// and the Newton residual a_i + h gamma f_I(z) - z, and forms and solves the
+// 3x3 Newton blocks in FP32 (Schur complement on the stiff species w, whose
+// diagonal 1 + h gamma (1/eps + u) dominates): the Newton iteration then
+// converges to the same FP64 residual, at a rate that the FP32 solve changes
+// by ~cond(M) 1e-7.  Norm weights are FP32 there.  B300's FP64 rate (1/64
+// of FP32) makes the FP64 block solve the cost of the whole step.
+// Step control (PID), failure handling and the initial step are
+// the readings stated beside the host code.  Control runs on the host; each
+// Newton iteration and each step's error norm returns one scalar (per-block
+// partial sums reduced on the host in a fixed order).
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "ark.cuh"
+
+namespace bdfb {
+
+namespace {
+
+constexpr int AT = 256;        // threads per block
+constexpr int NS = 4;          // stages
+
+struct Tab {
+  double c[NS], ae[NS][NS], ai[NS][NS], b[NS], bh[NS];
+};
+
+// the published rational coefficients of ARK3(2)4L[2]SA
+Tab ark_tab() {
+  Tab T = {};
+  const double gam = 1767732205903.0 / 4055673282236.0;
+  T.c[0] = 0.0;
+  T.c[1] = 1767732205903.0 / 2027836641118.0;
+  T.c[2] = 0.6;
+  T.c[3] = 1.0;
+  T.ae[1][0] = 1767732205903.0 / 2027836641118.0;
+  T.ae[2][0] = 5535828885825.0 / 10492691773637.0;
+  T.ae[2][1] = 788022342437.0 / 10882634858940.0;
+  T.ae[3][0] = 6485989280629.0 / 16251701735622.0;
+  T.ae[3][1] = -4246266847089.0 / 9704473918619.0;
+  T.ae[3][2] = 10755448449292.0 / 10357097424841.0;
+  T.ai[1][0] = gam;
+  T.ai[1][1] = gam;
+  T.ai[2][0] = 2746238789719.0 / 10658868560708.0;
+  T.ai[2][1] = -640167445237.0 / 6845629431997.0;
+  T.ai[2][2] = gam;
+  T.ai[3][0] = 1471266399579.0 / 7840856788654.0;
+  T.ai[3][1] = -4482444167858.0 / 7529755066697.0;
+  T.ai[3][2] = 11266239266428.0 / 11593286722821.0;
+  T.ai[3][3] = gam;
+  for (int i = 0; i < NS; ++i) T.b[i] = T.ai[3][i];
+  T.bh[0] = 2756255671327.0 / 12835298489170.0;
+  T.bh[1] = -10771552573575.0 / 22201958757719.0;
+  T.bh[2] = 9247589265047.0 / 10645013368117.0;
+  T.bh[3] = 2193209047091.0 / 5459859503100.0;
+  return T;
+}
+
+struct Par {
+  int64_t np;
+  double A, B, reps, cdx;      // reps = 1/eps, cdx = c/dx
+};
+
+__device__ __forceinline__ void react(const Par& P, double u, double v, double w, double f[3]) {
+  f[0] = P.A - (w + 1.0) * u + v * u * u;
+  f[1] = w * u - v * u * u;
+  f[2] = (P.B - w) * P.reps - w * u;
+}
+
+// -c da/dx at point q by upwind differences (backward for c >= 0)
+__device__ __forceinline__ double advect(const Par& P, const double* a, int64_t q) {
+  if (P.cdx >= 0.0) return -P.cdx * (a[q] - a[q == 0 ? P.np - 1 : q - 1]);
+  return -P.cdx * (a[q + 1 == P.np ? 0 : q + 1] - a[q]);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < AT / 32; ++w) s += sh[w];
+  return s;
+}
+
+// norm weights: FP64 (precision 0) or FP32 (precision 1)
+template <int PREC>
+struct Wt {
+  using T = double;
+};
+template <>
+struct Wt<1> {
+  using T = float;
+};
+
+// one stage's right-hand sides at z: g = f_E + f_I and f_I
+__global__ void __launch_bounds__(AT) k_ark_rhs(Par P, const double* __restrict__ z, double* __restrict__ g,
+                                                double* __restrict__ fi) {
+  const int64_t np = P.np;
+  for (int64_t q = (int64_t)blockIdx.x * AT + threadIdx.x; q < np; q += (int64_t)gridDim.x * AT) {
+    double r[3];
+    react(P, z[q], z[np + q], z[2 * np + q], r);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      g[s * np + q] = advect(P, z + s * np, q) + r[s];
+      fi[s * np + q] = r[s];
+    }
+  }
+}
+
+struct Stage {
+  int nj;                      // previous stages
+  double ce[NS], ci[NS];       // AE_ij and AI_ij - AE_ij of row i
+  const double* g[NS];
+  const double* fi[NS];
+};
+
+// 3x3 Newton block M = I - hg J_R(u, v, w) solved for r, FP64 adjugate
+__device__ __forceinline__ bool solve64(const Par& P, double hg, double u, double v, double w, const double r[3],
+                                        double d[3]) {
+  const double m00 = 1.0 - hg * (-(w + 1.0) + 2.0 * u * v), m01 = -hg * (u * u), m02 = hg * u;
+  const double m10 = -hg * (w - 2.0 * u * v), m11 = 1.0 + hg * (u * u), m12 = -hg * u;
+  const double m20 = hg * w, m21 = 0.0, m22 = 1.0 + hg * (P.reps + u);
+  const double c00 = m11 * m22 - m12 * m21, c01 = m02 * m21 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+  const double c10 = m12 * m20 - m10 * m22, c11 = m00 * m22 - m02 * m20, c12 = m02 * m10 - m00 * m12;
+  const double c20 = m10 * m21 - m11 * m20, c21 = m01 * m20 - m00 * m21, c22 = m00 * m11 - m01 * m10;
+  const double det = m00 * c00 + m01 * c10 + m02 * c20;
+  const double rd = 1.0 / det;
+  d[0] = (c00 * r[0] + c01 * r[1] + c02 * r[2]) * rd;
+  d[1] = (c10 * r[0] + c11 * r[1] + c12 * r[2]) * rd;
+  d[2] = (c20 * r[0] + c21 * r[1] + c22 * r[2]) * rd;
+  return det != 0.0;
+}
+
+// the same block in FP32: eliminate w first (row 3 of M has no v entry and
+// the dominant diagonal 1 + hg (1/eps + u)), then Cramer on the 2x2 (u, v)
+// Schur complement
+__device__ __forceinline__ bool solve32(const Par& P, double hg, double u, double v, double w, const double r[3],
+                                        double d[3]) {
+  const float h = (float)hg, uf = (float)u, vf = (float)v, wf = (float)w;
+  const float uu = uf * uf, uv2 = 2.0f * uf * vf;
+  const float m00 = 1.0f - h * (uv2 - (wf + 1.0f)), m01 = -h * uu, m02 = h * uf;
+  const float m10 = -h * (wf - uv2), m11 = 1.0f + h * uu, m12 = -h * uf;
+  const float m20 = h * wf, m22 = 1.0f + h * ((float)P.reps + uf);
+  const float r0 = (float)r[0], r1 = (float)r[1], r2 = (float)r[2];
+  const float iw = 1.0f / m22;
+  const float s0 = m02 * iw, s1 = m12 * iw;
+  const float a00 = m00 - s0 * m20, a10 = m10 - s1 * m20;
+  const float b0 = r0 - s0 * r2, b1 = r1 - s1 * r2;
+  const float det = a00 * m11 - m01 * a10;
+  const float id = 1.0f / det;
+  const float du = (b0 * m11 - m01 * b1) * id;
+  const float dv = (a00 * b1 - a10 * b0) * id;
+  const float dw = (r2 - m20 * du) * iw;
+  d[0] = (double)du;
+  d[1] = (double)dv;
+  d[2] = (double)dw;
+  return det != 0.0f && m22 != 0.0f;
+}
+
+// One Newton iteration of an implicit stage at every point.  FIRST: form
+// a = y + h sum_j (ce_j g_j + ci_j fi_j), store it, and start from the
+// predictor z = a + hg fi_0.  delta = (I - hg J_R(z))^{-1} (a + hg f_I(z) - z);
+// z += delta; per-block partial sums of (delta ewt)^2; *bad = 1 on a
+// singular block or a non-finite value.
+template <bool FIRST, int PREC>
+__global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, double hg,
+                                                   const double* __restrict__ y, double* __restrict__ a,
+                                                   double* __restrict__ z,
+                                                   const typename Wt<PREC>::T* __restrict__ ewt,
+                                                   double* __restrict__ part, int* __restrict__ bad) {
+  __shared__ double sh[AT / 32];
+  const int64_t np = P.np;
+  double acc = 0.0;
+  bool ok = true;
+  for (int64_t q = (int64_t)blockIdx.x * AT + threadIdx.x; q < np; q += (int64_t)gridDim.x * AT) {
+    double av[3], zv[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int64_t i = s * np + q;
+      if (FIRST) {
+        double sum = 0.0;
+        for (int j = 0; j < S.nj; ++j) sum += S.ce[j] * S.g[j][i] + S.ci[j] * S.fi[j][i];
+        av[s] = y[i] + h * sum;
+        a[i] = av[s];
+        zv[s] = av[s] + hg * S.fi[0][i];
+      } else {
+        av[s] = a[i];
+        zv[s] = z[i];
+      }
+    }
+    double f[3], r[3], d[3];
+    react(P, zv[0], zv[1], zv[2], f);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) r[s] = av[s] + hg * f[s] - zv[s];
+    const bool nonsing = PREC == 0 ? solve64(P, hg, zv[0], zv[1], zv[2], r, d)
+                                   : solve32(P, hg, zv[0], zv[1], zv[2], r, d);
+    if (!nonsing || !isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2])) ok = false;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) z[s * np + q] = zv[s] + d[s];
+    if (PREC == 0) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const double e = d[s] * (double)ewt[s * np + q];
+        acc += e * e;
+      }
+    } else {
+      float a32 = 0.0f;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const float e = (float)d[s] * (float)ewt[s * np + q];
+        a32 += e * e;
+      }
+      acc += (double)a32;
+    }
+  }
+  if (!ok) *bad = 1;
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+struct Finish {
+  double b[NS], d[NS];         // b and b - bhat
+  const double* g[NS];
+};
+
+// ynew = y + h sum b_k g_k, err = h sum (b_k - bhat_k) g_k; partial sums
+// of (err ewt)^2; ewtn = weights of ynew
+template <int PREC>
+__global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h, double rtol, double atol,
+                                                   const double* __restrict__ y,
+                                                   const typename Wt<PREC>::T* __restrict__ ewt,
+                                                   double* __restrict__ ynew,
+                                                   typename Wt<PREC>::T* __restrict__ ewtn,
+                                                   double* __restrict__ part) {
+  using W = typename Wt<PREC>::T;
+  __shared__ double sh[AT / 32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
+    double s = 0.0, e = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const double g = F.g[k][i];
+      s += F.b[k] * g;
+      e += F.d[k] * g;
+    }
+    const double yn = y[i] + h * s;
+    ynew[i] = yn;
+    if (PREC == 0) {
+      ewtn[i] = (W)(1.0 / (rtol * fabs(yn) + atol));
+      const double ee = h * e * (double)ewt[i];
+      acc += ee * ee;
+    } else {
+      ewtn[i] = (W)(1.0f / ((float)rtol * fabsf((float)yn) + (float)atol));
+      const float ee = (float)(h * e) * (float)ewt[i];
+      acc += (double)(ee * ee);
+    }
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(AT) k_ark_ewt(int64_t N, double rtol, double atol, const double* __restrict__ y,
+                                                typename Wt<PREC>::T* __restrict__ ewt) {
+  for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
+    if (PREC == 0) ewt[i] = 1.0 / (rtol * fabs(y[i]) + atol);
+    else ewt[i] = 1.0f / ((float)rtol * fabsf((float)y[i]) + (float)atol);
+  }
+}
+
+// initial step: per-block maxima of |f_i| / (0.1 |y_i| + atol)
+__global__ void __launch_bounds__(AT) k_ark_ratio(int64_t N, double atol, const double* __restrict__ f,
+                                                  const double* __restrict__ y, double* __restrict__ part) {
+  __shared__ double sh[AT / 32];
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT)
+    m = fmax(m, fabs(f[i]) / (0.1 * fabs(y[i]) + atol));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < AT / 32; ++w) m = fmax(m, sh[w]);
+    part[blockIdx.x] = fmax(m, sh[0]);
+  }
+}
+
+// out = y + hg f0
+__global__ void __launch_bounds__(AT) k_ark_axpy(int64_t N, double hg, const double* __restrict__ y,
+                                                 const double* __restrict__ f0, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT)
+    out[i] = y[i] + hg * f0[i];
+}
+
+// partial sums of (((f1 - f0) / hg) ewt)^2
+template <int PREC>
+__global__ void __launch_bounds__(AT) k_ark_dq(int64_t N, double hg, const double* __restrict__ f1,
+                                               const double* __restrict__ f0,
+                                               const typename Wt<PREC>::T* __restrict__ ewt,
+                                               double* __restrict__ part) {
+  __shared__ double sh[AT / 32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
+    const double d = (f1[i] - f0[i]) / hg * (double)ewt[i];
+    acc += d * d;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+}  // namespace
+
+struct ArkLine {
+  Par P = {};
+  int64_t N = 0;
+  double rtol = 1e-6, atol = 1e-10;
+  int64_t mxstep = 100000;
+  int prec = 0;
+  cudaStream_t s = nullptr;
+  Tab T = {};
+  double *y = nullptr, *ynew = nullptr, *a = nullptr, *z = nullptr;
+  void *ewt = nullptr, *ewtn = nullptr;   // double (precision 0) or float (1)
+  double* g[NS] = {};          // f_E + f_I of each stage
+  double* fi[NS] = {};         // f_I of each stage
+  double *part = nullptr, *hpart = nullptr;
+  int *dbad = nullptr, *hbad = nullptr;
+  int nblk = 0;
+  double t = 0.0, h = 0.0, e1 = 0.0, e2 = 0.0;
+  bool started = false, first = true, initialized = false;
+  int64_t nst = 0, nfe = 0, nfi = 0, nni = 0, ncfn = 0, netf = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.0f;
+};
+
+#define ACHK(call)     \
+  do {                 \
+    int r_ = (call);   \
+    if (r_) return r_; \
+  } while (0)
+
+static int blocks_for(int64_t n) {
+  const int64_t b = (n + AT - 1) / AT;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 8));
+}
+
+template <int PREC>
+static const typename Wt<PREC>::T* wts(const void* p) {
+  return static_cast<const typename Wt<PREC>::T*>(p);
+}
+
+// sum (or max) of the per-block partials of the last reduction kernel
+static int host_reduce(ArkLine* g, int nb, bool max_of, double* out, bool* bad) {
+  BDFB_CUDA(cudaMemcpyAsync(g->hpart, g->part, nb * sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  if (bad) BDFB_CUDA(cudaMemcpyAsync(g->hbad, g->dbad, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  BDFB_CUDA(cudaStreamSynchronize(g->s));
+  double r = 0.0;
+  for (int b = 0; b < nb; ++b) r = max_of ? std::max(r, g->hpart[b]) : r + g->hpart[b];
+  *out = r;
+  if (bad) *bad = *g->hbad != 0;
+  return 0;
+}
+
+static int ark_rhs(ArkLine* g, const double* z, int k) {
+  k_ark_rhs<<<blocks_for(g->P.np), AT, 0, g->s>>>(g->P, z, g->g[k], g->fi[k]);
+  BDFB_CUDA(cudaGetLastError());
+  g->nfe++;
+  g->nfi++;
+  return 0;
+}
+
+static int ark_ewt(ArkLine* g) {
+  if (g->prec == 0)
+    k_ark_ewt<0><<<blocks_for(g->N), AT, 0, g->s>>>(g->N, g->rtol, g->atol, g->y, static_cast<double*>(g->ewt));
+  else
+    k_ark_ewt<1><<<blocks_for(g->N), AT, 0, g->s>>>(g->N, g->rtol, g->atol, g->y, static_cast<float*>(g->ewt));
+  BDFB_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// Initial step (reading): the BDF path's difference estimate of ||y''||
+// along h f, applied to f = f_E + f_I; h0 = half the estimate within
+// [100 eps t, min(0.1 |tout - t|, the step where h |f_i| = 0.1 |y_i| + atol)].
+static int ark_h0(ArkLine* g, double tout) {
+  const int64_t N = g->N;
+  const int nb = blocks_for(N);
+  double* f0 = g->g[0];
+  double* yt = g->a;
+  double* f1 = g->z;
+  ACHK(ark_rhs(g, g->y, 0));             // g_0 = f_E + f_I at y
+  k_ark_ratio<<<nb, AT, 0, g->s>>>(N, g->atol, f0, g->y, g->part);
+  BDFB_CUDA(cudaGetLastError());
+  double inv = 0.0;
+  ACHK(host_reduce(g, nb, true, &inv, nullptr));
+  const double tdist = std::fabs(tout - g->t);
+  const double hlb = 100.0 * 2.220446049250313e-16 * std::max(std::fabs(g->t), std::fabs(tout));
+  double hub = 0.1 * tdist;
+  if (inv * hub > 1.0) hub = 1.0 / inv;
+  if (hub < hlb) hub = hlb;
+  double hg = std::sqrt(hlb * hub), hnew = hg;
+  for (int it = 0; it < 4; ++it) {
+    k_ark_axpy<<<nb, AT, 0, g->s>>>(N, hg, g->y, f0, yt);
+    k_ark_rhs<<<blocks_for(g->P.np), AT, 0, g->s>>>(g->P, yt, f1, g->fi[1]);
+    if (g->prec == 0) k_ark_dq<0><<<nb, AT, 0, g->s>>>(N, hg, f1, f0, wts<0>(g->ewt), g->part);
+    else k_ark_dq<1><<<nb, AT, 0, g->s>>>(N, hg, f1, f0, wts<1>(g->ewt), g->part);
+    BDFB_CUDA(cudaGetLastError());
+    g->nfe++;
+    g->nfi++;
+    double ss = 0.0;
+    ACHK(host_reduce(g, nb, false, &ss, nullptr));
+    const double ydd = std::sqrt(ss / (double)N);
+    hnew = (ydd * hub * hub > 2.0) ? std::sqrt(2.0 / ydd) : std::sqrt(hg * hub);
+    const double rat = hnew / hg;
+    if (it > 0 && rat > 0.5 && rat < 2.0) break;
+    hg = hnew;
+  }
+  double h0 = 0.5 * hnew;
+  if (h0 < hlb) h0 = hlb;
+  if (h0 > hub) h0 = hub;
+  g->h = tout >= g->t ? h0 : -h0;
+  g->started = true;
+  return 0;
+}
+
+template <bool FIRST>
+static void launch_newton(ArkLine* g, const Stage& S, double hs, double hg, int nb) {
+  if (g->prec == 0)
+    k_ark_newton<FIRST, 0><<<nb, AT, 0, g->s>>>(g->P, S, hs, hg, g->y, g->a, g->z, wts<0>(g->ewt), g->part,
+                                                g->dbad);
+  else
+    k_ark_newton<FIRST, 1><<<nb, AT, 0, g->s>>>(g->P, S, hs, hg, g->y, g->a, g->z, wts<1>(g->ewt), g->part,
+                                                g->dbad);
+}
+
+// Newton solve of implicit stage i (1..3) with step hs; *failed on a
+// recoverable failure.  Test (reading): rate R = max(0.3 R, del/del_prev),
+// converged when del min(1, R) <= 0.1, diverged when del > 2.3 del_prev,
+// at most 3 iterations.
+static int ark_stage(ArkLine* g, int i, double hs, bool* failed) {
+  const int64_t np = g->P.np;
+  const int nb = blocks_for(np);
+  Stage S = {};
+  S.nj = i;
+  for (int j = 0; j < i; ++j) {
+    S.ce[j] = g->T.ae[i][j];
+    S.ci[j] = g->T.ai[i][j] - g->T.ae[i][j];
+    S.g[j] = g->g[j];
+    S.fi[j] = g->fi[j];
+  }
+  const double hg = hs * g->T.ai[i][i];
+  double crate = 1.0, delp = 0.0;
+  *failed = true;
+  BDFB_CUDA(cudaMemsetAsync(g->dbad, 0, sizeof(int), g->s));
+  for (int m = 1; m <= 3; ++m) {
+    if (m == 1) launch_newton<true>(g, S, hs, hg, nb);
+    else launch_newton<false>(g, S, hs, hg, nb);
+    BDFB_CUDA(cudaGetLastError());
+    g->nfi++;
+    double ss = 0.0;
+    bool bad = false;
+    ACHK(host_reduce(g, nb, false, &ss, &bad));
+    if (bad) return 0;
+    g->nni++;
+    const double del = std::sqrt(ss / (double)g->N);
+    if (!std::isfinite(del)) return 0;
+    if (m > 1) crate = std::max(0.3 * crate, del / delp);
+    if (del * std::min(1.0, crate) <= 0.1) { *failed = false; return 0; }
+    if (m >= 2 && del > 2.3 * delp) return 0;
+    delp = del;
+  }
+  return 0;
+}
+
+int ark_create(int64_t nx, double A, double B, double eps, double c, double len, ArkLine** out) {
+  if (!out || nx < 2 || nx > ((int64_t)1 << 30) || !(eps > 0.0) || !std::isfinite(c) || !(len > 0.0))
+    return BDFB_ILL_INPUT;
+  ArkLine* g = new (std::nothrow) ArkLine();
+  if (!g) return BDFB_MEM_FAIL;
+  g->P.np = nx;
+  g->P.A = A;
+  g->P.B = B;
+  g->P.reps = 1.0 / eps;
+  g->P.cdx = c / (len / (double)nx);
+  g->N = 3 * nx;
+  g->T = ark_tab();
+  g->nblk = (int)std::max<int64_t>(1, (int64_t)sm_count() * 8);
+  const size_t vb = g->N * sizeof(double);
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; ok = false; }
+  };
+  alloc((void**)&g->y, vb); alloc((void**)&g->ynew, vb); alloc((void**)&g->a, vb); alloc((void**)&g->z, vb);
+  alloc(&g->ewt, vb); alloc(&g->ewtn, vb);       // room for either weight type
+  for (int k = 0; k < NS; ++k) { alloc((void**)&g->g[k], vb); alloc((void**)&g->fi[k], vb); }
+  alloc((void**)&g->part, g->nblk * sizeof(double));
+  if (ok && cudaMalloc(&g->dbad, sizeof(int)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost(&g->hpart, g->nblk * sizeof(double)) != cudaSuccess) { g->hpart = nullptr; ok = false; }
+  if (ok && cudaMallocHost(&g->hbad, sizeof(int)) != cudaSuccess) { g->hbad = nullptr; ok = false; }
+  if (ok && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess)) ok = false;
+  if (!ok) {
+    ark_destroy(g);
+    return BDFB_MEM_FAIL;
+  }
+  *out = g;
+  return 0;
+}
+
+void ark_destroy(ArkLine* g) {
+  if (!g) return;
+  cudaFree(g->y); cudaFree(g->ynew); cudaFree(g->ewt); cudaFree(g->ewtn); cudaFree(g->a); cudaFree(g->z);
+  for (int k = 0; k < NS; ++k) { cudaFree(g->g[k]); cudaFree(g->fi[k]); }
+  cudaFree(g->part);
+  cudaFree(g->dbad);
+  if (g->hpart) cudaFreeHost(g->hpart);
+  if (g->hbad) cudaFreeHost(g->hbad);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+  delete g;
+}
+
+void ark_set_stream(ArkLine* g, cudaStream_t s) { g->s = s; }
+void ark_set_tolerances(ArkLine* g, double rtol, double atol) { g->rtol = rtol; g->atol = atol; }
+
+int ark_set_mxstep(ArkLine* g, int64_t v) {
+  if (v < 1) return BDFB_ILL_INPUT;
+  g->mxstep = v;
+  return 0;
+}
+
+int ark_set_precision(ArkLine* g, int prec) {
+  if (prec != 0 && prec != 1) return BDFB_ILL_INPUT;
+  g->prec = prec;                // the weights are recomputed at the next integrate
+  return 0;
+}
+
+int ark_init(ArkLine* g, double t0, const double* y0, int mem) {
+  BDFB_CUDA(cudaMemcpyAsync(g->y, y0, g->N * sizeof(double),
+                            mem == BDFB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->s));
+  BDFB_CUDA(cudaStreamSynchronize(g->s));
+  g->t = t0;
+  g->h = 0.0;
+  g->e1 = g->e2 = 0.0;
+  g->started = false;
+  g->first = true;
+  g->initialized = true;
+  g->nst = g->nfe = g->nfi = g->nni = g->ncfn = g->netf = 0;
+  return 0;
+}
+
+// Step control (reading; the paper names ARKODE's IMEX method but no
+// controller): PID on e_k = 1.5 dsm_k (>= 1e-10),
+// eta = 0.96 e_n^{-0.58/3} e_{n-1}^{0.21/3} e_{n-2}^{-0.1/3} (missing history
+// replaced by the newest value), within [0.1, 20] (1e4 after the first step),
+// and 1 when it falls in [1, 1.5].  Error-test failure:
+// eta = 0.96 (1.5 dsm)^{-1/3} within [0.1, 0.9], at most 0.3 from the second
+// failure in a step, 7 failures -> BDFB_ERR_FAILURE.  Newton failure: eta =
+// 0.25, 10 failures -> BDFB_CONV_FAILURE.  The last step lands on tout.
+static int ark_step(ArkLine* g, double tout, bool* reached) {
+  const int64_t N = g->N;
+  const int nbN = blocks_for(N);
+  int ncf = 0, nef = 0;
+  bool have_stage1 = false;
+  for (;;) {
+    bool last = false;
+    double hs = g->h;
+    if ((g->t + g->h - tout) * g->h >= 0.0) { hs = tout - g->t; last = true; }
+    if (g->t + hs == g->t) return BDFB_ERR_FAILURE;
+    if (!have_stage1) { ACHK(ark_rhs(g, g->y, 0)); have_stage1 = true; }
+    bool failed = false;
+    for (int i = 1; i < NS && !failed; ++i) {
+      ACHK(ark_stage(g, i, hs, &failed));
+      if (!failed) ACHK(ark_rhs(g, g->z, i));
+    }
+    if (failed) {
+      g->ncfn++;
+      if (++ncf >= 10) return BDFB_CONV_FAILURE;
+      g->h = hs * 0.25;
+      continue;
+    }
+    Finish F = {};
+    for (int k = 0; k < NS; ++k) {
+      F.b[k] = g->T.b[k];
+      F.d[k] = g->T.b[k] - g->T.bh[k];
+      F.g[k] = g->g[k];
+    }
+    if (g->prec == 0)
+      k_ark_finish<0><<<nbN, AT, 0, g->s>>>(N, F, hs, g->rtol, g->atol, g->y, wts<0>(g->ewt), g->ynew,
+                                            static_cast<double*>(g->ewtn), g->part);
+    else
+      k_ark_finish<1><<<nbN, AT, 0, g->s>>>(N, F, hs, g->rtol, g->atol, g->y, wts<1>(g->ewt), g->ynew,
+                                            static_cast<float*>(g->ewtn), g->part);
+    BDFB_CUDA(cudaGetLastError());
+    double ss = 0.0;
+    ACHK(host_reduce(g, nbN, false, &ss, nullptr));
+    const double dsm = std::sqrt(ss / (double)N);
+    if (!(dsm <= 1.0)) {
+      g->netf++;
+      if (++nef >= 7) return BDFB_ERR_FAILURE;
+      double eta = 0.96 * std::pow(1.5 * dsm, -1.0 / 3.0);
+      if (!(eta >= 0.1)) eta = 0.1;
+      if (eta > 0.9) eta = 0.9;
+      if (nef >= 2 && eta > 0.3) eta = 0.3;
+      g->h = hs * eta;
+      continue;
+    }
+    std::swap(g->y, g->ynew);
+    std::swap(g->ewt, g->ewtn);
+    g->t = last ? tout : g->t + hs;
+    g->nst++;
+    double e0 = 1.5 * dsm;
+    if (e0 < 1e-10) e0 = 1e-10;
+    const double p1 = g->e1 > 0.0 ? g->e1 : e0, p2 = g->e2 > 0.0 ? g->e2 : p1;
+    double eta = 0.96 * std::pow(e0, -0.58 / 3.0) * std::pow(p1, 0.21 / 3.0) * std::pow(p2, -0.1 / 3.0);
+    const double cap = g->first ? 1.0e4 : 20.0;
+    if (eta > cap) eta = cap;
+    if (eta < 0.1) eta = 0.1;
+    if (eta >= 1.0 && eta <= 1.5) eta = 1.0;
+    g->e2 = p1;
+    g->e1 = e0;
+    g->h = hs * eta;
+    g->first = false;
+    *reached = last;
+    return 0;
+  }
+}
+
+int ark_integrate(ArkLine* g, double tout, double* y, int mem) {
+  if (!g->initialized) return BDFB_ILL_INPUT;
+  int ret = 0;
+  BDFB_CUDA(cudaEventRecord(g->ev0, g->s));
+  if (tout != g->t) {
+    ACHK(ark_ewt(g));
+    if (!g->started) ret = ark_h0(g, tout);
+    const int64_t nst0 = g->nst;
+    while (!ret && (tout - g->t) * g->h > 0.0) {
+      if (g->nst - nst0 >= g->mxstep) { ret = BDFB_TOO_MUCH_WORK; break; }
+      bool reached = false;
+      ret = ark_step(g, tout, &reached);
+      if (ret) break;
+      if (reached) { g->t = tout; break; }
+    }
+  }
+  BDFB_CUDA(cudaEventRecord(g->ev1, g->s));
+  if (y)
+    BDFB_CUDA(cudaMemcpyAsync(y, g->y, g->N * sizeof(double),
+                              mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->s));
+  BDFB_CUDA(cudaStreamSynchronize(g->s));
+  cudaEventElapsedTime(&g->last_ms, g->ev0, g->ev1);
+  return ret;
+}
+
+void ark_stats(ArkLine* g, int64_t out[8], double* last_ms) {
+  out[0] = g->nst; out[1] = g->nfe; out[2] = g->nfi; out[3] = g->nni;
+  out[4] = g->ncfn; out[5] = g->netf; out[6] = 0; out[7] = 0;
+  *last_ms = g->last_ms;
+}
+
+}  // namespace bdfb

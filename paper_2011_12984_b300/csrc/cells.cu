@@ -22,6 +22,7 @@
 
 #include "cellcore.cuh"
 #include "mixed.cuh"
+#include "ark.cuh"
 #include "grid.cuh"
 #include "mlp.cuh"
 
@@ -1169,7 +1170,11 @@ struct bdfb_ctx {
   cudaStream_t cstream[NVAR] = {};  // one per variant, forked from `stream`
   float last_ms = 0.f;
   int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
-  GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D: the grouped grid integrator
+  GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D / 1D: the grouped grid integrator
+  ArkLine* ark = nullptr;     // BDFB_BRUSSELATOR1D with option "imex": the IMEX ARK integrator
+  int imex = 0;
+  int line_prec = 0;          // "precision" of the IMEX path
+  double line_par[6] = {};    // A, B, eps, c, length, nx of the 1-D line
   // option "grouped": the cells as one system with task-local Newton solves
   int grouped = 0;
   bool gfresh = true;         // the grouped integrator needs the state of bdfb_init
@@ -1199,6 +1204,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   grid_destroy(c->grid);
+  ark_destroy(c->ark);
   grid_destroy(c->gg);
   cudaFree(c->d_glu); cudaFree(c->d_gluoff); cudaFree(c->d_gdinv); cudaFree(c->d_gperm);
   cudaFree(c->d_gcrate); cudaFree(c->d_gflag); cudaFree(c->d_giters);
@@ -1368,6 +1374,7 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
     const int64_t nx = (int64_t)par[5];
     if ((double)nx != par[5] || nx != prob->ncell) { free_ctx(c); return BDFB_ILL_INPUT; }
     TRY(grid_create_line_or_cube(1, nx, par[0], par[1], par[2], 0.0, par[3], par[4], &c->grid));
+    for (int i = 0; i < 6; ++i) c->line_par[i] = par[i];
     c->ny = 3 * prob->ncell;
     BDFB_CUDA(cudaEventCreate(&c->ev0));
     BDFB_CUDA(cudaEventCreate(&c->ev1));
@@ -1493,6 +1500,7 @@ extern "C" int bdfb_set_stream(bdfb_ctx* ctx, void* stream) {
   if (!ctx) return BDFB_ILL_INPUT;
   ctx->stream = as_stream(stream);
   if (ctx->grid) grid_set_stream(ctx->grid, ctx->stream);
+  if (ctx->ark) ark_set_stream(ctx->ark, ctx->stream);
   return BDFB_SUCCESS;
 }
 
@@ -1502,12 +1510,39 @@ extern "C" int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol) {
   ctx->rtol = rtol;
   ctx->atol = atol;
   if (ctx->grid) grid_set_tolerances(ctx->grid, rtol, atol);
+  if (ctx->ark) ark_set_tolerances(ctx->ark, rtol, atol);
   return BDFB_SUCCESS;
 }
 
 extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   if (!ctx || !key) return BDFB_ILL_INPUT;
-  if (ctx->grid) return grid_set_option(ctx->grid, key, v);
+  if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "imex")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && !ctx->ark) {
+      const double* p = ctx->line_par;
+      int r = ark_create((int64_t)p[5], p[0], p[1], p[2], p[3], p[4], &ctx->ark);
+      if (r) return r;
+      ark_set_stream(ctx->ark, ctx->stream);
+      ark_set_tolerances(ctx->ark, ctx->rtol, ctx->atol);
+      r = ark_set_mxstep(ctx->ark, ctx->mxstep);
+      if (!r) r = ark_set_precision(ctx->ark, ctx->line_prec);
+      if (r) return r;
+    }
+    ctx->imex = (int)v;
+    return BDFB_SUCCESS;
+  }
+  if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "precision")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    ctx->line_prec = (int)v;
+    return ctx->ark ? ark_set_precision(ctx->ark, (int)v) : BDFB_SUCCESS;
+  }
+  if (ctx->grid) {
+    if (!std::strcmp(key, "mxstep") && v >= 1) {
+      ctx->mxstep = v;
+      if (ctx->ark) ark_set_mxstep(ctx->ark, v);
+    }
+    return grid_set_option(ctx->grid, key, v);
+  }
   if (!std::strcmp(key, "mxstep")) {
     if (v < 1 || v > 1000000000) return BDFB_ILL_INPUT;
     ctx->mxstep = v;
@@ -1547,7 +1582,8 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
   if (!ctx || !std::isfinite(t0) || (ctx->ny > 0 && !y0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
   if (ctx->grid) {
-    const int r = grid_init(ctx->grid, t0, y0, mem);
+    int r = grid_init(ctx->grid, t0, y0, mem);
+    if (!r && ctx->ark) r = ark_init(ctx->ark, t0, y0, mem);
     ctx->initialized = r == 0;
     return r;
   }
@@ -1946,7 +1982,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
   if (ctx->grid) {
-    const int r = grid_integrate(ctx->grid, tout, y, mem);
+    const int r = ctx->imex ? ark_integrate(ctx->ark, tout, y, mem) : grid_integrate(ctx->grid, tout, y, mem);
     if (status) {
       const int32_t sv = r;
       if (mem == BDFB_MEM_HOST) *status = sv;
@@ -2034,6 +2070,18 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
     out->last_kernel_ms = ms;
     return BDFB_SUCCESS;
   }
+  if (ctx->grid && ctx->imex) {    // IMEX ARK: blocks are formed at every Newton iteration
+    int64_t g[8];
+    double ms = 0.0;
+    ark_stats(ctx->ark, g, &ms);
+    std::memset(out, 0, sizeof *out);
+    out->ncell = ctx->ncell;
+    out->nsteps = g[0]; out->nfevals = g[2]; out->nlinsetups = g[3]; out->nniters = g[3];
+    out->nncfails = g[4]; out->netfails = g[5];
+    out->max_steps = out->min_steps = g[0];
+    out->last_kernel_ms = ms;
+    return BDFB_SUCCESS;
+  }
   if (ctx->grid) {
     int64_t g[8];
     double ms = 0.0;
@@ -2080,7 +2128,8 @@ extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (ctx->grid) {
     int64_t g[8];
     double ms = 0.0;
-    grid_stats(ctx->grid, g, &ms);
+    if (ctx->imex) ark_stats(ctx->ark, g, &ms);
+    else grid_stats(ctx->grid, g, &ms);
     if (mem == BDFB_MEM_HOST) std::memcpy(out, g, sizeof g);
     else BDFB_CUDA(cudaMemcpy(out, g, sizeof g, cudaMemcpyHostToDevice));
     return BDFB_SUCCESS;
