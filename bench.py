@@ -718,7 +718,7 @@ def run_part(args):
         out = mixed54_workload(torch, bdfb, gen, reps=max(1, args.steps))
     elif args.part == "imex":
         out = imex_workload(torch, bdfb, gen, args.line_nx, args.line_length, tout=args.grid_tout,
-                            reps=max(1, args.steps))
+                            precisions=(args.precision,), reps=max(1, args.steps))
     elif args.part == "grouped":
         out = grouped_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "line":
