@@ -480,6 +480,37 @@ def imex_workload(torch, bdfb, gen, nx, length, tout=10.0, precisions=(0, 1), re
     return out
 
 
+def shared_sparse_workload(torch, bdfb, gen, ncell=100_000, n=128, reps=1):
+    """Cells sharing one sparse network (the submodel case with one pattern
+    for every block, Sec. 5): a banded n-species mechanism (reactions within
+    windows of 6 species), integrated as one grouped system with task-local
+    Newton solves on the shared sparse LU (BDFB_MASSACTION_SHARED); and the
+    10-species shared network of the learned-guess leg on both the shared
+    sparse path and the per-cell dense path."""
+    out = {}
+    for name, p in ((f"banded_{n}_species", gen.mass_action_banded(ncell, n=n)),
+                    ("network_10_species", gen.mass_action_shared(ncell, n=10))):
+        y0 = torch.from_numpy(bdfb.species_major(p)).cuda()
+        y = torch.empty_like(y0)
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, shared_network=True) as I:
+            t = timed_integrations(torch, I, y0, y, TOUT, reps)
+            st, row = I.stats(), I.cell_stats()[0]
+        yc = bdfb.cell_major(p, y.cpu().numpy())
+        out[name] = {"workload": f"{ncell} cells sharing one {int(p.n[0])}-species network "
+                                 f"({int(p.rxn_off[1])} reactions), t in [0,1e-3], rtol 1e-6, atol 1e-10",
+                     "cells_per_s": ncell / t, "s": t, "steps": st["max_steps"],
+                     "newton_iters_per_cell": st["nniters"] / ncell,
+                     "lu_entries_with_fill": int(row[6]), "matrix_entries": int(row[7]),
+                     "accuracy": accuracy(p, yc, ncheck=128)}
+        if int(p.n[0]) <= 56:
+            yd = torch.from_numpy(p.y0).cuda()
+            yo = torch.empty_like(yd)
+            with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, autotune=1) as I:
+                td = timed_integrations(torch, I, yd, yo, TOUT, max(reps, 2))
+            out[name]["per_cell_dense_cells_per_s"] = ncell / td
+    return out
+
+
 def grouped_workload(torch, bdfb, gen, ncell=100_000, reps=1, flush=None):
     """The mass-action workload integrated as ONE system (option "grouped":
     one step size and order, error test over every species, task-local
@@ -635,6 +666,7 @@ def run_ours(args):
                    "grouped_vs_per_cell_100k": grouped_workload(torch, bdfb, gen, ncell=NCELL, flush=flush),
                    # the paper's single-GPU demo sizes (Sec. 7.2: n_x = 1e7, b = 1000, t_f = 10) and
                    # its one-node Summit problem (Sec. 7.1: n_x = 6e5, b = 10, t_f = 10, run there on 6 GPUs)
+                   "shared_sparse_network": shared_sparse_workload(torch, bdfb, gen, ncell=NCELL),
                    "imex_demo_1e7": imex_workload(torch, bdfb, gen, 10_000_000, 1000.0),
                    "imex_demo_6e5_b10": imex_workload(torch, bdfb, gen, 600_000, 10.0, precisions=(1,))}
     variants = {"batched_fp64": value}
@@ -719,6 +751,8 @@ def run_part(args):
     elif args.part == "imex":
         out = imex_workload(torch, bdfb, gen, args.line_nx, args.line_length, tout=args.grid_tout,
                             precisions=(args.precision,), reps=max(1, args.steps))
+    elif args.part == "shared":
+        out = shared_sparse_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "grouped":
         out = grouped_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "line":
@@ -751,7 +785,7 @@ def main():
                     help="comma-separated cell sizes (default 3,10,32,54: the workload)")
     ap.add_argument("--part", default="all",
                     choices=["all", "grid", "nvector", "learned", "robertson", "mixed54", "line", "grouped",
-                             "imex"],
+                             "imex", "shared"],
                     help="run one leg alone and print its JSON (for profiling); all: the benchmark")
     ap.add_argument("--grid-nx", type=int, default=256, help="--part grid: grid points per dimension")
     ap.add_argument("--grid-tout", type=float, default=1.0, help="--part grid / line: end time")

@@ -56,7 +56,8 @@ typedef enum {
   BDFB_ROBERTSON = 0,
   BDFB_MASSACTION = 1,
   BDFB_BRUSSELATOR3D = 2,
-  BDFB_BRUSSELATOR1D = 3
+  BDFB_BRUSSELATOR1D = 3,
+  BDFB_MASSACTION_SHARED = 4
 } bdfb_kind;
 
 const char* bdfb_strerror(int code);
@@ -143,6 +144,35 @@ int bdfb_batched_lu_solve(int64_t nb, int n, const double* lu, const int32_t* pi
 int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b, double* x,
                              int32_t* sweeps, void* stream);
 
+/* ------------------------------- shared-pattern block-sparse matrices
+ * Block-diagonal matrices whose square blocks share one sparsity pattern
+ * (Sec. 5: the submodel case's blocks keep one copy of the CSR row pointers
+ * and column indices for all blocks).  bdfb_sparse_create analyses the
+ * pattern once on the host: LU without pivoting, pivots taken in row order
+ * (the paper's batched QR pivots neither), fill-in and elimination schedule.
+ * Device values are entry-major: entry e of block b at v[e nb + b] (one
+ * thread per block; a warp's accesses are 32 consecutive doubles).
+ *  create:  n (1..2048), nnz, rowptr[n+1], colind[nnz] (host, 0-based, no
+ *           duplicates, columns in any order); the diagonal joins the
+ *           pattern.  BDFB_ILL_INPUT on a malformed pattern.  *out owns
+ *           device copies of the schedule; free with bdfb_sparse_destroy.
+ *  lu_nnz:  entries of the factor's pattern (with fill).
+ *  load:    lu (device, lu_nnz x nb doubles) <- the blocks' values a
+ *           (device, block-major: a[b nnz + e] in the CSR order of create),
+ *           fill entries zero.
+ *  factor:  every block in place: L unit lower (multipliers), U upper with
+ *           its diagonal replaced by the reciprocal; info[b] (device, may be
+ *           NULL) = 0 or k + 1 for a zero or non-finite pivot at step k.
+ *  solve:   x <- M_b^{-1} x for every block, x device entry-major (x[i nb + b]).
+ * All calls are asynchronous on `stream`. */
+typedef struct bdfb_sparse bdfb_sparse;
+int bdfb_sparse_create(int n, int nnz, const int32_t* rowptr, const int32_t* colind, bdfb_sparse** out);
+void bdfb_sparse_destroy(bdfb_sparse* sp);
+int64_t bdfb_sparse_lu_nnz(const bdfb_sparse* sp);
+int bdfb_sparse_load(const bdfb_sparse* sp, int64_t nb, const double* a, double* lu, void* stream);
+int bdfb_sparse_factor(const bdfb_sparse* sp, int64_t nb, double* lu, int32_t* info, void* stream);
+int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, double* x, void* stream);
+
 /* ---------------------------------------------------- per-cell problems
  * kind BDFB_ROBERTSON: k[3 c + {0,1,2}] = (k1, k2, k3) of cell c, n = 3.
  * kind BDFB_MASSACTION: cell c has n[c] species (1 <= n <= 56) stored at
@@ -176,6 +206,17 @@ int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b
  *   3x3 Newton blocks in FP32 and keeps FP32 norm weights, with the state,
  *   stage sums, reaction terms and Newton residual in FP64 (the iteration
  *   converges to the same FP64 residual test).
+ * kind BDFB_MASSACTION_SHARED: ncell cells that share ONE network (the
+ *   submodel case of Sec. 2 and Sec. 5 with one sparsity pattern for every
+ *   block): n[0] species (1..255), reactions rxn_off[0] = 0 .. rxn_off[1]
+ *   (at most 65535), reactants / products / k of that network (host memory
+ *   only; y_off unused).  y is species-major, y[s ncell + c].  Integrated as
+ *   one grouped system (shared step size and order, error test over all
+ *   species) with task-local Newton solves per cell on the shared sparse
+ *   pattern of M = I - gamma J (bdfb_sparse's LU, one thread per cell);
+ *   options mxstep and qmax.  bdfb_get_cell_stats gives one row: nst, nfe,
+ *   nsetups, nni (summed over cells), ncfn, netf, LU entries with fill,
+ *   entries of M's pattern.
  * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
  * arrays live; bdfb_create copies everything it needs, so the caller may
  * free its arrays when bdfb_create returns. */

@@ -38,6 +38,7 @@ ROBERTSON = 0
 MASSACTION = 1
 BRUSSELATOR3D = 2
 BRUSSELATOR1D = 3
+MASSACTION_SHARED = 4
 
 _vp = C.c_void_p
 _i64 = C.c_int64
@@ -85,6 +86,12 @@ _sig("bdfb_nv_work_doubles", _i64, [_i64, C.c_int])
 _sig("bdfb_batched_lu_factor", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
 _sig("bdfb_batched_lu_solve", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp])
 _sig("bdfb_batched_solve_mixed", C.c_int, [_i64, C.c_int, _vp, _vp, _vp, _vp, _vp])
+_sig("bdfb_sparse_create", C.c_int, [C.c_int, C.c_int, _vp, _vp, C.POINTER(_vp)])
+_sig("bdfb_sparse_destroy", None, [_vp])
+_sig("bdfb_sparse_lu_nnz", _i64, [_vp])
+_sig("bdfb_sparse_load", C.c_int, [_vp, _i64, _vp, _vp, _vp])
+_sig("bdfb_sparse_factor", C.c_int, [_vp, _i64, _vp, _vp, _vp])
+_sig("bdfb_sparse_solve", C.c_int, [_vp, _i64, _vp, _vp, _vp])
 _sig("bdfb_create", C.c_int, [C.POINTER(Problem), C.POINTER(_vp)])
 _sig("bdfb_destroy", None, [_vp])
 _sig("bdfb_set_stream", C.c_int, [_vp, _vp])
@@ -270,10 +277,65 @@ def mlp_train(X, T, params, m, v, packed, grad, loss_hist, batch, nsteps, t0=0, 
 
 
 # ------------------------------------------------------------- integrator
-class Integrator:
-    """Owns a ``bdfb_ctx``.  ``problem`` is a generator problem (host arrays)."""
+class SparsePattern:
+    """One sparsity pattern shared by every block of a block-diagonal matrix
+    (``bdfb_sparse``).  rowptr / colind: host int32 CSR of the n x n block."""
 
-    def __init__(self, problem, rtol=1e-6, atol=1e-10, stream=None, **options):
+    def __init__(self, n, rowptr, colind):
+        self._rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self._ci = np.ascontiguousarray(colind, dtype=np.int32)
+        self.n = int(n)
+        self.nnz = int(self._ci.size)
+        h = _vp()
+        check(lib.bdfb_sparse_create(self.n, self.nnz, self._rp.ctypes.data,
+                                     self._ci.ctypes.data if self.nnz else None, C.byref(h)),
+              "bdfb_sparse_create")
+        self.h = h
+        self.lu_nnz = int(lib.bdfb_sparse_lu_nnz(h))
+
+    def load(self, a, lu, stream=None):
+        """lu [lu_nnz, nb] <- a [nb, nnz] (CUDA float64 tensors)"""
+        check(lib.bdfb_sparse_load(self.h, a.shape[0], _dptr(a), _dptr(lu), _stream(stream)), "bdfb_sparse_load")
+
+    def factor(self, lu, info=None, stream=None):
+        check(lib.bdfb_sparse_factor(self.h, lu.shape[1], _dptr(lu), _dptr(info), _stream(stream)),
+              "bdfb_sparse_factor")
+
+    def solve(self, lu, x, stream=None):
+        """x [n, nb] <- M_b^{-1} x"""
+        check(lib.bdfb_sparse_solve(self.h, lu.shape[1], _dptr(lu), _dptr(x), _stream(stream)),
+              "bdfb_sparse_solve")
+
+    def close(self):
+        if self.h:
+            lib.bdfb_sparse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def species_major(problem, y=None):
+    """cell-major values (the generators' layout) -> species-major (the
+    layout of a shared-network integrator, y[s ncell + c])"""
+    y = problem.y0 if y is None else y
+    n = int(problem.n[0])
+    return np.ascontiguousarray(np.asarray(y).reshape(problem.ncell, n).T).reshape(-1)
+
+
+def cell_major(problem, y):
+    n = int(problem.n[0])
+    return np.ascontiguousarray(np.asarray(y).reshape(n, problem.ncell).T).reshape(-1)
+
+
+class Integrator:
+    """Owns a ``bdfb_ctx``.  ``problem`` is a generator problem (host arrays).
+    ``shared_network=True`` (a problem whose cells all carry cell 0's network)
+    creates a BDFB_MASSACTION_SHARED context: one copy of the network, states
+    species-major (see ``species_major``), grouped integration on the shared
+    sparse pattern."""
+
+    def __init__(self, problem, rtol=1e-6, atol=1e-10, stream=None, shared_network=False, **options):
         self._keep = []
         p = Problem()
         p.mem = MEM_HOST
@@ -284,7 +346,17 @@ class Integrator:
             self._keep.append(a)
             return a.ctypes.data
 
-        if problem.kind == "robertson":
+        if shared_network:
+            if problem.kind != "massaction" or not getattr(problem, "shared", False):
+                raise ValueError("shared_network needs a problem whose cells share one network")
+            R = int(problem.rxn_off[1] - problem.rxn_off[0])
+            p.kind = MASSACTION_SHARED
+            p.n = host(problem.n[:1], np.int32)
+            p.rxn_off = host([0, R], np.int64)
+            p.reactants = host(problem.reactants[:R], np.uint8)
+            p.products = host(problem.products[:R], np.uint8)
+            p.k = host(problem.k[:R], np.float64)
+        elif problem.kind == "robertson":
             p.kind = ROBERTSON
             p.k = host(problem.k, np.float64)
         elif problem.kind == "brusselator3d":
@@ -312,6 +384,7 @@ class Integrator:
         else:
             self.ncell = problem.ncell
             self.ny = int(problem.y_off[-1])
+        self.stat_rows = 1 if shared_network else self.ncell
         self.set_stream(stream)
         check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")
         for k, v in options.items():
@@ -379,7 +452,7 @@ class Integrator:
                      "bdfb_set_record")
 
     def cell_stats(self):
-        out = np.zeros((self.ncell, 8), np.int64)
+        out = np.zeros((self.stat_rows, 8), np.int64)
         check(lib.bdfb_get_cell_stats(self.h, out.ctypes.data, MEM_HOST), "bdfb_get_cell_stats")
         return out
 

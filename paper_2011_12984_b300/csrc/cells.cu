@@ -25,6 +25,7 @@
 #include "ark.cuh"
 #include "grid.cuh"
 #include "mlp.cuh"
+#include "sparse.cuh"
 
 namespace bdfb {
 
@@ -1172,6 +1173,7 @@ struct bdfb_ctx {
   int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D / 1D: the grouped grid integrator
   ArkLine* ark = nullptr;     // BDFB_BRUSSELATOR1D with option "imex": the IMEX ARK integrator
+  SharedInt* shared = nullptr;  // BDFB_MASSACTION_SHARED: grouped cells on one sparse network
   int imex = 0;
   int line_prec = 0;          // "precision" of the IMEX path
   double line_par[6] = {};    // A, B, eps, c, length, nx of the 1-D line
@@ -1205,6 +1207,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaSetDevice(c->device);
   grid_destroy(c->grid);
   ark_destroy(c->ark);
+  shared_destroy(c->shared);
   grid_destroy(c->gg);
   cudaFree(c->d_glu); cudaFree(c->d_gluoff); cudaFree(c->d_gdinv); cudaFree(c->d_gperm);
   cudaFree(c->d_gcrate); cudaFree(c->d_gflag); cudaFree(c->d_giters);
@@ -1348,7 +1351,7 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   *out = nullptr;
   if (prob->ncell < 0 ||
       (prob->kind != BDFB_ROBERTSON && prob->kind != BDFB_MASSACTION && prob->kind != BDFB_BRUSSELATOR3D &&
-       prob->kind != BDFB_BRUSSELATOR1D) ||
+       prob->kind != BDFB_BRUSSELATOR1D && prob->kind != BDFB_MASSACTION_SHARED) ||
       (prob->mem != BDFB_MEM_HOST && prob->mem != BDFB_MEM_DEVICE) || !prob->k)
     return BDFB_ILL_INPUT;
   bdfb_ctx* c = new (std::nothrow) bdfb_ctx();
@@ -1356,6 +1359,14 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
   cudaGetDevice(&c->device);
   c->kind = prob->kind;
   c->ncell = prob->ncell;
+  if (prob->kind == BDFB_MASSACTION_SHARED) {   // grouped cells on one sparse network
+    TRY(shared_create(prob, &c->shared));
+    c->ny = (int64_t)prob->n[0] * prob->ncell;
+    BDFB_CUDA(cudaEventCreate(&c->ev0));
+    BDFB_CUDA(cudaEventCreate(&c->ev1));
+    *out = c;
+    return BDFB_SUCCESS;
+  }
   if (prob->kind == BDFB_BRUSSELATOR3D) {   // one coupled system on a grid
     std::vector<double> par;
     TRY(fetch(par, prob->k, 5, prob->mem));
@@ -1500,6 +1511,7 @@ extern "C" int bdfb_set_stream(bdfb_ctx* ctx, void* stream) {
   if (!ctx) return BDFB_ILL_INPUT;
   ctx->stream = as_stream(stream);
   if (ctx->grid) grid_set_stream(ctx->grid, ctx->stream);
+  if (ctx->shared) shared_set_stream(ctx->shared, ctx->stream);
   if (ctx->ark) ark_set_stream(ctx->ark, ctx->stream);
   return BDFB_SUCCESS;
 }
@@ -1510,12 +1522,14 @@ extern "C" int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol) {
   ctx->rtol = rtol;
   ctx->atol = atol;
   if (ctx->grid) grid_set_tolerances(ctx->grid, rtol, atol);
+  if (ctx->shared) shared_set_tolerances(ctx->shared, rtol, atol);
   if (ctx->ark) ark_set_tolerances(ctx->ark, rtol, atol);
   return BDFB_SUCCESS;
 }
 
 extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   if (!ctx || !key) return BDFB_ILL_INPUT;
+  if (ctx->shared) return shared_set_option(ctx->shared, key, v);
   if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "imex")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     if (v == 1 && !ctx->ark) {
@@ -1581,6 +1595,11 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
 extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem) {
   if (!ctx || !std::isfinite(t0) || (ctx->ny > 0 && !y0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->shared) {
+    const int r = shared_init(ctx->shared, t0, y0, mem);
+    ctx->initialized = r == 0;
+    return r;
+  }
   if (ctx->grid) {
     int r = grid_init(ctx->grid, t0, y0, mem);
     if (!r && ctx->ark) r = ark_init(ctx->ark, t0, y0, mem);
@@ -1981,6 +2000,15 @@ static int grouped_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* sta
 extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
   if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->shared) {
+    const int r = shared_integrate(ctx->shared, tout, y, mem);
+    if (status && ctx->ncell > 0) {
+      std::vector<int32_t> sv(ctx->ncell, r);
+      if (mem == BDFB_MEM_HOST) std::memcpy(status, sv.data(), ctx->ncell * sizeof(int32_t));
+      else BDFB_CUDA(cudaMemcpy(status, sv.data(), ctx->ncell * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return r;
+  }
   if (ctx->grid) {
     const int r = ctx->imex ? ark_integrate(ctx->ark, tout, y, mem) : grid_integrate(ctx->grid, tout, y, mem);
     if (status) {
@@ -2070,6 +2098,20 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
     out->last_kernel_ms = ms;
     return BDFB_SUCCESS;
   }
+  if (ctx->shared) {               // every cell takes every grouped step
+    int64_t g[8];
+    double ms = 0.0, h = 0.0;
+    int q = 0;
+    shared_stats(ctx->shared, g, &ms, &q, &h);
+    std::memset(out, 0, sizeof *out);
+    const int64_t C = ctx->ncell;
+    out->ncell = C;
+    out->nsteps = g[0] * C; out->nfevals = g[1] * C; out->nlinsetups = g[2] * C;
+    out->nniters = g[3]; out->nncfails = g[4] * C; out->netfails = g[5] * C;
+    out->max_steps = out->min_steps = g[0];
+    out->last_kernel_ms = ms;
+    return BDFB_SUCCESS;
+  }
   if (ctx->grid && ctx->imex) {    // IMEX ARK: blocks are formed at every Newton iteration
     int64_t g[8];
     double ms = 0.0;
@@ -2125,6 +2167,15 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
 extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (!ctx || (!out && ctx->ncell > 0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->shared) {
+    int64_t g[8];
+    double ms = 0.0, h = 0.0;
+    int q = 0;
+    shared_stats(ctx->shared, g, &ms, &q, &h);
+    if (mem == BDFB_MEM_HOST) std::memcpy(out, g, sizeof g);
+    else BDFB_CUDA(cudaMemcpy(out, g, sizeof g, cudaMemcpyHostToDevice));
+    return BDFB_SUCCESS;
+  }
   if (ctx->grid) {
     int64_t g[8];
     double ms = 0.0;
@@ -2172,7 +2223,7 @@ extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
   if (!ctx || !out) return BDFB_ILL_INPUT;
   std::memset(out, 0, 3 * NCLASS * sizeof(int32_t));
   if (trial_ms) std::memset(trial_ms, 0, NCLASS * NVAR * sizeof(float));
-  if (ctx->grid) return BDFB_SUCCESS;
+  if (ctx->grid || ctx->shared) return BDFB_SUCCESS;
   const bool learn = ctx->predictor || ctx->rec_x;
   for (int64_t i = 0; i < ctx->ncell; ++i) out[3 * ctx->h_cls[i] + 2]++;
   for (int cl = 0; cl < NCLASS; ++cl) {
@@ -2189,14 +2240,14 @@ extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
 }
 
 extern "C" int bdfb_load_mlp(bdfb_ctx* ctx, const void* packed, int64_t bytes) {
-  if (!ctx || ctx->grid || (packed && bytes != PACKED_BYTES)) return BDFB_ILL_INPUT;
+  if (!ctx || ctx->grid || ctx->shared || (packed && bytes != PACKED_BYTES)) return BDFB_ILL_INPUT;
   if (packed && (reinterpret_cast<uintptr_t>(packed) & 15u)) return BDFB_ILL_INPUT;
   ctx->mlp = packed;
   return BDFB_SUCCESS;
 }
 
 extern "C" int bdfb_set_record(bdfb_ctx* ctx, float* x, float* t, int64_t cap, unsigned long long* count) {
-  if (!ctx || ctx->grid) return BDFB_ILL_INPUT;
+  if (!ctx || ctx->grid || ctx->shared) return BDFB_ILL_INPUT;
   if (!x) {
     ctx->rec_x = nullptr; ctx->rec_t = nullptr; ctx->rec_cap = 0; ctx->rec_count = nullptr;
     return BDFB_SUCCESS;

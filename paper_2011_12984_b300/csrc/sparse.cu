@@ -1,0 +1,634 @@
+// sparse.cu - shared-pattern block-diagonal matrices (Sec. 5: the blocks of
+// the submodel case share one sparsity pattern, so one copy of the CSR index
+// arrays serves every block) with a batched sparse LU, and the grouped
+// integrator of many cells that share one sparse mass-action network.
+//
+// B300 design: one thread per block, values stored entry-major
+// (entry e of block b at v[e nb + b]).  The symbolic factorisation (fill-in
+// of LU without pivoting in the given order, and the elimination schedule)
+// is computed once on the host; every thread then runs the same schedule on
+// its own block, so the warp never diverges and every load and store of a
+// warp touches 32 consecutive doubles.  The paper's batched sparse QR needs
+// no pivoting; LU here takes the pivots in order too (M = I - gamma J has a
+// unit diagonal plus gamma times the Jacobian's; a zero pivot is reported
+// and fails the Newton solve, which repeats the step with a smaller h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "grid.cuh"
+#include "sparse.cuh"
+
+namespace bdfb {
+
+namespace {
+
+constexpr int ST = 128;                // threads per block of the per-cell kernels
+constexpr int SP_NMAX = 2048;          // largest block dimension
+
+// Symbolic LU of one pattern (no pivoting, natural order) and the schedules
+// the kernels run.  Entries of the factor's pattern are numbered row-major.
+struct Symb {
+  int n = 0, nnz = 0;
+  std::vector<int> pos;                           // n*n -> entry or -1
+  std::vector<int> diag;                          // [n]
+  std::vector<int> lptr, lpos, uptr, upos, tptr, tgt;
+  std::vector<int> rlptr, rlpos, rlcol, ruptr, rupos, rucol;
+};
+
+Symb symbolic(int n, const std::vector<uint8_t>& A) {
+  std::vector<uint8_t> P = A;
+  for (int i = 0; i < n; ++i) P[(size_t)i * n + i] = 1;
+  for (int k = 0; k < n; ++k)
+    for (int i = k + 1; i < n; ++i) {
+      if (!P[(size_t)i * n + k]) continue;
+      for (int j = k + 1; j < n; ++j)
+        if (P[(size_t)k * n + j]) P[(size_t)i * n + j] = 1;
+    }
+  Symb S;
+  S.n = n;
+  S.pos.assign((size_t)n * n, -1);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (P[(size_t)i * n + j]) S.pos[(size_t)i * n + j] = S.nnz++;
+  S.diag.resize(n);
+  for (int k = 0; k < n; ++k) S.diag[k] = S.pos[(size_t)k * n + k];
+  S.lptr.push_back(0); S.uptr.push_back(0); S.tptr.push_back(0);
+  for (int k = 0; k < n; ++k) {
+    std::vector<int> L, U;
+    for (int i = k + 1; i < n; ++i)
+      if (P[(size_t)i * n + k]) L.push_back(i);
+    for (int j = k + 1; j < n; ++j)
+      if (P[(size_t)k * n + j]) U.push_back(j);
+    for (int i : L) S.lpos.push_back(S.pos[(size_t)i * n + k]);
+    for (int j : U) S.upos.push_back(S.pos[(size_t)k * n + j]);
+    for (int i : L)
+      for (int j : U) S.tgt.push_back(S.pos[(size_t)i * n + j]);   // present by construction of the fill
+    S.lptr.push_back((int)S.lpos.size());
+    S.uptr.push_back((int)S.upos.size());
+    S.tptr.push_back((int)S.tgt.size());
+  }
+  S.rlptr.push_back(0); S.ruptr.push_back(0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (P[(size_t)i * n + j]) { S.rlpos.push_back(S.pos[(size_t)i * n + j]); S.rlcol.push_back(j); }
+    for (int j = i + 1; j < n; ++j)
+      if (P[(size_t)i * n + j]) { S.rupos.push_back(S.pos[(size_t)i * n + j]); S.rucol.push_back(j); }
+    S.rlptr.push_back((int)S.rlpos.size());
+    S.ruptr.push_back((int)S.rupos.size());
+  }
+  return S;
+}
+
+// device copies of the schedules
+struct LUDev {
+  int n, nnz;
+  const int *diag, *lptr, *lpos, *uptr, *upos, *tptr, *tgt;
+  const int *rlptr, *rlpos, *rlcol, *ruptr, *rupos, *rucol;
+};
+
+template <typename T>
+int upload(T** d, const std::vector<T>& h) {
+  *d = nullptr;
+  const size_t bytes = std::max<size_t>(1, h.size()) * sizeof(T);
+  BDFB_CUDA(cudaMalloc(d, bytes));
+  if (!h.empty()) BDFB_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+struct LUOwn {
+  LUDev D = {};
+  std::vector<void*> bufs;
+  ~LUOwn() {
+    for (void* p : bufs) cudaFree(p);
+  }
+  int make(const Symb& S) {
+    D.n = S.n;
+    D.nnz = S.nnz;
+    int* p = nullptr;
+#define UP(field, vec)                         \
+  do {                                         \
+    int r_ = upload(&p, S.vec);                \
+    if (r_) return r_;                         \
+    bufs.push_back(p);                         \
+    D.field = p;                               \
+  } while (0)
+    UP(diag, diag); UP(lptr, lptr); UP(lpos, lpos); UP(uptr, uptr); UP(upos, upos); UP(tptr, tptr); UP(tgt, tgt);
+    UP(rlptr, rlptr); UP(rlpos, rlpos); UP(rlcol, rlcol); UP(ruptr, ruptr); UP(rupos, rupos); UP(rucol, rucol);
+#undef UP
+    return 0;
+  }
+};
+
+// LU of block c in place: L unit lower (multipliers), U upper with its
+// diagonal replaced by the reciprocal.  Returns 0 or k + 1 for a zero or
+// non-finite pivot at step k.
+__device__ __forceinline__ int lu_factor_sp(const LUDev& L, int64_t nb, double* v, int64_t c) {
+  for (int k = 0; k < L.n; ++k) {
+    double* dk = v + (int64_t)L.diag[k] * nb + c;
+    const double piv = *dk;
+    if (!(piv != 0.0) || !isfinite(piv)) return k + 1;
+    const double inv = 1.0 / piv;
+    *dk = inv;
+    const int l0 = L.lptr[k], l1 = L.lptr[k + 1], u0 = L.uptr[k], u1 = L.uptr[k + 1];
+    const int nu = u1 - u0;
+    const int* t = L.tgt + L.tptr[k];
+    for (int a = l0; a < l1; ++a) {
+      double* lp = v + (int64_t)L.lpos[a] * nb + c;
+      const double m = *lp * inv;
+      *lp = m;
+      const int* ta = t + (a - l0) * nu;
+      for (int b = 0; b < nu; ++b) {
+        double* tp = v + (int64_t)ta[b] * nb + c;
+        *tp -= m * v[(int64_t)L.upos[u0 + b] * nb + c];
+      }
+    }
+  }
+  return 0;
+}
+
+// x <- (LU)^{-1} x for block c; x entry-major [n][nb]
+__device__ __forceinline__ void lu_solve_sp(const LUDev& L, int64_t nb, const double* v, double* x, int64_t c) {
+  for (int i = 0; i < L.n; ++i) {
+    double s = x[(int64_t)i * nb + c];
+    for (int e = L.rlptr[i]; e < L.rlptr[i + 1]; ++e) s -= v[(int64_t)L.rlpos[e] * nb + c] * x[(int64_t)L.rlcol[e] * nb + c];
+    x[(int64_t)i * nb + c] = s;
+  }
+  for (int i = L.n - 1; i >= 0; --i) {
+    double s = x[(int64_t)i * nb + c];
+    for (int e = L.ruptr[i]; e < L.ruptr[i + 1]; ++e) s -= v[(int64_t)L.rupos[e] * nb + c] * x[(int64_t)L.rucol[e] * nb + c];
+    x[(int64_t)i * nb + c] = s * v[(int64_t)L.diag[i] * nb + c];
+  }
+}
+
+// ---- standalone batched matrices
+__global__ void __launch_bounds__(ST) k_sp_zero(int64_t total, double* v) {
+  for (int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x; i < total; i += (int64_t)gridDim.x * ST) v[i] = 0.0;
+}
+
+// lu[map[e] nb + b] = a[b nnz + e], one thread per (b, e) (reads coalesced)
+__global__ void __launch_bounds__(ST) k_sp_load(int64_t nb, int nnz, const int* __restrict__ map,
+                                                const double* __restrict__ a, double* __restrict__ lu) {
+  const int64_t total = nb * nnz;
+  for (int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x; i < total; i += (int64_t)gridDim.x * ST) {
+    const int64_t b = i / nnz;
+    const int e = (int)(i - b * nnz);
+    lu[(int64_t)map[e] * nb + b] = a[i];
+  }
+}
+
+__global__ void __launch_bounds__(ST) k_sp_factor(LUDev L, int64_t nb, double* lu, int32_t* info) {
+  const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (c >= nb) return;
+  const int r = lu_factor_sp(L, nb, lu, c);
+  if (info) info[c] = r;
+}
+
+__global__ void __launch_bounds__(ST) k_sp_solve(LUDev L, int64_t nb, const double* lu, double* x) {
+  const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (c >= nb) return;
+  lu_solve_sp(L, nb, lu, x, c);
+}
+
+// ---- a network shared by every cell
+struct NetDev {
+  int n, R;
+  int64_t nb;                  // cells
+  const uint32_t* reac;        // 4 reactant indices per reaction, 8 bits each (255 = none)
+  const double* k;             // [R]
+  const int* inc_off;          // [n + 1] species-major incidence lists
+  const uint16_t* inc;         // (r << 1) | produced, reaction order, consumption first
+  const int* jac_off;          // [4 R + 1] scatter lists of d rate_r / d y_(reactant a)
+  const int* jac_pos;          // LU entry
+  const int8_t* jac_sgn;       // +1: the species is a reactant (M += gamma d), -1: a product
+  LUDev L;
+};
+
+__device__ __forceinline__ void net_rates(const NetDev& D, const double* y, double* rates, int64_t c) {
+  const int64_t nb = D.nb;
+  for (int r = 0; r < D.R; ++r) {
+    const uint32_t rr = D.reac[r];
+    double v = D.k[r];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const uint32_t s = (rr >> (8 * a)) & 255u;
+      if (s != 255u) v *= y[(int64_t)s * nb + c];
+    }
+    rates[(int64_t)r * nb + c] = v;
+  }
+}
+
+__device__ __forceinline__ void net_f(const NetDev& D, const double* rates, double* f, int64_t c) {
+  const int64_t nb = D.nb;
+  for (int s = 0; s < D.n; ++s) {
+    double acc = 0.0;
+    for (int e = D.inc_off[s]; e < D.inc_off[s + 1]; ++e) {
+      const uint16_t ent = D.inc[e];
+      const double v = rates[(int64_t)(ent >> 1) * nb + c];
+      acc = (ent & 1) ? acc + v : acc - v;
+    }
+    f[(int64_t)s * nb + c] = acc;
+  }
+}
+
+// M = I - gamma J(y) in the LU pattern of cell c, then its LU
+__device__ __forceinline__ int net_setup(const NetDev& D, const double* y, double gamma, double* lu, int64_t c) {
+  const int64_t nb = D.nb;
+  for (int e = 0; e < D.L.nnz; ++e) lu[(int64_t)e * nb + c] = 0.0;
+  for (int k = 0; k < D.n; ++k) lu[(int64_t)D.L.diag[k] * nb + c] = 1.0;
+  for (int r = 0; r < D.R; ++r) {
+    const uint32_t rr = D.reac[r];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (((rr >> (8 * a)) & 255u) == 255u) continue;
+      double d = D.k[r];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t s = (rr >> (8 * b)) & 255u;
+        if (b != a && s != 255u) d *= y[(int64_t)s * nb + c];
+      }
+      const double gd = gamma * d;
+      for (int e = D.jac_off[4 * r + a]; e < D.jac_off[4 * r + a + 1]; ++e) {
+        double* p = lu + (int64_t)D.jac_pos[e] * nb + c;
+        *p = D.jac_sgn[e] > 0 ? *p + gd : *p - gd;
+      }
+    }
+  }
+  return lu_factor_sp(D.L, nb, lu, c);
+}
+
+__global__ void __launch_bounds__(ST) k_net_rhs(NetDev D, const double* __restrict__ y, double* __restrict__ f,
+                                                double* __restrict__ rates) {
+  const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (c >= D.nb) return;
+  net_rates(D, y, rates, c);
+  net_f(D, rates, f, c);
+}
+
+struct NewtonArgs {
+  const double *zp0, *zp1, *ewt;
+  double gamma, gammap, rl1, Eq;
+  int setup;
+  double* acor;
+  double* crate;               // per cell, kept between solves
+  int* failed;
+  unsigned long long* iters;   // [0] completed iterations (sum), [1] RHS sweeps (max)
+};
+
+// Task-local Newton solve of every cell (the grouped mode's solve): each
+// cell iterates on its own block to its own test, as the per-cell
+// integrator's Newton: rate R = max(0.3 R, |d_m| / |d_{m-1}|), converged when
+// |d_m| min(1, R) E_q <= 0.1, diverged when |d_m| > 2 |d_{m-1}|, <= 3
+// iterations; a stale M scales the correction by 2 / (1 + gamma / gamma_p).
+__global__ void __launch_bounds__(ST) k_net_newton(NetDev D, NewtonArgs A, double* __restrict__ lu,
+                                                   double* __restrict__ rates, double* __restrict__ yv,
+                                                   double* __restrict__ fv, double* __restrict__ xv) {
+  const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
+  if (c >= D.nb) return;
+  const int64_t nb = D.nb;
+  const int n = D.n;
+  double crate = A.crate[c];
+  if (A.setup) {
+    crate = 1.0;
+    if (net_setup(D, A.zp0, A.gamma, lu, c)) {
+      A.crate[c] = crate;
+      atomicOr(A.failed, 1);
+      return;
+    }
+  }
+  for (int s = 0; s < n; ++s) A.acor[(int64_t)s * nb + c] = 0.0;
+  const double rn = 1.0 / (double)n;
+  const double eq2 = A.Eq * A.Eq * 100.0;
+  const double scst = A.gamma != A.gammap ? 2.0 / (1.0 + A.gamma / A.gammap) : 1.0;
+  double delp2 = 0.0;
+  bool conv = false;
+  int it = 1, nit = 0;
+  for (; it <= 3; ++it) {
+    for (int s = 0; s < n; ++s) {
+      const int64_t i = (int64_t)s * nb + c;
+      yv[i] = A.zp0[i] + A.acor[i];
+    }
+    net_rates(D, yv, rates, c);
+    net_f(D, rates, fv, c);
+    bool fin = true;
+    for (int s = 0; s < n; ++s) fin = fin && isfinite(fv[(int64_t)s * nb + c]);
+    if (!fin) break;
+    ++nit;
+    for (int s = 0; s < n; ++s) {
+      const int64_t i = (int64_t)s * nb + c;
+      xv[i] = A.gamma * fv[i] - A.zp1[i] * A.rl1 - A.acor[i];
+    }
+    lu_solve_sp(D.L, nb, lu, xv, c);
+    double del2 = 0.0;
+    for (int s = 0; s < n; ++s) {
+      const int64_t i = (int64_t)s * nb + c;
+      double x = xv[i];
+      if (A.gamma != A.gammap) x *= scst;
+      const double e = x * A.ewt[i];
+      del2 += e * e;
+      A.acor[i] += x;
+    }
+    del2 *= rn;
+    if (it > 1) crate = fmax(0.3 * crate, sqrt(del2 / delp2));
+    const double cr = fmin(1.0, crate);
+    if (del2 * cr * cr * eq2 <= 1.0) { conv = true; break; }
+    if (it >= 2 && del2 > 4.0 * delp2) break;
+    delp2 = del2;
+  }
+  A.crate[c] = crate;
+  atomicAdd(A.iters, (unsigned long long)nit);
+  atomicMax(A.iters + 1, (unsigned long long)(it > 3 ? 3 : it));
+  if (!conv) atomicOr(A.failed, 1);
+}
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + ST - 1) / ST, 1 << 30)); }
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI: matrices
+}  // namespace bdfb
+
+struct bdfb_sparse {
+  bdfb::Symb S;
+  bdfb::LUOwn own;
+  int n = 0, nnz_in = 0;
+  int* dmap = nullptr;         // input CSR entry -> LU entry
+};
+
+extern "C" int bdfb_sparse_create(int n, int nnz, const int32_t* rowptr, const int32_t* colind,
+                                  bdfb_sparse** out) {
+  using namespace bdfb;
+  if (!out || n < 1 || n > SP_NMAX || nnz < 0 || !rowptr || (nnz > 0 && !colind)) return BDFB_ILL_INPUT;
+  *out = nullptr;
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return BDFB_ILL_INPUT;
+  std::vector<uint8_t> A((size_t)n * n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) return BDFB_ILL_INPUT;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int j = colind[e];
+      if (j < 0 || j >= n || A[(size_t)i * n + j]) return BDFB_ILL_INPUT;   // range, duplicates
+      A[(size_t)i * n + j] = 1;
+    }
+  }
+  bdfb_sparse* sp = new (std::nothrow) bdfb_sparse();
+  if (!sp) return BDFB_MEM_FAIL;
+  sp->S = symbolic(n, A);
+  sp->n = n;
+  sp->nnz_in = nnz;
+  std::vector<int> map(std::max(nnz, 1));
+  for (int i = 0; i < n; ++i)
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) map[e] = sp->S.pos[(size_t)i * n + colind[e]];
+  int r = sp->own.make(sp->S);
+  if (!r) r = upload(&sp->dmap, map);
+  if (r) {
+    cudaFree(sp->dmap);
+    delete sp;
+    return r;
+  }
+  *out = sp;
+  return BDFB_SUCCESS;
+}
+
+extern "C" void bdfb_sparse_destroy(bdfb_sparse* sp) {
+  if (!sp) return;
+  cudaFree(sp->dmap);
+  delete sp;
+}
+
+extern "C" int64_t bdfb_sparse_lu_nnz(const bdfb_sparse* sp) { return sp ? sp->S.nnz : BDFB_ILL_INPUT; }
+
+extern "C" int bdfb_sparse_load(const bdfb_sparse* sp, int64_t nb, const double* a, double* lu, void* stream) {
+  using namespace bdfb;
+  if (!sp || nb < 0 || (nb > 0 && (!a || !lu))) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  cudaStream_t s = as_stream(stream);
+  const int64_t tot = nb * sp->S.nnz;
+  const int g = (int)std::min<int64_t>((tot + ST - 1) / ST, (int64_t)sm_count() * 16);
+  k_sp_zero<<<g, ST, 0, s>>>(tot, lu);
+  if (sp->nnz_in > 0) {
+    const int64_t tin = nb * sp->nnz_in;
+    const int gi = (int)std::min<int64_t>((tin + ST - 1) / ST, (int64_t)sm_count() * 16);
+    k_sp_load<<<gi, ST, 0, s>>>(nb, sp->nnz_in, sp->dmap, a, lu);
+  }
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_sparse_factor(const bdfb_sparse* sp, int64_t nb, double* lu, int32_t* info, void* stream) {
+  using namespace bdfb;
+  if (!sp || nb < 0 || (nb > 0 && !lu)) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  k_sp_factor<<<grid_for(nb), ST, 0, as_stream(stream)>>>(sp->own.D, nb, lu, info);
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
+extern "C" int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, double* x, void* stream) {
+  using namespace bdfb;
+  if (!sp || nb < 0 || (nb > 0 && (!lu || !x))) return BDFB_ILL_INPUT;
+  if (nb == 0) return BDFB_SUCCESS;
+  k_sp_solve<<<grid_for(nb), ST, 0, as_stream(stream)>>>(sp->own.D, nb, lu, x);
+  BDFB_CUDA(cudaGetLastError());
+  return BDFB_SUCCESS;
+}
+
+// ------------------------------------------------- cells sharing one network
+namespace bdfb {
+
+struct SharedInt {
+  NetDev D = {};
+  LUOwn own;
+  std::vector<void*> bufs;
+  int nnz_m = 0;               // entries of M's own pattern
+  double *lu = nullptr, *rates = nullptr, *yv = nullptr, *fv = nullptr, *xv = nullptr, *crate = nullptr;
+  int* dflag = nullptr;
+  unsigned long long* diters = nullptr;
+  GridBDF* gg = nullptr;
+  cudaStream_t s = nullptr;
+  ~SharedInt() {
+    grid_destroy(gg);
+    for (void* p : bufs) cudaFree(p);
+  }
+};
+
+static int net_rhs_cb(void* user, const double* y, double* f, cudaStream_t s) {
+  SharedInt* S = static_cast<SharedInt*>(user);
+  k_net_rhs<<<grid_for(S->D.nb), ST, 0, s>>>(S->D, y, f, S->rates);
+  BDFB_CUDA(cudaGetLastError());
+  return 0;
+}
+
+static int net_solve_cb(void* user, const double* zp0, const double* zp1, const double* ewt, double gamma,
+                        double gammap, double rl1, double Eq, int setup, double* acor, int* failed,
+                        int64_t* iters, int64_t* sweeps, cudaStream_t s) {
+  SharedInt* S = static_cast<SharedInt*>(user);
+  NewtonArgs A;
+  A.zp0 = zp0; A.zp1 = zp1; A.ewt = ewt;
+  A.gamma = gamma; A.gammap = gammap; A.rl1 = rl1; A.Eq = Eq;
+  A.setup = setup;
+  A.acor = acor;
+  A.crate = S->crate;
+  A.failed = S->dflag;
+  A.iters = S->diters;
+  BDFB_CUDA(cudaMemsetAsync(S->dflag, 0, sizeof(int), s));
+  BDFB_CUDA(cudaMemsetAsync(S->diters, 0, 2 * sizeof(unsigned long long), s));
+  k_net_newton<<<grid_for(S->D.nb), ST, 0, s>>>(S->D, A, S->lu, S->rates, S->yv, S->fv, S->xv);
+  BDFB_CUDA(cudaGetLastError());
+  int fl = 0;
+  unsigned long long it[2] = {0, 0};
+  BDFB_CUDA(cudaMemcpyAsync(&fl, S->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaMemcpyAsync(it, S->diters, sizeof it, cudaMemcpyDeviceToHost, s));
+  BDFB_CUDA(cudaStreamSynchronize(s));
+  *failed = fl;
+  *iters = (int64_t)it[0];
+  *sweeps = (int64_t)it[1];
+  return 0;
+}
+
+int shared_create(const bdfb_problem* prob, SharedInt** out) {
+  *out = nullptr;
+  if (prob->mem != BDFB_MEM_HOST || !prob->n || !prob->rxn_off || !prob->reactants || !prob->products ||
+      prob->ncell < 1)
+    return BDFB_ILL_INPUT;
+  const int n = prob->n[0];
+  const int64_t R64 = prob->rxn_off[1] - prob->rxn_off[0];
+  if (prob->rxn_off[0] != 0 || n < 1 || n > 255 || R64 < 0 || R64 > 65535) return BDFB_ILL_INPUT;
+  const int R = (int)R64;
+  // network, pattern of J (rows: affected species, columns: reactants)
+  std::vector<uint32_t> reac(std::max(R, 1));
+  std::vector<uint8_t> A((size_t)n * n, 0);
+  std::vector<std::vector<uint16_t>> incs(n);
+  for (int r = 0; r < R; ++r) {
+    const uint8_t* ra = prob->reactants + 4 * r;
+    const uint8_t* pa = prob->products + 4 * r;
+    uint32_t packed = 0;
+    for (int a = 0; a < 4; ++a) {
+      if ((ra[a] != 255 && ra[a] >= n) || (pa[a] != 255 && pa[a] >= n)) return BDFB_ILL_INPUT;
+      for (int b = 0; b < a; ++b)
+        if ((ra[a] != 255 && ra[a] == ra[b]) || (pa[a] != 255 && pa[a] == pa[b])) return BDFB_ILL_INPUT;
+      packed |= (uint32_t)ra[a] << (8 * a);
+    }
+    reac[r] = packed;
+    for (int a = 0; a < 4; ++a) {
+      if (ra[a] == 255) continue;
+      for (int b = 0; b < 4; ++b) {
+        if (ra[b] != 255) A[(size_t)ra[b] * n + ra[a]] = 1;
+        if (pa[b] != 255) A[(size_t)pa[b] * n + ra[a]] = 1;
+      }
+    }
+    for (int a = 0; a < 4; ++a)
+      if (ra[a] != 255) incs[ra[a]].push_back((uint16_t)(r << 1));
+    for (int a = 0; a < 4; ++a)
+      if (pa[a] != 255) incs[pa[a]].push_back((uint16_t)((r << 1) | 1));
+  }
+  SharedInt* S = new (std::nothrow) SharedInt();
+  if (!S) return BDFB_MEM_FAIL;
+  for (uint8_t v : A) S->nnz_m += v != 0;
+  const Symb sy = symbolic(n, A);
+  int r = S->own.make(sy);
+  std::vector<int> inc_off(n + 1, 0);
+  std::vector<uint16_t> inc;
+  for (int s2 = 0; s2 < n; ++s2) {
+    inc.insert(inc.end(), incs[s2].begin(), incs[s2].end());
+    inc_off[s2 + 1] = (int)inc.size();
+  }
+  // Jacobian scatter lists in reaction order
+  std::vector<int> jac_off(4 * (size_t)R + 1, 0), jac_pos;
+  std::vector<int8_t> jac_sgn;
+  for (int rr = 0; rr < R; ++rr) {
+    const uint8_t* ra = prob->reactants + 4 * rr;
+    const uint8_t* pa = prob->products + 4 * rr;
+    for (int a = 0; a < 4; ++a) {
+      if (ra[a] != 255)
+        for (int b = 0; b < 4; ++b) {
+          if (ra[b] != 255) { jac_pos.push_back(sy.pos[(size_t)ra[b] * n + ra[a]]); jac_sgn.push_back(1); }
+          if (pa[b] != 255) { jac_pos.push_back(sy.pos[(size_t)pa[b] * n + ra[a]]); jac_sgn.push_back(-1); }
+        }
+      jac_off[4 * (size_t)rr + a + 1] = (int)jac_pos.size();
+    }
+  }
+  std::vector<double> k(prob->k, prob->k + R);
+  uint32_t* dreac = nullptr;
+  double* dk = nullptr;
+  int *dinc_off = nullptr, *djoff = nullptr, *djpos = nullptr;
+  uint16_t* dinc = nullptr;
+  int8_t* djsgn = nullptr;
+  if (!r) { r = upload(&dreac, reac); S->bufs.push_back(dreac); }
+  if (!r) { r = upload(&dk, k); S->bufs.push_back(dk); }
+  if (!r) { r = upload(&dinc_off, inc_off); S->bufs.push_back(dinc_off); }
+  if (!r) { r = upload(&dinc, inc); S->bufs.push_back(dinc); }
+  if (!r) { r = upload(&djoff, jac_off); S->bufs.push_back(djoff); }
+  if (!r) { r = upload(&djpos, jac_pos); S->bufs.push_back(djpos); }
+  if (!r) { r = upload(&djsgn, jac_sgn); S->bufs.push_back(djsgn); }
+  const int64_t nb = prob->ncell;
+  auto alloc = [&](double** p, size_t count) {
+    if (r) return;
+    if (cudaMalloc(p, std::max<size_t>(count, 1) * sizeof(double)) != cudaSuccess) { *p = nullptr; r = BDFB_MEM_FAIL; return; }
+    S->bufs.push_back(*p);
+  };
+  alloc(&S->lu, (size_t)sy.nnz * nb);
+  alloc(&S->rates, (size_t)std::max(R, 1) * nb);
+  alloc(&S->yv, (size_t)n * nb);
+  alloc(&S->fv, (size_t)n * nb);
+  alloc(&S->xv, (size_t)n * nb);
+  alloc(&S->crate, (size_t)nb);
+  if (!r && cudaMalloc(&S->dflag, sizeof(int)) != cudaSuccess) r = BDFB_MEM_FAIL;
+  if (!r) S->bufs.push_back(S->dflag);
+  if (!r && cudaMalloc(&S->diters, 2 * sizeof(unsigned long long)) != cudaSuccess) r = BDFB_MEM_FAIL;
+  if (!r) S->bufs.push_back(S->diters);
+  if (r) {
+    delete S;
+    return r;
+  }
+  S->D.n = n;
+  S->D.R = R;
+  S->D.nb = nb;
+  S->D.reac = dreac;
+  S->D.k = dk;
+  S->D.inc_off = dinc_off;
+  S->D.inc = dinc;
+  S->D.jac_off = djoff;
+  S->D.jac_pos = djpos;
+  S->D.jac_sgn = djsgn;
+  S->D.L = S->own.D;
+  GridExternal ext;
+  ext.user = S;
+  ext.rhs = net_rhs_cb;
+  ext.solve = net_solve_cb;
+  r = grid_create_external((int64_t)n * nb, ext, &S->gg);
+  if (r) {
+    delete S;
+    return r;
+  }
+  *out = S;
+  return 0;
+}
+
+void shared_destroy(SharedInt* S) { delete S; }
+
+void shared_set_stream(SharedInt* S, cudaStream_t s) {
+  S->s = s;
+  grid_set_stream(S->gg, s);
+}
+
+void shared_set_tolerances(SharedInt* S, double rtol, double atol) { grid_set_tolerances(S->gg, rtol, atol); }
+
+int shared_set_option(SharedInt* S, const char* key, int64_t v) {
+  if (!std::strcmp(key, "mxstep") || !std::strcmp(key, "qmax")) return grid_set_option(S->gg, key, v);
+  return BDFB_ILL_INPUT;
+}
+
+int shared_init(SharedInt* S, double t0, const double* y0, int mem) { return grid_init(S->gg, t0, y0, mem); }
+
+int shared_integrate(SharedInt* S, double tout, double* y, int mem) { return grid_integrate(S->gg, tout, y, mem); }
+
+void shared_stats(SharedInt* S, int64_t out[8], double* last_ms, int* q, double* h) {
+  grid_stats(S->gg, out, last_ms);
+  out[6] = S->D.L.nnz;
+  out[7] = S->nnz_m;
+  grid_next_step(S->gg, q, h);
+}
+
+}  // namespace bdfb

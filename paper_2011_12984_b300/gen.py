@@ -151,6 +151,7 @@ class MassActionProblem:
     k: np.ndarray          # [nrxn] float64
     y0: np.ndarray         # [sum n] float64
     kind: str = "massaction"
+    shared: bool = False   # every cell carries the network of cell 0
 
     @property
     def ncell(self) -> int:
@@ -172,7 +173,7 @@ class MassActionProblem:
         return MassActionProblem(n=n.copy(), y_off=y_off, rxn_off=rxn_off,
                                  reactants=self.reactants[ri].copy(),
                                  products=self.products[ri].copy(),
-                                 k=self.k[ri].copy(), y0=self.y0[yi].copy())
+                                 k=self.k[ri].copy(), y0=self.y0[yi].copy(), shared=self.shared)
 
 
 def _pick_distinct(u: np.ndarray, n: int) -> np.ndarray:
@@ -269,7 +270,50 @@ def mass_action_shared(ncell: int, n: int = 10, seed: int = DEFAULT_SEED, networ
                              rxn_off=np.arange(ncell + 1, dtype=np.int64) * R,
                              reactants=np.tile(base.reactants, (ncell, 1)),
                              products=np.tile(base.products, (ncell, 1)),
-                             k=np.tile(base.k, ncell), y0=y0.reshape(-1))
+                             k=np.tile(base.k, ncell), y0=y0.reshape(-1), shared=True)
+
+
+def mass_action_banded(ncell: int, n: int = 128, window: int = 6, seed: int = DEFAULT_SEED,
+                       rxn_per_species: int = 2, mvals=(2, 3),
+                       log10k=(-2.0, 8.0)) -> MassActionProblem:
+    """``ncell`` cells that share one sparse ``n``-species network (a larger
+    mechanism whose reactions couple nearby species, as chains of reactions
+    do) and differ in their initial states.
+
+    Reaction r of the network (stream ``seed + 2``, key 0) uses draws
+    1 + 11 r ... 11 + 11 r: m from ``mvals``, a window start b uniform in
+    [0, n - window], m distinct reactants and m distinct products among
+    species b .. b + window - 1 (partial Fisher-Yates), log10 k uniform in
+    ``log10k``.  The Jacobian of every cell then has one banded pattern
+    (|i - j| < window).  Cell c's Dirichlet(1, ..., 1) state uses draws
+    1 .. n of its stream under ``seed``.  The problem is expanded per cell
+    (the layout of the other generators); ``shared`` marks it."""
+    if not (2 <= window <= n <= 255):
+        raise ValueError("need 2 <= window <= n <= 255")
+    R = rxn_per_species * n
+    key = stream_keys(seed + 2, np.zeros(1, dtype=np.uint64))
+    d = 1 + 11 * np.arange(R)[:, None] + np.arange(11)[None, :]
+    u = uniform(key[:, None], d)                              # [R, 11]
+    mv = np.asarray([m for m in mvals if m <= window], dtype=np.int64)
+    m = mv[np.minimum((u[:, 0] * len(mv)).astype(np.int64), len(mv) - 1)]
+    base = np.minimum((u[:, 1] * (n - window + 1)).astype(np.int64), n - window)
+    ra = _pick_distinct(u[:, 2:6], window).astype(np.int64) + base[:, None]
+    pa = _pick_distinct(u[:, 6:10], window).astype(np.int64) + base[:, None]
+    keep = np.arange(MAXM)[None, :] < m[:, None]
+    reac = np.where(keep, ra, _NONE).astype(np.uint8)
+    prod = np.where(keep, pa, _NONE).astype(np.uint8)
+    k = np.power(10.0, log10k[0] + u[:, 10] * (log10k[1] - log10k[0]))
+    keys = stream_keys(seed, np.arange(ncell, dtype=np.uint64))
+    y0 = np.empty((ncell, n), np.float64)
+    for c0 in range(0, ncell, 65536):
+        kc = keys[c0:c0 + 65536][:, None]
+        e = -np.log1p(-uniform(kc, 1 + np.arange(n)[None, :]))
+        y0[c0:c0 + 65536] = e / e.sum(axis=1, keepdims=True)
+    return MassActionProblem(n=np.full(ncell, n, np.int32),
+                             y_off=np.arange(ncell + 1, dtype=np.int64) * n,
+                             rxn_off=np.arange(ncell + 1, dtype=np.int64) * R,
+                             reactants=np.tile(reac, (ncell, 1)), products=np.tile(prod, (ncell, 1)),
+                             k=np.tile(k, ncell), y0=y0.reshape(-1), shared=True)
 
 
 # --------------------------------------------------------------------------

@@ -86,3 +86,24 @@ def test_binding_imports_and_fails_loudly_without_library(tmp_path):
     assert "raise ImportError" in src
     from paper_2011_12984_b300 import bdfb
     assert bdfb.lib is not None
+
+
+def test_sparse_pattern_rejected_without_gpu(lib):
+    """malformed shared patterns fail in the host analysis, before any device call"""
+    L, _ = lib
+    ILL = -22
+    L.bdfb_sparse_create.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    h = C.c_void_p()
+    rp = (C.c_int32 * 3)(0, 1, 2)
+    ok_ci = (C.c_int32 * 2)(0, 1)
+    assert L.bdfb_sparse_create(0, 0, rp, ok_ci, C.byref(h)) == ILL          # n < 1
+    assert L.bdfb_sparse_create(2049, 0, rp, ok_ci, C.byref(h)) == ILL       # n too large
+    bad_ci = (C.c_int32 * 2)(0, 2)
+    assert L.bdfb_sparse_create(2, 2, rp, bad_ci, C.byref(h)) == ILL         # column out of range
+    dup_rp = (C.c_int32 * 3)(0, 2, 2)
+    dup_ci = (C.c_int32 * 2)(1, 1)
+    assert L.bdfb_sparse_create(2, 2, dup_rp, dup_ci, C.byref(h)) == ILL     # duplicate entry
+    bad_rp = (C.c_int32 * 3)(0, 2, 1)
+    assert L.bdfb_sparse_create(2, 1, bad_rp, ok_ci, C.byref(h)) == ILL      # decreasing rowptr
+    L.bdfb_sparse_factor.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert L.bdfb_sparse_factor(None, 4, None, None, None) == ILL
