@@ -73,3 +73,22 @@ def test_mass_action_shared_network():
     q = gen.mass_action(50, sizes=(10,), seed=11)
     assert np.array_equal(p.y0, q.y0)
     assert np.allclose(np.add.reduceat(p.y0, p.y_off[:-1]), 1.0, rtol=0, atol=1e-14)
+
+
+def test_banded_network_is_shared_banded_and_conservative():
+    p = gen.mass_action_banded(5, n=64, window=6)
+    q = gen.mass_action_banded(5, n=64, window=6)
+    np.testing.assert_array_equal(p.reactants, q.reactants)       # deterministic
+    np.testing.assert_array_equal(p.y0, q.y0)
+    R = int(p.rxn_off[1])
+    assert R == 128 and p.shared and p.subset([2, 3]).shared
+    for c in range(1, 5):                                          # one network for all cells
+        np.testing.assert_array_equal(p.reactants[c * R:(c + 1) * R], p.reactants[:R])
+        np.testing.assert_array_equal(p.k[c * R:(c + 1) * R], p.k[:R])
+    for ra, pa in zip(p.reactants[:R], p.products[:R]):
+        r = [int(x) for x in ra if x != 255]
+        s = [int(x) for x in pa if x != 255]
+        assert len(r) == len(s) and len(set(r)) == len(r) and len(set(s)) == len(s)  # sum y conserved
+        assert max(r + s) - min(r + s) < 6                         # within one window
+    np.testing.assert_allclose(np.add.reduceat(p.y0, p.y_off[:-1]), 1.0, rtol=1e-14)
+    assert not np.array_equal(p.y0[:64], p.y0[64:128])             # states differ per cell
