@@ -441,13 +441,32 @@ def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps
                 raise RuntimeError(f"line integrate returned {r}")
         gs = li.cell_stats()[0]
     t = min(ts[1:])
-    return {"workload": f"Brusselator 1-D advection-reaction (the paper's demo) {nx} points x 3, length {length}, "
+    orate = line_oracle_rate(gen, "bdf", nx, length, tout, 50_000)
+    return {"oracle": orate,
+            "workload": f"Brusselator 1-D advection-reaction (the paper's demo) {nx} points x 3, length {length}, "
                         f"c 0.01, A 1, B 3.5, eps 5e-6, t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 blocks",
             "points_per_s": nx / t, "seconds": t, "steps": int(gs[0]), "newton_iters": int(gs[3]),
             "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
 
 
-def imex_workload(torch, bdfb, gen, nx, length, tout=10.0, precisions=(0, 1), reps=1):
+def line_oracle_rate(gen, method, nx, length, tout, nsample):
+    """the oracle (one host thread: one coupled system) on the first-order
+    line with the workload's spacing and nsample points: points per second
+    of the same integration"""
+    import oracle
+    ns = min(nx, nsample)
+    p = gen.brusselator1d(ns, length=length * ns / nx)
+    t0 = time.perf_counter()
+    if method == "ark":
+        r, _, st = oracle.bruss_ark_integrate(p, 0.0, tout, RTOL, ATOL)
+    else:
+        r, _, st = oracle.bruss_integrate(p, 0.0, tout, RTOL, ATOL)
+    dt = time.perf_counter() - t0
+    return {"points_per_s": ns / dt, "seconds": dt, "steps": int(st[0]), "ret": int(r), "cores": 1,
+            "sample": f"{ns} points at the same spacing ({length * ns / nx:g} long), same t range"}
+
+
+def imex_workload(torch, bdfb, gen, nx, length, tout=10.0, precisions=(0, 1), reps=1, oracle_points=None):
     """The paper's demonstration problem with its own integrator type (Sec. 7):
     IMEX additive Runge-Kutta (ARK3(2)4L[2]SA), first-order upwind advection
     explicit, Brusselator reactions implicit, every implicit stage solved by
@@ -477,6 +496,8 @@ def imex_workload(torch, bdfb, gen, nx, length, tout=10.0, precisions=(0, 1), re
         out[name] = {"seconds": t, "points_per_s": nx / t, "steps": int(cs[0]), "newton_iters": int(cs[3]),
                      "error_test_failures": int(cs[5]), "newton_failures": int(cs[4]),
                      "ms_per_step": 1e3 * t / max(1, int(cs[0]))}
+    if oracle_points:
+        out["oracle"] = line_oracle_rate(gen, "ark", nx, length, tout, oracle_points)
     return out
 
 
@@ -508,6 +529,13 @@ def shared_sparse_workload(torch, bdfb, gen, ncell=100_000, n=128, reps=1):
             with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, autotune=1) as I:
                 td = timed_integrations(torch, I, yd, yo, TOUT, max(reps, 2))
             out[name]["per_cell_dense_cells_per_s"] = ncell / td
+        import oracle
+        sub = p.subset(np.arange(min(128, ncell)))
+        t0 = time.perf_counter()
+        oracle.integrate_cells_grouped(sub, 0.0, TOUT, RTOL, ATOL)
+        dt = time.perf_counter() - t0
+        out[name]["oracle_grouped"] = {"cells_per_s": sub.ncell / dt, "cores": 1,
+                                       "sample": f"first {sub.ncell} cells as one grouped system (dense LU)"}
     return out
 
 
@@ -529,6 +557,13 @@ def grouped_workload(torch, bdfb, gen, ncell=100_000, reps=1, flush=None):
                      "max_steps": st["max_steps"], "newton_iters_per_cell": st["nniters"] / ncell,
                      "accuracy": accuracy(p, y.cpu().numpy(), ncheck=256)}
     out["per_cell_over_grouped"] = out["per_cell"]["cells_per_s"] / out["grouped_task_local_newton"]["cells_per_s"]
+    import oracle
+    sub = p.subset(np.arange(min(512, ncell)))
+    t0 = time.perf_counter()
+    oracle.integrate_cells_grouped(sub, 0.0, TOUT, RTOL, ATOL)
+    dt = time.perf_counter() - t0
+    out["oracle_grouped"] = {"cells_per_s": sub.ncell / dt, "cores": 1,
+                             "sample": f"first {sub.ncell} cells as one grouped system"}
     return out
 
 
@@ -667,8 +702,9 @@ def run_ours(args):
                    # the paper's single-GPU demo sizes (Sec. 7.2: n_x = 1e7, b = 1000, t_f = 10) and
                    # its one-node Summit problem (Sec. 7.1: n_x = 6e5, b = 10, t_f = 10, run there on 6 GPUs)
                    "shared_sparse_network": shared_sparse_workload(torch, bdfb, gen, ncell=NCELL),
-                   "imex_demo_1e7": imex_workload(torch, bdfb, gen, 10_000_000, 1000.0),
-                   "imex_demo_6e5_b10": imex_workload(torch, bdfb, gen, 600_000, 10.0, precisions=(1,))}
+                   "imex_demo_1e7": imex_workload(torch, bdfb, gen, 10_000_000, 1000.0, oracle_points=20_000),
+                   "imex_demo_6e5_b10": imex_workload(torch, bdfb, gen, 600_000, 10.0, precisions=(1,),
+                                                      oracle_points=5_000)}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
                        ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):

@@ -125,7 +125,7 @@ struct LUOwn {
 // LU of block c in place: L unit lower (multipliers), U upper with its
 // diagonal replaced by the reciprocal.  Returns 0 or k + 1 for a zero or
 // non-finite pivot at step k.
-__device__ __forceinline__ int lu_factor_sp(const LUDev& L, int64_t nb, double* v, int64_t c) {
+__device__ __forceinline__ int lu_factor_sp(const LUDev& L, int64_t nb, double* __restrict__ v, int64_t c) {
   for (int k = 0; k < L.n; ++k) {
     double* dk = v + (int64_t)L.diag[k] * nb + c;
     const double piv = *dk;
@@ -150,14 +150,17 @@ __device__ __forceinline__ int lu_factor_sp(const LUDev& L, int64_t nb, double* 
 }
 
 // x <- (LU)^{-1} x for block c; x entry-major [n][nb]
-__device__ __forceinline__ void lu_solve_sp(const LUDev& L, int64_t nb, const double* v, double* x, int64_t c) {
+__device__ __forceinline__ void lu_solve_sp(const LUDev& L, int64_t nb, const double* __restrict__ v,
+                                            double* __restrict__ x, int64_t c) {
   for (int i = 0; i < L.n; ++i) {
     double s = x[(int64_t)i * nb + c];
+#pragma unroll 4
     for (int e = L.rlptr[i]; e < L.rlptr[i + 1]; ++e) s -= v[(int64_t)L.rlpos[e] * nb + c] * x[(int64_t)L.rlcol[e] * nb + c];
     x[(int64_t)i * nb + c] = s;
   }
   for (int i = L.n - 1; i >= 0; --i) {
     double s = x[(int64_t)i * nb + c];
+#pragma unroll 4
     for (int e = L.ruptr[i]; e < L.ruptr[i + 1]; ++e) s -= v[(int64_t)L.rupos[e] * nb + c] * x[(int64_t)L.rucol[e] * nb + c];
     x[(int64_t)i * nb + c] = s * v[(int64_t)L.diag[i] * nb + c];
   }
@@ -206,8 +209,10 @@ struct NetDev {
   LUDev L;
 };
 
-__device__ __forceinline__ void net_rates(const NetDev& D, const double* y, double* rates, int64_t c) {
+__device__ __forceinline__ void net_rates(const NetDev& D, const double* __restrict__ y, double* __restrict__ rates,
+                                          int64_t c) {
   const int64_t nb = D.nb;
+#pragma unroll 4
   for (int r = 0; r < D.R; ++r) {
     const uint32_t rr = D.reac[r];
     double v = D.k[r];
@@ -220,10 +225,13 @@ __device__ __forceinline__ void net_rates(const NetDev& D, const double* y, doub
   }
 }
 
-__device__ __forceinline__ void net_f(const NetDev& D, const double* rates, double* f, int64_t c) {
+__device__ __forceinline__ void net_f(const NetDev& D, const double* __restrict__ rates, double* __restrict__ f,
+                                      int64_t c) {
   const int64_t nb = D.nb;
+#pragma unroll 2
   for (int s = 0; s < D.n; ++s) {
     double acc = 0.0;
+#pragma unroll 4
     for (int e = D.inc_off[s]; e < D.inc_off[s + 1]; ++e) {
       const uint16_t ent = D.inc[e];
       const double v = rates[(int64_t)(ent >> 1) * nb + c];
@@ -234,7 +242,8 @@ __device__ __forceinline__ void net_f(const NetDev& D, const double* rates, doub
 }
 
 // M = I - gamma J(y) in the LU pattern of cell c, then its LU
-__device__ __forceinline__ int net_setup(const NetDev& D, const double* y, double gamma, double* lu, int64_t c) {
+__device__ __forceinline__ int net_setup(const NetDev& D, const double* __restrict__ y, double gamma,
+                                         double* __restrict__ lu, int64_t c) {
   const int64_t nb = D.nb;
   for (int e = 0; e < D.L.nnz; ++e) lu[(int64_t)e * nb + c] = 0.0;
   for (int k = 0; k < D.n; ++k) lu[(int64_t)D.L.diag[k] * nb + c] = 1.0;
