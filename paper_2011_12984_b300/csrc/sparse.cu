@@ -196,84 +196,179 @@ __global__ void __launch_bounds__(ST) k_sp_solve(LUDev L, int64_t nb, const doub
 }
 
 // ---- a network shared by every cell
+// Every table below holds offsets already multiplied by the cell count nb
+// (entry e of cell c at v[e nb + c]): the kernels add them to per-cell base
+// pointers, so an access costs one address add.  The context checks that
+// every offset fits an int32.
 struct NetDev {
   int n, R;
   int64_t nb;                  // cells
-  const uint32_t* reac;        // 4 reactant indices per reaction, 8 bits each (255 = none)
+  const int* reac;             // [4 R] reactant offsets s nb, -1 = empty slot
   const double* k;             // [R]
   const int* inc_off;          // [n + 1] species-major incidence lists
-  const uint16_t* inc;         // (r << 1) | produced, reaction order, consumption first
+  const int* inc;              // (r nb) << 1 | produced, reaction order, consumption first
   const int* jac_off;          // [4 R + 1] scatter lists of d rate_r / d y_(reactant a)
-  const int* jac_pos;          // LU entry
+  const int* jac_pos;          // LU entry offsets
   const int8_t* jac_sgn;       // +1: the species is a reactant (M += gamma d), -1: a product
-  LUDev L;
+  int nnz;                     // LU entries (with fill)
+  const int *diag, *lptr, *lpos, *uptr, *upos, *tptr, *tgt;   // factor schedule (offsets)
+  const int *rlptr, *rlpos, *rlcol, *ruptr, *rupos, *rucol;   // solve schedule (offsets)
+  // banded factors (every entry within BW of the diagonal): offset of
+  // (i, i - d) at bl[i BW + d - 1], of (i, i + d) at bu[i BW + d - 1], -1 if absent
+  const int* bl;
+  const int* bu;
 };
 
-__device__ __forceinline__ void net_rates(const NetDev& D, const double* __restrict__ y, double* __restrict__ rates,
-                                          int64_t c) {
+constexpr int BW = 8;          // widest band the register-window solve takes
+
+// LU of cell c in place (v = the cell's base pointer): L unit lower, U upper
+// with its diagonal replaced by the reciprocal; 0 or k + 1 for a zero or
+// non-finite pivot at step k
+__device__ __forceinline__ int net_factor(const NetDev& D, double* __restrict__ v) {
+  for (int k = 0; k < D.n; ++k) {
+    double* dk = v + D.diag[k];
+    const double piv = *dk;
+    if (!(piv != 0.0) || !isfinite(piv)) return k + 1;
+    const double inv = 1.0 / piv;
+    *dk = inv;
+    const int l0 = D.lptr[k], l1 = D.lptr[k + 1], u0 = D.uptr[k], u1 = D.uptr[k + 1];
+    const int nu = u1 - u0;
+    const int* t = D.tgt + D.tptr[k];
+    for (int a = l0; a < l1; ++a) {
+      double* lp = v + D.lpos[a];
+      const double m = *lp * inv;
+      *lp = m;
+      const int* ta = t + (a - l0) * nu;
+#pragma unroll 4
+      for (int b = 0; b < nu; ++b) v[ta[b]] -= m * v[D.upos[u0 + b]];
+    }
+  }
+  return 0;
+}
+
+// x <- (LU)^{-1} x for one cell (v, x: the cell's base pointers)
+__device__ __forceinline__ void net_solve(const NetDev& D, const double* __restrict__ v, double* __restrict__ x) {
+  const int64_t nb = D.nb;
+  for (int i = 0; i < D.n; ++i) {
+    double s = x[i * nb];
+#pragma unroll 4
+    for (int e = D.rlptr[i]; e < D.rlptr[i + 1]; ++e) s -= v[D.rlpos[e]] * x[D.rlcol[e]];
+    x[i * nb] = s;
+  }
+  for (int i = D.n - 1; i >= 0; --i) {
+    double s = x[i * nb];
+#pragma unroll 4
+    for (int e = D.ruptr[i]; e < D.ruptr[i + 1]; ++e) s -= v[D.rupos[e]] * x[D.rucol[e]];
+    x[i * nb] = s * v[D.diag[i]];
+  }
+}
+
+// The same solves for a banded factor with the last BW solved values in
+// registers: each row's dependence on the rows above (below) it runs through
+// registers, and every load of the row (its right-hand side and factor
+// entries) is independent of that chain.  Rows go in chunks of BW so that
+// every register index is static.
+__device__ __forceinline__ void net_solve_band(const NetDev& D, const double* __restrict__ v,
+                                               double* __restrict__ x) {
+  const int n = D.n;
+  const int64_t nb = D.nb;
+  double ring[BW];
+#pragma unroll
+  for (int t = 0; t < BW; ++t) ring[t] = 0.0;
+  for (int i0 = 0; i0 < n; i0 += BW) {
+#pragma unroll
+    for (int t = 0; t < BW; ++t) {
+      const int i = i0 + t;
+      if (i < n) {
+        double s = x[i * nb];
+        const int* bl = D.bl + i * BW;
+#pragma unroll
+        for (int d = 1; d <= BW; ++d) {
+          const int p = bl[d - 1];
+          if (p >= 0) s -= v[p] * ring[(t - d + BW) % BW];
+        }
+        ring[t] = s;
+        x[i * nb] = s;
+      }
+    }
+  }
+  for (int j0 = 0; j0 < n; j0 += BW) {           // rows i = n - 1 - (j0 + t)
+#pragma unroll
+    for (int t = 0; t < BW; ++t) {
+      const int i = n - 1 - (j0 + t);
+      if (i >= 0) {
+        double s = x[i * nb];                      // the forward value of row i
+        const int* bu = D.bu + i * BW;
+#pragma unroll
+        for (int d = 1; d <= BW; ++d) {
+          const int p = bu[d - 1];
+          if (p >= 0) s -= v[p] * ring[(t - d + BW) % BW];
+        }
+        s *= v[D.diag[i]];
+        ring[t] = s;
+        x[i * nb] = s;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void net_rates(const NetDev& D, const double* __restrict__ y, double* __restrict__ rates) {
   const int64_t nb = D.nb;
 #pragma unroll 4
   for (int r = 0; r < D.R; ++r) {
-    const uint32_t rr = D.reac[r];
     double v = D.k[r];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const uint32_t s = (rr >> (8 * a)) & 255u;
-      if (s != 255u) v *= y[(int64_t)s * nb + c];
+      const int o = D.reac[4 * r + a];
+      if (o >= 0) v *= y[o];
     }
-    rates[(int64_t)r * nb + c] = v;
+    rates[r * nb] = v;
   }
 }
 
-__device__ __forceinline__ void net_f(const NetDev& D, const double* __restrict__ rates, double* __restrict__ f,
-                                      int64_t c) {
-  const int64_t nb = D.nb;
-#pragma unroll 2
-  for (int s = 0; s < D.n; ++s) {
-    double acc = 0.0;
+// f_s of species s from the rates (reaction order, consumption first)
+__device__ __forceinline__ double net_fs(const NetDev& D, const double* __restrict__ rates, int s) {
+  double acc = 0.0;
 #pragma unroll 4
-    for (int e = D.inc_off[s]; e < D.inc_off[s + 1]; ++e) {
-      const uint16_t ent = D.inc[e];
-      const double v = rates[(int64_t)(ent >> 1) * nb + c];
-      acc = (ent & 1) ? acc + v : acc - v;
-    }
-    f[(int64_t)s * nb + c] = acc;
+  for (int e = D.inc_off[s]; e < D.inc_off[s + 1]; ++e) {
+    const int ent = D.inc[e];
+    const double v = rates[ent >> 1];
+    acc = (ent & 1) ? acc + v : acc - v;
   }
+  return acc;
 }
 
-// M = I - gamma J(y) in the LU pattern of cell c, then its LU
+// M = I - gamma J(y) in the LU pattern of one cell, then its LU
 __device__ __forceinline__ int net_setup(const NetDev& D, const double* __restrict__ y, double gamma,
-                                         double* __restrict__ lu, int64_t c) {
+                                         double* __restrict__ lu) {
   const int64_t nb = D.nb;
-  for (int e = 0; e < D.L.nnz; ++e) lu[(int64_t)e * nb + c] = 0.0;
-  for (int k = 0; k < D.n; ++k) lu[(int64_t)D.L.diag[k] * nb + c] = 1.0;
+  for (int e = 0; e < D.nnz; ++e) lu[e * nb] = 0.0;
+  for (int k = 0; k < D.n; ++k) lu[D.diag[k]] = 1.0;
   for (int r = 0; r < D.R; ++r) {
-    const uint32_t rr = D.reac[r];
+    const int* ro = D.reac + 4 * r;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      if (((rr >> (8 * a)) & 255u) == 255u) continue;
+      if (ro[a] < 0) continue;
       double d = D.k[r];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint32_t s = (rr >> (8 * b)) & 255u;
-        if (b != a && s != 255u) d *= y[(int64_t)s * nb + c];
-      }
+      for (int b = 0; b < 4; ++b)
+        if (b != a && ro[b] >= 0) d *= y[ro[b]];
       const double gd = gamma * d;
       for (int e = D.jac_off[4 * r + a]; e < D.jac_off[4 * r + a + 1]; ++e) {
-        double* p = lu + (int64_t)D.jac_pos[e] * nb + c;
+        double* p = lu + D.jac_pos[e];
         *p = D.jac_sgn[e] > 0 ? *p + gd : *p - gd;
       }
     }
   }
-  return lu_factor_sp(D.L, nb, lu, c);
+  return net_factor(D, lu);
 }
 
 __global__ void __launch_bounds__(ST) k_net_rhs(NetDev D, const double* __restrict__ y, double* __restrict__ f,
                                                 double* __restrict__ rates) {
   const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
   if (c >= D.nb) return;
-  net_rates(D, y, rates, c);
-  net_f(D, rates, f, c);
+  net_rates(D, y + c, rates + c);
+  for (int s = 0; s < D.n; ++s) f[s * D.nb + c] = net_fs(D, rates + c, s);
 }
 
 struct NewtonArgs {
@@ -293,21 +388,29 @@ struct NewtonArgs {
 // iterations; a stale M scales the correction by 2 / (1 + gamma / gamma_p).
 __global__ void __launch_bounds__(ST) k_net_newton(NetDev D, NewtonArgs A, double* __restrict__ lu,
                                                    double* __restrict__ rates, double* __restrict__ yv,
-                                                   double* __restrict__ fv, double* __restrict__ xv) {
+                                                   double* __restrict__ xv) {
   const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
   if (c >= D.nb) return;
   const int64_t nb = D.nb;
   const int n = D.n;
+  const double* z0 = A.zp0 + c;
+  const double* z1 = A.zp1 + c;
+  const double* ew = A.ewt + c;
+  double* ac = A.acor + c;
+  double* luc = lu + c;
+  double* rc = rates + c;
+  double* yc = yv + c;
+  double* xc = xv + c;
   double crate = A.crate[c];
   if (A.setup) {
     crate = 1.0;
-    if (net_setup(D, A.zp0, A.gamma, lu, c)) {
+    if (net_setup(D, z0, A.gamma, luc)) {
       A.crate[c] = crate;
       atomicOr(A.failed, 1);
       return;
     }
   }
-  for (int s = 0; s < n; ++s) A.acor[(int64_t)s * nb + c] = 0.0;
+  for (int s = 0; s < n; ++s) ac[s * nb] = 0.0;
   const double rn = 1.0 / (double)n;
   const double eq2 = A.Eq * A.Eq * 100.0;
   const double scst = A.gamma != A.gammap ? 2.0 / (1.0 + A.gamma / A.gammap) : 1.0;
@@ -315,29 +418,25 @@ __global__ void __launch_bounds__(ST) k_net_newton(NetDev D, NewtonArgs A, doubl
   bool conv = false;
   int it = 1, nit = 0;
   for (; it <= 3; ++it) {
-    for (int s = 0; s < n; ++s) {
-      const int64_t i = (int64_t)s * nb + c;
-      yv[i] = A.zp0[i] + A.acor[i];
-    }
-    net_rates(D, yv, rates, c);
-    net_f(D, rates, fv, c);
+    for (int s = 0; s < n; ++s) yc[s * nb] = z0[s * nb] + ac[s * nb];
+    net_rates(D, yc, rc);
     bool fin = true;
-    for (int s = 0; s < n; ++s) fin = fin && isfinite(fv[(int64_t)s * nb + c]);
+    for (int s = 0; s < n; ++s) {              // x = gamma f - z1 / l1 - acor
+      const double f = net_fs(D, rc, s);
+      fin = fin && isfinite(f);
+      xc[s * nb] = A.gamma * f - z1[s * nb] * A.rl1 - ac[s * nb];
+    }
     if (!fin) break;
     ++nit;
-    for (int s = 0; s < n; ++s) {
-      const int64_t i = (int64_t)s * nb + c;
-      xv[i] = A.gamma * fv[i] - A.zp1[i] * A.rl1 - A.acor[i];
-    }
-    lu_solve_sp(D.L, nb, lu, xv, c);
+    if (D.bl) net_solve_band(D, luc, xc);
+    else net_solve(D, luc, xc);
     double del2 = 0.0;
     for (int s = 0; s < n; ++s) {
-      const int64_t i = (int64_t)s * nb + c;
-      double x = xv[i];
+      double x = xc[s * nb];
       if (A.gamma != A.gammap) x *= scst;
-      const double e = x * A.ewt[i];
+      const double e = x * ew[s * nb];
       del2 += e * e;
-      A.acor[i] += x;
+      ac[s * nb] += x;
     }
     del2 *= rn;
     if (it > 1) crate = fmax(0.3 * crate, sqrt(del2 / delp2));
@@ -448,10 +547,9 @@ namespace bdfb {
 
 struct SharedInt {
   NetDev D = {};
-  LUOwn own;
   std::vector<void*> bufs;
   int nnz_m = 0;               // entries of M's own pattern
-  double *lu = nullptr, *rates = nullptr, *yv = nullptr, *fv = nullptr, *xv = nullptr, *crate = nullptr;
+  double *lu = nullptr, *rates = nullptr, *yv = nullptr, *xv = nullptr, *crate = nullptr;
   int* dflag = nullptr;
   unsigned long long* diters = nullptr;
   GridBDF* gg = nullptr;
@@ -459,6 +557,14 @@ struct SharedInt {
   ~SharedInt() {
     grid_destroy(gg);
     for (void* p : bufs) cudaFree(p);
+  }
+  template <typename T>
+  int up(const T** d, const std::vector<T>& h) {
+    T* p = nullptr;
+    const int r = upload(&p, h);
+    if (!r) bufs.push_back(p);
+    *d = p;
+    return r;
   }
 };
 
@@ -483,7 +589,7 @@ static int net_solve_cb(void* user, const double* zp0, const double* zp1, const 
   A.iters = S->diters;
   BDFB_CUDA(cudaMemsetAsync(S->dflag, 0, sizeof(int), s));
   BDFB_CUDA(cudaMemsetAsync(S->diters, 0, 2 * sizeof(unsigned long long), s));
-  k_net_newton<<<grid_for(S->D.nb), ST, 0, s>>>(S->D, A, S->lu, S->rates, S->yv, S->fv, S->xv);
+  k_net_newton<<<grid_for(S->D.nb), ST, 0, s>>>(S->D, A, S->lu, S->rates, S->yv, S->xv);
   BDFB_CUDA(cudaGetLastError());
   int fl = 0;
   unsigned long long it[2] = {0, 0};
@@ -505,21 +611,18 @@ int shared_create(const bdfb_problem* prob, SharedInt** out) {
   const int64_t R64 = prob->rxn_off[1] - prob->rxn_off[0];
   if (prob->rxn_off[0] != 0 || n < 1 || n > 255 || R64 < 0 || R64 > 65535) return BDFB_ILL_INPUT;
   const int R = (int)R64;
+  const int64_t nb = prob->ncell;
   // network, pattern of J (rows: affected species, columns: reactants)
-  std::vector<uint32_t> reac(std::max(R, 1));
   std::vector<uint8_t> A((size_t)n * n, 0);
-  std::vector<std::vector<uint16_t>> incs(n);
+  std::vector<std::vector<int>> incs(n);
   for (int r = 0; r < R; ++r) {
     const uint8_t* ra = prob->reactants + 4 * r;
     const uint8_t* pa = prob->products + 4 * r;
-    uint32_t packed = 0;
     for (int a = 0; a < 4; ++a) {
       if ((ra[a] != 255 && ra[a] >= n) || (pa[a] != 255 && pa[a] >= n)) return BDFB_ILL_INPUT;
       for (int b = 0; b < a; ++b)
         if ((ra[a] != 255 && ra[a] == ra[b]) || (pa[a] != 255 && pa[a] == pa[b])) return BDFB_ILL_INPUT;
-      packed |= (uint32_t)ra[a] << (8 * a);
     }
-    reac[r] = packed;
     for (int a = 0; a < 4; ++a) {
       if (ra[a] == 255) continue;
       for (int b = 0; b < 4; ++b) {
@@ -528,19 +631,31 @@ int shared_create(const bdfb_problem* prob, SharedInt** out) {
       }
     }
     for (int a = 0; a < 4; ++a)
-      if (ra[a] != 255) incs[ra[a]].push_back((uint16_t)(r << 1));
+      if (ra[a] != 255) incs[ra[a]].push_back(r << 1);
     for (int a = 0; a < 4; ++a)
-      if (pa[a] != 255) incs[pa[a]].push_back((uint16_t)((r << 1) | 1));
+      if (pa[a] != 255) incs[pa[a]].push_back((r << 1) | 1);
   }
-  SharedInt* S = new (std::nothrow) SharedInt();
-  if (!S) return BDFB_MEM_FAIL;
-  for (uint8_t v : A) S->nnz_m += v != 0;
   const Symb sy = symbolic(n, A);
-  int r = S->own.make(sy);
-  std::vector<int> inc_off(n + 1, 0);
-  std::vector<uint16_t> inc;
+  // every table holds offsets times nb: they must fit an int32 (the rate
+  // offsets keep one more bit for the production flag)
+  const int64_t lim = (int64_t)1 << 30;
+  if ((int64_t)sy.nnz * nb >= lim || (int64_t)std::max(R, 1) * nb >= lim || (int64_t)n * nb >= lim)
+    return BDFB_ILL_INPUT;
+  auto sc = [nb](int v) { return v < 0 ? -1 : (int)((int64_t)v * nb); };
+  auto scv = [&](const std::vector<int>& v) {
+    std::vector<int> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = sc(v[i]);
+    return o;
+  };
+  std::vector<int> reac(4 * (size_t)std::max(R, 1), -1);
+  for (int r = 0; r < R; ++r)
+    for (int a = 0; a < 4; ++a) {
+      const uint8_t s2 = prob->reactants[4 * r + a];
+      reac[4 * (size_t)r + a] = s2 == 255 ? -1 : sc(s2);
+    }
+  std::vector<int> inc_off(n + 1, 0), inc;
   for (int s2 = 0; s2 < n; ++s2) {
-    inc.insert(inc.end(), incs[s2].begin(), incs[s2].end());
+    for (int ent : incs[s2]) inc.push_back((int)(((int64_t)(ent >> 1) * nb) << 1) | (ent & 1));
     inc_off[s2 + 1] = (int)inc.size();
   }
   // Jacobian scatter lists in reaction order
@@ -552,26 +667,60 @@ int shared_create(const bdfb_problem* prob, SharedInt** out) {
     for (int a = 0; a < 4; ++a) {
       if (ra[a] != 255)
         for (int b = 0; b < 4; ++b) {
-          if (ra[b] != 255) { jac_pos.push_back(sy.pos[(size_t)ra[b] * n + ra[a]]); jac_sgn.push_back(1); }
-          if (pa[b] != 255) { jac_pos.push_back(sy.pos[(size_t)pa[b] * n + ra[a]]); jac_sgn.push_back(-1); }
+          if (ra[b] != 255) { jac_pos.push_back(sc(sy.pos[(size_t)ra[b] * n + ra[a]])); jac_sgn.push_back(1); }
+          if (pa[b] != 255) { jac_pos.push_back(sc(sy.pos[(size_t)pa[b] * n + ra[a]])); jac_sgn.push_back(-1); }
         }
       jac_off[4 * (size_t)rr + a + 1] = (int)jac_pos.size();
     }
   }
-  std::vector<double> k(prob->k, prob->k + R);
-  uint32_t* dreac = nullptr;
-  double* dk = nullptr;
-  int *dinc_off = nullptr, *djoff = nullptr, *djpos = nullptr;
-  uint16_t* dinc = nullptr;
-  int8_t* djsgn = nullptr;
-  if (!r) { r = upload(&dreac, reac); S->bufs.push_back(dreac); }
-  if (!r) { r = upload(&dk, k); S->bufs.push_back(dk); }
-  if (!r) { r = upload(&dinc_off, inc_off); S->bufs.push_back(dinc_off); }
-  if (!r) { r = upload(&dinc, inc); S->bufs.push_back(dinc); }
-  if (!r) { r = upload(&djoff, jac_off); S->bufs.push_back(djoff); }
-  if (!r) { r = upload(&djpos, jac_pos); S->bufs.push_back(djpos); }
-  if (!r) { r = upload(&djsgn, jac_sgn); S->bufs.push_back(djsgn); }
-  const int64_t nb = prob->ncell;
+  // band tables when every factor entry lies within BW of the diagonal
+  bool banded = true;
+  for (int i = 0; i < n && banded; ++i)
+    for (int j = 0; j < n; ++j)
+      if (sy.pos[(size_t)i * n + j] >= 0 && std::abs(i - j) > BW) { banded = false; break; }
+  std::vector<int> bl, bu;
+  if (banded) {
+    bl.assign((size_t)n * BW, -1);
+    bu.assign((size_t)n * BW, -1);
+    for (int i = 0; i < n; ++i)
+      for (int d = 1; d <= BW; ++d) {
+        if (i - d >= 0) bl[(size_t)i * BW + d - 1] = sc(sy.pos[(size_t)i * n + i - d]);
+        if (i + d < n) bu[(size_t)i * BW + d - 1] = sc(sy.pos[(size_t)i * n + i + d]);
+      }
+  }
+  SharedInt* S = new (std::nothrow) SharedInt();
+  if (!S) return BDFB_MEM_FAIL;
+  for (uint8_t v : A) S->nnz_m += v != 0;
+  NetDev& D = S->D;
+  D.n = n;
+  D.R = R;
+  D.nb = nb;
+  D.nnz = sy.nnz;
+  int r = 0;
+  const std::vector<double> k(prob->k, prob->k + R);
+  if (!r) r = S->up(&D.reac, reac);
+  if (!r) r = S->up(&D.k, k);
+  if (!r) r = S->up(&D.inc_off, inc_off);
+  if (!r) r = S->up(&D.inc, inc);
+  if (!r) r = S->up(&D.jac_off, jac_off);
+  if (!r) r = S->up(&D.jac_pos, jac_pos);
+  if (!r) r = S->up(&D.jac_sgn, jac_sgn);
+  if (!r) r = S->up(&D.diag, scv(sy.diag));
+  if (!r) r = S->up(&D.lptr, sy.lptr);
+  if (!r) r = S->up(&D.lpos, scv(sy.lpos));
+  if (!r) r = S->up(&D.uptr, sy.uptr);
+  if (!r) r = S->up(&D.upos, scv(sy.upos));
+  if (!r) r = S->up(&D.tptr, sy.tptr);
+  if (!r) r = S->up(&D.tgt, scv(sy.tgt));
+  if (!r) r = S->up(&D.rlptr, sy.rlptr);
+  if (!r) r = S->up(&D.rlpos, scv(sy.rlpos));
+  if (!r) r = S->up(&D.rlcol, scv(sy.rlcol));
+  if (!r) r = S->up(&D.ruptr, sy.ruptr);
+  if (!r) r = S->up(&D.rupos, scv(sy.rupos));
+  if (!r) r = S->up(&D.rucol, scv(sy.rucol));
+  if (!r && banded) r = S->up(&D.bl, bl);
+  if (!r && banded) r = S->up(&D.bu, bu);
+  if (!banded) D.bl = D.bu = nullptr;
   auto alloc = [&](double** p, size_t count) {
     if (r) return;
     if (cudaMalloc(p, std::max<size_t>(count, 1) * sizeof(double)) != cudaSuccess) { *p = nullptr; r = BDFB_MEM_FAIL; return; }
@@ -580,33 +729,17 @@ int shared_create(const bdfb_problem* prob, SharedInt** out) {
   alloc(&S->lu, (size_t)sy.nnz * nb);
   alloc(&S->rates, (size_t)std::max(R, 1) * nb);
   alloc(&S->yv, (size_t)n * nb);
-  alloc(&S->fv, (size_t)n * nb);
   alloc(&S->xv, (size_t)n * nb);
   alloc(&S->crate, (size_t)nb);
   if (!r && cudaMalloc(&S->dflag, sizeof(int)) != cudaSuccess) r = BDFB_MEM_FAIL;
   if (!r) S->bufs.push_back(S->dflag);
   if (!r && cudaMalloc(&S->diters, 2 * sizeof(unsigned long long)) != cudaSuccess) r = BDFB_MEM_FAIL;
   if (!r) S->bufs.push_back(S->diters);
-  if (r) {
-    delete S;
-    return r;
-  }
-  S->D.n = n;
-  S->D.R = R;
-  S->D.nb = nb;
-  S->D.reac = dreac;
-  S->D.k = dk;
-  S->D.inc_off = dinc_off;
-  S->D.inc = dinc;
-  S->D.jac_off = djoff;
-  S->D.jac_pos = djpos;
-  S->D.jac_sgn = djsgn;
-  S->D.L = S->own.D;
   GridExternal ext;
   ext.user = S;
   ext.rhs = net_rhs_cb;
   ext.solve = net_solve_cb;
-  r = grid_create_external((int64_t)n * nb, ext, &S->gg);
+  if (!r) r = grid_create_external((int64_t)n * nb, ext, &S->gg);
   if (r) {
     delete S;
     return r;
@@ -635,7 +768,7 @@ int shared_integrate(SharedInt* S, double tout, double* y, int mem) { return gri
 
 void shared_stats(SharedInt* S, int64_t out[8], double* last_ms, int* q, double* h) {
   grid_stats(S->gg, out, last_ms);
-  out[6] = S->D.L.nnz;
+  out[6] = S->D.nnz;
   out[7] = S->nnz_m;
   grid_next_step(S->gg, q, h);
 }
