@@ -156,17 +156,46 @@ __device__ __forceinline__ bool solve64(const Par& P, double hg, double u, doubl
   return det != 0.0;
 }
 
+// FP64 <-> FP32 conversions on the integer pipe, from the IEEE-754 binary64
+// and binary32 layouts (B300 issues FP64, and conversions to and from it, at
+// 2 per cycle per SM; the integer pipe at 64).  to_f32 truncates the
+// significand (round toward zero), flushes magnitudes below 2^-126 to a
+// signed zero and maps magnitudes from 2^128 up, infinities and NaN to
+// infinity or NaN; to_f64 is exact for every normal binary32 and zero.
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);          // top 23 significand bits
+  unsigned bits;
+  if (e == 0x7ff) bits = sign | 0x7f800000u | (m != 0u || (lo & 0x1fffffffu) != 0u ? 0x400000u : 0u);
+  else if (e - 896 >= 255) bits = sign | 0x7f800000u;
+  else if (e - 896 <= 0) bits = sign;
+  else bits = sign | ((unsigned)(e - 896) << 23) | m;
+  return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned m = b & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);                 // zero (subnormals flushed)
+  const unsigned e64 = e == 0xffu ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)(sign | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // the same block in FP32: eliminate w first (row 3 of M has no v entry and
 // the dominant diagonal 1 + hg (1/eps + u)), then Cramer on the 2x2 (u, v)
 // Schur complement
 __device__ __forceinline__ bool solve32(const Par& P, double hg, double u, double v, double w, const double r[3],
-                                        double d[3]) {
-  const float h = (float)hg, uf = (float)u, vf = (float)v, wf = (float)w;
+                                        float d[3]) {
+  const float h = (float)hg, uf = to_f32(u), vf = to_f32(v), wf = to_f32(w);
   const float uu = uf * uf, uv2 = 2.0f * uf * vf;
   const float m00 = 1.0f - h * (uv2 - (wf + 1.0f)), m01 = -h * uu, m02 = h * uf;
   const float m10 = -h * (wf - uv2), m11 = 1.0f + h * uu, m12 = -h * uf;
   const float m20 = h * wf, m22 = 1.0f + h * ((float)P.reps + uf);
-  const float r0 = (float)r[0], r1 = (float)r[1], r2 = (float)r[2];
+  const float r0 = to_f32(r[0]), r1 = to_f32(r[1]), r2 = to_f32(r[2]);
   const float iw = 1.0f / m22;
   const float s0 = m02 * iw, s1 = m12 * iw;
   const float a00 = m00 - s0 * m20, a10 = m10 - s1 * m20;
@@ -176,9 +205,9 @@ __device__ __forceinline__ bool solve32(const Par& P, double hg, double u, doubl
   const float du = (b0 * m11 - m01 * b1) * id;
   const float dv = (a00 * b1 - a10 * b0) * id;
   const float dw = (r2 - m20 * du) * iw;
-  d[0] = (double)du;
-  d[1] = (double)dv;
-  d[2] = (double)dw;
+  d[0] = du;
+  d[1] = dv;
+  d[2] = dw;
   return det != 0.0f && m22 != 0.0f;
 }
 
@@ -196,6 +225,7 @@ __global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, dou
   __shared__ double sh[AT / 32];
   const int64_t np = P.np;
   double acc = 0.0;
+  float acc32 = 0.0f;
   bool ok = true;
   for (int64_t q = (int64_t)blockIdx.x * AT + threadIdx.x; q < np; q += (int64_t)gridDim.x * AT) {
     double av[3], zv[3];
@@ -213,32 +243,34 @@ __global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, dou
         zv[s] = z[i];
       }
     }
-    double f[3], r[3], d[3];
+    double f[3], r[3];
     react(P, zv[0], zv[1], zv[2], f);
 #pragma unroll
     for (int s = 0; s < 3; ++s) r[s] = av[s] + hg * f[s] - zv[s];
-    const bool nonsing = PREC == 0 ? solve64(P, hg, zv[0], zv[1], zv[2], r, d)
-                                   : solve32(P, hg, zv[0], zv[1], zv[2], r, d);
-    if (!nonsing || !isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2])) ok = false;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) z[s * np + q] = zv[s] + d[s];
     if (PREC == 0) {
+      double d[3];
+      const bool nonsing = solve64(P, hg, zv[0], zv[1], zv[2], r, d);
+      if (!nonsing || !isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2])) ok = false;
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
+        z[s * np + q] = zv[s] + d[s];
         const double e = d[s] * (double)ewt[s * np + q];
         acc += e * e;
       }
     } else {
-      float a32 = 0.0f;
+      float d[3];
+      const bool nonsing = solve32(P, hg, zv[0], zv[1], zv[2], r, d);
+      if (!nonsing || !isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2])) ok = false;
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
-        const float e = (float)d[s] * (float)ewt[s * np + q];
-        a32 += e * e;
+        z[s * np + q] = zv[s] + to_f64(d[s]);
+        const float e = d[s] * (float)ewt[s * np + q];
+        acc32 += e * e;
       }
-      acc += (double)a32;
     }
   }
   if (!ok) *bad = 1;
+  if (PREC == 1) acc = (double)acc32;
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -260,6 +292,7 @@ __global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h
   using W = typename Wt<PREC>::T;
   __shared__ double sh[AT / 32];
   double acc = 0.0;
+  float acc32 = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
     double s = 0.0, e = 0.0;
 #pragma unroll
@@ -275,11 +308,12 @@ __global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h
       const double ee = h * e * (double)ewt[i];
       acc += ee * ee;
     } else {
-      ewtn[i] = (W)(1.0f / ((float)rtol * fabsf((float)yn) + (float)atol));
-      const float ee = (float)(h * e) * (float)ewt[i];
-      acc += (double)(ee * ee);
+      ewtn[i] = (W)(1.0f / ((float)rtol * fabsf(to_f32(yn)) + (float)atol));
+      const float ee = to_f32(h * e) * (float)ewt[i];
+      acc32 += ee * ee;
     }
   }
+  if (PREC == 1) acc = (double)acc32;
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -289,7 +323,7 @@ __global__ void __launch_bounds__(AT) k_ark_ewt(int64_t N, double rtol, double a
                                                 typename Wt<PREC>::T* __restrict__ ewt) {
   for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
     if (PREC == 0) ewt[i] = 1.0 / (rtol * fabs(y[i]) + atol);
-    else ewt[i] = 1.0f / ((float)rtol * fabsf((float)y[i]) + (float)atol);
+    else ewt[i] = 1.0f / ((float)rtol * fabsf(to_f32(y[i])) + (float)atol);
   }
 }
 
