@@ -210,28 +210,39 @@ def nvector_ceilings(nv, hbm_gbs, sm_mhz):
 def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
     """The coupled-system workload: Brusselator reaction-diffusion on a
     periodic nx^3 grid (3 nx^3 unknowns), one shared step, Newton + GMRES
-    (Krylov dimension 5) with the 3x3 reaction blocks as preconditioner."""
+    (Krylov dimension 5) with the 3x3 reaction blocks as preconditioner;
+    FP64 throughout, then with the preconditioner and the GMRES operator in
+    FP32 (option precision 1), compared with the FP64 result."""
     p = gen.brusselator3d(nx)
     y0 = torch.from_numpy(p.y0).cuda()
     y = torch.empty_like(y0)
-    ts = []
-    with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5) as gi:
-        for _ in range(reps + 1):
-            gi.init(0.0, y0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = gi.integrate(tout, y)
-            torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t0)
-            if r != 0:
-                raise RuntimeError(f"grid integrate returned {r}")
-        gs = gi.cell_stats()[0]
-    t = min(ts[1:])
-    return {"workload": f"Brusselator 3-D {nx}^3 x 3 = {3 * nx ** 3} unknowns, A=1, B=3, eps=5e-6, D=1e-2, "
-                        f"t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 block Jacobi",
-            "grid_points_per_s": nx ** 3 / t, "seconds": t, "steps": int(gs[0]),
-            "ms_per_step": 1e3 * t / max(1, gs[0]), "newton_iters": int(gs[3]), "gmres_iters": int(gs[6]),
-            "jacobian_setups": int(gs[2])}
+    out, yref = {}, None
+    for prec in (0, 1):
+        ts = []
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5, precision=prec) as gi:
+            for _ in range(reps + 1):
+                gi.init(0.0, y0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = gi.integrate(tout, y)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                if r != 0:
+                    raise RuntimeError(f"grid integrate returned {r}")
+            gs = gi.cell_stats()[0]
+        t = min(ts[1:])
+        res = {"grid_points_per_s": nx ** 3 / t, "seconds": t, "steps": int(gs[0]),
+               "ms_per_step": 1e3 * t / max(1, gs[0]), "newton_iters": int(gs[3]), "gmres_iters": int(gs[6]),
+               "jacobian_setups": int(gs[2])}
+        if prec == 0:
+            yref = y.clone()
+            out.update(res)
+        else:
+            d = ((y - yref).abs() / (RTOL * yref.abs() + ATOL)).max().item()
+            out["fp32_preconditioner_and_operator"] = {**res, "max_weighted_diff_vs_fp64": d}
+    out["workload"] = (f"Brusselator 3-D {nx}^3 x 3 = {3 * nx ** 3} unknowns, A=1, B=3, eps=5e-6, D=1e-2, "
+                       f"t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 block Jacobi")
+    return out
 
 
 def timed_integrations(torch, integ, y0, y, tout, reps, flush=None):

@@ -187,6 +187,12 @@ int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, doubl
  *   nx + l] for species s = u, v, w.  Integrated with one shared step size,
  *   global WRMS norms, Newton + GMRES (option "maxl", default 5, at most 16)
  *   left-preconditioned by the 3x3 reaction blocks; control on the host.
+ *   Option "precision" 1 forms the preconditioner blocks and applies the
+ *   Newton operator inside GMRES in FP32 (the right-hand side, the Newton
+ *   residual, the Krylov basis and its orthogonalisation stay FP64: inexact
+ *   Newton-Krylov with a matrix-vector product accurate to ~1e-7, far inside
+ *   the linear tolerance); 0 (default) is FP64 throughout.  The same option
+ *   selects this for BDFB_BRUSSELATOR1D's BDF path.
  * kind BDFB_BRUSSELATOR1D: the demonstration problem of Sec. 7 as one
  *   coupled system: the same reaction terms with advection -c d/dx (first-
  *   order upwind differences) on a periodic line of nx points over

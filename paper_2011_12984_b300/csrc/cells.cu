@@ -1548,6 +1548,8 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "precision")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     ctx->line_prec = (int)v;
+    const int r = grid_set_option(ctx->grid, "precision", v);   // the BDF / GMRES path
+    if (r) return r;
     return ctx->ark ? ark_set_precision(ctx->ark, (int)v) : BDFB_SUCCESS;
   }
   if (ctx->grid) {

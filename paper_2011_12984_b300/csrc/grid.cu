@@ -109,22 +109,37 @@ __device__ __forceinline__ void bruss_jr(double reps, double u, double v, double
   J[6] = -w;                       J[7] = 0.0;     J[8] = -reps - u;
 }
 
-// Pinv = (I - gamma J_R(y))^{-1} per point, by the adjugate formula
+// the reaction Jacobian in FP32 (precision 1: the preconditioner and the
+// Newton operator inside GMRES)
+__device__ __forceinline__ void bruss_jr32(float reps, float u, float v, float w, float* J) {
+  J[0] = -(w + 1.0f) + 2.0f * u * v; J[1] = u * u;   J[2] = -u;
+  J[3] = w - 2.0f * u * v;           J[4] = -u * u;  J[5] = u;
+  J[6] = -w;                         J[7] = 0.0f;    J[8] = -reps - u;
+}
+
+template <typename T> __device__ __forceinline__ T ld(const double* p) { return *p; }
+template <> __device__ __forceinline__ float ld<float>(const double* p) { return to_f32(*p); }
+
+// Pinv = (I - gamma J_R(y))^{-1} per point, by the adjugate formula, in T
+// (double: precision 0; float: precision 1, the preconditioner in FP32)
+template <typename T>
 __global__ void k_bruss_psetup(int64_t np, double reps, double gamma, const double* __restrict__ y,
-                               double* __restrict__ Pinv, int* __restrict__ singular) {
+                               T* __restrict__ Pinv, int* __restrict__ singular) {
+  const T gm = (T)gamma;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-    double J[9];
-    bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
-    const double a = 1.0 - gamma * J[0], b = -gamma * J[1], c = -gamma * J[2];
-    const double d = -gamma * J[3], e = 1.0 - gamma * J[4], f = -gamma * J[5];
-    const double g = -gamma * J[6], h = -gamma * J[7], i = 1.0 - gamma * J[8];
-    const double A0 = e * i - f * h, A1 = c * h - b * i, A2 = b * f - c * e;
-    const double B0 = f * g - d * i, B1 = a * i - c * g, B2 = c * d - a * f;
-    const double C0 = d * h - e * g, C1 = b * g - a * h, C2 = a * e - b * d;
-    const double det = a * A0 + b * B0 + c * C0;
-    if (!(det != 0.0) || !isfinite(det)) { *singular = 1; continue; }
-    const double r = 1.0 / det;
-    double* P = Pinv + 9 * p;
+    T J[9];
+    if constexpr (sizeof(T) == 8) bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
+    else bruss_jr32((float)reps, ld<T>(y + p), ld<T>(y + np + p), ld<T>(y + 2 * np + p), J);
+    const T a = (T)1 - gm * J[0], b = -gm * J[1], c = -gm * J[2];
+    const T d = -gm * J[3], e = (T)1 - gm * J[4], f = -gm * J[5];
+    const T g = -gm * J[6], h = -gm * J[7], i = (T)1 - gm * J[8];
+    const T A0 = e * i - f * h, A1 = c * h - b * i, A2 = b * f - c * e;
+    const T B0 = f * g - d * i, B1 = a * i - c * g, B2 = c * d - a * f;
+    const T C0 = d * h - e * g, C1 = b * g - a * h, C2 = a * e - b * d;
+    const T det = a * A0 + b * B0 + c * C0;
+    if (!(det != (T)0) || !isfinite(det)) { *singular = 1; continue; }
+    const T r = (T)1 / det;
+    T* P = Pinv + 9 * p;
     P[0] = A0 * r; P[1] = A1 * r; P[2] = A2 * r;
     P[3] = B0 * r; P[4] = B1 * r; P[5] = B2 * r;
     P[6] = C0 * r; P[7] = C1 * r; P[8] = C2 * r;
@@ -133,72 +148,90 @@ __global__ void k_bruss_psetup(int64_t np, double reps, double gamma, const doub
 
 // w = S P^{-1} (u - gamma (D lap(u) + J_R(y) u)),  u = S^{-1} v, S = diag(ewt);
 // S^{-1} = diag(sc) with sc = rtol |y| + atol, so unscaling is a product
+template <typename T>
 __global__ void k_bruss_apply(int nx, double D, double reps, double gamma, const double* __restrict__ v,
                               const double* __restrict__ ewt, const double* __restrict__ sc,
-                              const double* __restrict__ y, const double* __restrict__ Pinv,
+                              const double* __restrict__ y, const T* __restrict__ Pinv,
                               double* __restrict__ w) {
   Pt Q;
   if (!stencil_point(nx, Q)) return;
   const int64_t n = nx, np = n * n * n, p = Q.p;
-  const double c = D * (double)(n * n);
-  double u[3], lap[3];
+  const T c = (T)(D * (double)(n * n));
+  const T gm = (T)gamma;
+  T u[3], lap[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const double* vs = v + s * np;
     const double* ss = sc + s * np;
-    u[s] = vs[p] * ss[p];
-    double sum = 0.0;
+    u[s] = ld<T>(vs + p) * ld<T>(ss + p);
+    T sum = (T)0;
 #pragma unroll
-    for (int t = 0; t < 6; ++t) sum += vs[Q.o[t]] * ss[Q.o[t]];
-    lap[s] = c * (sum - 6.0 * u[s]);
+    for (int t = 0; t < 6; ++t) sum += ld<T>(vs + Q.o[t]) * ld<T>(ss + Q.o[t]);
+    lap[s] = c * (sum - (T)6 * u[s]);
   }
-  double J[9];
-  bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
-  double a[3];
+  T J[9];
+  if constexpr (sizeof(T) == 8) bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
+  else bruss_jr32((float)reps, ld<T>(y + p), ld<T>(y + np + p), ld<T>(y + 2 * np + p), J);
+  T a[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) a[s] = u[s] - gamma * (lap[s] + J[3 * s] * u[0] + J[3 * s + 1] * u[1] + J[3 * s + 2] * u[2]);
-  const double* P = Pinv + 9 * p;
+  for (int s = 0; s < 3; ++s) a[s] = u[s] - gm * (lap[s] + J[3 * s] * u[0] + J[3 * s + 1] * u[1] + J[3 * s + 2] * u[2]);
+  const T* P = Pinv + 9 * p;
 #pragma unroll
-  for (int s = 0; s < 3; ++s)
-    w[s * np + p] = ewt[s * np + p] * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+  for (int s = 0; s < 3; ++s) {
+    const T o = ld<T>(ewt + s * np + p) * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+    if constexpr (sizeof(T) == 8) w[s * np + p] = o;
+    else w[s * np + p] = to_f64(o);
+  }
 }
 
 // the same operator on the 1-D line, advection in place of diffusion
+template <typename T>
 __global__ void k_bruss1_apply(int64_t np, double cdx, double reps, double gamma, const double* __restrict__ v,
                                const double* __restrict__ ewt, const double* __restrict__ sc,
-                               const double* __restrict__ y, const double* __restrict__ Pinv,
+                               const double* __restrict__ y, const T* __restrict__ Pinv,
                                double* __restrict__ w) {
+  const T cx = (T)cdx, gm = (T)gamma;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pl = p == 0 ? np - 1 : p - 1, pr = p + 1 == np ? 0 : p + 1;
-    double u[3], adv[3];
+    T u[3], adv[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const double* vs = v + s * np;
       const double* ss = sc + s * np;
-      u[s] = vs[p] * ss[p];
-      adv[s] = cdx >= 0.0 ? -cdx * (u[s] - vs[pl] * ss[pl]) : -cdx * (vs[pr] * ss[pr] - u[s]);
+      u[s] = ld<T>(vs + p) * ld<T>(ss + p);
+      adv[s] = cdx >= 0.0 ? -cx * (u[s] - ld<T>(vs + pl) * ld<T>(ss + pl))
+                          : -cx * (ld<T>(vs + pr) * ld<T>(ss + pr) - u[s]);
     }
-    double J[9];
-    bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
-    double a[3];
+    T J[9];
+    if constexpr (sizeof(T) == 8) bruss_jr(reps, y[p], y[np + p], y[2 * np + p], J);
+    else bruss_jr32((float)reps, ld<T>(y + p), ld<T>(y + np + p), ld<T>(y + 2 * np + p), J);
+    T a[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s)
-      a[s] = u[s] - gamma * (adv[s] + J[3 * s] * u[0] + J[3 * s + 1] * u[1] + J[3 * s + 2] * u[2]);
-    const double* P = Pinv + 9 * p;
+      a[s] = u[s] - gm * (adv[s] + J[3 * s] * u[0] + J[3 * s + 1] * u[1] + J[3 * s + 2] * u[2]);
+    const T* P = Pinv + 9 * p;
 #pragma unroll
-    for (int s = 0; s < 3; ++s)
-      w[s * np + p] = ewt[s * np + p] * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+    for (int s = 0; s < 3; ++s) {
+      const T o = ld<T>(ewt + s * np + p) * (P[3 * s] * a[0] + P[3 * s + 1] * a[1] + P[3 * s + 2] * a[2]);
+      if constexpr (sizeof(T) == 8) w[s * np + p] = o;
+      else w[s * np + p] = to_f64(o);
+    }
   }
 }
 
 // v = S P^{-1} b
-__global__ void k_prec_scale(int64_t np, const double* __restrict__ b, const double* __restrict__ Pinv,
+template <typename T>
+__global__ void k_prec_scale(int64_t np, const double* __restrict__ b, const T* __restrict__ Pinv,
                              const double* __restrict__ ewt, double* __restrict__ v) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-    const double b0 = b[p], b1 = b[np + p], b2 = b[2 * np + p];
-    const double* P = Pinv + 9 * p;
+    const T b0 = ld<T>(b + p), b1 = ld<T>(b + np + p), b2 = ld<T>(b + 2 * np + p);
+    const T* P = Pinv + 9 * p;
 #pragma unroll
-    for (int s = 0; s < 3; ++s) v[s * np + p] = ewt[s * np + p] * (P[3 * s] * b0 + P[3 * s + 1] * b1 + P[3 * s + 2] * b2);
+    for (int s = 0; s < 3; ++s) {
+      const T o = ld<T>(ewt + s * np + p) * (P[3 * s] * b0 + P[3 * s + 1] * b1 + P[3 * s + 2] * b2);
+      if constexpr (sizeof(T) == 8) v[s * np + p] = o;
+      else v[s * np + p] = to_f64(o);
+    }
   }
 }
 
@@ -209,7 +242,7 @@ __global__ void k_ewt(int64_t N, double rtol, double atol, const double* __restr
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double s = rtol * fabs(y[i]) + atol;
     sc[i] = s;
-    e[i] = 1.0 / s;
+    e[i] = recip_nr(s);
   }
 }
 
@@ -291,6 +324,7 @@ struct GridBDF {
   GridExternal ext = {};
   double rtol = 1e-6, atol = 1e-10;
   int maxl = 5;
+  int prec = 0;               // 1: preconditioner and GMRES operator in FP32
   int64_t mxstep = 100000;
   int qmax = GQMAX;
   cudaStream_t s = nullptr;
@@ -401,7 +435,8 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   const double sqrtN = std::sqrt((double)N);
   double H[(MAXL_MAX + 1) * MAXL_MAX] = {0};
   double gv[MAXL_MAX + 1] = {0}, cs[MAXL_MAX] = {0}, sn[MAXL_MAX] = {0}, yv[MAXL_MAX] = {0};
-  k_prec_scale<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, g->Pinv, g->ewt, g->V[0]);
+  if (g->prec) k_prec_scale<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, (const float*)g->Pinv, g->ewt, g->V[0]);
+  else k_prec_scale<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, g->Pinv, g->ewt, g->V[0]);
   BDFB_CUDA(cudaGetLastError());
   double beta2;
   const double* v0 = g->V[0];
@@ -416,12 +451,19 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   int k = 0;
   bool conv = false;
   for (int j = 0; j < maxl; ++j) {
-    if (g->dim == 1)
-      k_bruss1_apply<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->cdx, g->reps, g->gamma, g->V[j], g->ewt, g->sc,
-                                                      ycur, g->Pinv, g->w);
+    const float* P32 = (const float*)g->Pinv;
+    if (g->dim == 1 && g->prec)
+      k_bruss1_apply<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->cdx, g->reps, g->gamma, g->V[j], g->ewt,
+                                                             g->sc, ycur, P32, g->w);
+    else if (g->dim == 1)
+      k_bruss1_apply<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->cdx, g->reps, g->gamma, g->V[j], g->ewt,
+                                                              g->sc, ycur, g->Pinv, g->w);
+    else if (g->prec)
+      k_bruss_apply<float><<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j],
+                                                                   g->ewt, g->sc, ycur, P32, g->w);
     else
-      k_bruss_apply<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j], g->ewt,
-                                                            g->sc, ycur, g->Pinv, g->w);
+      k_bruss_apply<double><<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j],
+                                                                    g->ewt, g->sc, ycur, g->Pinv, g->w);
     BDFB_CUDA(cudaGetLastError());
     double hcol[MAXL_MAX + 1];
     GCHK(g_dots(g, g->w, g->V, j + 1, hcol));        // classical Gram-Schmidt
@@ -475,7 +517,10 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
 
 static int g_psetup(GridBDF* g, const double* y) {
   BDFB_CUDA(cudaMemsetAsync(g->dsing, 0, sizeof(int), g->s));
-  k_bruss_psetup<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, g->Pinv, g->dsing);
+  if (g->prec)
+    k_bruss_psetup<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, (float*)g->Pinv, g->dsing);
+  else
+    k_bruss_psetup<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, g->Pinv, g->dsing);
   BDFB_CUDA(cudaGetLastError());
   int sing = 0;
   BDFB_CUDA(cudaMemcpyAsync(&sing, g->dsing, sizeof(int), cudaMemcpyDeviceToHost, g->s));
@@ -833,6 +878,10 @@ int grid_set_option(GridBDF* g, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "qmax")) {
     if (v < 1 || v > GQMAX) return BDFB_ILL_INPUT;
     g->qmax = (int)v;
+  } else if (!std::strcmp(key, "precision") && !g->external) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    g->prec = (int)v;
+    g->force_setup = true;      // the preconditioner's storage type changes
   } else {
     return BDFB_ILL_INPUT;
   }

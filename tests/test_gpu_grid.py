@@ -13,9 +13,9 @@ from paper_2011_12984_b300 import bdfb, gen
 pytestmark = pytest.mark.gpu
 
 
-def run_grid(p, tout, rtol, atol, y0=None, maxl=5, device_io=True):
+def run_grid(p, tout, rtol, atol, y0=None, maxl=5, device_io=True, precision=0):
     y0 = p.y0 if y0 is None else y0
-    with bdfb.Integrator(p, rtol=rtol, atol=atol, maxl=maxl) as I:
+    with bdfb.Integrator(p, rtol=rtol, atol=atol, maxl=maxl, precision=precision) as I:
         if device_io:
             I.init(0.0, torch.from_numpy(np.ascontiguousarray(y0)).cuda())
             y = torch.empty(y0.size, dtype=torch.float64, device="cuda")
@@ -28,11 +28,13 @@ def run_grid(p, tout, rtol, atol, y0=None, maxl=5, device_io=True):
         return ret, y, I.cell_stats()[0], I.stats()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nx,tout", [(6, 0.05), (10, 0.02)])
-def test_grid_matches_oracle(nx, tout):
+def test_grid_matches_oracle(nx, tout, precision):
+    """precision 1: FP32 preconditioner and GMRES operator (same bars)"""
     p = gen.brusselator3d(nx, seed=nx)
     rtol, atol = 1e-6, 1e-10
-    ret, y, gs, _ = run_grid(p, tout, rtol, atol)
+    ret, y, gs, _ = run_grid(p, tout, rtol, atol, precision=precision)
     assert ret == 0
     ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
@@ -79,24 +81,26 @@ def test_grid_64_cubed_properties():
     assert gs[0] > 0 and st["nsteps"] == gs[0]
 
 
-def test_grid_256_cubed_steady_state():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_256_cubed_steady_state(precision):
     """The benchmark's 256^3 grid (50 331 648 unknowns) in its launch
     configuration: started at the exact steady state it must stay there."""
     p = gen.brusselator3d(256, noise=0.0)
-    ret, y, gs, _ = run_grid(p, 0.1, 1e-6, 1e-10)
+    ret, y, gs, _ = run_grid(p, 0.1, 1e-6, 1e-10, precision=precision)
     assert ret == 0
     assert np.max(np.abs(y - p.y0) / np.abs(p.y0)) <= 1e-12
     assert gs[0] > 0
 
 
 # ------------------------------------------------ the 1-D advection demo (Sec. 7)
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nx,length,tout", [(40, 10.0, 0.5), (200, 100.0, 1.0)])
-def test_line_matches_oracle(nx, length, tout):
+def test_line_matches_oracle(nx, length, tout, precision):
     """The demo problem (paper's initial state) against the oracle's grouped
     integrator, as for the 3-D grid."""
     p = gen.brusselator1d(nx, length=length)
     rtol, atol = 1e-6, 1e-10
-    ret, y, gs, _ = run_grid(p, tout, rtol, atol)
+    ret, y, gs, _ = run_grid(p, tout, rtol, atol, precision=precision)
     assert ret == 0
     ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
