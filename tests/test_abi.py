@@ -107,3 +107,36 @@ def test_sparse_pattern_rejected_without_gpu(lib):
     assert L.bdfb_sparse_create(2, 1, bad_rp, ok_ci, C.byref(h)) == ILL      # decreasing rowptr
     L.bdfb_sparse_factor.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     assert L.bdfb_sparse_factor(None, 4, None, None, None) == ILL
+
+
+class _Problem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mem", C.c_int32), ("ncell", C.c_int64), ("n", C.c_void_p),
+                ("y_off", C.c_void_p), ("rxn_off", C.c_void_p), ("reactants", C.c_void_p),
+                ("products", C.c_void_p), ("k", C.c_void_p)]
+
+
+def test_shared_network_rejected_without_gpu(lib):
+    """BDFB_MASSACTION_SHARED: a malformed network fails in the host checks"""
+    L, _ = lib
+    ILL = -22
+    L.bdfb_create.argtypes = [C.POINTER(_Problem), C.POINTER(C.c_void_p)]
+
+    def make(n, rxn, reac, prod, ncell=4, mem=0):
+        arrs = dict(n=(C.c_int32 * 1)(n), rxn=(C.c_int64 * 2)(0, rxn),
+                    reac=(C.c_uint8 * len(reac))(*reac), prod=(C.c_uint8 * len(prod))(*prod),
+                    k=(C.c_double * max(rxn, 1))(*([1.0] * max(rxn, 1))))
+        p = _Problem(4, mem, ncell, C.cast(arrs["n"], C.c_void_p), None, C.cast(arrs["rxn"], C.c_void_p),
+                     C.cast(arrs["reac"], C.c_void_p), C.cast(arrs["prod"], C.c_void_p),
+                     C.cast(arrs["k"], C.c_void_p))
+        return p, arrs
+
+    h = C.c_void_p()
+    ok_r, ok_p = [0, 1, 255, 255], [2, 255, 255, 255]
+    for bad in (dict(n=0, rxn=1, reac=ok_r, prod=ok_p),                 # no species
+                dict(n=256, rxn=1, reac=ok_r, prod=ok_p),               # more than 255
+                dict(n=3, rxn=1, reac=[0, 3, 255, 255], prod=ok_p),     # species out of range
+                dict(n=3, rxn=1, reac=[1, 1, 255, 255], prod=ok_p),     # repeated reactant
+                dict(n=3, rxn=1, reac=ok_r, prod=ok_p, mem=1),          # device arrays
+                dict(n=3, rxn=1, reac=ok_r, prod=ok_p, ncell=0)):       # no cells
+        p, keep = make(**bad)
+        assert L.bdfb_create(C.byref(p), C.byref(h)) == ILL, bad
