@@ -211,7 +211,11 @@ int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, doubl
  *   path's arithmetic: 0 (default) FP64 throughout; 1 forms and solves the
  *   3x3 Newton blocks in FP32 and keeps FP32 norm weights, with the state,
  *   stage sums, reaction terms and Newton residual in FP64 (the iteration
- *   converges to the same FP64 residual test).
+ *   converges to the same FP64 residual test).  Option "device_loop" 1 runs
+ *   the IMEX step loop to tout in one cooperative launch (grid-wide barriers
+ *   in place of host round trips: every block takes the same decisions from
+ *   the same sums); 0 drives it from the host; -1 (default) takes the
+ *   former up to 2e6 points.
  * kind BDFB_MASSACTION_SHARED: ncell cells that share ONE network (the
  *   submodel case of Sec. 2 and Sec. 5 with one sparsity pattern for every
  *   block): n[0] species (1..255), reactions rxn_off[0] = 0 .. rxn_off[1]

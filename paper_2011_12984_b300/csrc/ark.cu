@@ -33,8 +33,11 @@
 // partial sums reduced on the host in a fixed order).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "ark.cuh"
 
@@ -43,6 +46,9 @@ namespace bdfb {
 namespace {
 
 constexpr int AT = 256;        // threads per block
+// largest line the automatic choice integrates with the device-side step loop
+// (the host loop wins from ~1e7 points, where bandwidth, not barriers, binds)
+constexpr int64_t DEVICE_LOOP_MAX_POINTS = 2000000;
 constexpr int NS = 4;          // stages
 
 struct Tab {
@@ -117,9 +123,9 @@ struct Wt<1> {
   using T = float;
 };
 
-// one stage's right-hand sides at z: g = f_E + f_I and f_I
-__global__ void __launch_bounds__(AT) k_ark_rhs(Par P, const double* __restrict__ z, double* __restrict__ g,
-                                                double* __restrict__ fi) {
+// one stage's right-hand sides at z: g = f_E + f_I and f_I (grid-stride)
+__device__ __forceinline__ void dev_rhs(const Par& P, const double* __restrict__ z, double* __restrict__ g,
+                                        double* __restrict__ fi) {
   const int64_t np = P.np;
   for (int64_t q = (int64_t)blockIdx.x * AT + threadIdx.x; q < np; q += (int64_t)gridDim.x * AT) {
     double r[3];
@@ -130,6 +136,11 @@ __global__ void __launch_bounds__(AT) k_ark_rhs(Par P, const double* __restrict_
       fi[s * np + q] = r[s];
     }
   }
+}
+
+__global__ void __launch_bounds__(AT) k_ark_rhs(Par P, const double* __restrict__ z, double* __restrict__ g,
+                                                double* __restrict__ fi) {
+  dev_rhs(P, z, g, fi);
 }
 
 struct Stage {
@@ -187,13 +198,13 @@ __device__ __forceinline__ bool solve32(const Par& P, double hg, double u, doubl
 // predictor z = a + hg fi_0.  delta = (I - hg J_R(z))^{-1} (a + hg f_I(z) - z);
 // z += delta; per-block partial sums of (delta ewt)^2; *bad = 1 on a
 // singular block or a non-finite value.
+// Returns the block's sum in thread 0 (+infinity when any point of the
+// block is bad); every thread of the block calls it.
 template <bool FIRST, int PREC>
-__global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, double hg,
-                                                   const double* __restrict__ y, double* __restrict__ a,
-                                                   double* __restrict__ z,
-                                                   const typename Wt<PREC>::T* __restrict__ ewt,
-                                                   double* __restrict__ part, int* __restrict__ bad) {
-  __shared__ double sh[AT / 32];
+__device__ __forceinline__ double dev_newton(const Par& P, const Stage& S, double h, double hg,
+                                             const double* __restrict__ y, double* __restrict__ a,
+                                             double* __restrict__ z,
+                                             const typename Wt<PREC>::T* __restrict__ ewt, double* sh) {
   const int64_t np = P.np;
   double acc = 0.0;
   float acc32 = 0.0f;
@@ -240,10 +251,24 @@ __global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, dou
       }
     }
   }
-  if (!ok) *bad = 1;
   if (PREC == 1) acc = (double)acc32;
+  const int anybad = __syncthreads_or(!ok);
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  return anybad ? (double)INFINITY : s;
+}
+
+template <bool FIRST, int PREC>
+__global__ void __launch_bounds__(AT) k_ark_newton(Par P, Stage S, double h, double hg,
+                                                   const double* __restrict__ y, double* __restrict__ a,
+                                                   double* __restrict__ z,
+                                                   const typename Wt<PREC>::T* __restrict__ ewt,
+                                                   double* __restrict__ part, int* __restrict__ bad) {
+  __shared__ double sh[AT / 32];
+  const double v = dev_newton<FIRST, PREC>(P, S, h, hg, y, a, z, ewt, sh);
+  if (threadIdx.x == 0) {
+    if (!isfinite(v)) *bad = 1;
+    part[blockIdx.x] = isfinite(v) ? v : 0.0;
+  }
 }
 
 struct Finish {
@@ -254,14 +279,12 @@ struct Finish {
 // ynew = y + h sum b_k g_k, err = h sum (b_k - bhat_k) g_k; partial sums
 // of (err ewt)^2; ewtn = weights of ynew
 template <int PREC>
-__global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h, double rtol, double atol,
-                                                   const double* __restrict__ y,
-                                                   const typename Wt<PREC>::T* __restrict__ ewt,
-                                                   double* __restrict__ ynew,
-                                                   typename Wt<PREC>::T* __restrict__ ewtn,
-                                                   double* __restrict__ part) {
+__device__ __forceinline__ double dev_finish(int64_t N, const Finish& F, double h, double rtol, double atol,
+                                             const double* __restrict__ y,
+                                             const typename Wt<PREC>::T* __restrict__ ewt,
+                                             double* __restrict__ ynew, typename Wt<PREC>::T* __restrict__ ewtn,
+                                             double* sh) {
   using W = typename Wt<PREC>::T;
-  __shared__ double sh[AT / 32];
   double acc = 0.0;
   float acc32 = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * AT + threadIdx.x; i < N; i += (int64_t)gridDim.x * AT) {
@@ -285,8 +308,19 @@ __global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h
     }
   }
   if (PREC == 1) acc = (double)acc32;
-  const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  return block_sum(acc, sh);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(AT) k_ark_finish(int64_t N, Finish F, double h, double rtol, double atol,
+                                                   const double* __restrict__ y,
+                                                   const typename Wt<PREC>::T* __restrict__ ewt,
+                                                   double* __restrict__ ynew,
+                                                   typename Wt<PREC>::T* __restrict__ ewtn,
+                                                   double* __restrict__ part) {
+  __shared__ double sh[AT / 32];
+  const double v = dev_finish<PREC>(N, F, h, rtol, atol, y, ewt, ynew, ewtn, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
 template <int PREC>
@@ -338,6 +372,164 @@ __global__ void __launch_bounds__(AT) k_ark_dq(int64_t N, double hg, const doubl
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// ---- the whole integration to tout in one cooperative launch
+// Control state shared by every block (each thread keeps an identical copy
+// in registers; block 0 writes it back at the end).
+struct ArkState {
+  double t, h, e1, e2;
+  int first, cur, status, pad;
+  long long nst, nfe, nfi, nni, ncfn, netf;
+};
+
+struct CoopArgs {
+  Par P;
+  int64_t N;
+  Tab T;
+  double rtol, atol, tout;
+  long long mxstep;
+  double* y[2];                // y and the next step's y; A.st->cur picks
+  void* ewt[2];
+  double *a, *z;
+  double* g[NS];
+  double* fi[NS];
+  double* part;                // [2][gridDim.x] block partials, used alternately
+  ArkState* st;
+};
+
+// Sum of one value per block over the grid, in the same (fixed) order in
+// every block, so that every block takes the same control decisions.
+__device__ __forceinline__ double grid_sum(cooperative_groups::grid_group& grid, double blockval,
+                                           double* part, int& buf, double* sh) {
+  double* p = part + (size_t)buf * gridDim.x;
+  if (threadIdx.x == 0) p[blockIdx.x] = blockval;
+  grid.sync();
+  double v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += AT) v += p[b];
+  __syncthreads();                          // sh is free again
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) sh[AT / 32] = v;
+  __syncthreads();
+  v = sh[AT / 32];
+  buf ^= 1;
+  return v;
+}
+
+// The step loop of ark_step / ark_integrate (same method, same readings, the
+// same decisions in the same order) run on the device: every block runs the
+// control logic on identical values, and grid-wide barriers replace the host
+// round trips.  Bounded: at most mxstep steps of at most 17 attempts.
+template <int PREC>
+__global__ void __launch_bounds__(AT) k_ark_coop(CoopArgs A) {
+  using W = typename Wt<PREC>::T;
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ double sh[AT / 32 + 1];
+  ArkState S = *A.st;
+  const double N = (double)A.N;
+  int buf = 0, status = 0;
+  const long long nst0 = S.nst;
+  while ((A.tout - S.t) * S.h > 0.0) {
+    if (S.nst - nst0 >= A.mxstep) { status = BDFB_TOO_MUCH_WORK; break; }
+    const double* y = A.y[S.cur];
+    double* ynew = A.y[S.cur ^ 1];
+    const W* ewt = static_cast<const W*>(A.ewt[S.cur]);
+    W* ewtn = static_cast<W*>(A.ewt[S.cur ^ 1]);
+    int ncf = 0, nef = 0;
+    bool have1 = false, reached = false, accepted = false;
+    for (;;) {
+      bool last = false;
+      double hs = S.h;
+      if ((S.t + S.h - A.tout) * S.h >= 0.0) { hs = A.tout - S.t; last = true; }
+      if (S.t + hs == S.t) { status = BDFB_ERR_FAILURE; break; }
+      if (!have1) {
+        dev_rhs(A.P, y, A.g[0], A.fi[0]);
+        S.nfe++; S.nfi++;
+        have1 = true;
+        grid.sync();
+      }
+      bool failed = false;
+      for (int i = 1; i < NS && !failed; ++i) {
+        Stage St;
+        St.nj = i;
+        for (int j = 0; j < NS; ++j) {
+          St.ce[j] = j < i ? A.T.ae[i][j] : 0.0;
+          St.ci[j] = j < i ? A.T.ai[i][j] - A.T.ae[i][j] : 0.0;
+          St.g[j] = A.g[j];
+          St.fi[j] = A.fi[j];
+        }
+        const double hg = hs * A.T.ai[i][i];
+        double crate = 1.0, delp = 0.0;
+        failed = true;
+        for (int m = 1; m <= 3; ++m) {
+          const double bv = m == 1 ? dev_newton<true, PREC>(A.P, St, hs, hg, y, A.a, A.z, ewt, sh)
+                                   : dev_newton<false, PREC>(A.P, St, hs, hg, y, A.a, A.z, ewt, sh);
+          const double ss = grid_sum(grid, bv, A.part, buf, sh);
+          S.nfi++;
+          if (!isfinite(ss)) break;
+          S.nni++;
+          const double del = sqrt(ss / N);
+          if (m > 1) crate = fmax(0.3 * crate, del / delp);
+          if (del * fmin(1.0, crate) <= 0.1) { failed = false; break; }
+          if (m >= 2 && del > 2.3 * delp) break;
+          delp = del;
+        }
+        if (!failed) {
+          dev_rhs(A.P, A.z, A.g[i], A.fi[i]);
+          S.nfe++; S.nfi++;
+          grid.sync();
+        }
+      }
+      if (failed) {
+        S.ncfn++;
+        if (++ncf >= 10) { status = BDFB_CONV_FAILURE; break; }
+        S.h = hs * 0.25;
+        continue;
+      }
+      Finish F;
+      for (int k = 0; k < NS; ++k) {
+        F.b[k] = A.T.b[k];
+        F.d[k] = A.T.b[k] - A.T.bh[k];
+        F.g[k] = A.g[k];
+      }
+      const double bv = dev_finish<PREC>(A.N, F, hs, A.rtol, A.atol, y, ewt, ynew, ewtn, sh);
+      const double dsm = sqrt(grid_sum(grid, bv, A.part, buf, sh) / N);
+      if (!(dsm <= 1.0)) {
+        S.netf++;
+        if (++nef >= 7) { status = BDFB_ERR_FAILURE; break; }
+        double eta = 0.96 * pow(1.5 * dsm, -1.0 / 3.0);
+        if (!(eta >= 0.1)) eta = 0.1;
+        if (eta > 0.9) eta = 0.9;
+        if (nef >= 2 && eta > 0.3) eta = 0.3;
+        S.h = hs * eta;
+        continue;
+      }
+      S.cur ^= 1;
+      S.t = last ? A.tout : S.t + hs;
+      S.nst++;
+      double e0 = 1.5 * dsm;
+      if (e0 < 1e-10) e0 = 1e-10;
+      const double p1 = S.e1 > 0.0 ? S.e1 : e0, p2 = S.e2 > 0.0 ? S.e2 : p1;
+      double eta = 0.96 * pow(e0, -0.58 / 3.0) * pow(p1, 0.21 / 3.0) * pow(p2, -0.1 / 3.0);
+      const double cap = S.first ? 1.0e4 : 20.0;
+      if (eta > cap) eta = cap;
+      if (eta < 0.1) eta = 0.1;
+      if (eta >= 1.0 && eta <= 1.5) eta = 1.0;
+      S.e2 = p1;
+      S.e1 = e0;
+      S.h = hs * eta;
+      S.first = 0;
+      reached = last;
+      accepted = true;
+      break;
+    }
+    if (status || !accepted) break;
+    if (reached) { S.t = A.tout; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.status = status;
+    *A.st = S;
+  }
+}
+
 }  // namespace
 
 struct ArkLine {
@@ -360,6 +552,11 @@ struct ArkLine {
   int64_t nst = 0, nfe = 0, nfi = 0, nni = 0, ncfn = 0, netf = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.0f;
+  int device_loop = -1;        // 1: the step loop in one cooperative launch; 0: host-driven;
+                               // -1: the former up to DEVICE_LOOP_MAX_POINTS points
+  ArkState* dstate = nullptr;
+  double* cpart = nullptr;     // partials of the cooperative kernel
+  int coop_blocks[2] = {0, 0};
 };
 
 #define ACHK(call)     \
@@ -526,6 +723,22 @@ int ark_create(int64_t nx, double A, double B, double eps, double c, double len,
   if (ok && cudaMallocHost(&g->hpart, g->nblk * sizeof(double)) != cudaSuccess) { g->hpart = nullptr; ok = false; }
   if (ok && cudaMallocHost(&g->hbad, sizeof(int)) != cudaSuccess) { g->hbad = nullptr; ok = false; }
   if (ok && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess)) ok = false;
+  if (ok && cudaMalloc(&g->dstate, sizeof(ArkState)) != cudaSuccess) { g->dstate = nullptr; ok = false; }
+  // co-resident blocks of the cooperative kernels (all of them must fit at once)
+  for (int pr = 0; ok && pr < 2; ++pr) {
+    int per_sm = 0;
+    const cudaError_t e = pr == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ark_coop<0>, AT, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ark_coop<1>, AT, 0);
+    if (e != cudaSuccess) ok = false;
+    // about 4 points per thread, at least one block per SM (measured on the
+    // demonstration problem at 1e5 points: 49 blocks 1.15 s, 148 blocks
+    // 0.58 s, 296 blocks 0.76 s), at most the co-resident blocks
+    const int64_t want = std::max<int64_t>((nx + 4 * AT - 1) / (4 * AT), sm_count());
+    g->coop_blocks[pr] = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
+  }
+  int coop = 0;
+  if (ok && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, 0) == cudaSuccess && !coop) g->device_loop = 0;
+  if (ok) alloc((void**)&g->cpart, 2 * (size_t)std::max(g->coop_blocks[0], g->coop_blocks[1]) * sizeof(double));
   if (!ok) {
     ark_destroy(g);
     return BDFB_MEM_FAIL;
@@ -544,6 +757,8 @@ void ark_destroy(ArkLine* g) {
   if (g->hbad) cudaFreeHost(g->hbad);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
+  cudaFree(g->dstate);
+  cudaFree(g->cpart);
   delete g;
 }
 
@@ -554,6 +769,56 @@ int ark_set_mxstep(ArkLine* g, int64_t v) {
   if (v < 1) return BDFB_ILL_INPUT;
   g->mxstep = v;
   return 0;
+}
+
+int ark_set_device_loop(ArkLine* g, int on) {
+  if (on < -1 || on > 1) return BDFB_ILL_INPUT;
+  int coop = 0;
+  if (on && (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, 0) != cudaSuccess || !coop))
+    return BDFB_ILL_INPUT;
+  g->device_loop = on;
+  return 0;
+}
+
+// the step loop to tout in one cooperative launch (state in and out through
+// device memory); *reached-equivalent: the kernel stops at tout
+static int ark_run_device(ArkLine* g, double tout) {
+  ArkState st = {};
+  st.t = g->t; st.h = g->h; st.e1 = g->e1; st.e2 = g->e2;
+  st.first = g->first ? 1 : 0;
+  st.cur = 0;
+  st.nst = g->nst; st.nfe = g->nfe; st.nfi = g->nfi; st.nni = g->nni; st.ncfn = g->ncfn; st.netf = g->netf;
+  BDFB_CUDA(cudaMemcpyAsync(g->dstate, &st, sizeof st, cudaMemcpyHostToDevice, g->s));
+  CoopArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.P = g->P;
+  A.N = g->N;
+  A.T = g->T;
+  A.rtol = g->rtol;
+  A.atol = g->atol;
+  A.tout = tout;
+  A.mxstep = g->mxstep;
+  A.y[0] = g->y; A.y[1] = g->ynew;
+  A.ewt[0] = g->ewt; A.ewt[1] = g->ewtn;
+  A.a = g->a;
+  A.z = g->z;
+  for (int k = 0; k < NS; ++k) { A.g[k] = g->g[k]; A.fi[k] = g->fi[k]; }
+  A.part = g->cpart;
+  A.st = g->dstate;
+  void* args[] = {&A};
+  const int nb = g->coop_blocks[g->prec];
+  BDFB_CUDA(cudaLaunchCooperativeKernel(g->prec == 0 ? (const void*)k_ark_coop<0> : (const void*)k_ark_coop<1>,
+                                        dim3(nb), dim3(AT), args, 0, g->s));
+  BDFB_CUDA(cudaMemcpyAsync(&st, g->dstate, sizeof st, cudaMemcpyDeviceToHost, g->s));
+  BDFB_CUDA(cudaStreamSynchronize(g->s));
+  if (st.cur) {
+    std::swap(g->y, g->ynew);
+    std::swap(g->ewt, g->ewtn);
+  }
+  g->t = st.t; g->h = st.h; g->e1 = st.e1; g->e2 = st.e2;
+  g->first = st.first != 0;
+  g->nst = st.nst; g->nfe = st.nfe; g->nfi = st.nfi; g->nni = st.nni; g->ncfn = st.ncfn; g->netf = st.netf;
+  return st.status;
 }
 
 int ark_set_precision(ArkLine* g, int prec) {
@@ -660,8 +925,10 @@ int ark_integrate(ArkLine* g, double tout, double* y, int mem) {
   if (tout != g->t) {
     ACHK(ark_ewt(g));
     if (!g->started) ret = ark_h0(g, tout);
+    const bool dev = g->device_loop == 1 || (g->device_loop < 0 && g->P.np <= DEVICE_LOOP_MAX_POINTS);
+    if (!ret && dev) ret = ark_run_device(g, tout);
     const int64_t nst0 = g->nst;
-    while (!ret && (tout - g->t) * g->h > 0.0) {
+    while (!ret && !dev && (tout - g->t) * g->h > 0.0) {
       if (g->nst - nst0 >= g->mxstep) { ret = BDFB_TOO_MUCH_WORK; break; }
       bool reached = false;
       ret = ark_step(g, tout, &reached);

@@ -19,6 +19,10 @@ int ark_set_mxstep(ArkLine* g, int64_t v);
 // 0: FP64 throughout; 1: FP32 3x3 Newton blocks and norm weights, FP64 state,
 // stage sums and Newton residual
 int ark_set_precision(ArkLine* g, int prec);
+// 1 (default where cooperative launches exist): the step loop to tout runs
+// in one cooperative launch with grid-wide barriers instead of host round
+// trips; 0: host-driven, one launch and one readback per reduction
+int ark_set_device_loop(ArkLine* g, int on);
 int ark_init(ArkLine* g, double t0, const double* y0, int mem);
 // advance to tout (last step clamped onto tout); y (3 nx, species-major) out
 int ark_integrate(ArkLine* g, double tout, double* y, int mem);

@@ -1176,6 +1176,7 @@ struct bdfb_ctx {
   SharedInt* shared = nullptr;  // BDFB_MASSACTION_SHARED: grouped cells on one sparse network
   int imex = 0;
   int line_prec = 0;          // "precision" of the IMEX path
+  int line_dloop = -1;        // "device_loop" of the IMEX path (-1: by size)
   double line_par[6] = {};    // A, B, eps, c, length, nx of the 1-D line
   // option "grouped": the cells as one system with task-local Newton solves
   int grouped = 0;
@@ -1540,9 +1541,19 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
       ark_set_tolerances(ctx->ark, ctx->rtol, ctx->atol);
       r = ark_set_mxstep(ctx->ark, ctx->mxstep);
       if (!r) r = ark_set_precision(ctx->ark, ctx->line_prec);
+      if (!r && ctx->line_dloop != -1) r = ark_set_device_loop(ctx->ark, ctx->line_dloop);
       if (r) return r;
     }
     ctx->imex = (int)v;
+    return BDFB_SUCCESS;
+  }
+  if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "device_loop")) {
+    if (v < -1 || v > 1) return BDFB_ILL_INPUT;
+    if (ctx->ark) {
+      const int r = ark_set_device_loop(ctx->ark, (int)v);
+      if (r) return r;
+    }
+    ctx->line_dloop = (int)v;
     return BDFB_SUCCESS;
   }
   if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "precision")) {

@@ -124,3 +124,21 @@ def test_imex_needs_init_after_option():
             I.integrate(0.1, y)
         I.init(0.0, torch.from_numpy(p.y0).cuda())
         assert I.integrate(0.1, y) == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_loop_matches_host_loop(precision):
+    """The step loop in one cooperative launch (default) takes the host-driven
+    loop's decisions: the same method and readings, sums in another order."""
+    p = gen.brusselator1d(20011, length=100.0)
+    out = {}
+    for loop in (0, 1):
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, imex=1, precision=precision, device_loop=loop) as I:
+            I.init(0.0, torch.from_numpy(p.y0).cuda())
+            y = torch.empty(p.y0.size, dtype=torch.float64, device="cuda")
+            assert I.integrate(0.25, y) == 0
+            assert I.integrate(0.5, y) == 0          # a second call continues the state
+            out[loop] = (y.cpu().numpy(), I.cell_stats()[0])
+    (yh, sh), (yd, sd) = out[0], out[1]
+    assert abs(int(sd[0]) - int(sh[0])) <= 2 and abs(int(sd[5]) - int(sh[5])) <= 2, (sd, sh)
+    assert werr(yd, yh).max() <= 0.5
