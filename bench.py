@@ -429,35 +429,45 @@ def slowest_rank_time(torch, dist, t, device):
     return float(tt.item())
 
 
-def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps=1):
+def line_workload(torch, bdfb, gen, nx=10_000_000, length=1000.0, tout=3.0, reps=1, oracle_points=50_000):
     """The paper's demonstration problem (Sec. 7) as one coupled system:
     Brusselator reactions (A = 1, B = 3.5, eps = 5e-6) advected with c = 0.01
     on a periodic line of nx points over [0, length) by first-order upwind
     differences, the paper's Gaussian-bump initial state, t in [0, tout];
     BDF with Newton + GMRES(5), 3x3 reaction blocks as preconditioner
-    (advection implicit in the Newton operator)."""
+    (advection implicit in the Newton operator); FP64, then with the
+    preconditioner and the GMRES operator in FP32 (option precision 1)."""
     p = gen.brusselator1d(nx, length=length)
     y0 = torch.from_numpy(p.y0).cuda()
     y = torch.empty_like(y0)
-    ts = []
-    with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5) as li:
-        for _ in range(reps + 1):
-            li.init(0.0, y0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = li.integrate(tout, y)
-            torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t0)
-            if r != 0:
-                raise RuntimeError(f"line integrate returned {r}")
-        gs = li.cell_stats()[0]
-    t = min(ts[1:])
-    orate = line_oracle_rate(gen, "bdf", nx, length, tout, 50_000)
-    return {"oracle": orate,
-            "workload": f"Brusselator 1-D advection-reaction (the paper's demo) {nx} points x 3, length {length}, "
-                        f"c 0.01, A 1, B 3.5, eps 5e-6, t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 blocks",
-            "points_per_s": nx / t, "seconds": t, "steps": int(gs[0]), "newton_iters": int(gs[3]),
-            "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
+    out, yref = {}, None
+    for prec in (0, 1):
+        ts = []
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5, precision=prec) as li:
+            for _ in range(reps + 1):
+                li.init(0.0, y0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = li.integrate(tout, y)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                if r != 0:
+                    raise RuntimeError(f"line integrate returned {r}")
+            gs = li.cell_stats()[0]
+        t = min(ts[1:])
+        res = {"points_per_s": nx / t, "seconds": t, "steps": int(gs[0]), "newton_iters": int(gs[3]),
+               "gmres_iters": int(gs[6]), "jacobian_setups": int(gs[2])}
+        if prec == 0:
+            yref = y.clone()
+            out.update(res)
+        else:
+            d = ((y - yref).abs() / (RTOL * yref.abs() + ATOL)).max().item()
+            out["fp32_preconditioner_and_operator"] = {**res, "max_weighted_diff_vs_fp64": d}
+    if oracle_points:
+        out["oracle"] = line_oracle_rate(gen, "bdf", nx, length, tout, oracle_points)
+    out["workload"] = (f"Brusselator 1-D advection-reaction (the paper's demo) {nx} points x 3, length {length}, "
+                       f"c 0.01, A 1, B 3.5, eps 5e-6, t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 blocks")
+    return out
 
 
 def line_oracle_rate(gen, method, nx, length, tout, nsample):
@@ -803,7 +813,8 @@ def run_part(args):
     elif args.part == "grouped":
         out = grouped_workload(torch, bdfb, gen, ncell=args.ncell, reps=max(1, args.steps))
     elif args.part == "line":
-        out = line_workload(torch, bdfb, gen, nx=args.line_nx, tout=args.grid_tout, reps=max(1, args.steps))
+        out = line_workload(torch, bdfb, gen, nx=args.line_nx, tout=args.grid_tout, reps=max(1, args.steps),
+                            oracle_points=0)
     else:
         out = learned_workload(torch, bdfb, gen, ncell=args.ncell, train_steps=20000)
     print(json.dumps({"part": args.part, **out}))
