@@ -70,7 +70,7 @@ __device__ __forceinline__ double uop(double x, double a, double b) {
   if (OP == UOP_ABS) return fabs(x);
   if (OP == UOP_INV) return 1.0 / x;
   if (OP == UOP_ADDCONST) return x + a;
-  return 1.0 / (a * fabs(x) + b);
+  return recip_nr(a * fabs(x) + b);     // error weights without an FP64 division
 }
 
 template <int OP>

@@ -113,7 +113,8 @@ def test_large_vectors_sampled():
 def test_support_ops(n, off):
     """Scale, Const, Abs, Inv, AddConst: one correctly rounded operation per
     element, so bitwise equal to the oracle; error weights within 2 ulp (the
-    kernel may fuse rtol |y| + atol into one multiply-add)."""
+    kernel may fuse rtol |y| + atol into one multiply-add, and takes the
+    reciprocal by Newton-Raphson from an FP32 seed, within half an ulp)."""
     (x,) = gen.uniform_vectors(n, 1, seed=n + 7)
     x = x + np.sign(x) * 1e-3                      # keep 1/x finite
     dx = to_dev(x, off)
