@@ -246,6 +246,16 @@ __global__ void k_ewt(int64_t N, double rtol, double atol, const double* __restr
   }
 }
 
+// acor += delta; y = zp0 + acor (one pass for the Newton update)
+__global__ void k_newton_update(int64_t N, const double* __restrict__ delta, double* __restrict__ acor,
+                                const double* __restrict__ zp0, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = acor[i] + delta[i];
+    acor[i] = a;
+    y[i] = zp0[i] + a;
+  }
+}
+
 __global__ void k_mul(int64_t N, const double* __restrict__ x, const double* __restrict__ d, double* __restrict__ o) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     o[i] = x[i] * d[i];
@@ -438,6 +448,10 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   if (g->prec) k_prec_scale<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, (const float*)g->Pinv, g->ewt, g->V[0]);
   else k_prec_scale<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, g->Pinv, g->ewt, g->V[0]);
   BDFB_CUDA(cudaGetLastError());
+  // The basis is stored unnormalised: basis vector i is sig[i] V[i], the
+  // scales kept on the host and folded into the coefficients of the next
+  // linear combination, so no pass over the vectors only rescales one.
+  double sig[MAXL_MAX + 1] = {0};
   double beta2;
   const double* v0 = g->V[0];
   GCHK(g_dots(g, g->V[0], &v0, 1, &beta2));
@@ -446,7 +460,7 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
     BDFB_CUDA(cudaMemsetAsync(g->b, 0, N * sizeof(double), g->s));
     return 0;
   }
-  GCHK(bdfb_nv_linear_sum(N, 1.0 / beta, g->V[0], 0.0, g->V[0], g->V[0], g->s));
+  sig[0] = 1.0 / beta;
   gv[0] = beta;
   int k = 0;
   bool conv = false;
@@ -465,23 +479,27 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
       k_bruss_apply<double><<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j],
                                                                     g->ewt, g->sc, ycur, g->Pinv, g->w);
     BDFB_CUDA(cudaGetLastError());
+    // w = sig[j] A V[j]: h_ij = (w, basis_i) = sig[j] sig[i] (A V[j], V[i]);
+    // classical Gram-Schmidt into V[j + 1]: sig[j] (A V[j] - sum c_i V[i])
+    // with c_i = h_ij sig[i] / sig[j]
     double hcol[MAXL_MAX + 1];
-    GCHK(g_dots(g, g->w, g->V, j + 1, hcol));        // classical Gram-Schmidt
+    GCHK(g_dots(g, g->w, g->V, j + 1, hcol));
+    for (int i = 0; i <= j; ++i) hcol[i] *= sig[j] * sig[i];
     {
       const double* xs[MAXL_MAX + 2];
       double c[MAXL_MAX + 2];
       xs[0] = g->w;
       c[0] = 1.0;
-      for (int i = 0; i <= j; ++i) { xs[i + 1] = g->V[i]; c[i + 1] = -hcol[i]; }
-      GCHK(bdfb_nv_linear_combination(N, j + 2, c, xs, g->w, g->s));
+      for (int i = 0; i <= j; ++i) { xs[i + 1] = g->V[i]; c[i + 1] = -hcol[i] * sig[i] / sig[j]; }
+      GCHK(bdfb_nv_linear_combination(N, j + 2, c, xs, g->V[j + 1], g->s));
     }
     for (int i = 0; i <= j; ++i) H[i * maxl + j] = hcol[i];
     double hn2;
-    const double* wp = g->w;
-    GCHK(g_dots(g, g->w, &wp, 1, &hn2));
-    const double hn = std::sqrt(hn2);
+    const double* wp = g->V[j + 1];
+    GCHK(g_dots(g, g->V[j + 1], &wp, 1, &hn2));
+    const double hn = sig[j] * std::sqrt(hn2);
     H[(j + 1) * maxl + j] = hn;
-    if (hn > 0.0) GCHK(bdfb_nv_linear_sum(N, 1.0 / hn, g->w, 0.0, g->w, g->V[j + 1], g->s));
+    sig[j + 1] = hn > 0.0 ? sig[j] / hn : 0.0;
     for (int i = 0; i < j; ++i) {
       const double h0 = H[i * maxl + j], h1 = H[(i + 1) * maxl + j];
       H[i * maxl + j] = cs[i] * h0 + sn[i] * h1;
@@ -507,8 +525,9 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   }
   {
     const double* xs[MAXL_MAX];
-    for (int i = 0; i < k; ++i) xs[i] = g->V[i];
-    GCHK(bdfb_nv_linear_combination(N, k, yv, xs, g->tmp, g->s));
+    double c[MAXL_MAX];
+    for (int i = 0; i < k; ++i) { xs[i] = g->V[i]; c[i] = yv[i] * sig[i]; }
+    GCHK(bdfb_nv_linear_combination(N, k, c, xs, g->tmp, g->s));
   }
   k_mul<<<gblocks(N), GT, 0, g->s>>>(N, g->tmp, g->sc, g->b);     // x = S^{-1} (V y)
   BDFB_CUDA(cudaGetLastError());
@@ -594,8 +613,8 @@ static int g_newton(GridBDF* g, double Eq, double* acnrm) {
       GCHK(g_gmres(g, g->y, 0.05 * 0.1 / Eq));
       double del;
       GCHK(g_wrms(g, g->b, &del));
-      GCHK(bdfb_nv_linear_sum(N, 1.0, g->acor, 1.0, g->b, g->acor, g->s));
-      GCHK(bdfb_nv_linear_sum(N, 1.0, g->zp0, 1.0, g->acor, g->y, g->s));
+      k_newton_update<<<gblocks(N), GT, 0, g->s>>>(N, g->b, g->acor, g->zp0, g->y);
+      BDFB_CUDA(cudaGetLastError());
       g->nni++;
       if (!std::isfinite(del)) break;
       if (it > 1) g->crate = std::max(0.3 * g->crate, del / delp);
