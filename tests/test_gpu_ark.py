@@ -142,3 +142,18 @@ def test_device_loop_matches_host_loop(precision):
     (yh, sh), (yd, sd) = out[0], out[1]
     assert abs(int(sd[0]) - int(sh[0])) <= 2 and abs(int(sd[5]) - int(sh[5])) <= 2, (sd, sh)
     assert werr(yd, yh).max() <= 0.5
+
+
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_negative_advection_speed(device_loop):
+    """c < 0: the upwind difference looks forward; both step loops"""
+    p = gen.brusselator1d(1000, length=10.0, c=-0.02)
+    with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, imex=1, device_loop=device_loop) as I:
+        I.init(0.0, torch.from_numpy(p.y0).cuda())
+        y = torch.empty(p.y0.size, dtype=torch.float64, device="cuda")
+        assert I.integrate(1.0, y) == 0
+        cs = I.cell_stats()[0]
+    ro, yo, so = oracle.bruss_ark_integrate(p, 0.0, 1.0, RTOL, ATOL)
+    assert ro == 0
+    assert abs(int(cs[0]) - int(so[0])) <= max(2, 0.03 * so[0])
+    assert werr(y.cpu().numpy(), yo).max() <= 0.5

@@ -140,3 +140,19 @@ def test_line_fourier_mode_of_pure_advection(c):
     assert ret == 0
     exact = np.real(np.exp(lam1 * tout) * np.exp(1j * th * j))
     assert np.max(np.abs(y[nx:2 * nx] - exact)) <= 20 * 1e-8
+
+
+@pytest.mark.parametrize("maxl", [1, 2, 16])
+def test_grid_krylov_dimensions(maxl):
+    """GMRES(1), GMRES(2) and GMRES(16) against the oracle's GMRES of the same
+    dimension (inexact Newton with a short basis, full Krylov with a long one)"""
+    p = gen.brusselator3d(6, seed=2)
+    ret, y, gs, _ = run_grid(p, 0.05, 1e-6, 1e-10, maxl=maxl)
+    assert ret == 0
+    ro, yo, so = oracle.bruss_integrate(p, 0.0, 0.05, 1e-6, 1e-10, maxl=maxl)
+    rt, yt, _ = oracle.bruss_integrate(p, 0.0, 0.05, 1e-10, 1e-14, maxl=5)
+    assert ro == 0 and rt == 0
+    w = 1e-6 * np.abs(yt) + 1e-10
+    eg, eo = np.max(np.abs(y - yt) / w), np.max(np.abs(yo - yt) / w)
+    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
+    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)

@@ -120,12 +120,16 @@ def run_shared(p, tout, rtol, atol):
         return bdfb.cell_major(p, y.cpu().numpy()), I.stats(), I.cell_stats()[0]
 
 
-@pytest.mark.parametrize("which", ["banded128", "shared10"])
+@pytest.mark.parametrize("which", ["banded128", "shared10", "shared40"])
 def test_grouped_shared_network_against_oracle(which):
+    """banded128 takes the register-window solves; shared10 and shared40 (a
+    random network: general pattern with fill) the general schedule"""
     if which == "banded128":
         p = gen.mass_action_banded(96, n=128)
-    else:
+    elif which == "shared10":
         p = gen.mass_action_shared(1000, n=10)
+    else:
+        p = gen.mass_action_shared(200, n=40)
     tout, rtol, atol = 1e-3, 1e-6, 1e-10
     y, stats, row = run_shared(p, tout, rtol, atol)
     yt, stt, _ = oracle.integrate_cells(p, 0.0, tout, 1e-10, 1e-14, threads=THREADS)
