@@ -30,6 +30,7 @@ NCELL = 100_000
 TOUT = 1.0e-3
 RTOL, ATOL = 1.0e-6, 1.0e-10
 SIZES = (3, 10, 32, 54)
+K_CELLS_STEP_DRAM_BYTES = 453_013_504     # 395.9 MB read + 57.1 MB written (see `traffic` below)
 METRIC = "cells integrated to t_end per second at stated error; NVECTOR op HBM GB/s"
 UNIT = "cells/s"
 WORKLOAD = ("mass-action 100k: 100000 independent cells, n ~ U{3,10,32,54}, 2n reactions "
@@ -759,7 +760,11 @@ def run_ours(args):
                 mst = vi.stats()
                 variants["mixed_refine_sweeps_per_solve"] = mst["nrefine"] / max(1, mst["nniters"])
                 variants["mixed_fp64_fallbacks"] = mst["nrefine_fallback"]
-    traffic = None
+    # DRAM bytes read + written by one timed step's four k_cells launches, from one
+    # ncu capture of `bench.py --quick --steps 2 --warmup 1` (profiles/
+    # launches_massaction_100k.md); valid while the kernels are those of that capture
+    traffic = K_CELLS_STEP_DRAM_BYTES if (NCELL == 100_000 and SIZES == (3, 10, 32, 54) and not args.mapping
+                                          and args.precision == 0) else None
     acc = accuracy(prob, yh)
     cpu_v, cpu_threads, cpu_ns, cpu_dt, cpu_fail = cpu_oracle_rate(prob)
     st_sum = integ.stats()
