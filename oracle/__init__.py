@@ -38,7 +38,8 @@ QMAX = 5
 class Options(C.Structure):
     _fields_ = [("rtol", _d), ("atol", _d), ("mxstep", _i64), ("qmax", C.c_int),
                 ("fixed_h", _d), ("fixed_q", C.c_int), ("h0", _d),
-                ("trace_y", _pd), ("trace_acor", _pd), ("trace_cap", _i64), ("z_init", _pd)]
+                ("trace_y", _pd), ("trace_acor", _pd), ("trace_cap", _i64), ("z_init", _pd),
+                ("interp", C.c_int)]
 
 
 class Cells(C.Structure):
@@ -77,6 +78,8 @@ def lib():
                                           C.POINTER(Options), _pd, _pi64, _pi64]
         L.or_cells_integrate.argtypes = [C.POINTER(Cells), _i64, _i64, _d, _pd, _d, _d, _d,
                                          _i64, _pd, _pi32, _pi64]
+        L.or_cells_integrate_mode.argtypes = [C.POINTER(Cells), _i64, _i64, _d, _pd, _d, _d, _d,
+                                              _i64, C.c_int, _pd, _pi32, _pi64]
         L.or_cells_integrate_grouped.argtypes = [C.POINTER(Cells), _d, _pd, _d, _d, _d, _i64,
                                                  _pd, _pi64]
         L.or_ark_table.argtypes = [_pd, _pd, _pd, _pd, _pd]
@@ -208,7 +211,7 @@ def bdf_constants(q):
 
 
 def linear_integrate(A, Cs, t0, y0, tout, rtol=1e-6, atol=1e-10, fixed_h=0.0, fixed_q=0,
-                     h0=0.0, mxstep=100000, trace=0, z_init=None):
+                     h0=0.0, mxstep=100000, trace=0, z_init=None, interp=False):
     """y' = A y + sum_k Cs[k] t^k.  Returns (ret, y, stats, trace_y, trace_acor)."""
     A = _f64(np.atleast_2d(A))
     N = A.shape[0]
@@ -221,7 +224,7 @@ def linear_integrate(A, Cs, t0, y0, tout, rtol=1e-6, atol=1e-10, fixed_h=0.0, fi
     zi = None if z_init is None else _f64(z_init)
     opt = Options(rtol, atol, mxstep, QMAX, fixed_h, fixed_q, h0,
                   _p(ty) if trace else None, _p(ta) if trace else None, trace,
-                  None if zi is None else _p(zi))
+                  None if zi is None else _p(zi), int(interp))
     nt = _i64(0)
     ret = lib().or_linear_integrate(N, _p(A), Cs.shape[0], _p(Cs), t0, _p(y0), tout,
                                     C.byref(opt), _p(y), _p(st, _pi64), C.byref(nt))
@@ -286,7 +289,7 @@ def _cells_struct(prob):
 
 
 def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threads=1,
-                    y0=None):
+                    y0=None, interp=False):
     """Integrate the listed cells (default all) independently; returns
     (y, status, stats[ncell, 8]) over the whole problem (cells not listed keep y0
     and status 1).  ``threads`` > 1 spreads cell ranges over host threads."""
@@ -305,8 +308,8 @@ def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threa
         ranges = [(int(c), int(c) + 1) for c in cells]
 
     def run(r):
-        return L.or_cells_integrate(C.byref(s), r[0], r[1], t0, _p(y0), tout, rtol, atol, mxstep,
-                                    _p(y), _p(status, _pi32), _p(stats, _pi64))
+        return L.or_cells_integrate_mode(C.byref(s), r[0], r[1], t0, _p(y0), tout, rtol, atol, mxstep,
+                                         int(interp), _p(y), _p(status, _pi32), _p(stats, _pi64))
 
     if threads <= 1:
         for r in ranges:

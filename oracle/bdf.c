@@ -399,7 +399,7 @@ static int step(or_bdf* m, double tout, int* reached) {
   int fixed = m->opt.fixed_h > 0.0;
   for (;;) {
     int last = 0;
-    if (!fixed && (m->t + m->h - tout) * m->h >= 0.0) {
+    if (!fixed && !m->opt.interp && (m->t + m->h - tout) * m->h >= 0.0) {
       last = 1;
       if (m->t + m->h != tout) { rescale(m, (tout - m->t) / m->h); m->qwait = m->q + 1; }
     }
@@ -516,7 +516,17 @@ int or_bdf_solve(or_bdf* m, double tout, double* yout) {
     }
   }
 done:
-  memcpy(yout, Z(m, 0), sizeof(double) * N);
+  if (m->opt.interp && ret == 0 && m->started && m->t != tout) {
+    /* the history polynomial at tout (Horner in s = (tout - t_n) / h) */
+    double s = (tout - m->t) / m->h;
+    for (int64_t i = 0; i < N; ++i) {
+      double v = Z(m, m->q)[i];
+      for (int j = m->q - 1; j >= 0; --j) v = v * s + Z(m, j)[i];
+      yout[i] = v;
+    }
+  } else {
+    memcpy(yout, Z(m, 0), sizeof(double) * N);
+  }
   m->st.tcur = m->t;
   return ret;
 }

@@ -91,6 +91,10 @@ typedef struct {
   int64_t trace_cap;
   /* optional exact starting history z_0..z_{fixed_q} (fixed-step runs), N each */
   const double* z_init;
+  /* 1: step past tout and return the history polynomial's value at tout,
+   * y(tout) = sum_j z_j ((tout - t_n) / h)^j (CVODE's normal mode); 0: the
+   * last step lands on tout */
+  int interp;
 } or_options;
 
 typedef struct {
@@ -137,6 +141,11 @@ typedef struct {
 int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
                        const double* y0, double tout, double rtol, double atol,
                        int64_t mxstep, double* yout, int32_t* status, int64_t* stats);
+/* the same with the output mode of or_options.interp */
+int or_cells_integrate_mode(const or_cells* cells, int64_t c0, int64_t c1, double t0,
+                            const double* y0, double tout, double rtol, double atol,
+                            int64_t mxstep, int interp, double* yout, int32_t* status,
+                            int64_t* stats);
 
 /* All cells [0, ncell) as ONE system (the grouping of Sec. 2): one step size,
  * order and error test over every species, block-diagonal Newton matrix with

@@ -128,6 +128,13 @@ static void cell_user_of(const or_cells* cells, int64_t c, cell_user* u) {
 int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
                        const double* y0, double tout, double rtol, double atol,
                        int64_t mxstep, double* yout, int32_t* status, int64_t* stats) {
+  return or_cells_integrate_mode(cells, c0, c1, t0, y0, tout, rtol, atol, mxstep, 0, yout, status, stats);
+}
+
+int or_cells_integrate_mode(const or_cells* cells, int64_t c0, int64_t c1, double t0,
+                            const double* y0, double tout, double rtol, double atol,
+                            int64_t mxstep, int interp, double* yout, int32_t* status,
+                            int64_t* stats) {
   int worst = 0;
   for (int64_t c = c0; c < c1; ++c) {
     cell_user u;
@@ -142,6 +149,7 @@ int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
     opt.rtol = rtol;
     opt.atol = atol;
     opt.mxstep = mxstep;
+    opt.interp = interp;
     int ret;
     or_bdf* m = (u.J && u.M && u.piv) ? or_bdf_create(&sys, &opt, t0, y0 + yo) : NULL;
     if (!m) {

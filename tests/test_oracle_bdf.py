@@ -187,3 +187,35 @@ def test_observed_order(q):
     e = np.array([err(h) for h in hs])
     slope = np.polyfit(np.log(hs), np.log(e), 1)[0]
     assert abs(slope - q) < 0.15, (q, slope, e)
+
+
+# ---------------------------------------------------------------- output by interpolation
+def test_interpolation_exact_for_polynomials():
+    """Fixed steps of BDF3 from the exact history on y' = 3 t^2 (y = 1 + t^3):
+    the method and the degree-3 history polynomial are exact, so the value at
+    a tout off the step grid (s = (tout - t_n)/h in (0, 1/2), a short
+    extrapolation, and after a second call, behind the last step) is the cubic
+    to rounding.  A wrong sign of s or a wrong power fails it."""
+    h, q = 0.1, 3
+    t0 = 0.0
+    # Nordsieck history of y = 1 + t^3 at t0: z_j = h^j y^(j)(t0) / j!
+    z = np.array([[1.0], [0.0], [0.0], [h ** 3]])
+    Cs = np.array([[0.0], [0.0], [3.0]])
+    for tout in (0.73, 1.04):
+        ret, y, st, _, _ = oracle.linear_integrate([[0.0]], Cs, t0, [1.0], tout, fixed_h=h, fixed_q=q,
+                                                   z_init=z, interp=True, rtol=1e-12, atol=1e-14)
+        assert ret == 0
+        assert abs(y[0] - (1.0 + tout ** 3)) <= 1e-12, (tout, y[0])
+
+
+@pytest.mark.parametrize("lam,tout", [(-1.0, 5.0), (-1.0e3, 5.0e-3)])
+def test_interpolated_output_closed_form(lam, tout):
+    """Stepping past tout and interpolating meets the same bar as landing on
+    tout, with no more steps."""
+    for rtol in (1e-6, 1e-9):
+        ri, yi, si, _, _ = oracle.linear_integrate([[lam]], None, 0.0, [1.0], tout, rtol=rtol, atol=1e-14,
+                                                   interp=True)
+        rc, yc, sc, _, _ = oracle.linear_integrate([[lam]], None, 0.0, [1.0], tout, rtol=rtol, atol=1e-14)
+        assert ri == 0 and rc == 0
+        assert abs(yi[0] - np.exp(lam * tout)) <= 20 * rtol + 1e-13
+        assert si[0] <= sc[0]
