@@ -313,6 +313,16 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              Statistics: every cell counts every grouped step, RHS
  *              evaluation, setup and failure; nniters sums the cells'
  *              task-local iterations.
+ *  "interp"    0 = the last step is shortened to end exactly at tout and y
+ *              is the state there (default); 1 = steps are never shortened
+ *              for tout: the integrator steps until t_n >= tout and writes
+ *              the history polynomial sum_{j<=q} z_j s^j, s = (tout - t_n)/h
+ *              (the normal output mode of a Nordsieck BDF integrator,
+ *              Sec. 3).  The next call continues from t_n; a tout inside
+ *              the last step (tout <= t_n) is answered by interpolation
+ *              alone, with no step.  Every BDF path takes it (cells,
+ *              "grouped", BDFB_MASSACTION_SHARED, both grids); the line's
+ *              "imex" path always ends its steps at tout.
  * "mapping" 32 runs every cell on the smallest one-warp-per-cell kernel all
  * cells fit (NMAX 16 — the predictor's kernel, FP64 only — 32 or 56). */
 int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t value);

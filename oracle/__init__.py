@@ -81,14 +81,14 @@ def lib():
         L.or_cells_integrate_mode.argtypes = [C.POINTER(Cells), _i64, _i64, _d, _pd, _d, _d, _d,
                                               _i64, C.c_int, _pd, _pi32, _pi64]
         L.or_cells_integrate_grouped.argtypes = [C.POINTER(Cells), _d, _pd, _d, _d, _d, _i64,
-                                                 _pd, _pi64]
+                                                 C.c_int, _pd, _pi64]
         L.or_ark_table.argtypes = [_pd, _pd, _pd, _pd, _pd]
         L.or_ark_integrate.argtypes = [C.POINTER(ImexSystem), C.POINTER(ArkOptions), _d, _pd, _d,
                                        _pd, C.POINTER(ArkStats)]
         L.or_bruss_ark_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, _i64, _pd, _pi64]
         L.or_bruss_gmres.argtypes = [C.POINTER(Bruss), _pd, _d, _pd, _d, C.c_int, _pd, _pd]
         L.or_bruss_integrate.argtypes = [C.POINTER(Bruss), _d, _pd, _d, _d, _d, C.c_int, _i64,
-                                         _pd, _pi64]
+                                         C.c_int, _pd, _pi64]
         _lib = L
     return _lib
 
@@ -321,7 +321,7 @@ def integrate_cells(prob, t0, tout, rtol, atol, mxstep=100000, cells=None, threa
     return y, status, stats
 
 
-def integrate_cells_grouped(prob, t0, tout, rtol, atol, mxstep=100000, y0=None):
+def integrate_cells_grouped(prob, t0, tout, rtol, atol, mxstep=100000, y0=None, interp=False):
     """All cells as one system with task-local Newton solves (one step size and
     order, error test over every species); returns (y, ret, stats[8])."""
     s, keep = _cells_struct(prob)
@@ -329,7 +329,7 @@ def integrate_cells_grouped(prob, t0, tout, rtol, atol, mxstep=100000, y0=None):
     y = y0.copy()
     stats = np.zeros(8, np.int64)
     ret = lib().or_cells_integrate_grouped(C.byref(s), t0, _p(y0), tout, rtol, atol, mxstep,
-                                           _p(y), _p(stats, _pi64))
+                                           int(interp), _p(y), _p(stats, _pi64))
     del keep
     return y, ret, stats
 
@@ -367,13 +367,13 @@ def bruss_gmres(p, y, gamma, ewt, tol, maxl, b):
     return x, it, rn.value
 
 
-def bruss_integrate(p, t0, tout, rtol, atol, maxl=5, mxstep=100000, y0=None):
+def bruss_integrate(p, t0, tout, rtol, atol, maxl=5, mxstep=100000, y0=None, interp=False):
     s = bruss_struct(p)
     y0 = _f64(p.y0 if y0 is None else y0)
     y = np.empty_like(y0)
     st = np.zeros(8, np.int64)
     ret = lib().or_bruss_integrate(C.byref(s), t0, _p(y0), tout, rtol, atol, maxl, mxstep,
-                                   _p(y), _p(st, _pi64))
+                                   int(interp), _p(y), _p(st, _pi64))
     return ret, y, st
 
 

@@ -150,10 +150,11 @@ int or_cells_integrate_mode(const or_cells* cells, int64_t c0, int64_t c1, doubl
 /* All cells [0, ncell) as ONE system (the grouping of Sec. 2): one step size,
  * order and error test over every species, block-diagonal Newton matrix with
  * one dense LU per cell, task-local Newton solves (or_system.nblock = ncell).
+ * interp: the output mode of or_options.interp.
  * stats = {nst, nfe, nsetups, nni (summed over cells), ncfn, netf, qlast, 0}. */
 int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y0, double tout,
-                               double rtol, double atol, int64_t mxstep, double* yout,
-                               int64_t* stats);
+                               double rtol, double atol, int64_t mxstep, int interp,
+                               double* yout, int64_t* stats);
 
 /* y' = A y + sum_k C_k t^k, dense LU (pins of the BDF core) */
 int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, double t0,
@@ -174,9 +175,10 @@ typedef struct {
 void or_bruss_rhs(const or_bruss* p, const double* y, double* f);
 void or_bruss_jv(const or_bruss* p, const double* y, const double* v, double* jv);
 /* Integrate the whole grid as one system (shared h, global WRMS norms) with
- * Newton + GMRES(maxl) left-preconditioned by the 3x3 reaction blocks. */
+ * Newton + GMRES(maxl) left-preconditioned by the 3x3 reaction blocks;
+ * interp: the output mode of or_options.interp. */
 int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double tout,
-                       double rtol, double atol, int maxl, int64_t mxstep,
+                       double rtol, double atol, int maxl, int64_t mxstep, int interp,
                        double* yout, int64_t* stats);
 /* the two parts of the right-hand side and the reaction Jacobian of one
  * point (row-major 3x3): f = transport + reaction */

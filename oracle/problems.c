@@ -201,8 +201,8 @@ static int group_lsolve(void* p, double t, const double* ycur, double gamma,
 }
 
 int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y0, double tout,
-                               double rtol, double atol, int64_t mxstep, double* yout,
-                               int64_t* stats) {
+                               double rtol, double atol, int64_t mxstep, int interp,
+                               double* yout, int64_t* stats) {
   const int64_t C = cells->ncell;
   if (C <= 0) return 0;
   group_user g;
@@ -226,6 +226,7 @@ int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y
     opt.rtol = rtol;
     opt.atol = atol;
     opt.mxstep = mxstep;
+    opt.interp = interp;
     or_bdf* m = or_bdf_create(&sys, &opt, t0, y0);
     if (m) {
       ret = or_bdf_solve(m, tout, yout);
@@ -572,7 +573,7 @@ int or_bruss_gmres(const or_bruss* p, const double* y, double gamma, const doubl
 }
 
 int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double tout,
-                       double rtol, double atol, int maxl, int64_t mxstep,
+                       double rtol, double atol, int maxl, int64_t mxstep, int interp,
                        double* yout, int64_t* stats) {
   int64_t N = 3 * bruss_npts(p);
   bruss_user B;
@@ -584,6 +585,7 @@ int or_bruss_integrate(const or_bruss* p, double t0, const double* y0, double to
   opt.rtol = rtol;
   opt.atol = atol;
   opt.mxstep = mxstep;
+  opt.interp = interp;
   or_bdf* m = or_bdf_create(&sys, &opt, t0, y0);
   int ret = OR_MEM_FAIL;
   if (m) {

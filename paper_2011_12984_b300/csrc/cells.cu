@@ -84,6 +84,10 @@ struct Params {
   float* rec_t;               //   pairs of accepted steps, or null
   int64_t rec_cap;
   unsigned long long* rec_count;
+  // output mode: 0 the last step lands on tout (y = history plane 0); 1 the
+  // cells step past tout and yout receives the history polynomial at tout
+  int interp;
+  double* yout;
 };
 
 template <int G>
@@ -374,7 +378,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   }
   if (!C.retry) {
     C.last = 0;
-    if ((C.t + C.h - P.tout) * C.h >= 0.0) {
+    if (!P.interp && (C.t + C.h - P.tout) * C.h >= 0.0) {
       C.last = 1;
       if (C.t + C.h != P.tout) { rescale(C, (P.tout - C.t) / C.h); C.qwait = C.q + 1; }
     }
@@ -701,6 +705,18 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
 #pragma unroll
             for (int j = 0; j <= QMAX; ++j) P.z[(int64_t)j * P.ny + yo + i] = C.z[j][p];
             P.acorp[yo + i] = C.acorp[p];
+            if (P.yout) {
+              // the history polynomial at tout, sum_j z_j s^j with s = (tout - t) / h
+              // (Horner), for a cell past tout; otherwise its current state
+              double v = C.z[0][p];
+              if (P.interp && C.status == 0 && (C.flags & F_STARTED) && C.t != P.tout) {
+                const double sv = (P.tout - C.t) / C.h;
+                v = C.z[QMAX][p];
+#pragma unroll
+                for (int j = QMAX - 1; j >= 0; --j) v = j < C.q ? v * sv + C.z[j][p] : C.z[j][p];
+              }
+              P.yout[yo + i] = v;
+            }
           }
         }
         if (g.rank == 0) {
@@ -1180,6 +1196,9 @@ struct bdfb_ctx {
   double line_par[6] = {};    // A, B, eps, c, length, nx of the 1-D line
   // option "grouped": the cells as one system with task-local Newton solves
   int grouped = 0;
+  // option "interp": output by interpolation past tout; the output buffer
+  int interp = 0;
+  double* d_yout = nullptr;
   bool gfresh = true;         // the grouped integrator needs the state of bdfb_init
   GridBDF* gg = nullptr;
   double* d_glu = nullptr;    // per-cell LU factors (n x n each)
@@ -1214,7 +1233,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_gcrate); cudaFree(c->d_gflag); cudaFree(c->d_giters);
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
-  cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status);
+  cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status); cudaFree(c->d_yout);
   for (int k = 0; k < NVAR; ++k) cudaFree(c->d_fbws[k]);
   for (int m = 0; m < 3; ++m) { cudaFree(c->sched[m].d_tiles); cudaFree(c->sched[m].d_tcells); }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1595,6 +1614,15 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     if (v == 1 && (ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)) return BDFB_ILL_INPUT;
     ctx->predictor = (int)v;
+  } else if (!std::strcmp(key, "interp")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && !ctx->d_yout && ctx->ny > 0) {
+      if (cudaMalloc(&ctx->d_yout, ctx->ny * sizeof(double)) != cudaSuccess) {
+        ctx->d_yout = nullptr;
+        return BDFB_MEM_FAIL;
+      }
+    }
+    ctx->interp = (int)v;
   } else if (!std::strcmp(key, "grouped")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     ctx->grouped = (int)v;
@@ -1677,6 +1705,8 @@ static Params base_params(bdfb_ctx* ctx, double tout) {
   P.rec_t = ctx->rec_t;
   P.rec_cap = ctx->rec_cap;
   P.rec_count = ctx->rec_count;
+  P.interp = ctx->interp;
+  P.yout = ctx->interp ? ctx->d_yout : nullptr;
   return P;
 }
 
@@ -1834,6 +1864,7 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
       Pt.ntiles = nt;
       Pt.tile_counter = cnt2;
       Pt.worst = reinterpret_cast<int*>(cnt2 + NVAR);
+      Pt.yout = nullptr;                // trials leave the output alone
       Pt.status = nullptr;
       Pt.rec_x = nullptr;
       Pt.mlp = nullptr;
@@ -1994,6 +2025,7 @@ static int grouped_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* sta
   {
     int r = grid_set_option(ctx->gg, "mxstep", ctx->mxstep);
     if (!r) r = grid_set_option(ctx->gg, "qmax", ctx->qmax);
+    if (!r) r = grid_set_option(ctx->gg, "interp", ctx->interp);
     if (r) return r;
   }
   if (ctx->gfresh) {
@@ -2073,7 +2105,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   }
   BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
   if (y) {
-    BDFB_CUDA(cudaMemcpyAsync(y, ctx->d_z, ctx->ny * sizeof(double),
+    BDFB_CUDA(cudaMemcpyAsync(y, ctx->interp ? ctx->d_yout : ctx->d_z, ctx->ny * sizeof(double),
                               mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   }
   if (status) {

@@ -246,6 +246,15 @@ __global__ void k_ewt(int64_t N, double rtol, double atol, const double* __restr
   }
 }
 
+// y(tout) = sum_{j <= q} z_j s^j, s = (tout - t_n) / h (Horner)
+__global__ void k_interp(int64_t N, int q, GZ Z, double s, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = Z.z[q][i];
+    for (int j = q - 1; j >= 0; --j) v = v * s + Z.z[j][i];
+    out[i] = v;
+  }
+}
+
 // acor += delta; y = zp0 + acor (one pass for the Newton update)
 __global__ void k_newton_update(int64_t N, const double* __restrict__ delta, double* __restrict__ acor,
                                 const double* __restrict__ zp0, double* __restrict__ y) {
@@ -335,6 +344,7 @@ struct GridBDF {
   double rtol = 1e-6, atol = 1e-10;
   int maxl = 5;
   int prec = 0;               // 1: preconditioner and GMRES operator in FP32
+  int interp = 0;             // 1: step past tout, output the history polynomial at tout
   int64_t mxstep = 100000;
   int qmax = GQMAX;
   cudaStream_t s = nullptr;
@@ -684,7 +694,7 @@ static int g_step(GridBDF* g, double tout, bool* reached) {
   int ncf = 0, nef = 0;
   for (;;) {
     bool last = false;
-    if ((g->t + g->h - tout) * g->h >= 0.0) {
+    if (!g->interp && (g->t + g->h - tout) * g->h >= 0.0) {
       last = true;
       if (g->t + g->h != tout) { GCHK(g_rescale(g, (tout - g->t) / g->h)); g->qwait = g->q + 1; }
     }
@@ -897,6 +907,9 @@ int grid_set_option(GridBDF* g, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "qmax")) {
     if (v < 1 || v > GQMAX) return BDFB_ILL_INPUT;
     g->qmax = (int)v;
+  } else if (!std::strcmp(key, "interp")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    g->interp = (int)v;
   } else if (!std::strcmp(key, "precision") && !g->external) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     g->prec = (int)v;
@@ -940,8 +953,14 @@ int grid_integrate(GridBDF* g, double tout, double* y, int mem) {
     }
   }
   BDFB_CUDA(cudaEventRecord(g->e1, g->s));
+  const double* src = g->z[0];
+  if (g->interp && !ret && g->started && g->t != tout) {
+    k_interp<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), (tout - g->t) / g->h, g->tmp);
+    BDFB_CUDA(cudaGetLastError());
+    src = g->tmp;
+  }
   if (y)
-    BDFB_CUDA(cudaMemcpyAsync(y, g->z[0], g->N * sizeof(double),
+    BDFB_CUDA(cudaMemcpyAsync(y, src, g->N * sizeof(double),
                               mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->s));
   BDFB_CUDA(cudaStreamSynchronize(g->s));
   cudaEventElapsedTime(&g->last_ms, g->e0, g->e1);

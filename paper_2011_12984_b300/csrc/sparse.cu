@@ -758,7 +758,8 @@ void shared_set_stream(SharedInt* S, cudaStream_t s) {
 void shared_set_tolerances(SharedInt* S, double rtol, double atol) { grid_set_tolerances(S->gg, rtol, atol); }
 
 int shared_set_option(SharedInt* S, const char* key, int64_t v) {
-  if (!std::strcmp(key, "mxstep") || !std::strcmp(key, "qmax")) return grid_set_option(S->gg, key, v);
+  if (!std::strcmp(key, "mxstep") || !std::strcmp(key, "qmax") || !std::strcmp(key, "interp"))
+    return grid_set_option(S->gg, key, v);
   return BDFB_ILL_INPUT;
 }
 

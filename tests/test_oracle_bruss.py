@@ -14,6 +14,7 @@ and the 1-D advection-reaction demo of Sec. 7) and GMRES.
   either sign of c, J v and full-Krylov GMRES as above.
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_2011_12984_b300 import gen
@@ -37,7 +38,9 @@ def test_steady_state_stays():
     assert np.max(np.abs(y - p.y0) / np.abs(p.y0)) <= 1e-12
 
 
-def test_fourier_mode_of_free_diffusion():
+@pytest.mark.parametrize("interp", [False, True])
+def test_fourier_mode_of_free_diffusion(interp):
+    """the closed-form decay, in both output modes of the grid integrator"""
     nx, k = 8, (1, 2, 0)
     npts = nx ** 3
     y0 = np.zeros(3 * npts)
@@ -50,7 +53,7 @@ def test_fourier_mode_of_free_diffusion():
     jv = oracle.bruss_jv(p, y0, y0)
     assert np.max(np.abs(jv[npts:2 * npts] - L * y0[npts:2 * npts])) <= 1e-10 * abs(L)
     tout = 0.5 / abs(L)
-    ret, y, st = oracle.bruss_integrate(p, 0.0, tout, 1e-8, 1e-12, y0=y0)
+    ret, y, st = oracle.bruss_integrate(p, 0.0, tout, 1e-8, 1e-12, y0=y0, interp=interp)
     assert ret == 0
     assert np.max(np.abs(y[npts:2 * npts] - np.exp(L * tout) * y0[npts:2 * npts])) <= 20 * 1e-8
 

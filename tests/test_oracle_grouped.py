@@ -26,15 +26,20 @@ def replicate(p, cell, copies):
     return p.subset(np.full(copies, cell, np.int64))
 
 
+@pytest.mark.parametrize("interp", [False, True])
 @pytest.mark.parametrize("kind", ["robertson", "mass_action"])
-def test_one_cell_equals_per_cell(kind):
+def test_one_cell_equals_per_cell(kind, interp):
+    """in both output modes (the grouped entry point passes the mode through)"""
     p = gen.robertson(5).subset([2]) if kind == "robertson" else gen.mass_action(16, seed=5).subset([7])
     tout = 40.0 if kind == "robertson" else 1e-3
-    yg, r, sg = oracle.integrate_cells_grouped(p, 0.0, tout, 1e-6, 1e-10)
-    yc, sc, stc = oracle.integrate_cells(p, 0.0, tout, 1e-6, 1e-10)
+    yg, r, sg = oracle.integrate_cells_grouped(p, 0.0, tout, 1e-6, 1e-10, interp=interp)
+    yc, sc, stc = oracle.integrate_cells(p, 0.0, tout, 1e-6, 1e-10, interp=interp)
     assert r == 0 and sc[0] == 0
     assert sg[0] == stc[0, 0] and sg[3] == stc[0, 3] and sg[5] == stc[0, 5]
     np.testing.assert_allclose(yg, yc, rtol=1e-13, atol=1e-20)
+    if interp:
+        yk, _, _ = oracle.integrate_cells_grouped(p, 0.0, tout, 1e-6, 1e-10)
+        assert not np.array_equal(yg, yk)
 
 
 @pytest.mark.parametrize("copies", [2, 7])
