@@ -739,6 +739,7 @@ def run_ours(args):
                                                       oracle_points=5_000)}
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
+                       ("batched_fp64_gauss_jordan_inverse", {"lsolver": 1}),
                        ("batched_mixed_fp32_lu", {"precision": 1, "autotune": 1})):
         with bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, **opts) as vi:
             ts = []

@@ -313,6 +313,18 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              Statistics: every cell counts every grouped step, RHS
  *              evaluation, setup and failure; nniters sums the cells'
  *              task-local iterations.
+ *  "lsolver"   linear solver of the per-cell Newton systems M x = b:
+ *              0 = batched dense LU with partial pivoting (default);
+ *              1 = explicit inverse: each setup inverts every cell's M by
+ *              Gauss-Jordan elimination with partial pivoting in FP64 (the
+ *              task-local block inverse of the demonstration problem,
+ *              Sec. 7, for any block size) and each Newton solve is one
+ *              matrix-vector product.  Equal to LU in exact arithmetic;
+ *              three times the setup flops, no dependent triangular chain
+ *              in the solves.  With "precision" 1 the FP32 inverse of that
+ *              mode is used either way.  Not with "predictor", a recording
+ *              or "grouped".  Grid and shared-network contexts accept 0
+ *              only (GMRES, sparse LU).
  *  "interp"    0 = the last step is shortened to end exactly at tout and y
  *              is the state there (default); 1 = steps are never shortened
  *              for tout: the integrator steps until t_n >= tout and writes

@@ -80,17 +80,18 @@ struct UsesDr {
 };
 
 // per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
-// (mixed precision): M and its Gauss-Jordan inverse in FP32.  Both keep the
+// (mixed precision): M and its Gauss-Jordan inverse in FP32.  PREC = 2: M
+// and its Gauss-Jordan inverse in FP64.  All keep the
 // FP64 reaction derivatives of the last setup (computed once per reaction, then
 // gathered into the rows of J; mixed precision reuses them in the refinement
 // residual).
 template <int NMAX, int PREC = 0>
-struct CellSmem : RateBufs<NMAX, PREC == 0, UsesDr<NMAX, PREC>::value> {
+struct CellSmem : RateBufs<NMAX, PREC != 1, UsesDr<NMAX, PREC>::value> {
   static constexpr bool DR = UsesDr<NMAX, PREC>::value;
   typename std::conditional<PREC == 1, float, double>::type M[NMAX][NMAX + 1];
   // history saved before a step attempt; the FP64 kernel of the largest
   // cells keeps it in registers instead (its shared memory bounds residency)
-  static constexpr bool ZREG = PREC == 0 && NMAX >= 56;
+  static constexpr bool ZREG = PREC != 1 && NMAX >= 56;
   double zs[ZREG ? 1 : ZCOLS][NMAX];
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side

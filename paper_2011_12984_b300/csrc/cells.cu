@@ -423,7 +423,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       // the refinement residual
       reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
       C.mnorm = form_M32<G, NPL, NMAX>(g, cd, S, C.gamma);
-      info = gj_inverse<G, NMAX>(g, S.M, S.perm, reinterpret_cast<float*>(S.ybuf), n);
+      info = gj_inverse<G, NMAX, float>(g, S.M, S.perm, reinterpret_cast<float*>(S.ybuf), n);
       C.fp64mode = 0;
     } else {
       bool direct = true;
@@ -436,7 +436,10 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         }
       }
       if (direct) form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
-      info = lu_factor<G, NMAX, double, true>(g, S.M, S.dinv, S.perm, n);
+      if constexpr (PREC == 2)   // explicit inverse: each Newton solve is one product
+        info = gj_inverse<G, NMAX, double>(g, S.M, S.perm, S.ybuf, n);
+      else
+        info = lu_factor<G, NMAX, double, true>(g, S.M, S.dinv, S.perm, n);
     }
     C.nsetups++;
     C.gammap = C.gamma;
@@ -522,6 +525,8 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
             }
           }
           if (!solved) lu_solve<G, NPL, NMAX, double, true>(g, Mg, S.dinv, S.perm, S.ybuf, n, C.b);
+        } else if constexpr (PREC == 2) {
+          apply_inverse<G, NPL, NMAX, double>(g, S.M, S.ybuf, n, C.b, C.b);
         } else {
           lu_solve<G, NPL, NMAX, double, true>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
         }
@@ -761,8 +766,9 @@ struct VarSmem {
 };
 
 // Persistent kernel of one variant: each warp takes the next tile of the
-// range [t0, t1) from `counter` until none is left.  PREC 0: FP64
-// factorisation; PREC 1: FP32 factorisation with FP64 refinement.
+// range [t0, t1) from `counter` until none is left.  PREC 0: FP64 LU
+// factorisation; PREC 1: FP32 inverse with FP64 refinement; PREC 2: FP64
+// Gauss-Jordan inverse (Newton solves by one matrix-vector product).
 template <int V, int PREC>
 __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_constant__ Params P, int t0, int t1,
                                                            unsigned* counter, double* fbws) {
@@ -786,16 +792,21 @@ static int64_t fallback_doubles_per_warp(int v) {
 }
 
 typedef void (*cells_kernel_t)(const Params, int, int, unsigned*, double*);
-static const cells_kernel_t CELLS_KERNELS[2][NVAR] = {
+constexpr int NKPREC = 3;   // kernel rows: FP64 LU, FP32 inverse + refinement, FP64 inverse
+static const cells_kernel_t CELLS_KERNELS[NKPREC][NVAR] = {
     {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>, k_cells<5, 0>, k_cells<6, 0>,
      k_cells<7, 0>},
     {k_cells<0, 1>, k_cells<1, 1>, k_cells<2, 1>, k_cells<3, 1>, k_cells<4, 1>, nullptr, k_cells<6, 1>,
-     k_cells<7, 1>}};
-static const int CELLS_SMEM[2][NVAR] = {
+     k_cells<7, 1>},
+    {k_cells<0, 2>, k_cells<1, 2>, k_cells<2, 2>, k_cells<3, 2>, k_cells<4, 2>, nullptr, k_cells<6, 2>,
+     k_cells<7, 2>}};
+static const int CELLS_SMEM[NKPREC][NVAR] = {
     {VarSmem<0, 0>::bytes, VarSmem<1, 0>::bytes, VarSmem<2, 0>::bytes, VarSmem<3, 0>::bytes, VarSmem<4, 0>::bytes,
      VarSmem<5, 0>::bytes, VarSmem<6, 0>::bytes, VarSmem<7, 0>::bytes},
     {VarSmem<0, 1>::bytes, VarSmem<1, 1>::bytes, VarSmem<2, 1>::bytes, VarSmem<3, 1>::bytes, VarSmem<4, 1>::bytes,
-     0, VarSmem<6, 1>::bytes, VarSmem<7, 1>::bytes}};
+     0, VarSmem<6, 1>::bytes, VarSmem<7, 1>::bytes},
+    {VarSmem<0, 2>::bytes, VarSmem<1, 2>::bytes, VarSmem<2, 2>::bytes, VarSmem<3, 2>::bytes, VarSmem<4, 2>::bytes,
+     0, VarSmem<6, 2>::bytes, VarSmem<7, 2>::bytes}};
 static cells_kernel_t var_kernel(int pr, int v) { return CELLS_KERNELS[pr][v]; }
 static int var_smem(int pr, int v) { return CELLS_SMEM[pr][v]; }
 
@@ -1050,7 +1061,7 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
       }
     }
     anorm = gmaxd(g, anorm);
-    const int info = gj_inverse<32, LU_NMAX>(g, M32, S.perm, reinterpret_cast<float*>(S.ybuf), n);
+    const int info = gj_inverse<32, LU_NMAX, float>(g, M32, S.perm, reinterpret_cast<float*>(S.ybuf), n);
     double b[NPL], x[NPL], r[NPL];
     double bn = 0.0;
 #pragma unroll
@@ -1067,7 +1078,7 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
       float r32[NPL], c32[NPL];
 #pragma unroll
       for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
-      apply_inverse32<32, NPL, LU_NMAX>(g, M32, reinterpret_cast<float*>(S.ybuf), n, r32, c32);
+      apply_inverse<32, NPL, LU_NMAX, float>(g, M32, reinterpret_cast<float*>(S.ybuf), n, r32, c32);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
       g.sync();
@@ -1179,6 +1190,7 @@ struct bdfb_ctx {
   double rtol = 1e-6, atol = 1e-10;
   int64_t mxstep = 100000;
   int mapping = 0, precision = 0, graph = 0, qmax = QMAX;
+  int lsolver = 0;            // 1: FP64 Gauss-Jordan inverse instead of LU
   double t0 = 0.0;
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
@@ -1186,7 +1198,7 @@ struct bdfb_ctx {
   double* d_fbws[NVAR] = {};        // FP64 fallback workspace per variant (mixed precision, lazy)
   cudaStream_t cstream[NVAR] = {};  // one per variant, forked from `stream`
   float last_ms = 0.f;
-  int pgrid[2][NVAR] = {};    // persistent grid size [precision][variant]
+  int pgrid[NKPREC][NVAR] = {};   // persistent grid size [kernel row][variant]
   GridBDF* grid = nullptr;    // BDFB_BRUSSELATOR3D / 1D: the grouped grid integrator
   ArkLine* ark = nullptr;     // BDFB_BRUSSELATOR1D with option "imex": the IMEX ARK integrator
   SharedInt* shared = nullptr;  // BDFB_MASSACTION_SHARED: grouped cells on one sparse network
@@ -1282,7 +1294,7 @@ static int setup_launch(bdfb_ctx* c) {
   for (int k = 0; k < NVAR; ++k) {
     BDFB_CUDA(cudaEventCreateWithFlags(&c->evjoin[k], cudaEventDisableTiming));
     BDFB_CUDA(cudaStreamCreateWithFlags(&c->cstream[k], cudaStreamNonBlocking));
-    for (int pr = 0; pr < 2; ++pr) {
+    for (int pr = 0; pr < NKPREC; ++pr) {
       const cells_kernel_t kf = var_kernel(pr, k);
       if (!kf) continue;
       BDFB_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, var_smem(pr, k)));
@@ -1549,6 +1561,9 @@ extern "C" int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol) {
 
 extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
   if (!ctx || !key) return BDFB_ILL_INPUT;
+  // the grids solve by GMRES, shared networks by their sparse LU: only the
+  // default linear solver
+  if ((ctx->grid || ctx->shared) && !std::strcmp(key, "lsolver")) return v == 0 ? BDFB_SUCCESS : BDFB_ILL_INPUT;
   if (ctx->shared) return shared_set_option(ctx->shared, key, v);
   if (ctx->grid && ctx->kind == BDFB_BRUSSELATOR1D && !std::strcmp(key, "imex")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
@@ -1612,8 +1627,13 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
     ctx->qmax = (int)v;
   } else if (!std::strcmp(key, "predictor")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
-    if (v == 1 && (ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)) return BDFB_ILL_INPUT;
+    if (v == 1 && (ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0 || ctx->lsolver))
+      return BDFB_ILL_INPUT;
     ctx->predictor = (int)v;
+  } else if (!std::strcmp(key, "lsolver")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && (ctx->predictor || ctx->rec_x)) return BDFB_ILL_INPUT;
+    ctx->lsolver = (int)v;
   } else if (!std::strcmp(key, "interp")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     if (v == 1 && !ctx->d_yout && ctx->ny > 0) {
@@ -1666,10 +1686,14 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
   return BDFB_SUCCESS;
 }
 
+// kernel row of the factorisation options: FP32 inverse with refinement
+// (precision 1), FP64 Gauss-Jordan inverse (lsolver 1) or FP64 LU
+static int kernel_row(const bdfb_ctx* ctx) { return ctx->precision == 1 ? 1 : ctx->lsolver ? 2 : 0; }
+
 // The one-warp-per-cell kernel of mapping 32 (and of the learned guess): the
 // smallest shared-memory layout every cell fits
 static int one_warp_variant(const bdfb_ctx* ctx, bool learn) {
-  if (learn || (ctx->fits_w16 && ctx->precision == 0)) return VAR_W16;
+  if (learn || (ctx->fits_w16 && ctx->precision == 0 && !ctx->lsolver)) return VAR_W16;
   if (ctx->fits_w32) return VAR_W32;
   return 4;
 }
@@ -1990,7 +2014,7 @@ static int group_solve(void* user, const double* zp0, const double* zp1, const d
 }
 
 static int grouped_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
-  if (ctx->precision != 0 || ctx->predictor || ctx->rec_x) return BDFB_ILL_INPUT;
+  if (ctx->precision != 0 || ctx->lsolver || ctx->predictor || ctx->rec_x) return BDFB_ILL_INPUT;
   cudaStream_t s = ctx->stream;
   if (!ctx->gg) {
     const int64_t C = ctx->ncell;
@@ -2067,7 +2091,7 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   if (ctx->grouped) return grouped_integrate(ctx, tout, y, status, mem);
   if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
   cudaStream_t s = ctx->stream;
-  const int pr = ctx->precision;
+  const int pr = kernel_row(ctx);
   const bool learn = ctx->predictor || ctx->rec_x;
   // one warp per cell: the NMAX 16 kernel when every cell fits it
   // one warp per cell: the smallest one-warp kernel every cell fits
@@ -2275,7 +2299,7 @@ extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
     if (!out[3 * cl + 2]) continue;
     int v = cl;
     if (learn || ctx->mapping == 32) v = one_warp_variant(ctx, learn);
-    else if (ctx->autotune && ctx->tuned_prec == ctx->precision) v = ctx->tuned_var[cl];
+    else if (ctx->autotune && ctx->tuned_prec == kernel_row(ctx)) v = ctx->tuned_var[cl];
     out[3 * cl] = VAR_G[v];
     out[3 * cl + 1] = VAR_NMAX[v];
     if (trial_ms && ctx->autotune && ctx->tuned_prec >= 0)
@@ -2297,7 +2321,8 @@ extern "C" int bdfb_set_record(bdfb_ctx* ctx, float* x, float* t, int64_t cap, u
     ctx->rec_x = nullptr; ctx->rec_t = nullptr; ctx->rec_cap = 0; ctx->rec_count = nullptr;
     return BDFB_SUCCESS;
   }
-  if (!t || !count || cap < 0 || ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0)
+  if (!t || !count || cap < 0 || ctx->maxn > MLP_NO || !ctx->fits_w16 || ctx->precision != 0 ||
+      ctx->lsolver)
     return BDFB_ILL_INPUT;
   ctx->rec_x = x; ctx->rec_t = t; ctx->rec_cap = cap; ctx->rec_count = count;
   return BDFB_SUCCESS;

@@ -153,40 +153,43 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
   g.sync();
 }
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // In-place Gauss-Jordan inverse with partial pivoting (ties to the lowest
-// row) of the n x n FP32 matrix A; the block inverse the paper applies to
-// its 3x3 reaction blocks (Sec. 7), here for any block size.  Returns 0 or
-// k + 1 when no nonzero pivot exists in column k.  piv (n entries) and colk
-// (n floats): scratch.
-template <int G, int NMAX>
-__device__ __forceinline__ int gj_inverse(const Grp<G>& g, float (*A)[NMAX + 1], int16_t* piv,
-                                          float* colk, int n) {
+// row) of the n x n matrix A (FP32 or FP64); the block inverse the paper
+// applies to its 3x3 reaction blocks (Sec. 7), here for any block size.
+// Returns 0 or k + 1 when no nonzero pivot exists in column k.  piv (n
+// entries) and colk (n values): scratch.
+template <int G, int NMAX, typename T>
+__device__ __forceinline__ int gj_inverse(const Grp<G>& g, T (*A)[NMAX + 1], int16_t* piv,
+                                          T* colk, int n) {
   constexpr int R = LaneGrid<G>::R, C = LaneGrid<G>::C;
   constexpr int NJ = (NMAX + C - 1) / C;
   const int li = g.rank / C, lj = g.rank % C;
   for (int k = 0; k < n; ++k) {
-    float best = -1.0f;
+    T best = T(-1);
     int p = n;
     for (int i = k + g.rank; i < n; i += G) {
-      const float v = fabsf(A[i][k]);
+      const T v = A[i][k] < T(0) ? -A[i][k] : A[i][k];
       if (v > best) { best = v; p = i; }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(g.mask, best, o, G);
+      const T ob = __shfl_xor_sync(g.mask, best, o, G);
       const int op = __shfl_xor_sync(g.mask, p, o, G);
       if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
     }
-    if (!(best > 0.0f) || p >= n) return k + 1;
+    if (!(best > T(0)) || p >= n) return k + 1;
     if (g.rank == 0) piv[k] = (int16_t)p;
     if (p != k)
       for (int j = g.rank; j < n; j += G) {
-        const float t = A[k][j];
+        const T t = A[k][j];
         A[k][j] = A[p][j];
         A[p][j] = t;
       }
     g.sync();
-    const float pinv = 1.0f / A[k][k];
+    const T pinv = T(1) / A[k][k];
     g.sync();
     // row k <- row k / pivot, with the pivot slot becoming 1 / pivot; keep
     // column k (the elimination factors) before it is overwritten
@@ -194,19 +197,19 @@ __device__ __forceinline__ int gj_inverse(const Grp<G>& g, float (*A)[NMAX + 1],
     for (int i = g.rank; i < n; i += G) colk[i] = A[i][k];
     g.sync();
     // eliminate column k from every other row (lanes on an R x C grid)
-    float u[NJ];
+    T u[NJ];
 #pragma unroll
     for (int b = 0; b < NJ; ++b) {
       const int j = lj + C * b;
-      u[b] = j < n ? A[k][j] : 0.0f;
+      u[b] = j < n ? A[k][j] : T(0);
     }
     for (int i = li; i < n; i += R) {
       if (i == k) continue;
-      const float f = colk[i];
+      const T f = colk[i];
 #pragma unroll
       for (int b = 0; b < NJ; ++b) {
         const int j = lj + C * b;
-        if (j < n) A[i][j] = (j == k) ? -f * u[b] : fmaf(-f, u[b], A[i][j]);
+        if (j < n) A[i][j] = (j == k) ? -f * u[b] : fma_t(-f, u[b], A[i][j]);
       }
     }
     g.sync();
@@ -216,7 +219,7 @@ __device__ __forceinline__ int gj_inverse(const Grp<G>& g, float (*A)[NMAX + 1],
     const int p = piv[k];
     if (p != k)
       for (int i = g.rank; i < n; i += G) {
-        const float t = A[i][k];
+        const T t = A[i][k];
         A[i][k] = A[i][p];
         A[i][p] = t;
       }
@@ -225,10 +228,11 @@ __device__ __forceinline__ int gj_inverse(const Grp<G>& g, float (*A)[NMAX + 1],
   return 0;
 }
 
-// x = Ainv r in FP32 (lanes own rows; r gathered through shared memory)
-template <int G, int NPL, int NMAX>
-__device__ __forceinline__ void apply_inverse32(const Grp<G>& g, const float (*Ainv)[NMAX + 1], float* buf,
-                                                int n, const float (&r)[NPL], float (&x)[NPL]) {
+// x = Ainv r (lanes own rows; r gathered through shared memory); x may
+// alias r
+template <int G, int NPL, int NMAX, typename T>
+__device__ __forceinline__ void apply_inverse(const Grp<G>& g, const T (*Ainv)[NMAX + 1], T* buf,
+                                              int n, const T (&r)[NPL], T (&x)[NPL]) {
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     const int i = g.rank + G * p;
@@ -238,10 +242,10 @@ __device__ __forceinline__ void apply_inverse32(const Grp<G>& g, const float (*A
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     const int i = g.rank + G * p;
-    float s = 0.0f;
+    T s = T(0);
     if (i < n) {
-      const float* row = Ainv[i];
-      for (int j = 0; j < n; ++j) s = fmaf(row[j], buf[j], s);
+      const T* row = Ainv[i];
+      for (int j = 0; j < n; ++j) s = fma_t(row[j], buf[j], s);
     }
     x[p] = s;
   }
@@ -271,7 +275,7 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
     float r32[NPL], c32[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
-    apply_inverse32<G, NPL, NMAX>(g, S.M, buf, n, r32, c32);
+    apply_inverse<G, NPL, NMAX, float>(g, S.M, buf, n, r32, c32);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
     jac_vec<G, NPL, NMAX>(g, c, S, x, jx);
