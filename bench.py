@@ -193,6 +193,26 @@ NV_FP64_INST_PER_BYTE = {"linear_sum": 2 / 24, "linear_combination_6": 6 / 56, "
                          "dot_prod_multi_5": 5 / 48, "wrms_norm": 2 / 16}
 
 
+def dgemm_tflops(torch, n=8192, reps=3):
+    """FP64 throughput a library GEMM reaches on this part (cuBLAS DGEMM,
+    n x n x n): the measured counterpart of the nominal FP64 rate, for context
+    beside the per-cell kernels' FP64 roofline"""
+    a = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    b = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    c = torch.empty_like(a)
+    torch.matmul(a, b, out=c)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(a, b, out=c)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / reps
+    del a, b, c
+    return 2.0 * n ** 3 / t / 1e12
+
+
 def nvector_ceilings(nv, hbm_gbs, sm_mhz):
     """per op: the lower of the HBM copy rate and the FP64 issue limit
     (148 SMs x 2 FP64 lanes per cycle / FP64 instructions per byte); on B300
@@ -722,6 +742,10 @@ def run_ours(args):
     t_kern = sum(kern_s) / len(kern_s)
     flops = algorithmic_flops(prob, cs)
     achieved = flops / t_kern / 1e12
+    try:
+        dgemm_tf = dgemm_tflops(torch)
+    except RuntimeError:
+        dgemm_tf = None
     nv = nvector_bandwidth(torch, bdfb)
     grid = grid_workload(torch, bdfb, gen)
     learned = learned_workload(torch, bdfb, gen, train_steps=20000) if not args.no_learned else None
@@ -768,6 +792,7 @@ def run_ours(args):
                                           and args.precision == 0) else None
     acc = accuracy(prob, yh)
     cpu_v, cpu_threads, cpu_ns, cpu_dt, cpu_fail = cpu_oracle_rate(prob)
+    cpu1_v, _, cpu1_ns, cpu1_dt, _ = cpu_oracle_rate(prob, seconds=3.0, threads=1)
     st_sum = integ.stats()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -786,7 +811,9 @@ def run_ours(args):
         "roofline": {"kernel": "k_cells (persistent BDF/Newton)", "bound": "alu", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "kernel_ms": t_kern * 1e3, "algorithmic_fp64_flops": flops,
-                     "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)"},
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
+                     "fp64_dgemm_tflops_measured": dgemm_tf,
+                     "frac_of_dgemm": achieved / dgemm_tf if dgemm_tf else None},
         "variants_cells_per_s": variants,
         "coupled_grid": grid,
         "learned_guess": learned,
@@ -797,7 +824,9 @@ def run_ours(args):
                              "peak_source": f"hbm_gbs of {pk_kind}"},
         "nvector_ceilings": nvector_ceilings(nv, pk["hbm_gbs"], clk.summary().get("sm_mhz")),
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
-                         "sample": f"first {cpu_ns} of the {NCELL} cells ({cpu_dt:.1f} s, {cpu_fail} failed)"},
+                         "sample": f"first {cpu_ns} of the {NCELL} cells ({cpu_dt:.1f} s, {cpu_fail} failed)",
+                         "single_thread": {"value": cpu1_v, "cores": 1,
+                                           "sample": f"first {cpu1_ns} cells ({cpu1_dt:.1f} s)"}},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(8 * y0h.size),
                 "d2h_bytes_per_step": int(8 * y0h.size + 4 * prob.ncell)},
         "gpu_launches": args.steps * launches_per_step,
