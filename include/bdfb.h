@@ -332,7 +332,8 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              (the normal output mode of a Nordsieck BDF integrator,
  *              Sec. 3).  The next call continues from t_n; a tout inside
  *              the last step (tout <= t_n) is answered by interpolation
- *              alone, with no step.  Every BDF path takes it (cells,
+ *              alone, with no step (a tout before that step's start is
+ *              extrapolated from the same polynomial, not refused).  Every BDF path takes it (cells,
  *              "grouped", BDFB_MASSACTION_SHARED, both grids); the line's
  *              "imex" path always ends its steps at tout.
  * "mapping" 32 runs every cell on the smallest one-warp-per-cell kernel all

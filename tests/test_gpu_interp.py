@@ -163,3 +163,29 @@ def test_grid_and_line_interp_match_oracle(which):
     assert abs(gs[0, 0] / so[0] - 1.0) <= 0.1, (gs[0], so)
     (yc,), _, _ = run(p, [tout], rtol, atol)
     assert not np.array_equal(yc, y)
+
+
+def test_interp_edge_cases():
+    """tout = t0 returns the initial state bitwise (no step, nothing to
+    interpolate); a cell stopped by mxstep reports its status and the state
+    it reached (t_n < tout: no interpolation), like the clamped mode"""
+    p = gen.mass_action(100000, seed=8).subset(np.arange(64))
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, interp=1) as I:
+        I.init(0.0, p.y0.copy())
+        y = np.empty(p.y0.size)
+        st = np.empty(p.ncell, np.int32)
+        assert I.integrate(0.0, y, st) == 0
+        assert np.array_equal(y, p.y0)
+    outs = []
+    for interp in (0, 1):
+        with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, interp=interp, mxstep=1) as I:
+            I.init(0.0, p.y0.copy())
+            y = np.empty(p.y0.size)
+            st = np.empty(p.ncell, np.int32)
+            r = I.integrate(1e-3, y, st)
+            assert r == bdfb.TOO_MUCH_WORK and np.all(st == bdfb.TOO_MUCH_WORK)
+            outs.append(y.copy())
+    # one step from the same start (the first step is at most a tenth of
+    # tout - t0, so no clamp applies) is the same in both modes
+    assert np.array_equal(outs[0], outs[1])
+    assert not np.array_equal(outs[0], p.y0)

@@ -99,3 +99,13 @@ def test_invalid_combinations_refused():
         G.set_option("lsolver", 0)
         with pytest.raises(RuntimeError):
             G.set_option("lsolver", 1)
+
+
+def test_grouped_refuses_inverse_solves():
+    p = gen.mass_action(64, seed=1).subset(np.arange(8))
+    with bdfb.Integrator(p, grouped=1, lsolver=1) as I:
+        I.init(0.0, p.y0.copy())
+        y = np.empty(p.y0.size)
+        with pytest.raises(bdfb.BdfbError) as e:
+            I.integrate(1e-4, y)
+        assert e.value.code == bdfb.ILL_INPUT
