@@ -813,7 +813,10 @@ def run_ours(args):
                      "traffic": traffic, "kernel_ms": t_kern * 1e3, "algorithmic_fp64_flops": flops,
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
                      "fp64_dgemm_tflops_measured": dgemm_tf,
-                     "frac_of_dgemm": achieved / dgemm_tf if dgemm_tf else None},
+                     "frac_of_dgemm": achieved / dgemm_tf if dgemm_tf else None,
+                     # recorded, not measured by this run: ncu's FP64-pipe activity of the
+                     # 54-species launch (profiles/k_cells_massaction_n54.md)
+                     "fp64_pipe_active_pct_ncu_54_species": 77.1},
         "variants_cells_per_s": variants,
         "coupled_grid": grid,
         "learned_guess": learned,
