@@ -34,6 +34,20 @@ struct Grp {
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
     return v;
   }
+  // The same sum when only ranks [0, nl) can hold nonzero values: a
+  // butterfly over the smallest power-of-two span of ranks holding them,
+  // then rank 0's total to every lane.  FP64 adds are charged per warp
+  // instruction however few lanes use them, so a 3-species cell on 32 lanes
+  // adds in 2 levels instead of 5 (the broadcast is an integer shuffle).
+  // nl >= G gives sum(v) unchanged, bit for bit.
+  __device__ __forceinline__ double sum_first(double v, int nl) const {
+    if (G == 1) return v;
+    int span = G;
+    while (span > 1 && (span >> 1) >= nl) span >>= 1;
+    if (span == G) return sum(v);
+    for (int o = span >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return __shfl_sync(mask, v, 0, G);
+  }
   __device__ __forceinline__ bool any(bool p) const {
     if (G == 1) return p;
     return (__ballot_sync(mask, p) & mask) != 0u;
@@ -135,7 +149,7 @@ __device__ __forceinline__ double wrms(const Grp<G>& g, int n, const double (&x)
       s = fma(v, v, s);
     }
   }
-  return sqrt(g.sum(s) / (double)n);
+  return sqrt(g.sum_first(s, n) / (double)n);
 }
 
 // squared WRMS norm, sum (x_i w_i)^2 / n, in FP64 (rn = 1/n).  The step loop
@@ -152,7 +166,7 @@ __device__ __forceinline__ double wrms2(const Grp<G>& g, int n, double rn, const
       s = fma(v, v, s);
     }
   }
-  return g.sum(s) * rn;
+  return g.sum_first(s, n) * rn;
 }
 
 // step-size ratio 1 / ((safety^2 d2)^(e) + 1e-6) from a squared error norm d2,
