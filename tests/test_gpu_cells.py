@@ -63,10 +63,13 @@ def check_against_oracle(prob, tout, rtol, atol, y, cstats, max_factor=1.5):
     return eg, eo
 
 
-def test_robertson_1000_cells():
-    """Robertson kinetics, 1000 cells, rtol 1e-4, atol 1e-8 over [0, 40]."""
+@pytest.mark.parametrize("opts", [{}, {"autotune": 1}])
+def test_robertson_1000_cells(opts):
+    """Robertson kinetics, 1000 cells, rtol 1e-4, atol 1e-8 over [0, 40]; with
+    the autotuner too (the benchmark's launch configuration: one warp per
+    cell, whose norms reduce over 4 of the 32 lanes)."""
     p = gen.robertson(1000)
-    ret, y, st, cs, stats = run_gpu(p, 0.0, 40.0, 1e-4, 1e-8)
+    ret, y, st, cs, stats = run_gpu(p, 0.0, 40.0, 1e-4, 1e-8, **opts)
     assert ret == 0 and np.all(st == 0)
     assert np.max(np.abs(y.reshape(-1, 3).sum(axis=1) - 1.0)) <= 1e-12   # sum y = 1
     check_against_oracle(p, 40.0, 1e-4, 1e-8, y, cs)
