@@ -246,14 +246,15 @@ __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem
   if (c.kind == BDFB_ROBERTSON) {
     const double* k = c.k;
     const double y0 = S.ybuf[0], y1 = S.ybuf[1], y2 = S.ybuf[2];
+    // every lane forms the three rows and keeps its own: FP64 instructions
+    // cost a warp issue slot whatever the active lanes, so per-row branches
+    // would issue each row's arithmetic separately
+    const double b = k[2] * y1 * y2, c2 = k[1] * y1 * y1;
+    const double f0 = fma(-k[0], y0, b), f1 = fma(k[0], y0, -b) - c2;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
       const int i = g.rank + G * p;
-      double v = 0.0;
-      if (i == 0) v = -k[0] * y0 + k[2] * y1 * y2;
-      else if (i == 1) v = k[0] * y0 - k[2] * y1 * y2 - k[1] * y1 * y1;
-      else if (i == 2) v = k[1] * y1 * y1;
-      f[p] = v;
+      f[p] = i == 0 ? f0 : (i == 1 ? f1 : (i == 2 ? c2 : 0.0));
     }
   } else {
     for (int r = g.rank; r < c.nr; r += G) {
