@@ -288,11 +288,15 @@ __device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellS
     double* row = S.M[i];
     for (int j = 0; j < n; ++j) row[j] = 0.0;
     if (c.kind == BDFB_ROBERTSON) {
+      // the entries once for every lane, each lane keeping its row (no
+      // divergent per-row FP64 branches)
       const double* k = c.k;
       const double y1 = S.ybuf[1], y2 = S.ybuf[2];
-      if (i == 0) { row[0] = -k[0]; row[1] = k[2] * y2; row[2] = k[2] * y1; }
-      else if (i == 1) { row[0] = k[0]; row[1] = -k[2] * y2 - 2.0 * k[1] * y1; row[2] = -k[2] * y1; }
-      else if (i == 2) { row[1] = 2.0 * k[1] * y1; }
+      const double a = k[2] * y2, b = k[2] * y1, d = 2.0 * k[1] * y1;
+      const double m11 = -a - d;
+      row[0] = i == 0 ? -k[0] : (i == 1 ? k[0] : 0.0);
+      row[1] = i == 0 ? a : (i == 1 ? m11 : d);
+      row[2] = i == 0 ? b : (i == 1 ? -b : 0.0);
     } else {
       const int e1 = __ldg(c.inc_off + i + 1);
       for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
