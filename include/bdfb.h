@@ -224,7 +224,8 @@ int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, doubl
  *   one grouped system (shared step size and order, error test over all
  *   species) with task-local Newton solves per cell on the shared sparse
  *   pattern of M = I - gamma J (bdfb_sparse's LU, one thread per cell);
- *   options mxstep and qmax; (LU entries with fill, reactions and species)
+ *   options mxstep, qmax, interp and lsolver 0 (any other option returns
+ *   BDFB_ILL_INPUT); (LU entries with fill, reactions and species)
  *   x ncell must stay below 2^30 (BDFB_ILL_INPUT otherwise: about 9e5
  *   cells of a 128-species banded network).  bdfb_get_cell_stats gives one row: nst, nfe,
  *   nsetups, nni (summed over cells), ncfn, netf, LU entries with fill,

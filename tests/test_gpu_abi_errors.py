@@ -74,3 +74,32 @@ def test_grid_context_rejects_cell_only_options():
         y = torch.empty(g.y0.size, dtype=torch.float64, device="cuda")
         assert G.integrate(0.01, y) == 0
         assert torch.isfinite(y).all()
+
+
+def test_shared_network_and_line_reject_foreign_options():
+    """a shared-network context takes mxstep, qmax, interp and lsolver 0
+    only; the line's own options take 0/1 (device_loop also -1); each refusal
+    leaves the context integrating"""
+    p = gen.mass_action_banded(32, n=40)
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, shared_network=True) as S:
+        for key, v in ((b"mapping", 32), (b"precision", 1), (b"graph", 1), (b"autotune", 1),
+                       (b"grouped", 1), (b"predictor", 1), (b"lsolver", 1), (b"interp", 2),
+                       (b"qmax", 6), (b"mxstep", 0)):
+            assert L.bdfb_set_option(S.h, key, v) == ILL, key
+        S.set_option("lsolver", 0)
+        S.init(0.0, torch.from_numpy(bdfb.species_major(p)).cuda())
+        y = torch.empty(p.y0.size, dtype=torch.float64, device="cuda")
+        assert S.integrate(1e-4, y) == 0
+        s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+        s1 = np.add.reduceat(bdfb.cell_major(p, y.cpu().numpy()), p.y_off[:-1])
+        assert np.max(np.abs(s1 - s0) / np.abs(s0)) <= 1e-12
+    q = gen.brusselator1d(64, length=10.0)
+    with bdfb.Integrator(q, rtol=1e-6, atol=1e-10) as Q:
+        for key, v in ((b"imex", 2), (b"device_loop", 2), (b"device_loop", -2), (b"precision", 2),
+                       (b"maxl", 0), (b"mapping", 32)):
+            assert L.bdfb_set_option(Q.h, key, v) == ILL, key
+        Q.set_option("imex", 1)
+        Q.init(0.0, torch.from_numpy(q.y0).cuda())
+        y = torch.empty(q.y0.size, dtype=torch.float64, device="cuda")
+        assert Q.integrate(0.1, y) == 0
+        assert torch.isfinite(y).all()
