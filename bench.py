@@ -30,7 +30,7 @@ NCELL = 100_000
 TOUT = 1.0e-3
 RTOL, ATOL = 1.0e-6, 1.0e-10
 SIZES = (3, 10, 32, 54)
-K_CELLS_STEP_DRAM_BYTES = 453_638_400     # 396.5 MB read + 57.2 MB written (see `traffic` below)
+K_CELLS_STEP_DRAM_BYTES = 451_684_352     # 395.1 MB read + 56.6 MB written (see `traffic` below)
 METRIC = "cells integrated to t_end per second at stated error; NVECTOR op HBM GB/s"
 UNIT = "cells/s"
 WORKLOAD = ("mass-action 100k: 100000 independent cells, n ~ U{3,10,32,54}, 2n reactions "
