@@ -210,6 +210,15 @@ def bdf_constants(q):
     return l[:q + 1], out[0], out[1], out[2]
 
 
+def bdf_choose(q, dsm, dqm1=0.0, dqp1=0.0, qmax=QMAX, grown_once=False):
+    """the step-size/order choice after an accepted step: (changed, q_new, eta)"""
+    L = lib()
+    L.or_bdf_choose.argtypes = [C.c_int, C.c_int, C.c_int, _d, _d, _d, _pi, _pd]
+    qn, eta = C.c_int(q), _d(1.0)
+    r = L.or_bdf_choose(q, qmax, int(grown_once), dsm, dqm1, dqp1, C.byref(qn), C.byref(eta))
+    return bool(r), qn.value, eta.value
+
+
 def linear_integrate(A, Cs, t0, y0, tout, rtol=1e-6, atol=1e-10, fixed_h=0.0, fixed_q=0,
                      h0=0.0, mxstep=100000, trace=0, z_init=None, interp=False):
     """y' = A y + sum_k Cs[k] t^k.  Returns (ret, y, stats, trace_y, trace_acor)."""
@@ -431,20 +440,33 @@ def bruss_ark_integrate(p, t0, tout, rtol, atol, mxstep=100000, y0=None):
 MLP_NPARAM = 5642
 
 
-def mlp_forward(params, X):
+def mlp_forward(params, X, bf16=False):
+    """network outputs; bf16: with the BF16 operands of the tensor-core form
+    (weights, inputs and hidden activations rounded, exact accumulation)"""
     params, X = _f64(params), _f64(np.atleast_2d(X))
     Y = np.empty((X.shape[0], 10))
-    lib().or_mlp_forward(_p(params), _i64(X.shape[0]), _p(X), _p(Y))
+    fn = lib().or_mlp_forward_bf16 if bf16 else lib().or_mlp_forward
+    fn(_p(params), _i64(X.shape[0]), _p(X), _p(Y))
     return Y
 
 
-def mlp_loss_grad(params, X, T):
+def mlp_loss_grad(params, X, T, bf16=False):
+    """(loss, gradient); bf16: back-propagation with BF16 operands"""
     params, X, T = _f64(params), _f64(np.atleast_2d(X)), _f64(np.atleast_2d(T))
     g = np.empty(MLP_NPARAM)
     L = lib()
-    L.or_mlp_loss_grad.restype = _d
-    loss = L.or_mlp_loss_grad(_p(params), _i64(X.shape[0]), _p(X), _p(T), _p(g))
+    fn = L.or_mlp_loss_grad_bf16 if bf16 else L.or_mlp_loss_grad
+    fn.restype = _d
+    loss = fn(_p(params), _i64(X.shape[0]), _p(X), _p(T), _p(g))
     return loss, g
+
+
+def bf16_round(x):
+    """elementwise round to nearest bfloat16 (ties to even)"""
+    L = lib()
+    L.or_bf16_round.restype = _d
+    L.or_bf16_round.argtypes = [_d]
+    return np.array([L.or_bf16_round(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
 
 
 def adam_step(params, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

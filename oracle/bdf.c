@@ -352,33 +352,50 @@ static int newton_local(or_bdf* m, double tnew, double Eq, double* acnrm) {
   }
 }
 
-/* choose step size and order after an accepted step (reading: safety
- * factors 6 for orders q and q-1, 10 for q+1; change only when the best
- * eta >= 1.5; eta <= 1e4 before the first increase, <= 10 after; ties keep q,
- * then prefer q-1) */
+/* The step-size and order choice from the three test quantities (reading:
+ * safety factors 6 for orders q and q-1, 10 for q+1; change only when the
+ * best eta >= 1.5; eta <= 1e4 before the first increase, <= 10 after; ties
+ * keep q, then prefer q-1).  dsm = E_q |Delta|, dqm1 = E_{q-1} |z_q| (used
+ * when q > 1), dqp1 = E_{q+1} |Delta - Delta_prev| (used when q < qmax).
+ * Returns 1 and sets *qnew, *eta when h (and maybe q) changes, else 0. */
+int or_bdf_choose(int q, int qmax, int grown_once, double dsm, double dqm1, double dqp1, int* qnew,
+                  double* eta) {
+  double eq = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
+  double eqm1 = 0.0, eqp1 = 0.0;
+  if (q > 1) eqm1 = 1.0 / (pow(6.0 * dqm1, 1.0 / q) + 1e-6);
+  if (q < qmax) eqp1 = 1.0 / (pow(10.0 * dqp1, 1.0 / (q + 2)) + 1e-6);
+  double etam = eq;
+  int qn = q;
+  if (eqm1 > etam) { etam = eqm1; qn = q - 1; }
+  if (eqp1 > etam) { etam = eqp1; qn = q + 1; }
+  if (etam < 1.5) return 0;
+  double cap = grown_once ? 10.0 : 1.0e4;
+  if (etam > cap) etam = cap;
+  *qnew = qn;
+  *eta = etam;
+  return 1;
+}
+
+/* choose step size and order after an accepted step (or_bdf_choose on the
+ * step's norms), every q+1 steps after a change and after every step that
+ * kept h */
 static void select_next(or_bdf* m, double dsm) {
   if (--m->qwait > 0) return;
   int q = m->q;
   double l[OR_QMAX + 2], E[3];
   or_bdf_constants(q, l, E);
-  double eq = 1.0 / (pow(6.0 * dsm, 1.0 / (q + 1)) + 1e-6);
-  double eqm1 = 0.0, eqp1 = 0.0;
-  if (q > 1) {
-    double d = E[1] * wrms(m, Z(m, q));
-    eqm1 = 1.0 / (pow(6.0 * d, 1.0 / q) + 1e-6);
-  }
+  double dqm1 = 0.0, dqp1 = 0.0;
+  if (q > 1) dqm1 = E[1] * wrms(m, Z(m, q));
   if (q < m->opt.qmax) {
     for (int64_t i = 0; i < m->N; ++i) m->b[i] = m->acor[i] - m->acor_prev[i];
-    double d = E[2] * wrms(m, m->b);
-    eqp1 = 1.0 / (pow(10.0 * d, 1.0 / (q + 2)) + 1e-6);
+    dqp1 = E[2] * wrms(m, m->b);
   }
-  double etam = eq;
   int qn = q;
-  if (eqm1 > etam) { etam = eqm1; qn = q - 1; }
-  if (eqp1 > etam) { etam = eqp1; qn = q + 1; }
-  if (etam < 1.5) { m->qwait = 1; return; }
-  double cap = m->grown_once ? 10.0 : 1.0e4;
-  if (etam > cap) etam = cap;
+  double etam = 1.0;
+  if (!or_bdf_choose(q, m->opt.qmax, m->grown_once, dsm, dqm1, dqp1, &qn, &etam)) {
+    m->qwait = 1;
+    return;
+  }
   m->grown_once = 1;
   if (qn == q + 1) {
     double fq = factorial(q + 1);

@@ -108,6 +108,12 @@ or_bdf* or_bdf_create(const or_system* sys, const or_options* opt, double t0, co
 /* integrate to tout; y at tout (or at the point reached) copied to yout */
 int or_bdf_solve(or_bdf* mem, double tout, double* yout);
 void or_bdf_stats(const or_bdf* mem, or_stats* st);
+/* the step-size and order choice after an accepted step from the test
+ * quantities dsm = E_q |Delta|, dqm1 = E_{q-1} |z_q|, dqp1 = E_{q+1}
+ * |Delta - Delta_prev|: returns 1 with the new order and step ratio, or 0
+ * when h is kept */
+int or_bdf_choose(int q, int qmax, int grown_once, double dsm, double dqm1, double dqp1, int* qnew,
+                  double* eta);
 void or_bdf_free(or_bdf* mem);
 /* method constants for order q: l[0..q] (coefficients of prod_{i=1}^q (1 + x/i)),
  * out[0] = E_q, out[1] = E_{q-1} (from z_q), out[2] = E_{q+1} (from Delta - Delta_prev) */
@@ -137,7 +143,8 @@ typedef struct {
 /* Integrate cells [c0, c1) independently from t0 to tout (per-cell step
  * control: every cell owns its h, q and history, Sec. 2 submodel case).
  * y0/yout are packed by y_off; status[c]; stats[c*8 + {nst, nfe, nsetups,
- * nni, ncfn, netf, qlast, 0}] when stats != NULL. */
+ * nni, ncfn, netf, qlast, hlast}] when stats != NULL (hlast: the last step
+ * size, its IEEE bits in the int64 slot). */
 int or_cells_integrate(const or_cells* cells, int64_t c0, int64_t c1, double t0,
                        const double* y0, double tout, double rtol, double atol,
                        int64_t mxstep, double* yout, int32_t* status, int64_t* stats);
@@ -151,7 +158,7 @@ int or_cells_integrate_mode(const or_cells* cells, int64_t c0, int64_t c1, doubl
  * order and error test over every species, block-diagonal Newton matrix with
  * one dense LU per cell, task-local Newton solves (or_system.nblock = ncell).
  * interp: the output mode of or_options.interp.
- * stats = {nst, nfe, nsetups, nni (summed over cells), ncfn, netf, qlast, 0}. */
+ * stats = {nst, nfe, nsetups, nni (summed over cells), ncfn, netf, qlast, hlast bits}. */
 int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y0, double tout,
                                double rtol, double atol, int64_t mxstep, int interp,
                                double* yout, int64_t* stats);
@@ -194,6 +201,11 @@ int or_bruss_gmres(const or_bruss* p, const double* y, double gamma, const doubl
 int or_mlp_nparam(void);
 void or_mlp_forward(const double* p, int64_t nrows, const double* X, double* Y);
 double or_mlp_loss_grad(const double* p, int64_t nrows, const double* X, const double* T, double* grad);
+/* the same with BF16 operands (weights, inputs, hidden activations, dY, dH)
+ * and exact accumulation: the learned guess's arithmetic */
+double or_bf16_round(double x);
+void or_mlp_forward_bf16(const double* p, int64_t nrows, const double* X, double* Y);
+double or_mlp_loss_grad_bf16(const double* p, int64_t nrows, const double* X, const double* T, double* grad);
 void or_adam_step(int64_t n, double* p, const double* g, double* m, double* v, int64_t t, double lr,
                   double b1, double b2, double eps);
 

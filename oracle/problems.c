@@ -161,7 +161,8 @@ int or_cells_integrate_mode(const or_cells* cells, int64_t c0, int64_t c1, doubl
         or_bdf_stats(m, &st);
         int64_t* s = stats + 8 * c;
         s[0] = st.nst; s[1] = st.nfe; s[2] = st.nsetups; s[3] = st.nni;
-        s[4] = st.ncfn; s[5] = st.netf; s[6] = st.qlast; s[7] = 0;
+        s[4] = st.ncfn; s[5] = st.netf; s[6] = st.qlast;
+        memcpy(&s[7], &st.hlast, sizeof st.hlast);   /* the last step size, as its bits */
       }
       or_bdf_free(m);
     }
@@ -234,7 +235,8 @@ int or_cells_integrate_grouped(const or_cells* cells, double t0, const double* y
         or_stats st;
         or_bdf_stats(m, &st);
         stats[0] = st.nst; stats[1] = st.nfe; stats[2] = st.nsetups; stats[3] = st.nni;
-        stats[4] = st.ncfn; stats[5] = st.netf; stats[6] = st.qlast; stats[7] = 0;
+        stats[4] = st.ncfn; stats[5] = st.netf; stats[6] = st.qlast;
+        memcpy(&stats[7], &st.hlast, sizeof st.hlast);
       }
       or_bdf_free(m);
     }
@@ -298,7 +300,8 @@ int or_linear_integrate(int64_t N, const double* A, int ncoef, const double* C, 
     or_bdf_stats(m, &st);
     if (stats) {
       stats[0] = st.nst; stats[1] = st.nfe; stats[2] = st.nsetups; stats[3] = st.nni;
-      stats[4] = st.ncfn; stats[5] = st.netf; stats[6] = st.qlast; stats[7] = 0;
+      stats[4] = st.ncfn; stats[5] = st.netf; stats[6] = st.qlast;
+      memcpy(&stats[7], &st.hlast, sizeof st.hlast);
     }
     if (ntrace) *ntrace = opt->trace_cap < st.nst ? opt->trace_cap : st.nst;
   }
