@@ -113,7 +113,9 @@ int64_t bdfb_nv_work_doubles(int64_t n, int nv);
  *    BDFB_ILL_INPUT.  Any n >= 0.
  *  - The first call on a device looks up the scratch's device address (a
  *    runtime query, no allocation); make that first call before any stream
- *    capture on that device.
+ *    capture on that device.  The address is cached for the life of the
+ *    process: cudaDeviceReset on that device invalidates it, so do not call
+ *    this entry point on a device after resetting it.
  *  - All calls on one device share the scratch: calls that overlap on the GPU
  *    (other streams or host threads) race, so serialise them.  Each call
  *    clears the scratch's arrival counter on `stream` before using it.
@@ -138,9 +140,12 @@ int bdfb_batched_lu_solve(int64_t nb, int n, const double* lu, const int32_t* pi
  * block a (not modified) solve a x = b: LU of the block in FP32, then
  * x += LU^{-1} r with the FP64 residual r = b - a x until the normwise
  * backward error |r|_inf / (|a|_inf |x|_inf + |b|_inf) <= 1e-12, at most 5
- * sweeps.  sweeps[blk] = sweeps used, -1 if 1e-12 was not reached (x holds
- * the last iterate), -2 if the FP32 factorisation met a zero pivot.
- * 1 <= n <= 64; all arrays device memory. */
+ * sweeps.  A block that does not reach 1e-12 in 5 sweeps (or whose FP32
+ * factorisation meets a zero pivot) is factored and solved in FP64 by
+ * partially pivoted LU instead, as the integrator does.  sweeps[blk] =
+ * refinement sweeps used (1..5), 0 when the FP64 fallback solved the block,
+ * -2 when the FP64 factorisation met an exactly zero pivot as well (x then
+ * holds the last refined iterate).  1 <= n <= 64; all arrays device memory. */
 int bdfb_batched_solve_mixed(int64_t nb, int n, const double* a, const double* b, double* x,
                              int32_t* sweeps, void* stream);
 

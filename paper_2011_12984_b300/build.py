@@ -3,7 +3,9 @@
     python -m paper_2011_12984_b300.build [--force] [--verbose]
 
 The library is plain CUDA C++ behind a C ABI (``include/bdfb.h``); it links
-the CUDA runtime statically and does not depend on PyTorch.
+the CUDA runtime statically and does not depend on PyTorch.  Each source is
+compiled to an object under ``_build/`` (in parallel; an object is rebuilt
+when its source or any header is newer), then the objects are linked.
 """
 from __future__ import annotations
 
@@ -11,37 +13,66 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libbdfb.so")
+OBJDIR = os.path.join(ROOT, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC"]
 
 
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def headers():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "bdfb.h")]
+
+
 def deps():
-    return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "bdfb.h")]
+    return sources() + headers()
+
+
+def _newest(paths):
+    return max(os.path.getmtime(p) for p in paths)
 
 
 def up_to_date() -> bool:
-    return os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps())
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest(deps() + [__file__])
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [NVCC, "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-o", tmp, *sources()]
+def _obj(src):
+    return os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+
+
+def _compile(src, force, verbose):
+    obj = _obj(src)
+    hdr = _newest(headers() + [__file__])
+    if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr):
+        return obj
+    tmp = obj + ".%d.tmp" % os.getpid()
+    cmd = [NVCC, *FLAGS, "-I", INCLUDE, "-c", "-o", tmp, src]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     subprocess.run(cmd, check=True)
+    os.replace(tmp, obj)
+    return obj
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not verbose and up_to_date():
+        return LIB
+    os.makedirs(OBJDIR, exist_ok=True)
+    srcs = sources()
+    with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, force, verbose), srcs))
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -736,8 +736,10 @@ int ark_create(int64_t nx, double A, double B, double eps, double c, double len,
     const int64_t want = std::max<int64_t>((nx + 4 * AT - 1) / (4 * AT), sm_count());
     g->coop_blocks[pr] = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
   }
-  int coop = 0;
-  if (ok && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, 0) == cudaSuccess && !coop) g->device_loop = 0;
+  int coop = 0, dev = 0;
+  if (ok && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && !coop)
+    g->device_loop = 0;
   if (ok) alloc((void**)&g->cpart, 2 * (size_t)std::max(g->coop_blocks[0], g->coop_blocks[1]) * sizeof(double));
   if (!ok) {
     ark_destroy(g);
@@ -773,8 +775,9 @@ int ark_set_mxstep(ArkLine* g, int64_t v) {
 
 int ark_set_device_loop(ArkLine* g, int on) {
   if (on < -1 || on > 1) return BDFB_ILL_INPUT;
-  int coop = 0;
-  if (on && (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, 0) != cudaSuccess || !coop))
+  int coop = 0, dev = 0;
+  if (on && (cudaGetDevice(&dev) != cudaSuccess ||
+             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop))
     return BDFB_ILL_INPUT;
   g->device_loop = on;
   return 0;

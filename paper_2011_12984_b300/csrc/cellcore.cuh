@@ -170,10 +170,59 @@ __device__ __forceinline__ double wrms2(const Grp<G>& g, int n, double rn, const
 }
 
 // step-size ratio 1 / ((safety^2 d2)^(e) + 1e-6) from a squared error norm d2,
-// in FP32: it only scales the next step (about 7 significant digits are ample)
+// in FP32 (about 7 significant digits): the seed of eta64 and the value the
+// step/order choice is made on when no two candidates are near a tie
 __device__ __forceinline__ double eta_from(double d2, float safety2, float e) {
   const float x = fmaxf((float)fmin(d2 * safety2, 1.0e30), 1.0e-37f);
   return (double)(1.0f / (exp2f(e * __log2f(x)) + 1.0e-6f));
+}
+
+// 2^n as a double for -1022 <= n <= 1023 (built from the exponent bits)
+__device__ __forceinline__ double pow2i(int n) {
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+
+// 1 / a for a > 0 normal: the FP32 reciprocal refined by one Newton step,
+// y <- y (2 - a y), in FP64 (relative error about 2^-47)
+__device__ __forceinline__ double recip64(double a) {
+  const double y = (double)__frcp_rn((float)a);
+  return y * fma(-a, y, 2.0);
+}
+
+// x^(1/k) for an even k in [2, 14] and x >= 0, to about 1e-13 relative: the
+// argument is reduced by an exact power of two 2^(jk) (root scaled by 2^j),
+// an FP32 root of the reduced argument seeds one Newton step for r^k = x,
+// r <- r + r (x / r^k - 1) / k, in FP64.
+__device__ __forceinline__ double root_k(double x, int k, double rk) {
+  if (!(x > 0.0)) return 0.0;
+  if (!(x < 1.0e308)) return x;
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+  const int j = e / k;
+  const double xs = x * pow2i(-j * k);          // |log2 xs| < k + 1: inside the FP32 range
+  const double r = (double)exp2f(__log2f((float)xs) / (float)k);
+  const double s = r * r;
+  double p = s;                                 // r^k = s^(k/2)
+  for (int i = 2; i < k; i += 2) p *= s;
+  const double t = fma(xs, recip64(p), -1.0);   // x / r^k - 1, about 1e-7
+  return fma(r * t, rk, r) * pow2i(j);
+}
+
+// 1 / k for an even k in [2, 14] without an FP64 division
+__device__ __forceinline__ double inv_even(int k) {
+  switch (k) {
+    case 2: return 1.0 / 2.0;
+    case 4: return 1.0 / 4.0;
+    case 6: return 1.0 / 6.0;
+    case 8: return 1.0 / 8.0;
+    case 10: return 1.0 / 10.0;
+    case 12: return 1.0 / 12.0;
+    default: return 1.0 / 14.0;
+  }
+}
+
+// the FP64 counterpart of eta_from: 1 / ((safety^2 d2)^(1/k) + 1e-6), k even
+__device__ __forceinline__ double eta64(double d2, double safety2, int k) {
+  return recip64(root_k(d2 * safety2, k, inv_even(k)) + 1.0e-6);
 }
 
 // finiteness on the integer pipe: an IEEE double is inf or NaN exactly when

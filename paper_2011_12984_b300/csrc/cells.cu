@@ -43,7 +43,7 @@ struct Consts {
 };
 
 struct CellState {
-  double t, h, gammap, crate, hlast;
+  double t, h, gammap, crate, hlast;   // crate: the squared Newton rate R^2
   int32_t q, qwait, nst, nstlp;
   int32_t nfe, nsetups, nni, ncfn;
   int32_t netf, flags, status, qlast;
@@ -240,17 +240,25 @@ __device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, cons
 
 // choose h and q after an accepted step (same rules as the oracle: safety
 // 6 / 6 / 10, change only if the best eta >= 1.5, eta <= 1e4 before the first
-// increase and <= 10 after, ties keep q then prefer q - 1)
+// increase and <= 10 after, ties keep q then prefer q - 1).  The candidates are
+// first formed in FP32 (eta_from); where two of them, or the best and the 1.5
+// threshold, lie within 1e-5 of each other (far above the FP32 error) all are
+// formed to FP64 accuracy (eta64) before choosing, so the choice is the one
+// FP64 arithmetic makes; the eta applied is always the FP64 one.
+__device__ __forceinline__ bool near_tie(double a, double b) { return fabs(a - b) <= 1.0e-5 * fmax(a, b); }
+
 template <int G, int NMAX>
 __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, int n, double rn,
                                             Cell<G, NMAX>& C, double dsm2) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   if (--C.qwait > 0) return;
   const int q = C.q;
-  // eta = 1 / ((safety * dsm)^(1/order) + 1e-6) from squared norms (FP32 ratio)
-  const double eq = eta_from(dsm2, 36.0f, 0.5f / (q + 1));
-  double eqm1 = 0.0, eqp1 = 0.0;
-  if (q > 1) {
+  const bool hm = q > 1, hp = q < P.qmax;
+  // squared test quantities of orders q, q - 1 (E_{q-1} |z_q|), q + 1
+  // (E_{q+1} |Delta - Delta_prev|); eta = 1 / ((safety^2 x)^(1/k) + 1e-6)
+  const double xq = dsm2;
+  double xm = 0.0, xp = 0.0;
+  if (hm) {
     double zq[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
@@ -261,13 +269,23 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
       zq[p] = v;
     }
     const double e = P.K.E[q][1];
-    eqm1 = eta_from(e * e * wrms2(g, n, rn, zq, C.ewt), 36.0f, 0.5f / q);
+    xm = e * e * wrms2(g, n, rn, zq, C.ewt);
   }
-  if (q < P.qmax) {
+  if (hp) {
 #pragma unroll
     for (int p = 0; p < NPL; ++p) C.b[p] = C.acor[p] - C.acorp[p];
     const double e = P.K.E[q][2];
-    eqp1 = eta_from(e * e * wrms2(g, n, rn, C.b, C.ewt), 100.0f, 0.5f / (q + 2));
+    xp = e * e * wrms2(g, n, rn, C.b, C.ewt);
+  }
+  double eq = eta_from(xq, 36.0f, 0.5f / (q + 1));
+  double eqm1 = hm ? eta_from(xm, 36.0f, 0.5f / q) : 0.0;
+  double eqp1 = hp ? eta_from(xp, 100.0f, 0.5f / (q + 2)) : 0.0;
+  const bool tie = near_tie(eq, 1.5) || (hm && (near_tie(eqm1, eq) || near_tie(eqm1, 1.5))) ||
+                   (hp && (near_tie(eqp1, eq) || near_tie(eqp1, 1.5) || (hm && near_tie(eqp1, eqm1))));
+  if (tie) {
+    eq = eta64(xq, 36.0, 2 * (q + 1));
+    if (hm) eqm1 = eta64(xm, 36.0, 2 * q);
+    if (hp) eqp1 = eta64(xp, 100.0, 2 * (q + 2));
   }
   double etam = eq;
   int qn = q;
@@ -275,6 +293,8 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
   if (eqp1 > etam) { etam = eqp1; qn = q + 1; }
   if (etam < 1.5) { C.qwait = 1; return; }
   const double cap = (C.flags & F_GROWN) ? 10.0 : 1.0e4;
+  if (!tie && etam < cap * 1.00001)
+    etam = qn == q ? eta64(xq, 36.0, 2 * (q + 1)) : (qn < q ? eta64(xm, 36.0, 2 * q) : eta64(xp, 100.0, 2 * (q + 2)));
   if (etam > cap) etam = cap;
   C.flags |= F_GROWN;
   if (qn == q + 1) {
@@ -513,6 +533,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
             } else {
               // refinement stalled: factor this setup's M in FP64 instead (in
               // the cell's global workspace) until the next setup
+              if (Mg == nullptr) { restore_z(g, n, S, C); C.status = BDFB_MEM_FAIL; return true; }  // never write through null
               C.nref_fb++;
               form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
               if (lu_factor<G, NMAX, double, true>(g, Mg, S.dinv, S.perm, n)) {
@@ -543,14 +564,19 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
 #pragma unroll
         for (int p = 0; p < NPL; ++p) C.acor[p] += C.b[p];
         C.nni++;
-        if (it > 1) C.crate = fmax(0.3 * C.crate, (double)sqrtf((float)(del2 / delp2)));
+        // the rate R = max(0.3 R_prev, |del| / |del_prev|) is carried squared
+        // (crate holds R^2; the division only when the ratio wins)
+        if (it > 1) {
+          const double r2 = 0.09 * C.crate;
+          C.crate = r2 * delp2 >= del2 ? r2 : del2 / delp2;
+        }
         // the rate carried over from earlier solves holds between the zero
         // start and the solution; a guessed start is tested with it only when
         // the guess lies closer to the new iterate than zero does
         // (|del| <= |Delta|), else with rate 1
-        double cr = fmin(1.0, C.crate);
-        if (nzguess && it == 1 && !(del2 <= wrms2(g, n, C.rn, C.acor, C.ewt))) cr = 1.0;
-        if (del2 * cr * cr * eq2 <= 1.0) {       // |del| min(1, rate) E_q / 0.1 <= 1
+        double cr2 = fmin(1.0, C.crate);
+        if (nzguess && it == 1 && !(del2 <= wrms2(g, n, C.rn, C.acor, C.ewt))) cr2 = 1.0;
+        if (del2 * cr2 * eq2 <= 1.0) {           // |del| min(1, R) E_q / 0.1 <= 1
           acnrm2 = (it == 1 && !guess) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
           conv = true;
           break;
@@ -590,7 +616,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     C.netf++;
     if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
     if (C.nef < 3) {
-      double eta = eta_from(dsm2, 36.0f, 0.5f / (q + 1));
+      double eta = eta64(dsm2, 36.0, 2 * (q + 1));
       if (!(eta >= 0.1)) eta = 0.1;
       if (C.nef >= 2 && eta > 0.2) eta = 0.2;
       rescale(C, eta);
@@ -830,7 +856,7 @@ struct GroupParams {
   const int64_t* lu_off;
   double* dinv;                  // per species
   int16_t* perm;                 // per species
-  double* crate;                 // per cell
+  double* crate;                 // per cell: the squared Newton rate R^2
   int* failed;
   unsigned long long* iters;     // [0] completed iterations (sum), [1] RHS evaluations (max)
 };
@@ -928,9 +954,11 @@ __device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& G
     const double del2 = wrms2(g, n, rn, b, w);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) acor[p] += b[p];
-    if (it > 1) crate = fmax(0.3 * crate, (double)sqrtf((float)(del2 / delp2)));
-    const double cr = fmin(1.0, crate);
-    if (del2 * cr * cr * eq2 <= 1.0) { conv = true; break; }
+    if (it > 1) {                 // R^2 = max(0.09 R_prev^2, del2 / delp2)
+      const double r2 = 0.09 * crate;
+      crate = r2 * delp2 >= del2 ? r2 : del2 / delp2;
+    }
+    if (del2 * fmin(1.0, crate) * eq2 <= 1.0) { conv = true; break; }
     if (it >= 2 && del2 > 4.0 * delp2) break;
     delp2 = del2;
   }
@@ -1032,8 +1060,9 @@ __global__ void __launch_bounds__(32) k_lu_solve(int64_t nb, int n, const double
 
 // Mixed-precision solve of dense blocks, the same scheme as the integrator's:
 // FP32 Gauss-Jordan inverse of each block, FP64 dense residual r = b - A x,
-// x += inv32 r until |r|/(|A| |x| + |b|) <= 1e-12 (at most MAXREF sweeps;
-// sweeps[b] = -1 if not reached).
+// x += inv32 r until |r|/(|A| |x| + |b|) <= 1e-12 (at most MAXREF sweeps);
+// a block that does not get there is solved by FP64 LU (sweeps[b] = 0), and
+// sweeps[b] = -2 only when that factorisation meets a zero pivot too.
 __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const double* a,
                                                    const double* bvec, double* xout, int32_t* sweeps) {
   extern __shared__ __align__(16) char smem[];
@@ -1104,12 +1133,25 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
       xn = gmaxd(g, xn);
       if (rn <= BERR_TOL * (anorm * xn + bn)) { sw = it; break; }
     }
+    if (sw < 0) {
+      // refinement stalled (or the FP32 factorisation met a zero pivot): the
+      // block is factored and solved in FP64 instead, as the integrator does
+      g.sync();
+      if (lu_factor<32, LU_NMAX, double>(g, A, S.dinv, S.perm, n) == 0) {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) x[p] = b[p];
+        lu_solve<32, NPL, LU_NMAX, double>(g, A, S.dinv, S.perm, S.ybuf, n, x);
+        sw = 0;
+      } else {
+        sw = -2;
+      }
+    }
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
       const int i = g.rank + 32 * p;
       if (i < n) xout[blk * n + i] = x[p];
     }
-    if (g.rank == 0) sweeps[blk] = info ? -2 : sw;
+    if (g.rank == 0) sweeps[blk] = sw;
     g.sync();
   }
 }
@@ -1762,6 +1804,8 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, in
     const int kv = v == 4 ? single : v;
     const cells_kernel_t kf = var_kernel(pr, kv);
     if (!kf) return BDFB_ILL_INPUT;
+    // mixed precision: the launched variant's FP64 fallback workspace must exist
+    if (pr == 1 && !ctx->d_fbws[kv]) return BDFB_MEM_FAIL;
     cudaStream_t cs = ctx->cstream[v];
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
     const int grid = std::min(ctx->pgrid[pr][kv], t1 - t0);
@@ -2113,9 +2157,11 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.tile_cells = S.d_tcells;
   P.ntiles = S.ntiles;
   if (pr == 1) {
+    // the workspace of the variant each range is launched on (variant 4's
+    // range runs on `single` under the one-warp-per-cell schedule)
     for (int v = 0; v < NVAR; ++v)
       if (S.vend[v] > S.vbeg[v]) {
-        const int r = ensure_fbws(ctx, v);
+        const int r = ensure_fbws(ctx, v == 4 ? single : v);
         if (r) return r;
       }
   }

@@ -537,7 +537,9 @@ static std::mutex g_noalloc_mu;
 
 // Device address of the scratch on the current device.  The host-side name
 // g_noalloc_scratch is only a stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the process's life; a
+// cudaDeviceReset reloads the module and leaves the cached address stale
+// (the entry point's documentation rules that use out).
 static int noalloc_scratch(double** out) {
   int dev = 0;
   BDFB_CUDA(cudaGetDevice(&dev));

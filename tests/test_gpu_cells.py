@@ -1,15 +1,37 @@
 """GPU parity of the batched per-cell BDF/Newton integrator against the oracle.
 
-Final states are compared with an oracle run at rtol = 1e-10 (the truth) in
-units of the run's own error weights, err_c = max_i |y_i - y*_i| /
-(rtol |y*_i| + atol).  Local error control does not bound the global error,
-and the oracle run at the same tolerance (same method, other rounding, so a
-slightly different but equally valid step sequence) exceeds 10 on some
-cells.  The bar: every cell within max(10, 1.5x the oracle's worst cell), the
-GPU's median and 99th percentile no wider than the oracle's, the share of
-cells within 10 no more than 2 points below the oracle's, and mean step counts
-within 5% of the oracle's.
+The comparison is cell by cell, with the oracle run at the same tolerances on
+the same inputs.  The GPU takes the oracle's decisions (Newton convergence,
+error test, Jacobian refresh, step size and order) in FP64, so the two differ
+only by the rounding of reductions and contracted multiply-adds.  The
+mass-action right-hand sides cancel terms up to ~1e8 times larger than
+their sum, so even such rounding differences move the step sizes a little
+(the oracle built with and without FMA contraction: final step sizes of
+cells with identical counters differ by 3.5e-8 relative at the median and
+up to 1e-2), which is why cells are sorted into three tiers:
+
+* same step sequence: the counters (steps, right-hand sides, setups, Newton
+  iterations, convergence and error-test failures), the last order and the
+  last step size (to 1e-6 relative) equal the oracle's.  The final states
+  must agree elementwise, max_i |y_i - y^o_i| / (rtol |y^o_i| + atol) <= 1e-3
+  (a step ratio formed in FP32 moved such cells by up to 2 units);
+* same decisions, drifted step sizes (counters equal, last step not): each
+  such cell within 3 e^o_c + 10 of the truth, e^o_c being the oracle's own
+  error on that cell, both in units of the run's error weights against the
+  oracle at rtol = 1e-10;
+* other cells (a ratio or a norm within rounding of a threshold sent the two
+  onto different, equally valid step sequences): within the range of the
+  oracle's own errors on the workload, max(10, 1.5 max_c e^o_c).
+
+The least shares are 0.65 of the cells in the first tier and 0.95 in the
+first two (measured: 0.70-0.84 and >= 0.98 on the mass-action tests), 0.9
+in the first on Robertson (0.94) and 0.45 on the shared 10-species network
+(0.56, its cells end their runs in a stiffer regime); the error
+distributions and the mean step count must follow the oracle's.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -19,6 +41,10 @@ from paper_2011_12984_b300 import bdfb, gen
 
 pytestmark = pytest.mark.gpu
 THREADS = max(1, min(32, oracle.host_threads()))
+MATCH_TOL = 1e-3          # weighted units, cells on the oracle's step sequence
+MATCH_TOL_INTERP = 1e-2   # the same, interpolated output (see check_against_oracle)
+H_TOL = 1e-6              # last step size, relative, for the same step sequence
+COUNTERS = [0, 1, 2, 3, 4, 5]   # nst, nfe, nsetups, nni, ncfn, netf
 
 
 def werr(y, yr, prob, rtol, atol):
@@ -44,23 +70,62 @@ def run_gpu(prob, t0, tout, rtol, atol, device_io=True, **opts):
         return ret, y, st, I.cell_stats(), I.stats()
 
 
-def check_against_oracle(prob, tout, rtol, atol, y, cstats, max_factor=1.5):
-    """max_factor: per-cell bound as a multiple of the oracle's worst cell
-    (1.5 for runs that take the oracle's decisions up to rounding; runs whose
-    Newton iterations start elsewhere differ as two valid integrations do)"""
-    yo, so, sto = oracle.integrate_cells(prob, 0.0, tout, rtol, atol, threads=THREADS)
+def tiers(cs, sto):
+    """(same step sequence, same decisions) masks from the per-cell counters
+    of the GPU (cs) and of the oracle (sto): columns 0..5 the counters, 6 the
+    last order, 7 the last step size's bits"""
+    same = np.all(cs[:, COUNTERS] == sto[:, COUNTERS], axis=1)
+    hg = np.ascontiguousarray(cs[:, 7]).view(np.float64)
+    ho = np.ascontiguousarray(sto[:, 7]).view(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        hclose = np.abs(hg - ho) <= H_TOL * np.abs(ho)
+    seq = same & (cs[:, 6] == sto[:, 6]) & hclose
+    return seq, same
+
+
+def check_against_oracle(prob, tout, rtol, atol, y, cstats, min_seq=0.65, min_same=0.95, same_decisions=True,
+                         interp=False, wide_factor=1.5):
+    """Cell-by-cell parity (module docstring).  min_seq, min_same: least
+    shares of cells on the oracle's step sequence and with its decisions.
+    same_decisions=False for runs whose Newton iterations start elsewhere
+    than the oracle's (the learned guess): no cell is expected to follow
+    the oracle's step sequence, every cell is held to the third tier's bound
+    max(10, wide_factor max_c e^o_c) and the distributions.  interp: both sides in the interpolated output
+    mode, where the output polynomial is evaluated at s = (tout - t_n) / h:
+    a step-time drift of one part in 1e6 of h moves it by up to that part of
+    a whole step's change (measured: up to 3e-3 units against 7e-5 for the
+    clamped output of the same cells), so the first tier's bar is 1e-2.
+    Returns (e, e^o, seq, same)."""
+    yo, so, sto = oracle.integrate_cells(prob, 0.0, tout, rtol, atol, threads=THREADS, interp=interp)
     yt, stt, _ = oracle.integrate_cells(prob, 0.0, tout, 1e-10, 1e-14, threads=THREADS)
     assert np.all(so == 0) and np.all(stt == 0)
     eg = werr(y, yt, prob, rtol, atol)
     eo = werr(yo, yt, prob, rtol, atol)
-    bound = max(10.0, max_factor * eo.max())
-    bad = eg > bound
-    assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10], bound)
+    seq, same = tiers(cstats, sto)
+    wide = max(10.0, wide_factor * eo.max())
+    d = werr(y, yo, prob, rtol, atol)
+    log = os.environ.get("BDFB_PARITY_LOG")
+    if log:                                   # record the tier shares of this comparison
+        with open(log, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""), "ncell": int(prob.ncell),
+                                "seq": float(seq.mean()), "same": float(same.mean()),
+                                "d_seq_max": float(d[seq].max()) if seq.any() else None}) + "\n")
+    if same_decisions:
+        assert seq.mean() >= min_seq, (seq.mean(), min_seq)
+        assert same.mean() >= min_same, (same.mean(), min_same)
+        bad = seq & (d > (MATCH_TOL_INTERP if interp else MATCH_TOL))
+        assert not bad.any(), (np.nonzero(bad)[0][:10], d[bad][:10])
+        bad = same & ~seq & (eg > 3.0 * eo + 10.0)
+        assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], eo[bad][:10])
+        bad = ~same & (eg > wide)
+    else:
+        bad = eg > wide
+    assert not bad.any(), (np.nonzero(bad)[0][:10], eg[bad][:10], wide)
     assert np.percentile(eg, 50) <= 1.5 * np.percentile(eo, 50) + 1.0
     assert np.percentile(eg, 99) <= 1.5 * np.percentile(eo, 99) + 1.0
     assert (eg <= 10).mean() >= (eo <= 10).mean() - 0.02
     assert abs(cstats[:, 0].mean() / sto[:, 0].mean() - 1.0) < 0.05
-    return eg, eo
+    return eg, eo, seq, same
 
 
 @pytest.mark.parametrize("opts", [{}, {"autotune": 1}])
@@ -72,7 +137,7 @@ def test_robertson_1000_cells(opts):
     ret, y, st, cs, stats = run_gpu(p, 0.0, 40.0, 1e-4, 1e-8, **opts)
     assert ret == 0 and np.all(st == 0)
     assert np.max(np.abs(y.reshape(-1, 3).sum(axis=1) - 1.0)) <= 1e-12   # sum y = 1
-    check_against_oracle(p, 40.0, 1e-4, 1e-8, y, cs)
+    check_against_oracle(p, 40.0, 1e-4, 1e-8, y, cs, min_seq=0.9, min_same=1.0)
     assert stats["nsteps"] == cs[:, 0].sum()
 
 

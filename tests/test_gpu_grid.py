@@ -1,8 +1,15 @@
 """GPU parity of the grouped grid integrator (Brusselator reaction-diffusion,
 one coupled system, Newton + left-preconditioned GMRES) against the oracle's
-grouped integrator: same method, same readings, so final states agree with an
-rtol = 1e-10 oracle truth as well as the oracle at the same tolerance does,
-and step counts agree."""
+grouped integrator.  The host-side step control takes the oracle's decisions
+in FP64 on norms that differ only by reduction order, so the whole run
+follows the oracle's step sequence: every counter (steps, right-hand sides,
+setups, Newton and GMRES iterations, failures) must equal the oracle's and
+the final states agree elementwise to 1e-3 of the error weights (FP64; the
+runs measured agree to 4e-8), or 2e-3 with the preconditioner and the GMRES
+operator in FP32 (precision 1: each Krylov product carries FP32 rounding, the
+runs measured agree to 1.3e-4).  Grids of 6^3, 10^3 and 32^3 (98 304
+unknowns: many blocks per reduction and a 3-D launch tiling) and lines of
+40 and 200 points."""
 import numpy as np
 import pytest
 import torch
@@ -28,10 +35,24 @@ def run_grid(p, tout, rtol, atol, y0=None, maxl=5, device_io=True, precision=0):
         return ret, y, I.cell_stats()[0], I.stats()
 
 
+MATCH_TOL = {0: 1e-3, 1: 2e-3}
+
+
+def check_system(y, gs, yo, so, yt, rtol, atol, precision):
+    """same step sequence as the oracle: equal counters, elementwise agreement"""
+    assert np.array_equal(gs[:8], so[:8]), (gs[:8], so[:8])
+    d = np.max(np.abs(y - yo) / (rtol * np.abs(yo) + atol))
+    assert d <= MATCH_TOL[precision], d
+    w = rtol * np.abs(yt) + atol
+    eg, eo = np.max(np.abs(y - yt) / w), np.max(np.abs(yo - yt) / w)
+    assert eg <= eo + 10.0 * MATCH_TOL[precision], (eg, eo)
+    assert gs[6] > 0                                         # GMRES iterations
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("nx,tout", [(6, 0.05), (10, 0.02)])
+@pytest.mark.parametrize("nx,tout", [(6, 0.05), (10, 0.02), (32, 0.1)])
 def test_grid_matches_oracle(nx, tout, precision):
-    """precision 1: FP32 preconditioner and GMRES operator (same bars)"""
+    """precision 1: FP32 preconditioner and GMRES operator"""
     p = gen.brusselator3d(nx, seed=nx)
     rtol, atol = 1e-6, 1e-10
     ret, y, gs, _ = run_grid(p, tout, rtol, atol, precision=precision)
@@ -39,12 +60,7 @@ def test_grid_matches_oracle(nx, tout, precision):
     ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
     assert ro == 0 and rt == 0
-    w = rtol * np.abs(yt) + atol
-    eg = np.max(np.abs(y - yt) / w)
-    eo = np.max(np.abs(yo - yt) / w)
-    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
-    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)        # steps
-    assert gs[6] > 0                                         # GMRES iterations
+    check_system(y, gs, yo, so, yt, rtol, atol, precision)
 
 
 def test_grid_steady_state_stays():
@@ -105,12 +121,7 @@ def test_line_matches_oracle(nx, length, tout, precision):
     ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, tout, 1e-10, 1e-14, maxl=5)
     assert ro == 0 and rt == 0
-    w = rtol * np.abs(yt) + atol
-    eg = np.max(np.abs(y - yt) / w)
-    eo = np.max(np.abs(yo - yt) / w)
-    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
-    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)
-    assert gs[6] > 0
+    check_system(y, gs, yo, so, yt, rtol, atol, precision)
 
 
 def test_line_uniform_steady_state_stays_at_1e6_points():
@@ -152,7 +163,4 @@ def test_grid_krylov_dimensions(maxl):
     ro, yo, so = oracle.bruss_integrate(p, 0.0, 0.05, 1e-6, 1e-10, maxl=maxl)
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, 0.05, 1e-10, 1e-14, maxl=5)
     assert ro == 0 and rt == 0
-    w = 1e-6 * np.abs(yt) + 1e-10
-    eg, eo = np.max(np.abs(y - yt) / w), np.max(np.abs(yo - yt) / w)
-    assert eg <= max(10.0, 1.5 * eo), (eg, eo)
-    assert abs(gs[0] / so[0] - 1.0) <= 0.1, (gs, so)
+    check_system(y, gs, yo, so, yt, 1e-6, 1e-10, 0)

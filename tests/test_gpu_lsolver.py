@@ -5,10 +5,10 @@ of the demonstration problem's task-local solver, Sec. 7, for any block
 size), and each Newton iteration solves by one product with the inverse.
 
 In exact arithmetic the solves equal the LU ones, so the run takes the
-oracle's decisions up to rounding: the bars of the per-cell parity tests
-(every cell within max(10, 1.5x the oracle's worst cell) of an rtol 1e-10
-truth in units of the run's error weights, median and 99th percentile no
-wider than the oracle's, mean step counts within 5%), in every kernel
+oracle's decisions up to rounding: the cell-by-cell bars of the per-cell
+parity tests (cells with the oracle's counters agree with it to 1e-3 of the
+error weights; every cell within 3x its oracle error + 10 of an rtol 1e-10
+truth; distributions and mean step counts as the oracle's), in every kernel
 variant (automatic tiles, one warp per cell, autotuned), on Robertson and
 on mass action; linear invariants to rounding; options that cannot combine
 with it are refused.
@@ -41,15 +41,9 @@ def run(prob, tout, rtol, atol, **opts):
         return y.cpu().numpy(), I.cell_stats(), I.mapping()
 
 
-def check(p, tout, rtol, atol, y, cs):
-    yo, so, sto = oracle.integrate_cells(p, 0.0, tout, rtol, atol, threads=THREADS)
-    yt, stt, _ = oracle.integrate_cells(p, 0.0, tout, 1e-10, 1e-14, threads=THREADS)
-    assert np.all(so == 0) and np.all(stt == 0)
-    eg, eo = werr(y, yt, p, rtol, atol), werr(yo, yt, p, rtol, atol)
-    assert np.all(eg <= max(10.0, 1.5 * eo.max())), (eg.max(), eo.max())
-    assert np.percentile(eg, 50) <= 1.5 * np.percentile(eo, 50) + 1.0
-    assert np.percentile(eg, 99) <= 1.5 * np.percentile(eo, 99) + 1.0
-    assert abs(cs[:, 0].mean() / sto[:, 0].mean() - 1.0) < 0.05
+def check(p, tout, rtol, atol, y, cs, **bars):
+    from test_gpu_cells import check_against_oracle
+    check_against_oracle(p, tout, rtol, atol, y, cs, **bars)
 
 
 @pytest.mark.parametrize("opts", [{}, {"mapping": 32}, {"autotune": 1}, {"graph": 1}])

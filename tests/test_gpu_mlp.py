@@ -1,10 +1,14 @@
 """GPU parity of the learned Newton initial guess.
 
 * forward pass and loss gradient of the BF16 tensor-core kernels against the
-  FP64 oracle network (tolerances from BF16 rounding: inputs, weights and
-  hidden activations each carry a relative error up to 2^-9, and the output
-  gradient too, so outputs and gradients agree to a few 1e-3 of their scale;
-  the bars are 3e-2 on the worst element and 1e-2 in RMS);
+  oracle network computed with the same BF16 operands (weights, inputs,
+  hidden activations, back-propagated gradients rounded where the kernels
+  round them) and exact accumulation.  The kernels accumulate in FP32, so a
+  hidden activation within FP32 rounding of a BF16 rounding boundary can
+  round the other way: one such flip moves an output by at most about 2^-8
+  of the output scale.  Bars: forward 8e-3 of the scale on the worst element
+  (two flips), 2e-4 in RMS; gradients 1e-4 in norm and 1e-3 on the worst
+  element of each tensor; the loss to 1e-5;
 * exact results where BF16 is exact: a network of permutation matrices
   returns permuted inputs bit for bit (catches any transposed operand);
 * Adam against the oracle's step, training against its own loss;
@@ -74,10 +78,10 @@ def test_forward_matches_oracle(rows):
     p = rand_params(5)
     X = rng.uniform(-1, 1, (rows, NI)).astype(np.float32).astype(np.float64)
     Y = gpu_forward(p, X)
-    Yo = oracle.mlp_forward(p, X)
+    Yo = oracle.mlp_forward(p, X, bf16=True)
     scale = np.abs(Yo).max()
-    assert np.abs(Y - Yo).max() <= 3e-2 * scale
-    assert np.sqrt(np.mean((Y - Yo) ** 2)) <= 1e-2 * np.sqrt(np.mean(Yo ** 2))
+    assert np.abs(Y - Yo).max() <= 8e-3 * scale
+    assert np.sqrt(np.mean((Y - Yo) ** 2)) <= 2e-4 * np.sqrt(np.mean(Yo ** 2))
 
 
 def test_forward_permutation_network_exact():
@@ -106,13 +110,13 @@ def test_loss_grad_matches_oracle(rows):
     X = rng.uniform(-1, 1, (rows, NI)).astype(np.float32).astype(np.float64)
     T = rng.standard_normal((rows, NO)).astype(np.float32).astype(np.float64)
     loss, g = gpu_loss_grad(p, X, T)
-    lo, go = oracle.mlp_loss_grad(p, X, T)
-    assert abs(loss - lo) <= 1e-2 * lo
+    lo, go = oracle.mlp_loss_grad(p, X, T, bf16=True)
+    assert abs(loss - lo) <= 1e-5 * lo
     for a, b in [(OFF_W1, OFF_B1), (OFF_B1, OFF_W2), (OFF_W2, OFF_B2), (OFF_B2, OFF_W3),
                  (OFF_W3, OFF_B3), (OFF_B3, NP)]:
         d = g[a:b] - go[a:b]
-        assert np.linalg.norm(d) <= 3e-2 * np.linalg.norm(go[a:b]), (a, b)
-        assert np.abs(d).max() <= 6e-2 * np.abs(go[a:b]).max(), (a, b)
+        assert np.linalg.norm(d) <= 1e-4 * np.linalg.norm(go[a:b]), (a, b)
+        assert np.abs(d).max() <= 1e-3 * np.abs(go[a:b]).max(), (a, b)
 
 
 def test_adam_matches_oracle():
@@ -158,6 +162,11 @@ def test_training_reduces_loss():
 
 # ------------------------------------------------------- integrator hooks
 RTOL, ATOL, TEND = 1e-6, 1e-10, 1e-3
+# A guessed Newton start converges to another point inside the Newton test's
+# ball (|delta| E_q <= 0.1 per iteration), so a learned run is a different
+# valid integration, not the oracle's step sequence: each cell is held to the
+# range of the oracle's errors widened to 4x (measured: up to 2.5x)
+LEARNED_WIDE = 4.0
 
 
 def run(prob, mlp=None, predictor=0, mapping=32, record=None):
@@ -198,7 +207,7 @@ def test_garbage_network_still_accurate(scale):
     assert stats["nguess"] > 0 and stats["nguess_fallback"] > 0
     s0 = np.add.reduceat(p.y0, p.y_off[:-1])
     assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
-    eg, eo = check_against_oracle(p, TEND, RTOL, ATOL, y, cs, max_factor=4.0)
+    check_against_oracle(p, TEND, RTOL, ATOL, y, cs, same_decisions=False, wide_factor=LEARNED_WIDE)
 
 
 def test_predictor_argument_checks():
@@ -262,7 +271,7 @@ def test_trained_network_guess():
     r0, y0, s0, c0, st0 = run(test)
     r1, y1, s1, c1, st1 = run(test, mlp=pk, predictor=1)
     assert r0 == r1 == 0 and np.all(s1 == 0)
-    check_against_oracle(test, TEND, RTOL, ATOL, y1, c1, max_factor=4.0)
+    check_against_oracle(test, TEND, RTOL, ATOL, y1, c1, same_decisions=False, wide_factor=LEARNED_WIDE)
     it0 = st0["nniters"] / st0["nsteps"]
     it1 = st1["nniters"] / st1["nsteps"]
     print(f"Newton iterations per step: plain {it0:.3f}, learned {it1:.3f}; "
@@ -284,7 +293,7 @@ def test_shared_network_full_size_sampled():
         assert ret == 0 and np.all(st == 0)
         assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
         ysub = np.concatenate([y[p.y_off[c]:p.y_off[c + 1]] for c in cells])
-        check_against_oracle(p.subset(cells), TEND, RTOL, ATOL, ysub, cs[cells])
+        check_against_oracle(p.subset(cells), TEND, RTOL, ATOL, ysub, cs[cells], min_seq=0.45)
         ys[mapping] = y
     w = RTOL * np.abs(ys[0]) + ATOL
     assert np.median(np.abs(ys[32] - ys[0]) / w) <= 3.0
