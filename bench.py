@@ -30,13 +30,21 @@ NCELL = 100_000
 TOUT = 1.0e-3
 RTOL, ATOL = 1.0e-6, 1.0e-10
 SIZES = (3, 10, 32, 54)
-K_CELLS_STEP_DRAM_BYTES = 451_684_352     # 395.1 MB read + 56.6 MB written (see `traffic` below)
+# DRAM bytes read + written by one timed step's k_cells launches (the four
+# size classes of the 100 000-cell workload), from one single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of `bench.py --quick --steps 2
+# --warmup 1` on the kernels of this source tree: a recorded figure, not
+# measured by the run that prints it
+K_CELLS_STEP_DRAM_BYTES = 451_684_352
+# the FP64 pipe's activity on the 54-species launch, recorded the same way
+# (sm__inst_executed_pipe_fp64, percent of peak while active)
+K54_FP64_PIPE_PCT = 77.1
 METRIC = "cells integrated to t_end per second at stated error; NVECTOR op HBM GB/s"
 UNIT = "cells/s"
 WORKLOAD = ("mass-action 100k: 100000 independent cells, n ~ U{3,10,32,54}, 2n reactions "
             "(2-4 distinct reactants/products), k log-U[1e-2,1e8], Dirichlet y0, t in [0,1e-3], "
             "rtol 1e-6, atol 1e-10, FP64")
-FP64_PEAK_TFLOPS = 1.25     # nominal B300 FP64 rate (recipe table); see the design doc
+FP64_NOMINAL_TFLOPS = 1.25  # nominal B300 FP64 rate: context only; the roofline divides by the measured DGEMM
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -141,6 +149,19 @@ def cpu_oracle_rate(prob, seconds=10.0, threads=None):
     return ns / dt, threads, ns, dt, int((st != 0).sum())
 
 
+def oracle_rate(prob, sample):
+    """the oracle (all host cores, cells spread over threads) on a subset of a
+    workload at the run's tolerances: cells per second; cells are independent,
+    so the rate carries over to the whole workload"""
+    import oracle
+    threads = oracle.host_threads()
+    t = time.perf_counter()
+    _, st, _ = oracle.integrate_cells(prob, 0.0, TOUT, RTOL, ATOL, threads=threads)
+    dt = time.perf_counter() - t
+    return {"cells_per_s": prob.ncell / dt, "seconds": dt, "cores": threads, "failed": int((st != 0).sum()),
+            "sample": sample}
+
+
 def accuracy(prob, y, ncheck=1024, seed=1):
     """weighted final-state error vs the oracle at rtol 1e-10 on a seeded sample"""
     import oracle
@@ -228,12 +249,37 @@ def nvector_ceilings(nv, hbm_gbs, sm_mhz):
     return out
 
 
-def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
+# the grid integrator's streaming vector operations (the NVECTOR kernels of the
+# GMRES and error-norm path, and the fused history and Newton-update passes)
+NVECTOR_KINDS = ("wrms_norm", "dot_prod_multi", "linear_combination", "linear_sum")
+STREAM_KINDS = NVECTOR_KINDS + ("predict", "accept", "rescale", "error_weights", "newton_update", "unscale")
+
+
+def op_bandwidth(prof, hbm_gbs):
+    """per kind of the integrator's op profile: launches, GB/s (algorithmic
+    bytes / summed event time), fraction of the measured HBM copy rate"""
+    out = {}
+    for k, (n, ms, gb) in prof.items():
+        if n:
+            out[k] = {"launches": n, "ms": round(ms, 3), "gb": round(gb, 3), "gbs": round(gb / (ms * 1e-3), 1),
+                      "frac_of_hbm": round(gb / (ms * 1e-3) / hbm_gbs, 3)}
+    for name, kinds in (("nvector_ops", NVECTOR_KINDS), ("all_streaming_ops", STREAM_KINDS)):
+        gb = sum(prof[k][2] for k in kinds)
+        ms = sum(prof[k][1] for k in kinds)
+        if ms > 0:
+            out[name] = {"gb": round(gb, 3), "ms": round(ms, 3), "gbs": round(gb / (ms * 1e-3), 1),
+                         "frac_of_hbm": round(gb / (ms * 1e-3) / hbm_gbs, 3)}
+    return out
+
+
+def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2, hbm_gbs=None):
     """The coupled-system workload: Brusselator reaction-diffusion on a
     periodic nx^3 grid (3 nx^3 unknowns), one shared step, Newton + GMRES
     (Krylov dimension 5) with the 3x3 reaction blocks as preconditioner;
     FP64 throughout, then with the preconditioner and the GMRES operator in
-    FP32 (option precision 1), compared with the FP64 result."""
+    FP32 (option precision 1), compared with the FP64 result.  A further run
+    of each with option "profile" times every vector operation with events:
+    achieved GB/s = algorithmic bytes / event time, per operation kind."""
     p = gen.brusselator3d(nx)
     y0 = torch.from_numpy(p.y0).cuda()
     y = torch.empty_like(y0)
@@ -251,10 +297,19 @@ def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
                 if r != 0:
                     raise RuntimeError(f"grid integrate returned {r}")
             gs = gi.cell_stats()[0]
+            prof = None
+            if hbm_gbs:
+                gi.set_option("profile", 1)
+                gi.init(0.0, y0)
+                if gi.integrate(tout, y) != 0:
+                    raise RuntimeError("profiled grid integrate failed")
+                prof = op_bandwidth(gi.op_profile(), hbm_gbs)
         t = min(ts[1:])
         res = {"grid_points_per_s": nx ** 3 / t, "seconds": t, "steps": int(gs[0]),
                "ms_per_step": 1e3 * t / max(1, gs[0]), "newton_iters": int(gs[3]), "gmres_iters": int(gs[6]),
                "jacobian_setups": int(gs[2])}
+        if prof:
+            res["vector_ops"] = prof
         if prec == 0:
             yref = y.clone()
             out.update(res)
@@ -264,6 +319,62 @@ def grid_workload(torch, bdfb, gen, nx=256, tout=1.0, reps=2):
     out["workload"] = (f"Brusselator 3-D {nx}^3 x 3 = {3 * nx ** 3} unknowns, A=1, B=3, eps=5e-6, D=1e-2, "
                        f"t in [0,{tout}], rtol 1e-6, atol 1e-10, GMRES(5) + 3x3 block Jacobi")
     return out
+
+
+class GridOracleLeg:
+    """The oracle on a smaller grid of the same workload (nx^3, same t range,
+    one host thread: one coupled system), run in a background thread while the
+    GPU legs run: its rate in grid points per second and an rtol 1e-10 truth
+    against which the GPU's final state at that size is measured."""
+
+    def __init__(self, gen, nx=64, tout=1.0):
+        import oracle
+        self.nx, self.tout = nx, tout
+        self.p = gen.brusselator3d(nx)
+        self.res = {}
+
+        def run():
+            t0 = time.perf_counter()
+            r, yo, so = oracle.bruss_integrate(self.p, 0.0, tout, RTOL, ATOL, maxl=5)
+            dt = time.perf_counter() - t0
+            rt, yt, _ = oracle.bruss_integrate(self.p, 0.0, tout, 1e-10, 1e-14, maxl=5)
+            self.res = {"ret": int(r), "truth_ret": int(rt), "seconds": dt, "yo": yo, "so": so, "yt": yt}
+
+        self.th = threading.Thread(target=run, daemon=True)
+        self.th.start()
+
+    def finish(self, torch, bdfb):
+        """join; the GPU at the same size and tolerances in both precisions:
+        counters against the oracle's, error against the truth"""
+        self.th.join()
+        R = self.res
+        p, nx = self.p, self.nx
+        w = RTOL * np.abs(R["yt"]) + ATOL
+        eo = np.abs(R["yo"] - R["yt"]) / w
+        out = {"oracle": {"points_per_s": nx ** 3 / R["seconds"], "seconds": R["seconds"], "cores": 1,
+                          "steps": int(R["so"][0]), "ret": R["ret"],
+                          "sample": f"{nx}^3 grid (same problem, same t range)",
+                          "error_vs_truth": {"max": float(eo.max()), "rms": float(np.sqrt(np.mean(eo * eo)))}},
+               "truth": f"oracle rtol 1e-10 atol 1e-14 at {nx}^3"}
+        y0 = torch.from_numpy(p.y0).cuda()
+        y = torch.empty_like(y0)
+        for prec in (0, 1):
+            with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, maxl=5, precision=prec) as gi:
+                gi.init(0.0, y0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = gi.integrate(self.tout, y)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                gs = gi.cell_stats()[0]
+            yg = y.cpu().numpy()
+            eg = np.abs(yg - R["yt"]) / w
+            out["fp64" if prec == 0 else "fp32_preconditioner_and_operator"] = {
+                "ret": int(r), "points_per_s": nx ** 3 / dt, "steps": int(gs[0]),
+                "counters_equal_oracle": bool(np.array_equal(gs[:8], R["so"][:8])),
+                "max_weighted_diff_vs_oracle": float(np.max(np.abs(yg - R["yo"]) / (RTOL * np.abs(R["yo"]) + ATOL))),
+                "error_vs_truth": {"max": float(eg.max()), "rms": float(np.sqrt(np.mean(eg * eg)))}}
+        return out
 
 
 def timed_integrations(torch, integ, y0, y, tout, reps, flush=None):
@@ -742,13 +853,20 @@ def run_ours(args):
     t_kern = sum(kern_s) / len(kern_s)
     flops = algorithmic_flops(prob, cs)
     achieved = flops / t_kern / 1e12
+    # the coupled workload's oracle (one host thread) runs beside the GPU-only legs
+    grid_leg = GridOracleLeg(gen) if not args.no_configs else None
     try:
         dgemm_tf = dgemm_tflops(torch)
     except RuntimeError:
         dgemm_tf = None
     nv = nvector_bandwidth(torch, bdfb)
-    grid = grid_workload(torch, bdfb, gen)
+    grid = grid_workload(torch, bdfb, gen, hbm_gbs=pk["hbm_gbs"])
     learned = learned_workload(torch, bdfb, gen, train_steps=20000) if not args.no_learned else None
+    if grid_leg is not None:
+        grid["oracle_64"] = grid_leg.finish(torch, bdfb)
+    if learned is not None:
+        learned["oracle"] = oracle_rate(gen.mass_action_shared(10_000, seed=gen.DEFAULT_SEED),
+                                        "first 10000 of the 1000000 cells")
     configs = None
     if not args.no_configs:
         configs = {"robertson_1000": robertson_workload(torch, bdfb, gen),
@@ -761,6 +879,8 @@ def run_ours(args):
                    "imex_demo_1e7": imex_workload(torch, bdfb, gen, 10_000_000, 1000.0, oracle_points=20_000),
                    "imex_demo_6e5_b10": imex_workload(torch, bdfb, gen, 600_000, 10.0, precisions=(1,),
                                                       oracle_points=5_000)}
+        configs["mixed_precision_262144x54"]["oracle"] = oracle_rate(
+            gen.mass_action(10_000, sizes=(54,), seed=gen.DEFAULT_SEED + 7), "first 10000 of the 262144 cells")
     variants = {"batched_fp64": value}
     for name, opts in (("plain_fp64_warp_per_cell", {"mapping": 32}),
                        ("batched_fp64_gauss_jordan_inverse", {"lsolver": 1}),
@@ -785,9 +905,6 @@ def run_ours(args):
                 mst = vi.stats()
                 variants["mixed_refine_sweeps_per_solve"] = mst["nrefine"] / max(1, mst["nniters"])
                 variants["mixed_fp64_fallbacks"] = mst["nrefine_fallback"]
-    # DRAM bytes read + written by one timed step's four k_cells launches, from one
-    # ncu capture of `bench.py --quick --steps 2 --warmup 1` (profiles/
-    # launches_massaction_100k.md); valid while the kernels are those of that capture
     traffic = K_CELLS_STEP_DRAM_BYTES if (NCELL == 100_000 and SIZES == (3, 10, 32, 54) and not args.mapping
                                           and args.precision == 0) else None
     acc = accuracy(prob, yh)
@@ -809,14 +926,15 @@ def run_ours(args):
                              "setups_per_cell": st_sum["nlinsetups"] / NCELL,
                              "failed_cells": st_sum["ncells_failed"]},
         "roofline": {"kernel": "k_cells (persistent BDF/Newton)", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak": dgemm_tf, "unit": "TFLOP/s", "frac": achieved / dgemm_tf if dgemm_tf else None,
                      "traffic": traffic, "kernel_ms": t_kern * 1e3, "algorithmic_fp64_flops": flops,
-                     "peak_source": "FP64 nominal 1.25 TFLOP/s (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
-                     "fp64_dgemm_tflops_measured": dgemm_tf,
-                     "frac_of_dgemm": achieved / dgemm_tf if dgemm_tf else None,
-                     # recorded, not measured by this run: ncu's FP64-pipe activity of the
-                     # 54-species launch (profiles/k_cells_massaction_n54.md)
-                     "fp64_pipe_active_pct_ncu_54_species": 77.1},
+                     "peak_source": "FP64 of measured: cuBLAS DGEMM 8192^3 timed in this run",
+                     "traffic_source": "recorded: ncu DRAM bytes of one timed step's k_cells launches, "
+                                       "single-pass capture of bench.py --quick at full size",
+                     "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+                     "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
+                     "recorded": {"fp64_pipe_active_pct_54_species_launch": K54_FP64_PIPE_PCT,
+                                  "how": "ncu sm__inst_executed_pipe_fp64 on one 8192-cell launch"}},
         "variants_cells_per_s": variants,
         "coupled_grid": grid,
         "learned_guess": learned,
@@ -846,7 +964,8 @@ def run_part(args):
     import torch
     from paper_2011_12984_b300 import bdfb, gen
     if args.part == "grid":
-        out = grid_workload(torch, bdfb, gen, nx=args.grid_nx, tout=args.grid_tout, reps=max(1, args.steps))
+        out = grid_workload(torch, bdfb, gen, nx=args.grid_nx, tout=args.grid_tout, reps=max(1, args.steps),
+                            hbm_gbs=peaks()[0]["hbm_gbs"])
     elif args.part == "nvector":
         out = nvector_bandwidth(torch, bdfb, reps=max(1, args.steps))
     elif args.part == "robertson":

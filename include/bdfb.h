@@ -354,6 +354,24 @@ int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem);
  * continue from tout (each call starts from a fresh Jacobian). */
 int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem);
 int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out);
+/* Per-operation timing of the grid integrator (BDFB_BRUSSELATOR3D, and
+ * BDFB_BRUSSELATOR1D on its BDF path), the measurement behind the paper's
+ * per-kernel bandwidth study (Sec. 6, Table 1).  Option "profile" 1 records
+ * CUDA events around every vector operation and kernel of the step loop on
+ * the context's stream (no extra synchronisation; the times are read when
+ * each bdfb_integrate returns) and clears the sums; 0 stops.  out (host,
+ * 3 * nkinds doubles, nkinds >= 14): for kind k, out[3k] = launches,
+ * out[3k + 1] = summed event milliseconds, out[3k + 2] = summed algorithmic
+ * gigabytes (the bytes the operation must move, N = unknowns, nv = vectors):
+ *   0 WrmsNorm 16N; 1 DotProdMulti 8(nv+1)N; 2 LinearCombination 8(nv+1)N;
+ *   3 LinearSum 24N; 4 prediction of z_0, z_1 8(q+3)N; 5 corrector and
+ *   Pascal shift 8(2q+3)N; 6 history rescale 16qN; 7 error weights 24N;
+ *   8 Newton update 40N; 9 unscaling product 24N; 10 right-hand side 16N;
+ *   11 preconditioned GMRES operator 64N (52N with FP32 blocks); 12 3x3
+ *   block setup 32N (20N); 13 preconditioning of the right-hand side 48N
+ *   (36N).  Returns 14 (the number of kinds), or BDFB_ILL_INPUT (null
+ *   pointers, nkinds < 14, or a context without a grid). */
+int bdfb_get_op_profile(bdfb_ctx* ctx, double* out, int32_t nkinds);
 /* per-cell counters, int64 [ncell][8] = nst, nfe, nsetups, nni, ncfn, netf, q, h-bits.
  * For BDFB_BRUSSELATOR3D one row for the whole system: nst, nfe, nsetups,
  * nni, ncfn, netf, GMRES iterations, GMRES solves that stopped at maxl.

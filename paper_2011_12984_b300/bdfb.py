@@ -101,6 +101,7 @@ _sig("bdfb_init", C.c_int, [_vp, _d, _vp, _i32])
 _sig("bdfb_integrate", C.c_int, [_vp, _d, _vp, _vp, _i32])
 _sig("bdfb_get_stats", C.c_int, [_vp, C.POINTER(Stats)])
 _sig("bdfb_get_cell_stats", C.c_int, [_vp, _vp, _i32])
+_sig("bdfb_get_op_profile", C.c_int, [_vp, _vp, _i32])
 _sig("bdfb_get_mapping", C.c_int, [_vp, _vp, _vp])
 _sig("bdfb_mlp_nparam", _i64, [])
 _sig("bdfb_mlp_packed_bytes", _i64, [])
@@ -112,6 +113,12 @@ _sig("bdfb_mlp_train", C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C
 _sig("bdfb_mlp_adam", C.c_int, [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp])
 _sig("bdfb_load_mlp", C.c_int, [_vp, _vp, _i64])
 _sig("bdfb_set_record", C.c_int, [_vp, _vp, _vp, _i64, _vp])
+
+
+# kinds of bdfb_get_op_profile, in order
+OP_KINDS = ("wrms_norm", "dot_prod_multi", "linear_combination", "linear_sum", "predict", "accept",
+            "rescale", "error_weights", "newton_update", "unscale", "rhs", "gmres_operator",
+            "block_setup", "precondition_rhs")
 
 
 class BdfbError(RuntimeError):
@@ -450,6 +457,13 @@ class Integrator:
             return check(lib.bdfb_set_record(self.h, None, None, 0, None), "bdfb_set_record")
         return check(lib.bdfb_set_record(self.h, _dptr(x), _dptr(t), x.shape[0], _dptr(count)),
                      "bdfb_set_record")
+
+    def op_profile(self):
+        """grid contexts with option profile=1: {kind: (launches, ms, GB)}"""
+        out = np.zeros(3 * len(OP_KINDS))
+        n = lib.bdfb_get_op_profile(self.h, out.ctypes.data, len(OP_KINDS))
+        check(n if n < 0 else 0, "bdfb_get_op_profile")
+        return {k: (int(out[3 * i]), float(out[3 * i + 1]), float(out[3 * i + 2])) for i, k in enumerate(OP_KINDS)}
 
     def cell_stats(self):
         out = np.zeros((self.stat_rows, 8), np.int64)

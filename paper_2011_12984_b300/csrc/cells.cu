@@ -450,8 +450,8 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       if constexpr (CellSmem<NMAX, PREC>::DR) {
         if (cd.kind == BDFB_MASSACTION) {
           // each reaction's derivatives once, then gathered into the rows
-          reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
-          form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gamma, S.M);
+          reaction_derivs<G, NPL, NMAX>(g, cd, S, y, -C.gamma);
+          form_M64_scaled<G, NPL, NMAX>(g, cd, S, S.M);
           direct = false;
         }
       }
@@ -908,8 +908,8 @@ __device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& G
     bool direct = true;
     if constexpr (CellSmem<NMAX, 0>::DR) {
       if (cd.kind == BDFB_MASSACTION) {
-        reaction_derivs<G, NPL, NMAX>(g, cd, S, z0);
-        form_M64_from_dr<G, NPL, NMAX>(g, cd, S, GP.gamma, S.M);
+        reaction_derivs<G, NPL, NMAX>(g, cd, S, z0, -GP.gamma);
+        form_M64_scaled<G, NPL, NMAX>(g, cd, S, S.M);
         direct = false;
       }
     }
@@ -2196,6 +2196,12 @@ static int fetch_states(bdfb_ctx* ctx, std::vector<CellState>& st) {
     BDFB_CUDA(cudaMemcpy(st.data(), ctx->d_state, ctx->ncell * sizeof(CellState), cudaMemcpyDeviceToHost));
   }
   return 0;
+}
+
+extern "C" int bdfb_get_op_profile(bdfb_ctx* ctx, double* out, int32_t nkinds) {
+  if (!ctx || !out || !ctx->grid || nkinds < GOP_N) return BDFB_ILL_INPUT;
+  grid_profile(ctx->grid, out);
+  return GOP_N;
 }
 
 extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {

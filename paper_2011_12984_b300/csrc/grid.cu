@@ -369,7 +369,55 @@ struct GridBDF {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float last_ms = 0;
   double l[GQMAX + 2][GQMAX + 2] = {}, E[GQMAX + 2][3] = {}, qfact[GQMAX + 3] = {};
+  // option "profile": events around every vector operation and kernel of the
+  // step loop, with its algorithmic bytes, summed per kind (grid_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pkind;
+  std::vector<double> pbytes;
+  size_t pused = 0;
+  int64_t pcalls[GOP_N] = {};
+  double pms[GOP_N] = {}, pgb[GOP_N] = {};
 };
+
+// one timed operation: events recorded on the step loop's stream before and
+// after (no synchronisation; the times are read when the call ends).  Each
+// scope reserves its own pair of events, and each wraps one launch only.
+struct GTimed {
+  GridBDF* g;
+  size_t idx = 0;
+  bool on = false;
+  GTimed(GridBDF* g_, int kind, double bytes) : g(g_) {
+    if (!g->prof) return;
+    while (g->pused + 2 > g->pev.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      g->pev.push_back(e);
+    }
+    idx = g->pused;
+    g->pused += 2;
+    g->pkind.push_back(kind);
+    g->pbytes.push_back(bytes);
+    on = cudaEventRecord(g->pev[idx], g->s) == cudaSuccess;
+  }
+  ~GTimed() {
+    if (on) cudaEventRecord(g->pev[idx + 1], g->s);
+  }
+};
+
+// fold the recorded events of a finished call into the per-kind sums
+static void prof_flush(GridBDF* g) {
+  for (size_t i = 0; i < g->pkind.size() && 2 * i + 1 < g->pused; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g->pev[2 * i], g->pev[2 * i + 1]) != cudaSuccess) continue;
+    g->pcalls[g->pkind[i]]++;
+    g->pms[g->pkind[i]] += ms;
+    g->pgb[g->pkind[i]] += g->pbytes[i] * 1e-9;
+  }
+  g->pkind.clear();
+  g->pbytes.clear();
+  g->pused = 0;
+}
 
 static double ell1(const GridBDF* g, int q) { return g->l[q][1]; }
 
@@ -400,7 +448,10 @@ static void make_tables(GridBDF* g) {
 
 // ---- reductions returning to the host (Sec. 4.1: a reduction synchronises)
 static int g_wrms(GridBDF* g, const double* x, double* out) {
-  GCHK(bdfb_nv_wrms_norm(g->N, x, g->ewt, g->dres, g->work, g->s));
+  {
+    GTimed t(g, GOP_WRMS, 16.0 * g->N);
+    GCHK(bdfb_nv_wrms_norm(g->N, x, g->ewt, g->dres, g->work, g->s));
+  }
   BDFB_CUDA(cudaMemcpyAsync(g->hres, g->dres, sizeof(double), cudaMemcpyDeviceToHost, g->s));
   BDFB_CUDA(cudaStreamSynchronize(g->s));
   *out = g->hres[0];
@@ -408,7 +459,10 @@ static int g_wrms(GridBDF* g, const double* x, double* out) {
 }
 
 static int g_dots(GridBDF* g, const double* x, const double* const* ys, int nv, double* out) {
-  GCHK(bdfb_nv_dot_prod_multi(g->N, nv, x, ys, g->dres, g->work, g->s));
+  {
+    GTimed t(g, GOP_DOTS, 8.0 * (nv + 1) * g->N);
+    GCHK(bdfb_nv_dot_prod_multi(g->N, nv, x, ys, g->dres, g->work, g->s));
+  }
   BDFB_CUDA(cudaMemcpyAsync(g->hres, g->dres, nv * sizeof(double), cudaMemcpyDeviceToHost, g->s));
   BDFB_CUDA(cudaStreamSynchronize(g->s));
   std::memcpy(out, g->hres, nv * sizeof(double));
@@ -419,17 +473,23 @@ static int g_rhs(GridBDF* g, const double* y, double* f) {
   if (g->external) {
     const int r = g->ext.rhs(g->ext.user, y, f, g->s);
     if (r) return r;
-  } else if (g->dim == 1)
-    k_bruss1_rhs<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->A, g->B, g->reps, g->cdx, y, f);
-  else
-    k_bruss_rhs<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->A, g->B, g->reps, g->D, y, f);
+  } else {
+    GTimed t(g, GOP_RHS, 16.0 * g->N);
+    if (g->dim == 1)
+      k_bruss1_rhs<<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->A, g->B, g->reps, g->cdx, y, f);
+    else
+      k_bruss_rhs<<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->A, g->B, g->reps, g->D, y, f);
+  }
   BDFB_CUDA(cudaGetLastError());
   g->nfe++;
   return 0;
 }
 
 static int g_ewt(GridBDF* g) {
-  k_ewt<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->rtol, g->atol, g->z[0], g->ewt, g->sc);
+  {
+    GTimed t(g, GOP_EWT, 24.0 * g->N);
+    k_ewt<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->rtol, g->atol, g->z[0], g->ewt, g->sc);
+  }
   BDFB_CUDA(cudaGetLastError());
   return 0;
 }
@@ -441,7 +501,10 @@ static GZ zcols(GridBDF* g) {
 }
 
 static int g_rescale(GridBDF* g, double eta) {
-  k_rescale<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), eta);
+  {
+    GTimed t(g, GOP_RESCALE, 16.0 * g->q * g->N);
+    k_rescale<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), eta);
+  }
   BDFB_CUDA(cudaGetLastError());
   g->h *= eta;
   return 0;
@@ -455,8 +518,11 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   const double sqrtN = std::sqrt((double)N);
   double H[(MAXL_MAX + 1) * MAXL_MAX] = {0};
   double gv[MAXL_MAX + 1] = {0}, cs[MAXL_MAX] = {0}, sn[MAXL_MAX] = {0}, yv[MAXL_MAX] = {0};
-  if (g->prec) k_prec_scale<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, (const float*)g->Pinv, g->ewt, g->V[0]);
-  else k_prec_scale<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, g->Pinv, g->ewt, g->V[0]);
+  {
+    GTimed t(g, GOP_PSCALE, (g->prec ? 36.0 : 48.0) * N);   // b, ewt, v; 3x3 blocks (FP32 or FP64)
+    if (g->prec) k_prec_scale<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, (const float*)g->Pinv, g->ewt, g->V[0]);
+    else k_prec_scale<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->b, g->Pinv, g->ewt, g->V[0]);
+  }
   BDFB_CUDA(cudaGetLastError());
   // The basis is stored unnormalised: basis vector i is sig[i] V[i], the
   // scales kept on the host and folded into the coefficients of the next
@@ -476,6 +542,9 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
   bool conv = false;
   for (int j = 0; j < maxl; ++j) {
     const float* P32 = (const float*)g->Pinv;
+    {
+    // v, ewt, sc, y and w, plus the 3x3 blocks (FP32 or FP64)
+    GTimed t(g, GOP_APPLY, (g->prec ? 52.0 : 64.0) * N);
     if (g->dim == 1 && g->prec)
       k_bruss1_apply<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->cdx, g->reps, g->gamma, g->V[j], g->ewt,
                                                              g->sc, ycur, P32, g->w);
@@ -488,6 +557,7 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
     else
       k_bruss_apply<double><<<stencil_grid(g->nx), ST_X, 0, g->s>>>(g->nx, g->D, g->reps, g->gamma, g->V[j],
                                                                     g->ewt, g->sc, ycur, g->Pinv, g->w);
+    }
     BDFB_CUDA(cudaGetLastError());
     // w = sig[j] A V[j]: h_ij = (w, basis_i) = sig[j] sig[i] (A V[j], V[i]);
     // classical Gram-Schmidt into V[j + 1]: sig[j] (A V[j] - sum c_i V[i])
@@ -501,6 +571,7 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
       xs[0] = g->w;
       c[0] = 1.0;
       for (int i = 0; i <= j; ++i) { xs[i + 1] = g->V[i]; c[i + 1] = -hcol[i] * sig[i] / sig[j]; }
+      GTimed t(g, GOP_LINCOMB, 8.0 * (j + 3) * N);
       GCHK(bdfb_nv_linear_combination(N, j + 2, c, xs, g->V[j + 1], g->s));
     }
     for (int i = 0; i <= j; ++i) H[i * maxl + j] = hcol[i];
@@ -537,19 +608,26 @@ static int g_gmres(GridBDF* g, const double* ycur, double tol) {
     const double* xs[MAXL_MAX];
     double c[MAXL_MAX];
     for (int i = 0; i < k; ++i) { xs[i] = g->V[i]; c[i] = yv[i] * sig[i]; }
+    GTimed t(g, GOP_LINCOMB, 8.0 * (k + 1) * N);
     GCHK(bdfb_nv_linear_combination(N, k, c, xs, g->tmp, g->s));
   }
-  k_mul<<<gblocks(N), GT, 0, g->s>>>(N, g->tmp, g->sc, g->b);     // x = S^{-1} (V y)
+  {
+    GTimed t(g, GOP_MUL, 24.0 * N);
+    k_mul<<<gblocks(N), GT, 0, g->s>>>(N, g->tmp, g->sc, g->b);     // x = S^{-1} (V y)
+  }
   BDFB_CUDA(cudaGetLastError());
   return 0;
 }
 
 static int g_psetup(GridBDF* g, const double* y) {
   BDFB_CUDA(cudaMemsetAsync(g->dsing, 0, sizeof(int), g->s));
-  if (g->prec)
-    k_bruss_psetup<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, (float*)g->Pinv, g->dsing);
-  else
-    k_bruss_psetup<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, g->Pinv, g->dsing);
+  {
+    GTimed t(g, GOP_PSETUP, (g->prec ? 20.0 : 32.0) * g->N);   // y; the 3x3 blocks (FP32 or FP64)
+    if (g->prec)
+      k_bruss_psetup<float><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, (float*)g->Pinv, g->dsing);
+    else
+      k_bruss_psetup<double><<<gblocks(g->np), GT, 0, g->s>>>(g->np, g->reps, g->gamma, y, g->Pinv, g->dsing);
+  }
   BDFB_CUDA(cudaGetLastError());
   int sing = 0;
   BDFB_CUDA(cudaMemcpyAsync(&sing, g->dsing, sizeof(int), cudaMemcpyDeviceToHost, g->s));
@@ -583,6 +661,7 @@ static int g_newton_external(GridBDF* g, double Eq, double* acnrm) {
     g->nfe += sweeps;
     if (!failed) {
       GCHK(g_wrms(g, g->acor, acnrm));
+      GTimed t(g, GOP_LINSUM, 24.0 * g->N);
       GCHK(bdfb_nv_linear_sum(g->N, 1.0, g->zp0, 1.0, g->acor, g->y, g->s));
       return 0;
     }
@@ -619,11 +698,17 @@ static int g_newton(GridBDF* g, double Eq, double* acnrm) {
       GCHK(g_rhs(g, g->y, g->f));
       const double* xs[3] = {g->f, g->zp1, g->acor};
       const double c[3] = {g->gamma, -1.0 / l1, -1.0};
-      GCHK(bdfb_nv_linear_combination(N, 3, c, xs, g->b, g->s));
+      {
+        GTimed t(g, GOP_LINCOMB, 32.0 * N);
+        GCHK(bdfb_nv_linear_combination(N, 3, c, xs, g->b, g->s));
+      }
       GCHK(g_gmres(g, g->y, 0.05 * 0.1 / Eq));
       double del;
       GCHK(g_wrms(g, g->b, &del));
-      k_newton_update<<<gblocks(N), GT, 0, g->s>>>(N, g->b, g->acor, g->zp0, g->y);
+      {
+        GTimed t(g, GOP_NEWTON, 40.0 * N);
+        k_newton_update<<<gblocks(N), GT, 0, g->s>>>(N, g->b, g->acor, g->zp0, g->y);
+      }
       BDFB_CUDA(cudaGetLastError());
       g->nni++;
       if (!std::isfinite(del)) break;
@@ -645,7 +730,10 @@ static int g_newton(GridBDF* g, double Eq, double* acnrm) {
 }
 
 static int g_predict(GridBDF* g) {
-  k_predict01<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), g->zp0, g->zp1);
+  {
+    GTimed t(g, GOP_PREDICT, 8.0 * (g->q + 3) * g->N);
+    k_predict01<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), g->zp0, g->zp1);
+  }
   BDFB_CUDA(cudaGetLastError());
   return 0;
 }
@@ -661,7 +749,10 @@ static int g_select(GridBDF* g, double dsm) {
     eqm1 = 1.0 / (std::pow(6.0 * g->E[q][1] * nz, 1.0 / q) + 1e-6);
   }
   if (q < g->qmax) {
-    GCHK(bdfb_nv_linear_sum(g->N, 1.0, g->acor, -1.0, g->acorp, g->tmp, g->s));
+    {
+      GTimed t(g, GOP_LINSUM, 24.0 * g->N);
+      GCHK(bdfb_nv_linear_sum(g->N, 1.0, g->acor, -1.0, g->acorp, g->tmp, g->s));
+    }
     double nd;
     GCHK(g_wrms(g, g->tmp, &nd));
     eqp1 = 1.0 / (std::pow(10.0 * g->E[q][2] * nd, 1.0 / (q + 2)) + 1e-6);
@@ -738,12 +829,15 @@ static int g_step(GridBDF* g, double tout, bool* reached) {
     }
     GL L;
     for (int j = 0; j <= GQMAX; ++j) L.l[j] = j <= g->q ? g->l[g->q][j] : 0.0;
-    switch (g->q) {
-      case 1: k_accept<1><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
-      case 2: k_accept<2><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
-      case 3: k_accept<3><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
-      case 4: k_accept<4><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
-      default: k_accept<5><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+    {
+      GTimed t(g, GOP_ACCEPT, 8.0 * (2 * g->q + 3) * N);   // z_0..z_q read and written, acor read
+      switch (g->q) {
+        case 1: k_accept<1><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+        case 2: k_accept<2><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+        case 3: k_accept<3><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+        case 4: k_accept<4><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+        default: k_accept<5><<<gblocks(N), GT, 0, g->s>>>(N, zcols(g), L, g->acor); break;
+      }
     }
     BDFB_CUDA(cudaGetLastError());
     g->t = tnew;
@@ -910,6 +1004,10 @@ int grid_set_option(GridBDF* g, const char* key, int64_t v) {
   } else if (!std::strcmp(key, "interp")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     g->interp = (int)v;
+  } else if (!std::strcmp(key, "profile")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    g->prof = v != 0;
+    for (int k = 0; k < GOP_N; ++k) { g->pcalls[k] = 0; g->pms[k] = 0.0; g->pgb[k] = 0.0; }
   } else if (!std::strcmp(key, "precision") && !g->external) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     g->prec = (int)v;
@@ -964,7 +1062,16 @@ int grid_integrate(GridBDF* g, double tout, double* y, int mem) {
                               mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->s));
   BDFB_CUDA(cudaStreamSynchronize(g->s));
   cudaEventElapsedTime(&g->last_ms, g->e0, g->e1);
+  if (g->prof) prof_flush(g);
   return ret;
+}
+
+void grid_profile(GridBDF* g, double* out) {
+  for (int k = 0; k < GOP_N; ++k) {
+    out[3 * k] = (double)g->pcalls[k];
+    out[3 * k + 1] = g->pms[k];
+    out[3 * k + 2] = g->pgb[k];
+  }
 }
 
 void grid_stats(GridBDF* g, int64_t out[8], double* last_ms) {

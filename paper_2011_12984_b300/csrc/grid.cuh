@@ -8,6 +8,12 @@ namespace bdfb {
 
 struct GridBDF;
 
+// kinds of timed operations of the profile option (bdfb_get_op_profile)
+enum GridOp {
+  GOP_WRMS, GOP_DOTS, GOP_LINCOMB, GOP_LINSUM, GOP_PREDICT, GOP_ACCEPT, GOP_RESCALE, GOP_EWT,
+  GOP_NEWTON, GOP_MUL, GOP_RHS, GOP_APPLY, GOP_PSETUP, GOP_PSCALE, GOP_N
+};
+
 int grid_create(int nx, double A, double B, double eps, double D, GridBDF** out);
 // dim 3: the nx^3 reaction-diffusion grid (D); dim 1: the advection-reaction
 // line of nx points over [0, len) with speed c (first-order upwind)
@@ -41,5 +47,8 @@ int grid_integrate(GridBDF* g, double tout, double* y, int mem);
 void grid_stats(GridBDF* g, int64_t out[8], double* last_ms);
 // order and step size the next step will try
 void grid_next_step(GridBDF* g, int* q, double* h);
+// option "profile": per GridOp kind, out[3k..3k+2] = launches, summed event
+// milliseconds, summed algorithmic GB since the option was set
+void grid_profile(GridBDF* g, double* out);
 
 }  // namespace bdfb

@@ -33,15 +33,18 @@ __device__ __forceinline__ float bcastf(const Grp<G>& g, float v, int src) {
   return G > 1 ? __shfl_sync(g.mask, v, src, G) : v;
 }
 
-// d rate_r / d y_{s_a} for every reaction r and reactant slot a at y (FP64),
-// into S.dr; lanes over reactions.
+// scale * d rate_r / d y_{s_a} for every reaction r and reactant slot a at y
+// (FP64), into S.dr; lanes over reactions.  scale = 1: the derivatives
+// themselves (kept by mixed precision for its residual); scale = -gamma:
+// their contributions to M = I - gamma J (form_M64_scaled).
 template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void reaction_derivs(const Grp<G>& g, const CellDesc& c,
-                                                CellSmem<NMAX, PREC>& S, const double (&y)[NPL]) {
+                                                CellSmem<NMAX, PREC>& S, const double (&y)[NPL],
+                                                double scale = 1.0) {
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   for (int r = g.rank; r < c.nr; r += G) {
     const uint32_t rc = __ldg(c.reac + r);
-    const double kr = __ldg(c.k + r);
+    const double kr = __ldg(c.k + r) * scale;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       double d = 0.0;
@@ -129,6 +132,39 @@ __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc
       }
     }
     for (int j = 0; j < n; ++j) row[j] = __dsub_rn(i == j ? 1.0 : 0.0, __dmul_rn(gamma, row[j]));
+  }
+  g.sync();
+}
+
+// M = I - gamma J into Mg from derivatives scaled by -gamma (reaction_derivs
+// with scale = -gamma): row i accumulates, in reaction order, +d for the
+// reactions producing species i and -d for those consuming it, then 1 on the
+// diagonal -- no separate pass forming 1 - gamma J
+template <int G, int NPL, int NMAX, int PREC>
+__device__ __forceinline__ void form_M64_scaled(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, PREC>& S,
+                                                double (*Mg)[NMAX + 1]) {
+  const int n = c.n;
+  g.sync();
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    if (i >= n) continue;
+    double* row = Mg[i];
+    for (int j = 0; j < n; ++j) row[j] = 0.0;
+    const int e1 = __ldg(c.inc_off + i + 1);
+    for (int e = __ldg(c.inc_off + i); e < e1; ++e) {
+      const uint32_t v = __ldg(c.inc + e);
+      const int r = (int)(v >> 1);
+      const uint32_t rc = __ldg(c.reac + r);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const uint32_t s = (rc >> (8 * a)) & 255u;
+        if (s == 255u) continue;
+        const double d = S.dr[a][r];
+        row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+      }
+    }
+    row[i] += 1.0;
   }
   g.sync();
 }

@@ -164,3 +164,35 @@ def test_grid_krylov_dimensions(maxl):
     rt, yt, _ = oracle.bruss_integrate(p, 0.0, 0.05, 1e-10, 1e-14, maxl=5)
     assert ro == 0 and rt == 0
     check_system(y, gs, yo, so, yt, 1e-6, 1e-10, 0)
+
+
+def test_grid_op_profile():
+    """Option "profile": every vector operation of the step loop is timed with
+    events and its algorithmic bytes counted; the run's result is the
+    unprofiled one bit for bit, the counted bytes follow the per-kind
+    formulas, and the timed operations fit inside the integration's span."""
+    p = gen.brusselator3d(32, seed=4)
+    N = p.y0.size
+    ret0, y0, gs0, st0 = run_grid(p, 0.05, 1e-6, 1e-10)
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, maxl=5) as I:
+        I.set_option("profile", 1)
+        I.init(0.0, torch.from_numpy(p.y0).cuda())
+        y = torch.empty(N, dtype=torch.float64, device="cuda")
+        assert I.integrate(0.05, y) == 0
+        prof, st = I.op_profile(), I.stats()
+    assert ret0 == 0 and np.array_equal(y.cpu().numpy(), y0)
+    for k in ("wrms_norm", "dot_prod_multi", "linear_combination", "predict", "accept", "error_weights",
+              "newton_update", "rhs", "gmres_operator", "block_setup", "precondition_rhs", "unscale"):
+        n, ms, gb = prof[k]
+        assert n > 0 and ms > 0 and gb > 0, k
+    n, ms, gb = prof["wrms_norm"]
+    assert abs(gb - n * 16 * N * 1e-9) <= 1e-9 * gb            # 16 bytes per element
+    n, ms, gb = prof["error_weights"]
+    assert n >= gs0[0]                                         # one per step at least
+    assert abs(gb - n * 24 * N * 1e-9) <= 1e-9 * gb
+    assert prof["gmres_operator"][0] == gs0[6]                 # one operator per GMRES iteration
+    total_ms = sum(v[1] for v in prof.values())
+    assert total_ms <= st["last_kernel_ms"] * 1.01
+    with bdfb.Integrator(gen.robertson(4)) as I:
+        with pytest.raises(bdfb.BdfbError):
+            I.op_profile()                                     # not a grid context

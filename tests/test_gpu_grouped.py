@@ -2,8 +2,9 @@
 one step size and order, error test over every species, task-local Newton
 solves per cell) against the oracle's grouped integration.
 
-The GPU runs the oracle's decisions up to rounding: the same step count
-within 5% and the same summed task-local iteration count within 10%.  Final
+The GPU runs the oracle's decisions up to rounding: step and summed
+task-local iteration counts within 5% and 10% of the range of the three
+oracle runs below.  Final
 states are compared with a tight-tolerance truth in units of the run's error
 weights.  Under one error norm over every species a single species' error
 is not bounded by the tolerance, and it depends strongly on the step
@@ -65,27 +66,29 @@ def accuracy(p, tout, rtol, atol, y):
     assert np.all(stt == 0)
     eg = werr(y, yt, rtol, atol)
     worst_max = worst_rms = 0.0
-    so = None
+    runs = []
     for f in (1.0, 1.0 + 1e-12, 1.0 - 1e-12):
         yo, ro, s = oracle.integrate_cells_grouped(p, 0.0, tout, rtol * f, atol)
         assert ro == 0
-        so = s if so is None else so
+        runs.append(s)
         eo = werr(yo, yt, rtol, atol)
         worst_max, worst_rms = max(worst_max, eo.max()), max(worst_rms, rms(eo))
     assert eg.max() <= max(10.0, 2.0 * worst_max), (eg.max(), worst_max)
     assert rms(eg) <= 1.5 * worst_rms, (rms(eg), worst_rms)
-    return so
+    return np.array(runs)
 
 
 def check(p, tout, rtol, atol, y, stats):
-    so = accuracy(p, tout, rtol, atol, y)
+    """step and Newton-iteration counts within 5% and 10% of the range the
+    three oracle runs span (their step sequences part by rounding alone)"""
+    runs = accuracy(p, tout, rtol, atol, y)
     C = p.ncell
     assert stats["nsteps"] % C == 0
     nst = stats["nsteps"] // C
-    assert abs(nst / so[0] - 1.0) <= 0.05, (nst, so[0])
-    assert abs(stats["nniters"] / so[3] - 1.0) <= 0.10, (stats["nniters"], so[3])
+    assert 0.95 * runs[:, 0].min() <= nst <= 1.05 * runs[:, 0].max(), (nst, runs[:, 0])
+    assert 0.9 * runs[:, 3].min() <= stats["nniters"] <= 1.1 * runs[:, 3].max(), (stats["nniters"], runs[:, 3])
     assert stats["max_steps"] == stats["min_steps"] == nst
-    return nst, so
+    return nst, runs[0]
 
 
 def test_mass_action_mixed_sizes():

@@ -136,18 +136,20 @@ def test_grouped_shared_network_against_oracle(which):
     assert np.all(stt == 0)
     w = lambda v: np.abs(v - yt) / (rtol * np.abs(yt) + atol)
     worst_max = worst_rms = 0.0
-    so = None
+    runs = []
     for f in (1.0, 1.0 + 1e-12, 1.0 - 1e-12):
         yo, ro, s = oracle.integrate_cells_grouped(p, 0.0, tout, rtol * f, atol)
         assert ro == 0
-        so = s if so is None else so
+        runs.append(s)
         worst_max, worst_rms = max(worst_max, w(yo).max()), max(worst_rms, rms(w(yo)))
+    runs = np.array(runs)
     eg = w(y)
     assert eg.max() <= max(10.0, 2.0 * worst_max), (eg.max(), worst_max)
     assert rms(eg) <= max(0.05, 1.5 * worst_rms), (rms(eg), worst_rms)
+    # counts within 5% / 10% of the range the three oracle runs span
     nst = stats["nsteps"] // p.ncell
-    assert abs(nst / so[0] - 1.0) <= 0.05, (nst, so)
-    assert abs(stats["nniters"] / so[3] - 1.0) <= 0.10, (stats["nniters"], so)
+    assert 0.95 * runs[:, 0].min() <= nst <= 1.05 * runs[:, 0].max(), (nst, runs[:, 0])
+    assert 0.9 * runs[:, 3].min() <= stats["nniters"] <= 1.1 * runs[:, 3].max(), (stats["nniters"], runs[:, 3])
     s0 = np.add.reduceat(p.y0, p.y_off[:-1])
     s1 = np.add.reduceat(y, p.y_off[:-1])
     assert np.max(np.abs(s1 - s0) / np.abs(s0)) <= 1e-12
