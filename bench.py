@@ -185,7 +185,8 @@ def nvector_bandwidth(torch, bdfb, n=1 << 25, reps=20):
     work = bdfb.nv_work(n, 8)
     s = torch.cuda.current_stream()
     ops = {
-        "linear_sum": (lambda: bdfb.nv_linear_sum(0.5, v[0], -1.0, v[1], v[2]), 24),
+        "linear_sum": (lambda: bdfb.nv_linear_sum(0.5, v[0], 0.25, v[1], v[2]), 24),
+        "linear_sum_difference": (lambda: bdfb.nv_linear_sum(0.5, v[0], -1.0, v[1], v[2]), 24),
         "linear_combination_6": (lambda: bdfb.nv_linear_combination([0.1] * 6, v[:6], v[6]), 8 * 7),
         "scale_add_multi_3": (lambda: bdfb.nv_scale_add_multi([0.1] * 3, v[0], v[1:4], v[4:7]), 8 * 7),
         "dot_prod_multi_5": (lambda: bdfb.nv_dot_prod_multi(v[0], v[1:6], out, work), 8 * 6),
@@ -210,8 +211,8 @@ def nvector_bandwidth(torch, bdfb, n=1 << 25, reps=20):
 
 # FP64 instructions per byte moved, per element of the benchmarked forms
 # (DFMA/DMUL/DADD all issue on the FP64 pipe, 2 lanes per SM per cycle)
-NV_FP64_INST_PER_BYTE = {"linear_sum": 2 / 24, "linear_combination_6": 6 / 56, "scale_add_multi_3": 3 / 56,
-                         "dot_prod_multi_5": 5 / 48, "wrms_norm": 2 / 16}
+NV_FP64_INST_PER_BYTE = {"linear_sum": 2 / 24, "linear_sum_difference": 1 / 24, "linear_combination_6": 6 / 56,
+                         "scale_add_multi_3": 3 / 56, "dot_prod_multi_5": 5 / 48, "wrms_norm": 2 / 16}
 
 
 def dgemm_tflops(torch, n=8192, reps=3):

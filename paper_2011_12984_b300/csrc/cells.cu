@@ -109,6 +109,7 @@ struct Cell {
   int nref, nref_fb, fp64mode;   // mixed precision: refinement sweeps, FP64 fallbacks, M in FP64
   double mnorm;                  // |M|_inf of the current setup (mixed precision)
   int nguess, nguess_fb;         // learned guesses taken, guesses abandoned for a zero start
+  int lastit;                    // Newton iterations of the last converged solve (gates the guess)
 };
 
 // The order-dependent loops are dispatched on q (group-uniform) to bodies
@@ -481,7 +482,10 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     // pass 0 starts from the network's guess when one is loaded; if that
     // Newton solve fails, pass 1 repeats it from zero (not a step failure)
     bool guess = false;
-    if constexpr (LEARN) guess = P.mlp != nullptr;
+    // the guess is consulted only after a zero-start solve that needed two
+    // or more iterations: where the zero start converges in one (most
+    // steps), no start can save an iteration, and an imperfect one costs one
+    if constexpr (LEARN) guess = P.mlp != nullptr && C.lastit >= 2;
     const double crate0 = C.crate;
     for (int pass = 0; pass < 2 && !conv; ++pass) {
       bool nzguess = false;     // this pass starts from a nonzero guess
@@ -579,6 +583,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         if (del2 * cr2 * eq2 <= 1.0) {           // |del| min(1, R) E_q / 0.1 <= 1
           acnrm2 = (it == 1 && !guess) ? del2 : wrms2(g, n, C.rn, C.acor, C.ewt);
           conv = true;
+          C.lastit = guess ? 0 : it;   // only a zero start's count re-arms the guess
           break;
         }
         if (it >= 2 && del2 > 4.0 * delp2) break;  // |del| > 2 |del_prev|: diverging
@@ -712,7 +717,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
     C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
     C.rn = 1.0 / (double)cd.n;
     C.nref = s.nrefine; C.nref_fb = s.nrefine_fb; C.fp64mode = 0; C.mnorm = 0.0;
-    C.nguess = s.nguess; C.nguess_fb = s.nguess_fb;
+    C.nguess = s.nguess; C.nguess_fb = s.nguess_fb; C.lastit = 0;
     C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {

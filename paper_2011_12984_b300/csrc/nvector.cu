@@ -33,6 +33,18 @@ static int grid_for(int64_t items, int threads, int per_sm) {
 }
 
 // ------------------------------------------------------------ LinearSum
+// z = a x + b y.  On B300 FP64 issues at 1/64 of FP32, so even this op is
+// co-limited by the FP64 pipe (two operations per 24 bytes); a coefficient of
+// +-1 (the sums and differences the integrators form) needs one: SB folds
+// b = +-1 into a fused multiply-add, SA folds a = +-1 (0: general).
+template <int SA, int SB>
+__device__ __forceinline__ double lsum(double a, double x, double b, double y) {
+  if (SB) return fma(a, x, SB > 0 ? y : -y);
+  if (SA) return fma(b, y, SA > 0 ? x : -x);
+  return fma(a, x, b * y);
+}
+
+template <int SA, int SB>
 __global__ void k_linear_sum2(int64_t n2, double a, const double2* x, double b, const double2* y,
                               double2* z) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -43,11 +55,12 @@ __global__ void k_linear_sum2(int64_t n2, double a, const double2* x, double b, 
     for (int u = 0; u < UNROLL; ++u) { xv[u] = __ldcs(x + i + u * stride); yv[u] = __ldcs(y + i + u * stride); }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u)
-      __stcs(z + i + u * stride, make_double2(a * xv[u].x + b * yv[u].x, a * xv[u].y + b * yv[u].y));
+      __stcs(z + i + u * stride, make_double2(lsum<SA, SB>(a, xv[u].x, b, yv[u].x),
+                                              lsum<SA, SB>(a, xv[u].y, b, yv[u].y)));
   }
   for (; i < n2; i += stride) {
     double2 xv = __ldcs(x + i), yv = __ldcs(y + i);
-    __stcs(z + i, make_double2(a * xv.x + b * yv.x, a * xv.y + b * yv.y));
+    __stcs(z + i, make_double2(lsum<SA, SB>(a, xv.x, b, yv.x), lsum<SA, SB>(a, xv.y, b, yv.y)));
   }
 }
 
@@ -373,9 +386,14 @@ extern "C" int bdfb_nv_linear_sum(int64_t n, double a, const double* x, double b
   if (aligned16(x) && aligned16(y) && aligned16(z)) {
     int64_t n2 = n >> 1;
     if (n2) {
-      k_linear_sum2<<<grid_for(n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(
-          n2, a, reinterpret_cast<const double2*>(x), b, reinterpret_cast<const double2*>(y),
-          reinterpret_cast<double2*>(z));
+      const double2 *x2 = reinterpret_cast<const double2*>(x), *y2 = reinterpret_cast<const double2*>(y);
+      double2* z2 = reinterpret_cast<double2*>(z);
+      const int g = grid_for(n2, ST_THREADS, 8);
+      if (b == 1.0) k_linear_sum2<0, 1><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
+      else if (b == -1.0) k_linear_sum2<0, -1><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
+      else if (a == 1.0) k_linear_sum2<1, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
+      else if (a == -1.0) k_linear_sum2<-1, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
+      else k_linear_sum2<0, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
     }
     if (n & 1) k_linear_sum1<<<1, 32, 0, s>>>(1, a, x + n - 1, b, y + n - 1, z + n - 1);
   } else {

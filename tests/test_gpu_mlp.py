@@ -251,9 +251,15 @@ def test_recording_one_row_per_accepted_step():
 
 
 def test_trained_network_guess():
-    """Record the plain run's pairs, train, integrate other cells of the
-    same network with the guess: accuracy bar met; Newton iterations per
-    step reported next to the plain run's."""
+    """Record the plain run's pairs, train, integrate other cells of the same
+    network with the guess.  What the trained network gains over the zero
+    start, asserted as measured: the guess is consulted only after a
+    zero-start solve that needed two or more Newton iterations (at most a
+    quarter of the steps); with (state, h, gamma) as its only features the
+    network's guesses start farther from the converged correction than zero
+    does on those steps, so the learned run takes slightly more Newton
+    iterations per step than the plain one (1.19 against 1.14 on the
+    1 000 000-cell workload), bounded here by 10 %; the accuracy bar holds."""
     from test_gpu_cells import check_against_oracle
     train = gen.mass_action_shared(4000, seed=24)
     _, cs, n, X, T = record(train, 2 * 10 ** 6)
@@ -274,9 +280,10 @@ def test_trained_network_guess():
     check_against_oracle(test, TEND, RTOL, ATOL, y1, c1, same_decisions=False, wide_factor=LEARNED_WIDE)
     it0 = st0["nniters"] / st0["nsteps"]
     it1 = st1["nniters"] / st1["nsteps"]
+    assert 0 < st1["nguess"] <= 0.25 * st1["nsteps"], (st1["nguess"], st1["nsteps"])
+    assert it1 <= 1.10 * it0, (it1, it0)
     print(f"Newton iterations per step: plain {it0:.3f}, learned {it1:.3f}; "
-          f"guesses {st1['nguess']}, redone from zero {st1['nguess_fallback']}; "
-          f"train loss {h[:20].mean():.3g} -> {h[-100:].mean():.3g}")
+          f"guesses {st1['nguess']} of {st1['nsteps']} steps, redone from zero {st1['nguess_fallback']}")
 
 
 def test_shared_network_full_size_sampled():

@@ -34,6 +34,18 @@ def test_linear_sum(n, off):
     assert np.all(np.abs(dx.cpu().numpy() - (2 * x + y)) <= 1e-14 * (np.abs(2 * x) + np.abs(y)))
 
 
+@pytest.mark.parametrize("a,b", [(0.75, 1.0), (0.75, -1.0), (1.0, -0.3), (-1.0, 0.3), (1.0, 1.0), (-1.0, -1.0)])
+def test_linear_sum_unit_coefficients(a, b):
+    """the one-operation forms for a coefficient of +-1 (sums, differences,
+    axpy) against the oracle, with an odd length (vector body and tail)"""
+    n = 262147
+    x, y = gen.uniform_vectors(n, 2, seed=7)
+    dz = to_dev(np.zeros(n))
+    bdfb.nv_linear_sum(a, to_dev(x), b, to_dev(y), dz)
+    ref = oracle.linear_sum(a, x, b, y)
+    assert np.all(np.abs(dz.cpu().numpy() - ref) <= 1e-14 * (np.abs(a * x) + np.abs(b * y)))
+
+
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("nv", [1, 3, 6, 16])
 def test_linear_combination(n, nv):
