@@ -177,6 +177,16 @@ __device__ __forceinline__ double eta_from(double d2, float safety2, float e) {
   return (double)(1.0f / (exp2f(e * __log2f(x)) + 1.0e-6f));
 }
 
+// the same ratio from FP32 work only: the squared norm converted on the
+// integer pipe (to_f32), clamped to [1e-37, 1e30] (NaN to the upper end), so
+// no FP64 instruction is issued -- the seed of the step/order choice
+__device__ __forceinline__ float eta_f(double d2, float safety2, float e) {
+  float x = to_f32(d2) * safety2;
+  if (!(x <= 1.0e30f)) x = 1.0e30f;
+  if (x < 1.0e-37f) x = 1.0e-37f;
+  return 1.0f / (exp2f(e * __log2f(x)) + 1.0e-6f);
+}
+
 // 2^n as a double for -1022 <= n <= 1023 (built from the exponent bits)
 __device__ __forceinline__ double pow2i(int n) {
   return __longlong_as_double((long long)(n + 1023) << 52);

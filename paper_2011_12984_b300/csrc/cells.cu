@@ -39,6 +39,7 @@ struct Consts {
   double l[QMAX + 1][QMAX + 1];  // l[q][j], coefficients of prod_{i<=q} (1 + x/i)
   double rl1[QMAX + 1];          // 1 / l[q][1]
   double E[QMAX + 1][3];         // E_q, E_{q-1}, E_{q+1}
+  double E2[QMAX + 1][3];        // their squares
   double qfact[QMAX + 2];        // q!
 };
 
@@ -242,11 +243,12 @@ __device__ __forceinline__ int start_cell(const Grp<G>& g, const Params& P, cons
 // choose h and q after an accepted step (same rules as the oracle: safety
 // 6 / 6 / 10, change only if the best eta >= 1.5, eta <= 1e4 before the first
 // increase and <= 10 after, ties keep q then prefer q - 1).  The candidates are
-// first formed in FP32 (eta_from); where two of them, or the best and the 1.5
-// threshold, lie within 1e-5 of each other (far above the FP32 error) all are
-// formed to FP64 accuracy (eta64) before choosing, so the choice is the one
-// FP64 arithmetic makes; the eta applied is always the FP64 one.
-__device__ __forceinline__ bool near_tie(double a, double b) { return fabs(a - b) <= 1.0e-5 * fmax(a, b); }
+// formed and compared in FP32 (eta_f: no FP64 instruction); where two of them,
+// or the best and the 1.5 threshold, lie within 1e-5 of each other (far above
+// the FP32 error) all are formed to FP64 accuracy (eta64) and compared in
+// FP64, so the choice is the one FP64 arithmetic makes; the eta applied is
+// always the FP64 one.
+__device__ __forceinline__ bool near_tie(float a, float b) { return fabsf(a - b) <= 1.0e-5f * fmaxf(a, b); }
 
 template <int G, int NMAX>
 __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, int n, double rn,
@@ -269,33 +271,36 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
         if (j == q) v = C.z[j][p];
       zq[p] = v;
     }
-    const double e = P.K.E[q][1];
-    xm = e * e * wrms2(g, n, rn, zq, C.ewt);
+    xm = wrms2(g, n, rn * P.K.E2[q][1], zq, C.ewt);
   }
   if (hp) {
 #pragma unroll
     for (int p = 0; p < NPL; ++p) C.b[p] = C.acor[p] - C.acorp[p];
-    const double e = P.K.E[q][2];
-    xp = e * e * wrms2(g, n, rn, C.b, C.ewt);
+    xp = wrms2(g, n, rn * P.K.E2[q][2], C.b, C.ewt);
   }
-  double eq = eta_from(xq, 36.0f, 0.5f / (q + 1));
-  double eqm1 = hm ? eta_from(xm, 36.0f, 0.5f / q) : 0.0;
-  double eqp1 = hp ? eta_from(xp, 100.0f, 0.5f / (q + 2)) : 0.0;
-  const bool tie = near_tie(eq, 1.5) || (hm && (near_tie(eqm1, eq) || near_tie(eqm1, 1.5))) ||
-                   (hp && (near_tie(eqp1, eq) || near_tie(eqp1, 1.5) || (hm && near_tie(eqp1, eqm1))));
-  if (tie) {
-    eq = eta64(xq, 36.0, 2 * (q + 1));
-    if (hm) eqm1 = eta64(xm, 36.0, 2 * q);
-    if (hp) eqp1 = eta64(xp, 100.0, 2 * (q + 2));
-  }
-  double etam = eq;
+  const float fq = eta_f(xq, 36.0f, 0.5f / (q + 1));
+  const float fm = hm ? eta_f(xm, 36.0f, 0.5f / q) : 0.0f;
+  const float fp = hp ? eta_f(xp, 100.0f, 0.5f / (q + 2)) : 0.0f;
+  const bool tie = near_tie(fq, 1.5f) || (hm && (near_tie(fm, fq) || near_tie(fm, 1.5f))) ||
+                   (hp && (near_tie(fp, fq) || near_tie(fp, 1.5f) || (hm && near_tie(fp, fm))));
+  double etam;
   int qn = q;
-  if (eqm1 > etam) { etam = eqm1; qn = q - 1; }
-  if (eqp1 > etam) { etam = eqp1; qn = q + 1; }
-  if (etam < 1.5) { C.qwait = 1; return; }
   const double cap = (C.flags & F_GROWN) ? 10.0 : 1.0e4;
-  if (!tie && etam < cap * 1.00001)
-    etam = qn == q ? eta64(xq, 36.0, 2 * (q + 1)) : (qn < q ? eta64(xm, 36.0, 2 * q) : eta64(xp, 100.0, 2 * (q + 2)));
+  if (tie) {
+    etam = eta64(xq, 36.0, 2 * (q + 1));
+    const double em = hm ? eta64(xm, 36.0, 2 * q) : 0.0;
+    const double ep = hp ? eta64(xp, 100.0, 2 * (q + 2)) : 0.0;
+    if (em > etam) { etam = em; qn = q - 1; }
+    if (ep > etam) { etam = ep; qn = q + 1; }
+    if (etam < 1.5) { C.qwait = 1; return; }
+  } else {
+    float fbest = fq;
+    if (fm > fbest) { fbest = fm; qn = q - 1; }
+    if (fp > fbest) { fbest = fp; qn = q + 1; }
+    if (fbest < 1.5f) { C.qwait = 1; return; }
+    etam = fbest >= ((C.flags & F_GROWN) ? 10.0f : 1.0e4f) * 1.00001f ? cap
+           : (qn == q ? eta64(xq, 36.0, 2 * (q + 1)) : (qn < q ? eta64(xm, 36.0, 2 * q) : eta64(xp, 100.0, 2 * (q + 2))));
+  }
   if (etam > cap) etam = cap;
   C.flags |= F_GROWN;
   if (qn == q + 1) {
@@ -433,8 +438,9 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   // ---- linear setup
   int jcur = 0;
   bool fail = false;
-  const double gratio = C.gamma / C.gammap;   // (not used before the first setup)
-  if (!C.setup_done || C.force_setup || fabs(gratio - 1.0) > 0.3 || C.nst >= C.nstlp + 20) {
+  // |gamma / gamma_setup - 1| > 0.3 tested without a division
+  const double dgam = C.gamma - C.gammap;
+  if (!C.setup_done || C.force_setup || fabs(dgam) > 0.3 * fabs(C.gammap) || C.nst >= C.nstlp + 20) {
     double y[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
@@ -473,7 +479,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   }
   // ---- Newton iteration (norms compared squared, in FP64)
   // a stale M's step scaling 2 / (1 + gamma / gamma_setup), once per attempt
-  const double scst = C.gamma != C.gammap ? 2.0 / (1.0 + gratio) : 1.0;
+  const double scst = C.gamma != C.gammap ? 2.0 * C.gammap / (C.gammap + C.gamma) : 1.0;
   double acnrm2 = 0.0;
   bool conv = false;
   float feat = 0.f;
@@ -1183,6 +1189,7 @@ static Consts make_consts() {
       for (int i = 1; i <= q + 1; ++i) l1 += 1.0 / (double)i;
       K.E[q][2] = 1.0 / ((q + 2) * l1);
     }
+    for (int k = 0; k < 3; ++k) K.E2[q][k] = K.E[q][k] * K.E[q][k];
   }
   return K;
 }
