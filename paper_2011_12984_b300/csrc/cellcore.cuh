@@ -386,12 +386,13 @@ __device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellS
 // Right-looking LU with partial pivoting of the n x n matrix in S.M (ties in
 // |pivot| go to the lowest row).  Returns 0 or k + 1 when pivot k is zero (or
 // no finite pivot exists).  pivk (optional) records the pivot row of each step.
+// One pivot at a time (the small groups, where the lanes form no grid).
 // UNITU: the strictly upper part is stored divided by its row's pivot (P M =
 // L D U' with U' unit upper, D = diag(1 / dinv)), so that a solve needs one
 // vector scaling by dinv instead of a multiply per back-substitution column.
 template <int G, int NMAX, typename T, bool UNITU = false>
-__device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* dinv, int16_t* perm, int n,
-                         int16_t* pivk = nullptr) {
+__device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* dinv, int16_t* perm, int n,
+                          int16_t* pivk = nullptr) {
   for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
   g.sync();
   for (int k = 0; k < n; ++k) {
@@ -461,6 +462,129 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     g.sync();
   }
   return 0;
+}
+
+// Partial pivoting at column k (rows k..n-1): the largest |M[i][k]|, ties to
+// the lowest row, found on integer keys (the bit patterns of non-negative
+// IEEE doubles order like their values; a NaN key exceeds every finite one and
+// is rejected), then rows k and p swapped across all columns.  Returns false
+// when the pivot is zero or not finite.
+template <int G, int NMAX, typename T>
+__device__ __forceinline__ bool pivot_swap(const Grp<G>& g, T (*M)[NMAX + 1], int16_t* perm, int n, int k,
+                                           int16_t* pivk) {
+  long long best = -1;
+  int p = n;
+  for (int i = k + g.rank; i < n; i += G) {
+    const long long v = __double_as_longlong(fabs((double)M[i][k]));
+    if (v > best) { best = v; p = i; }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(g.mask, best, o, G);
+    const int op = __shfl_xor_sync(g.mask, p, o, G);
+    if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+  }
+  if (p >= n || best <= 0 || best >= 0x7ff0000000000000LL) return false;
+  if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
+  if (p != k) {
+    for (int j = g.rank; j < n; j += G) {
+      const T a = M[k][j];
+      M[k][j] = M[p][j];
+      M[p][j] = a;
+    }
+    if (g.rank == 0) {
+      const int16_t a = perm[k];
+      perm[k] = perm[p];
+      perm[p] = a;
+    }
+  }
+  g.sync();
+  return true;
+}
+
+// LU with partial pivoting, P M = L U, in place (L unit lower below the
+// diagonal, U on and above; dinv[k] = 1 / U_kk; perm: row i of P M is row
+// perm[i] of M; pivk[k], if given, the row swapped with k at step k).  Returns
+// 0, or k + 1 when pivot k is zero or not finite.
+// Pivots are taken two at a time: column k is pivoted and scaled, column k+1
+// receives step k's update and is pivoted and scaled, row k+1 receives step
+// k's update, and the trailing block takes both rank-1 updates in one pass
+// (each element read and written once per two pivots, the two fused
+// multiply-adds in the order of two single steps, so the factors are those
+// of the one-pivot-at-a-time elimination bit for bit).
+// UNITU: the strictly upper part is stored divided by its row's pivot (P M =
+// L D U' with U' unit upper, D = diag(1 / dinv)), so that a solve needs one
+// vector scaling by dinv instead of a multiply per back-substitution column.
+template <int G, int NMAX, typename T, bool UNITU = false>
+__device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* dinv, int16_t* perm, int n,
+                         int16_t* pivk = nullptr) {
+  if constexpr (G < 8) {
+    return lu_factor1<G, NMAX, T, UNITU>(g, M, dinv, perm, n, pivk);
+  } else {
+  for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
+  g.sync();
+  constexpr int R = LaneGrid<G>::R, C = LaneGrid<G>::C;
+  constexpr int NJ = (NMAX + C - 1) / C;
+  const int li = g.rank / C, lj = g.rank % C;
+  int k = 0;
+  for (; k + 1 < n; k += 2) {
+    const int k1 = k + 1, k2 = k + 2;
+    // ---- column k
+    if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k, pivk)) return k + 1;
+    const T r0 = (T)1 / M[k][k];
+    if (g.rank == 0) dinv[k] = r0;
+    for (int i = k1 + g.rank; i < n; i += G) {
+      const T l = M[i][k] * r0;
+      M[i][k] = l;
+      M[i][k1] = fma(-l, M[k][k1], M[i][k1]);     // column k+1 gets step k's update
+    }
+    g.sync();
+    // ---- column k+1
+    if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k1, pivk)) return k1 + 1;
+    const T r1 = (T)1 / M[k1][k1];
+    if (g.rank == 0) dinv[k1] = r1;
+    for (int i = k2 + g.rank; i < n; i += G) M[i][k1] *= r1;
+    {
+      const T l = M[k1][k];                        // row k+1 gets step k's update
+      for (int j = k2 + g.rank; j < n; j += G) M[k1][j] = fma(-l, M[k][j], M[k1][j]);
+    }
+    g.sync();
+    // ---- both updates of the trailing block, lanes on an R x C grid; column
+    // slots past the trailing width would issue predicated-off FP64 work
+    {
+      const int nbu = (n - k2 + C - 1) / C;
+      T u0[NJ], u1[NJ];
+#pragma unroll
+      for (int b = 0; b < NJ; ++b) {
+        if (b >= nbu) break;
+        const int j = k2 + lj + C * b;
+        u0[b] = j < n ? M[k][j] : (T)0;
+        u1[b] = j < n ? M[k1][j] : (T)0;
+      }
+      for (int i = k2 + li; i < n; i += R) {
+        const T a0 = M[i][k], a1 = M[i][k1];
+#pragma unroll
+        for (int b = 0; b < NJ; ++b) {
+          if (b >= nbu) break;
+          const int j = k2 + lj + C * b;
+          if (j < n) M[i][j] = fma(-a1, u1[b], fma(-a0, u0[b], M[i][j]));
+        }
+      }
+      if constexpr (UNITU) {
+        g.sync();                     // every lane has read rows k and k+1
+        for (int j = k1 + g.rank; j < n; j += G) M[k][j] *= r0;
+        for (int j = k2 + g.rank; j < n; j += G) M[k1][j] *= r1;
+      }
+    }
+    g.sync();
+  }
+  if (k < n) {                        // the last pivot of an odd order
+    if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k, pivk)) return k + 1;
+    if (g.rank == 0) dinv[k] = (T)1 / M[k][k];
+    g.sync();
+  }
+  return 0;
+  }
 }
 
 // x <- (P M)^{-1} P x with the factors above; x distributed over the group.

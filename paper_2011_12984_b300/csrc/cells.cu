@@ -546,7 +546,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
               if (Mg == nullptr) { restore_z(g, n, S, C); C.status = BDFB_MEM_FAIL; return true; }  // never write through null
               C.nref_fb++;
               form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
-              if (lu_factor<G, NMAX, double, true>(g, Mg, S.dinv, S.perm, n)) {
+              if (lu_factor1<G, NMAX, double, true>(g, Mg, S.dinv, S.perm, n)) {
                 C.setup_done = 0;
                 break;                      // singular: counts as a Newton failure
               }
