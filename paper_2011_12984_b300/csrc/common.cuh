@@ -71,9 +71,11 @@ __device__ __forceinline__ double to_f64(float f) {
 // once, so the result lies within about half an ulp of the quotient (an
 // exact-arithmetic check of 6000 seeds over [1e-10, 1e10] found at most
 // 0.49991 ulp), for four FP64 FMAs instead of a full-precision division.
-// Magnitudes outside [1e-30, 1e30] take the division.
+// Magnitudes outside [2^-99, 2^101) (and zero, negative or non-finite s) take
+// the division; the range test reads the exponent bits on the integer pipe.
 __device__ __forceinline__ double recip_nr(double s) {
-  if (!(s >= 1e-30 && s <= 1e30)) return 1.0 / s;
+  const long long b = __double_as_longlong(s);
+  if ((unsigned long long)(b - (924LL << 52)) >= (200ULL << 52)) return 1.0 / s;
   double x = to_f64(__frcp_rn(to_f32(s)));
   double e = fma(-s, x, 1.0);
   x = fma(x, e, x);

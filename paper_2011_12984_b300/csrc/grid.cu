@@ -287,16 +287,23 @@ __global__ void k_ratio_max(int64_t N, double atol, const double* __restrict__ f
   }
 }
 
-// predicted z_0 and z_1 (Pascal sums of the history), z left untouched
-__global__ void k_predict01(int64_t N, int q, GZ Z, double* __restrict__ zp0, double* __restrict__ zp1) {
+// predicted z_0 and z_1 (Pascal sums of the history), z left untouched:
+// with the suffix sums s_j = z_j + s_{j+1} (j = q..1), z_0 + s_1 is the
+// predicted z_0 and s_1 + ... + s_q = sum_k k z_k the predicted z_1 (2q
+// additions per element, no multiplications)
+template <int Q>
+__global__ void k_predict01(int64_t N, GZ Z, double* __restrict__ zp0, double* __restrict__ zp1) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int k = q; k >= 1; --k) {
-      const double zk = Z.z[k][i];
-      s0 += zk;
-      s1 += (double)k * zk;        // C(k, 1) = k
+    double zz[Q + 1];
+#pragma unroll
+    for (int k = 0; k <= Q; ++k) zz[k] = Z.z[k][i];
+    double s = zz[Q], s1 = zz[Q];
+#pragma unroll
+    for (int k = Q - 1; k >= 1; --k) {
+      s += zz[k];
+      s1 += s;
     }
-    zp0[i] = Z.z[0][i] + s0;
+    zp0[i] = zz[0] + s;
     zp1[i] = s1;
   }
 }
@@ -732,7 +739,13 @@ static int g_newton(GridBDF* g, double Eq, double* acnrm) {
 static int g_predict(GridBDF* g) {
   {
     GTimed t(g, GOP_PREDICT, 8.0 * (g->q + 3) * g->N);
-    k_predict01<<<gblocks(g->N), GT, 0, g->s>>>(g->N, g->q, zcols(g), g->zp0, g->zp1);
+    switch (g->q) {
+      case 1: k_predict01<1><<<gblocks(g->N), GT, 0, g->s>>>(g->N, zcols(g), g->zp0, g->zp1); break;
+      case 2: k_predict01<2><<<gblocks(g->N), GT, 0, g->s>>>(g->N, zcols(g), g->zp0, g->zp1); break;
+      case 3: k_predict01<3><<<gblocks(g->N), GT, 0, g->s>>>(g->N, zcols(g), g->zp0, g->zp1); break;
+      case 4: k_predict01<4><<<gblocks(g->N), GT, 0, g->s>>>(g->N, zcols(g), g->zp0, g->zp1); break;
+      default: k_predict01<5><<<gblocks(g->N), GT, 0, g->s>>>(g->N, zcols(g), g->zp0, g->zp1); break;
+    }
   }
   BDFB_CUDA(cudaGetLastError());
   return 0;
