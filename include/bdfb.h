@@ -225,16 +225,21 @@ int bdfb_sparse_solve(const bdfb_sparse* sp, int64_t nb, const double* lu, doubl
  *   submodel case of Sec. 2 and Sec. 5 with one sparsity pattern for every
  *   block): n[0] species (1..255), reactions rxn_off[0] = 0 .. rxn_off[1]
  *   (at most 65535), reactants / products / k of that network (host memory
- *   only; y_off unused).  y is species-major, y[s ncell + c].  Integrated as
- *   one grouped system (shared step size and order, error test over all
- *   species) with task-local Newton solves per cell on the shared sparse
- *   pattern of M = I - gamma J (bdfb_sparse's LU, one thread per cell);
- *   options mxstep, qmax, interp and lsolver 0 (any other option returns
- *   BDFB_ILL_INPUT); (LU entries with fill, reactions and species)
+ *   only; y_off unused).  y is species-major, y[s ncell + c].  By default
+ *   integrated as one grouped system (shared step size and order, error test
+ *   over all species) with task-local Newton solves per cell on the shared
+ *   sparse pattern of M = I - gamma J (bdfb_sparse's LU, one thread per
+ *   cell).  Option "grouped" 0 (set before bdfb_init) integrates every cell
+ *   with its own step size and order instead, one thread per cell running
+ *   the per-cell integrator's step (the same readings as BDFB_MASSACTION)
+ *   on the shared sparse LU; per-cell statuses then fill `status`.
+ *   Options mxstep, qmax, interp, grouped and lsolver 0 (any other option
+ *   returns BDFB_ILL_INPUT); (LU entries with fill, reactions and species)
  *   x ncell must stay below 2^30 (BDFB_ILL_INPUT otherwise: about 9e5
- *   cells of a 128-species banded network).  bdfb_get_cell_stats gives one row: nst, nfe,
+ *   cells of a 128-species banded network).  bdfb_get_cell_stats gives, grouped, one row: nst, nfe,
  *   nsetups, nni (summed over cells), ncfn, netf, LU entries with fill,
- *   entries of M's pattern.
+ *   entries of M's pattern; per cell, one row per cell as for
+ *   BDFB_MASSACTION.
  * y_off / rxn_off have ncell + 1 entries starting at 0.  `mem` says where all
  * arrays live; bdfb_create copies everything it needs, so the caller may
  * free its arrays when bdfb_create returns. */

@@ -340,7 +340,8 @@ class Integrator:
     ``shared_network=True`` (a problem whose cells all carry cell 0's network)
     creates a BDFB_MASSACTION_SHARED context: one copy of the network, states
     species-major (see ``species_major``), grouped integration on the shared
-    sparse pattern."""
+    sparse pattern, or with option grouped=0 every cell with its own step
+    size and order on that pattern."""
 
     def __init__(self, problem, rtol=1e-6, atol=1e-10, stream=None, shared_network=False, **options):
         self._keep = []
@@ -391,6 +392,7 @@ class Integrator:
         else:
             self.ncell = problem.ncell
             self.ny = int(problem.y_off[-1])
+        self.shared = shared_network
         self.stat_rows = 1 if shared_network else self.ncell
         self.set_stream(stream)
         check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")
@@ -403,6 +405,8 @@ class Integrator:
 
     def set_option(self, key, value):
         check(lib.bdfb_set_option(self.h, key.encode(), int(value)), f"bdfb_set_option({key})")
+        if self.shared and key == "grouped":          # per-cell mode: one row of counters per cell
+            self.stat_rows = 1 if int(value) else self.ncell
 
     def set_tolerances(self, rtol, atol):
         check(lib.bdfb_set_tolerances(self.h, rtol, atol), "bdfb_set_tolerances")

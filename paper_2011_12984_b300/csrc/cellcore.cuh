@@ -10,6 +10,7 @@
 // same scalars and all control flow is uniform inside a group.
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
@@ -68,6 +69,47 @@ struct LaneGrid {
 };
 
 constexpr int ZCOLS = 6;      // Nordsieck columns z_0 .. z_5 (orders <= 5)
+
+// ------------------------------------------------------- BDF coefficients
+constexpr int QMAX = 5;
+
+// constant-step Nordsieck coefficients and error constants of orders 1..QMAX
+struct Consts {
+  double l[QMAX + 1][QMAX + 1];  // l[q][j], coefficients of prod_{i<=q} (1 + x/i)
+  double rl1[QMAX + 1];          // 1 / l[q][1]
+  double E[QMAX + 1][3];         // E_q, E_{q-1}, E_{q+1}
+  double E2[QMAX + 1][3];        // their squares
+  double qfact[QMAX + 2];        // q!
+};
+
+// the tables above, built on the host once
+inline Consts make_consts() {
+  Consts K;
+  std::memset(&K, 0, sizeof K);
+  for (int q = 1; q <= QMAX; ++q) {
+    double l[QMAX + 2] = {0};
+    l[0] = 1.0;
+    for (int i = 1; i <= q; ++i)
+      for (int j = i; j >= 1; --j) l[j] += l[j - 1] / (double)i;
+    for (int j = 0; j <= q; ++j) K.l[q][j] = l[j];
+  }
+  K.qfact[0] = 1.0;
+  for (int q = 1; q <= QMAX + 1; ++q) K.qfact[q] = K.qfact[q - 1] * q;
+  for (int q = 1; q <= QMAX; ++q) {
+    K.rl1[q] = 1.0 / K.l[q][1];
+    K.E[q][0] = 1.0 / ((q + 1) * K.l[q][1]);
+    K.E[q][1] = q > 1 ? K.qfact[q - 1] / K.l[q - 1][1] : 0.0;
+    if (q < QMAX) {
+      // l_1 of order q+1
+      double l1 = 0.0;
+      for (int i = 1; i <= q + 1; ++i) l1 += 1.0 / (double)i;
+      K.E[q][2] = 1.0 / ((q + 2) * l1);
+    }
+    for (int k = 0; k < 3; ++k) K.E2[q][k] = K.E[q][k] * K.E[q][k];
+  }
+  return K;
+}
+
 
 // reaction rates (RHS scratch) and dr[a][r] = d rate_r / d y_(reactant a) at
 // the setup point (mass action).  FP64 path: the rates live only inside a RHS call and

@@ -29,19 +29,12 @@
 
 namespace bdfb {
 
-constexpr int QMAX = 5;
 constexpr int NCLASS = 5;
 constexpr int CLS_G[NCLASS] = {1, 4, 8, 16, 32};
 constexpr int CLS_NMAX[NCLASS] = {4, 8, 16, 32, 56};
 constexpr int NMAX_ALL = 56;
 
-struct Consts {
-  double l[QMAX + 1][QMAX + 1];  // l[q][j], coefficients of prod_{i<=q} (1 + x/i)
-  double rl1[QMAX + 1];          // 1 / l[q][1]
-  double E[QMAX + 1][3];         // E_q, E_{q-1}, E_{q+1}
-  double E2[QMAX + 1][3];        // their squares
-  double qfact[QMAX + 2];        // q!
-};
+
 
 struct CellState {
   double t, h, gammap, crate, hlast;   // crate: the squared Newton rate R^2
@@ -1167,32 +1160,7 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
   }
 }
 
-static Consts make_consts() {
-  Consts K;
-  std::memset(&K, 0, sizeof K);
-  for (int q = 1; q <= QMAX; ++q) {
-    double l[QMAX + 2] = {0};
-    l[0] = 1.0;
-    for (int i = 1; i <= q; ++i)
-      for (int j = i; j >= 1; --j) l[j] += l[j - 1] / (double)i;
-    for (int j = 0; j <= q; ++j) K.l[q][j] = l[j];
-  }
-  K.qfact[0] = 1.0;
-  for (int q = 1; q <= QMAX + 1; ++q) K.qfact[q] = K.qfact[q - 1] * q;
-  for (int q = 1; q <= QMAX; ++q) {
-    K.rl1[q] = 1.0 / K.l[q][1];
-    K.E[q][0] = 1.0 / ((q + 1) * K.l[q][1]);
-    K.E[q][1] = q > 1 ? K.qfact[q - 1] / K.l[q - 1][1] : 0.0;
-    if (q < QMAX) {
-      // l_1 of order q+1
-      double l1 = 0.0;
-      for (int i = 1; i <= q + 1; ++i) l1 += 1.0 / (double)i;
-      K.E[q][2] = 1.0 / ((q + 2) * l1);
-    }
-    for (int k = 0; k < 3; ++k) K.E2[q][k] = K.E[q][k] * K.E[q][k];
-  }
-  return K;
-}
+
 
 }  // namespace bdfb
 
@@ -2125,6 +2093,7 @@ static int grouped_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* sta
 extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* status, int32_t mem) {
   if (!ctx || !ctx->initialized || !std::isfinite(tout)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->shared && shared_percell(ctx->shared)) return shared_integrate_cells(ctx->shared, tout, y, status, mem);
   if (ctx->shared) {
     const int r = shared_integrate(ctx->shared, tout, y, mem);
     if (status && ctx->ncell > 0) {
@@ -2231,6 +2200,25 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
     out->last_kernel_ms = ms;
     return BDFB_SUCCESS;
   }
+  if (ctx->shared && shared_percell(ctx->shared)) {   // sums over the cells' own counters
+    std::vector<int64_t> rows;
+    double ms = 0.0;
+    const int r = shared_cell_stats(ctx->shared, rows, &ms);
+    if (r) return r;
+    std::memset(out, 0, sizeof *out);
+    const int64_t C = ctx->ncell;
+    out->ncell = C;
+    out->min_steps = C ? INT64_MAX : 0;
+    for (int64_t c = 0; c < C; ++c) {
+      const int64_t* o = rows.data() + 8 * c;
+      out->nsteps += o[0]; out->nfevals += o[1]; out->nlinsetups += o[2]; out->nniters += o[3];
+      out->nncfails += o[4]; out->netfails += o[5];
+      out->max_steps = std::max(out->max_steps, o[0]);
+      out->min_steps = std::min(out->min_steps, o[0]);
+    }
+    out->last_kernel_ms = ms;
+    return BDFB_SUCCESS;
+  }
   if (ctx->shared) {               // every cell takes every grouped step
     int64_t g[8];
     double ms = 0.0, h = 0.0;
@@ -2300,6 +2288,16 @@ extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {
 extern "C" int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem) {
   if (!ctx || (!out && ctx->ncell > 0)) return BDFB_ILL_INPUT;
   if (mem != BDFB_MEM_HOST && mem != BDFB_MEM_DEVICE) return BDFB_ILL_INPUT;
+  if (ctx->shared && shared_percell(ctx->shared)) {
+    std::vector<int64_t> rows;
+    double ms = 0.0;
+    const int r = shared_cell_stats(ctx->shared, rows, &ms);
+    if (r) return r;
+    if (ctx->ncell == 0) return BDFB_SUCCESS;
+    if (mem == BDFB_MEM_HOST) std::memcpy(out, rows.data(), rows.size() * sizeof(int64_t));
+    else BDFB_CUDA(cudaMemcpy(out, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    return BDFB_SUCCESS;
+  }
   if (ctx->shared) {
     int64_t g[8];
     double ms = 0.0, h = 0.0;

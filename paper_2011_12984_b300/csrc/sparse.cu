@@ -18,6 +18,7 @@
 #include <new>
 #include <vector>
 
+#include "cellcore.cuh"
 #include "grid.cuh"
 #include "sparse.cuh"
 
@@ -451,6 +452,428 @@ __global__ void __launch_bounds__(ST) k_net_newton(NetDev D, NewtonArgs A, doubl
   if (!conv) atomicOr(A.failed, 1);
 }
 
+
+// ---------------------------------------------- per-cell step control
+// Every cell of the shared network integrated with its own step size and
+// order by one thread (the per-cell mode of the other cell workloads, on the
+// shared sparse pattern): the BDF/Newton step of the per-cell integrator --
+// prediction, Jacobian reuse, Newton with the rate test and a stale-M retry,
+// local error test, accept, step and order choice -- over the cell's
+// entry-major vectors, with M = I - gamma J factored by the shared sparse LU.
+// Threads of a warp run their cells' steps in lockstep where their control
+// agrees and serialise where it does not (a setup or a second Newton
+// iteration of one cell); every access of a warp touches 32 consecutive
+// doubles.
+struct NetCellState {
+  double t, h, gammap, crate, hlast;   // crate: the squared Newton rate R^2
+  int32_t q, qwait, nst, nstlp;
+  int32_t nfe, nsetups, nni, ncfn;
+  int32_t netf, flags, status, qlast;
+};
+enum { NF_STARTED = 1, NF_GROWN = 2 };
+
+struct NetCellArgs {
+  NetDev D;
+  double *z, *zs;                      // (QMAX + 1) n nb: plane j, species s at (j n + s) nb
+  double *acor, *acorp, *ewt;          // n nb
+  double *y, *x;                       // n nb scratch
+  double *lu, *rates;
+  NetCellState* st;
+  int32_t* status;                     // per cell (may be null)
+  double* yout;                        // interpolated output (interp), n nb
+  int* worst;
+  double tout, rtol, atol;
+  int32_t mxstep, qmax, interp;
+  Consts K;
+};
+
+struct NetCell {
+  double t, h, gamma, gammap, crate, hlast;
+  int q, qwait, nst, nstlp, nfe, nsetups, nni, ncfn, netf, qlast, flags, status;
+  int nst0, ncf, nef, setup_done, force_setup, tried_fresh, newstep, last, retry;
+};
+
+// the cell's vectors: base pointers already offset by the cell
+struct NetV {
+  double *z, *zs, *acor, *acorp, *ewt, *y, *x, *lu, *rates;
+  int64_t nb;
+  int n;
+  __device__ __forceinline__ double& Z(int j, int s) const { return z[((int64_t)j * n + s) * nb]; }
+  __device__ __forceinline__ double& ZS(int j, int s) const { return zs[((int64_t)j * n + s) * nb]; }
+  __device__ __forceinline__ double& at(double* a, int s) const { return a[(int64_t)s * nb]; }
+};
+
+// sum (x_s w_s)^2 over the cell's species, times rn
+__device__ __forceinline__ double net_wrms2(const NetV& V, const double* a, double rn) {
+  double s2 = 0.0;
+  for (int s = 0; s < V.n; ++s) {
+    const double v = a[(int64_t)s * V.nb] * V.ewt[(int64_t)s * V.nb];
+    s2 = fma(v, v, s2);
+  }
+  return s2 * rn;
+}
+
+// f(y) into out (rates into V.rates); false when an entry is not finite
+__device__ __forceinline__ bool net_f(const NetDev& D, const NetV& V, const double* y, double* out) {
+  net_rates(D, y, V.rates);
+  bool fin = true;
+  for (int s = 0; s < V.n; ++s) {
+    const double f = net_fs(D, V.rates, s);
+    fin = fin && finite_bits(f);
+    out[(int64_t)s * V.nb] = f;
+  }
+  return fin;
+}
+
+__device__ __forceinline__ void net_set_ewt(const NetCellArgs& A, const NetV& V) {
+  for (int s = 0; s < V.n; ++s) V.at(V.ewt, s) = 1.0 / (A.rtol * fabs(V.Z(0, s)) + A.atol);
+}
+
+__device__ __forceinline__ void net_rescale(const NetV& V, NetCell& C, double eta) {
+  for (int s = 0; s < V.n; ++s) {
+    double f = 1.0;
+    for (int j = 1; j <= C.q; ++j) {
+      f *= eta;
+      V.Z(j, s) *= f;
+    }
+  }
+  C.h *= eta;
+}
+
+__device__ __forceinline__ void net_restore(const NetV& V, const NetCell& C) {
+  for (int s = 0; s < V.n; ++s)
+    for (int j = 0; j <= C.q; ++j) V.Z(j, s) = V.ZS(j, s);
+}
+
+// saved copy of z_0..z_Q, then the prediction in place (registers per species)
+template <int Q>
+__device__ __forceinline__ void net_predict(const NetV& V) {
+  for (int s = 0; s < V.n; ++s) {
+    double zz[Q + 1];
+#pragma unroll
+    for (int j = 0; j <= Q; ++j) {
+      zz[j] = V.Z(j, s);
+      V.ZS(j, s) = zz[j];
+    }
+#pragma unroll
+    for (int k = 1; k <= Q; ++k)
+#pragma unroll
+      for (int j = Q; j >= k; --j) zz[j - 1] += zz[j];
+#pragma unroll
+    for (int j = 0; j <= Q; ++j) V.Z(j, s) = zz[j];
+  }
+}
+
+// initial step and history (the per-cell integrator's reading); 0 or a code
+__device__ int net_start(const NetCellArgs& A, const NetV& V, NetCell& C) {
+  const NetDev& D = A.D;
+  const int n = V.n;
+  net_set_ewt(A, V);
+  if (!net_f(D, V, V.z, V.acor)) return BDFB_RHSFUNC_FAIL;          // f0 in acor
+  C.nfe++;
+  const double tdist = fabs(A.tout - C.t);
+  const double tround = 2.220446049250313e-16 * fmax(fabs(C.t), fabs(A.tout));
+  const double hlb = 100.0 * tround;
+  double hub = 0.1 * tdist;
+  double inv = 0.0;
+  for (int s = 0; s < n; ++s) inv = fmax(inv, fabs(V.at(V.acor, s)) / (0.1 * fabs(V.Z(0, s)) + A.atol));
+  if (inv * hub > 1.0) hub = 1.0 / inv;
+  if (hub < hlb) hub = hlb;
+  double hg = sqrt(hlb * hub), hnew = hg;
+  const double rn = 1.0 / (double)n;
+  for (int it = 0; it < 4; ++it) {
+    bool ok = false;
+    for (int tries = 0; tries < 4; ++tries) {
+      for (int s = 0; s < n; ++s) V.at(V.y, s) = V.Z(0, s) + hg * V.at(V.acor, s);
+      ok = net_f(D, V, V.y, V.x);
+      C.nfe++;
+      if (ok) break;
+      hg *= 0.2;
+    }
+    if (!ok) return BDFB_RHSFUNC_FAIL;
+    for (int s = 0; s < n; ++s) V.at(V.x, s) = (V.at(V.x, s) - V.at(V.acor, s)) / hg;
+    const double ydd = sqrt(net_wrms2(V, V.x, rn));
+    hnew = (ydd * hub * hub > 2.0) ? sqrt(2.0 / ydd) : sqrt(hg * hub);
+    const double rat = hnew / hg;
+    if (it > 0 && rat > 0.5 && rat < 2.0) break;
+    hg = hnew;
+  }
+  double h0 = 0.5 * hnew;
+  if (h0 < hlb) h0 = hlb;
+  if (h0 > hub) h0 = hub;
+  C.h = (A.tout >= C.t) ? h0 : -h0;
+  for (int s = 0; s < n; ++s) {
+    V.Z(1, s) = C.h * V.at(V.acor, s);
+    for (int j = 2; j <= QMAX; ++j) V.Z(j, s) = 0.0;
+  }
+  C.q = 1;
+  C.qwait = 2;
+  C.flags |= NF_STARTED;
+  return 0;
+}
+
+// step size and order after an accepted step: the per-cell integrator's rules
+// (FP32 candidates, FP64 near ties and the FP64 applied ratio)
+__device__ __forceinline__ void net_select(const NetCellArgs& A, const NetV& V, NetCell& C, double dsm2, double rn) {
+  if (--C.qwait > 0) return;
+  const int q = C.q;
+  const bool hm = q > 1, hp = q < A.qmax;
+  const double xq = dsm2;
+  double xm = 0.0, xp = 0.0;
+  if (hm) {
+    double s2 = 0.0;
+    for (int s = 0; s < V.n; ++s) {
+      const double v = V.Z(q, s) * V.at(V.ewt, s);
+      s2 = fma(v, v, s2);
+    }
+    xm = s2 * (rn * A.K.E2[q][1]);
+  }
+  if (hp) {
+    double s2 = 0.0;
+    for (int s = 0; s < V.n; ++s) {
+      const double v = (V.at(V.acor, s) - V.at(V.acorp, s)) * V.at(V.ewt, s);
+      s2 = fma(v, v, s2);
+    }
+    xp = s2 * (rn * A.K.E2[q][2]);
+  }
+  const float fq = eta_f(xq, 36.0f, 0.5f / (q + 1));
+  const float fm = hm ? eta_f(xm, 36.0f, 0.5f / q) : 0.0f;
+  const float fp = hp ? eta_f(xp, 100.0f, 0.5f / (q + 2)) : 0.0f;
+  auto near = [](float a, float b) { return fabsf(a - b) <= 1.0e-5f * fmaxf(a, b); };
+  const bool tie = near(fq, 1.5f) || (hm && (near(fm, fq) || near(fm, 1.5f))) ||
+                   (hp && (near(fp, fq) || near(fp, 1.5f) || (hm && near(fp, fm))));
+  double etam;
+  int qn = q;
+  const double cap = (C.flags & NF_GROWN) ? 10.0 : 1.0e4;
+  if (tie) {
+    etam = eta64(xq, 36.0, 2 * (q + 1));
+    const double em = hm ? eta64(xm, 36.0, 2 * q) : 0.0;
+    const double ep = hp ? eta64(xp, 100.0, 2 * (q + 2)) : 0.0;
+    if (em > etam) { etam = em; qn = q - 1; }
+    if (ep > etam) { etam = ep; qn = q + 1; }
+    if (etam < 1.5) { C.qwait = 1; return; }
+  } else {
+    float fbest = fq;
+    if (fm > fbest) { fbest = fm; qn = q - 1; }
+    if (fp > fbest) { fbest = fp; qn = q + 1; }
+    if (fbest < 1.5f) { C.qwait = 1; return; }
+    etam = fbest >= ((C.flags & NF_GROWN) ? 10.0f : 1.0e4f) * 1.00001f ? cap
+           : (qn == q ? eta64(xq, 36.0, 2 * (q + 1)) : (qn < q ? eta64(xm, 36.0, 2 * q) : eta64(xp, 100.0, 2 * (q + 2))));
+  }
+  if (etam > cap) etam = cap;
+  C.flags |= NF_GROWN;
+  if (qn == q + 1) {
+    for (int s = 0; s < V.n; ++s) V.Z(q + 1, s) = V.at(V.acor, s) / A.K.qfact[q + 1];
+    C.q = q + 1;
+  } else if (qn == q - 1) {
+    for (int s = 0; s < V.n; ++s) V.Z(q, s) = 0.0;
+    C.q = q - 1;
+  }
+  net_rescale(V, C, etam);
+  C.qwait = C.q + 1;
+}
+
+// one step attempt; true when the cell is finished (tout reached or a
+// failure status set)
+__device__ __forceinline__ bool net_attempt(const NetCellArgs& A, const NetV& V, NetCell& C) {
+  const NetDev& D = A.D;
+  const int n = V.n;
+  const double rn = 1.0 / (double)n;
+  if (!(C.flags & NF_STARTED)) {
+    if (A.tout == C.t) { C.status = 0; return true; }
+    const int r = net_start(A, V, C);
+    if (r) { C.status = r; return true; }
+    C.newstep = 1;
+  }
+  if (C.newstep) {
+    if ((A.tout - C.t) * C.h <= 0.0) { C.status = 0; return true; }
+    if (C.nst - C.nst0 >= A.mxstep) { C.status = BDFB_TOO_MUCH_WORK; return true; }
+    net_set_ewt(A, V);
+    C.ncf = 0;
+    C.nef = 0;
+    C.newstep = 0;
+    C.retry = 0;
+  }
+  if (!C.retry) {
+    C.last = 0;
+    if (!A.interp && (C.t + C.h - A.tout) * C.h >= 0.0) {
+      C.last = 1;
+      if (C.t + C.h != A.tout) { net_rescale(V, C, (A.tout - C.t) / C.h); C.qwait = C.q + 1; }
+    }
+  }
+  C.retry = 0;
+  if (C.t + C.h == C.t) { C.status = BDFB_ERR_FAILURE; return true; }
+  const int q = C.q;
+  // save, then predict: z_{j-1} += z_j repeatedly (Pascal triangle)
+  switch (q) {
+    case 1: net_predict<1>(V); break;
+    case 2: net_predict<2>(V); break;
+    case 3: net_predict<3>(V); break;
+    case 4: net_predict<4>(V); break;
+    default: net_predict<5>(V); break;
+  }
+  const double tnew = C.last ? A.tout : C.t + C.h;
+  const double rl1 = A.K.rl1[q];
+  const double Eq = A.K.E[q][0];
+  C.gamma = C.h * rl1;
+  // ---- linear setup
+  int jcur = 0;
+  bool fail = false;
+  const double dgam = C.gamma - C.gammap;
+  if (!C.setup_done || C.force_setup || fabs(dgam) > 0.3 * fabs(C.gammap) || C.nst >= C.nstlp + 20) {
+    const int info = net_setup(D, V.z, C.gamma, V.lu);
+    C.nsetups++;
+    C.gammap = C.gamma;
+    C.crate = 1.0;
+    C.nstlp = C.nst;
+    C.force_setup = 0;
+    C.setup_done = 1;
+    jcur = 1;
+    if (info) { fail = true; C.setup_done = 0; }
+  }
+  // ---- Newton iteration (norms compared squared, in FP64)
+  const bool stale = C.gamma != C.gammap;
+  const double scst = stale ? 2.0 * C.gammap / (C.gammap + C.gamma) : 1.0;
+  double acnrm2 = 0.0;
+  bool conv = false;
+  if (!fail) {
+    for (int s = 0; s < n; ++s) V.at(V.acor, s) = 0.0;
+    double delp2 = 0.0;
+    const double eq2 = Eq * Eq * 100.0;   // (E_q / 0.1)^2
+    for (int it = 1; it <= 3; ++it) {
+      for (int s = 0; s < n; ++s) V.at(V.y, s) = V.Z(0, s) + V.at(V.acor, s);
+      const bool fin = net_f(D, V, V.y, V.x);
+      C.nfe++;
+      if (!fin) break;
+      for (int s = 0; s < n; ++s)
+        V.at(V.x, s) = C.gamma * V.at(V.x, s) - V.Z(1, s) * rl1 - V.at(V.acor, s);
+      if (D.bl) net_solve_band(D, V.lu, V.x);
+      else net_solve(D, V.lu, V.x);
+      double del2 = 0.0;
+      for (int s = 0; s < n; ++s) {
+        double d = V.at(V.x, s);
+        if (stale) d *= scst;
+        const double e = d * V.at(V.ewt, s);
+        del2 = fma(e, e, del2);
+        V.at(V.acor, s) += d;
+      }
+      del2 *= rn;
+      C.nni++;
+      if (it > 1) {                                  // R^2 = max(0.09 R_prev^2, del2 / delp2)
+        const double r2 = 0.09 * C.crate;
+        C.crate = r2 * delp2 >= del2 ? r2 : del2 / delp2;
+      }
+      if (del2 * fmin(1.0, C.crate) * eq2 <= 1.0) {  // |del| min(1, R) E_q / 0.1 <= 1
+        acnrm2 = it == 1 ? del2 : net_wrms2(V, V.acor, rn);
+        conv = true;
+        break;
+      }
+      if (it >= 2 && del2 > 4.0 * delp2) break;       // |del| > 2 |del_prev|: diverging
+      delp2 = del2;
+    }
+    if (!conv) fail = true;
+  }
+  if (fail) {
+    net_restore(V, C);
+    if (!jcur && !C.tried_fresh && C.setup_done) {   // stale M: retry once with a fresh one
+      C.force_setup = 1;
+      C.tried_fresh = 1;
+      C.retry = 1;
+      return false;
+    }
+    C.tried_fresh = 0;
+    C.ncf++;
+    C.ncfn++;
+    if (C.ncf >= 10) { C.status = BDFB_CONV_FAILURE; return true; }
+    net_rescale(V, C, 0.25);
+    C.qwait = C.q + 1;
+    C.force_setup = 1;
+    return false;
+  }
+  C.tried_fresh = 0;
+  // ---- local error test
+  const double dsm2 = acnrm2 * Eq * Eq;
+  if (!(dsm2 <= 1.0)) {
+    net_restore(V, C);
+    C.nef++;
+    C.netf++;
+    if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
+    if (C.nef < 3) {
+      double eta = eta64(dsm2, 36.0, 2 * (q + 1));
+      if (!(eta >= 0.1)) eta = 0.1;
+      if (C.nef >= 2 && eta > 0.2) eta = 0.2;
+      net_rescale(V, C, eta);
+      C.qwait = C.q + 1;
+    } else {                                         // third failure: order 1, h / 10, fresh slope
+      for (int s = 0; s < n; ++s)
+        for (int j = 2; j <= QMAX; ++j) V.Z(j, s) = 0.0;
+      C.q = 1;
+      C.h *= 0.1;
+      const bool fin = net_f(D, V, V.z, V.x);
+      C.nfe++;
+      if (!fin) { C.status = BDFB_RHSFUNC_FAIL; return true; }
+      for (int s = 0; s < n; ++s) V.Z(1, s) = C.h * V.at(V.x, s);
+      C.qwait = 2;
+    }
+    return false;
+  }
+  // ---- accept
+  for (int s = 0; s < n; ++s) {
+    const double a = V.at(V.acor, s);
+    for (int j = 0; j <= q; ++j) V.Z(j, s) = fma(A.K.l[q][j], a, V.Z(j, s));
+  }
+  C.t = tnew;
+  C.nst++;
+  C.hlast = C.h;
+  C.qlast = q;
+  net_select(A, V, C, dsm2, rn);
+  for (int s = 0; s < n; ++s) V.at(V.acorp, s) = V.at(V.acor, s);
+  C.newstep = 1;
+  if (C.last) { C.t = A.tout; C.status = 0; return true; }
+  return false;
+}
+
+__global__ void __launch_bounds__(ST, 8) k_net_cells(const __grid_constant__ NetCellArgs A) {
+  const int64_t c = (int64_t)blockIdx.x * ST + threadIdx.x;
+  const int64_t nb = A.D.nb;
+  if (c >= nb) return;
+  NetV V;
+  V.nb = nb;
+  V.n = A.D.n;
+  V.z = A.z + c; V.zs = A.zs + c; V.acor = A.acor + c; V.acorp = A.acorp + c; V.ewt = A.ewt + c;
+  V.y = A.y + c; V.x = A.x + c; V.lu = A.lu + c; V.rates = A.rates + c;
+  const NetCellState s = A.st[c];
+  NetCell C;
+  C.t = s.t; C.h = s.h; C.gammap = s.gammap; C.crate = s.crate; C.hlast = s.hlast;
+  C.q = s.q; C.qwait = s.qwait; C.nst = s.nst; C.nstlp = s.nstlp; C.nfe = s.nfe; C.nsetups = s.nsetups;
+  C.nni = s.nni; C.ncfn = s.ncfn; C.netf = s.netf; C.flags = s.flags; C.qlast = s.qlast; C.status = 0;
+  C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0; C.gamma = 0.0;
+  C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0;
+  while (!net_attempt(A, V, C)) {
+  }
+  if (A.yout) {
+    // the history polynomial at tout, sum_j z_j s^j with s = (tout - t) / h,
+    // for a cell past tout; otherwise its current state
+    const bool pol = A.interp && C.status == 0 && (C.flags & NF_STARTED) && C.t != A.tout;
+    const double sv = pol ? (A.tout - C.t) / C.h : 0.0;
+    for (int sp = 0; sp < V.n; ++sp) {
+      double v = V.Z(0, sp);
+      if (pol) {
+        v = V.Z(C.q, sp);
+        for (int j = C.q - 1; j >= 0; --j) v = v * sv + V.Z(j, sp);
+      }
+      A.yout[(int64_t)sp * nb + c] = v;
+    }
+  }
+  NetCellState o;
+  o.t = C.t; o.h = C.h; o.gammap = C.gammap; o.crate = C.crate; o.hlast = C.hlast;
+  o.q = C.q; o.qwait = C.qwait; o.nst = C.nst; o.nstlp = C.nstlp; o.nfe = C.nfe; o.nsetups = C.nsetups;
+  o.nni = C.nni; o.ncfn = C.ncfn; o.netf = C.netf; o.flags = C.flags; o.status = C.status; o.qlast = C.qlast;
+  A.st[c] = o;
+  if (A.status) A.status[c] = C.status;
+  if (C.status < 0) atomicMin(A.worst, C.status);
+}
+
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + ST - 1) / ST, 1 << 30)); }
 
 }  // namespace
@@ -554,9 +977,23 @@ struct SharedInt {
   unsigned long long* diters = nullptr;
   GridBDF* gg = nullptr;
   cudaStream_t s = nullptr;
+  // per-cell step control (option "grouped" 0): history, saved history,
+  // corrections, weights, states; allocated on first use
+  bool percell = false, pc_alloc = false;
+  double *z = nullptr, *zs = nullptr, *acor = nullptr, *acorp = nullptr, *ewt = nullptr, *yout = nullptr;
+  NetCellState* st = nullptr;
+  int32_t* dstatus = nullptr;
+  int* dworst = nullptr;
+  double rtol = 1e-6, atol = 1e-10;
+  int64_t mxstep = 100000;
+  int qmax = QMAX, interp = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float last_ms = 0.f;
   ~SharedInt() {
     grid_destroy(gg);
     for (void* p : bufs) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
   }
   template <typename T>
   int up(const T** d, const std::vector<T>& h) {
@@ -755,17 +1192,132 @@ void shared_set_stream(SharedInt* S, cudaStream_t s) {
   grid_set_stream(S->gg, s);
 }
 
-void shared_set_tolerances(SharedInt* S, double rtol, double atol) { grid_set_tolerances(S->gg, rtol, atol); }
+void shared_set_tolerances(SharedInt* S, double rtol, double atol) {
+  S->rtol = rtol;
+  S->atol = atol;
+  grid_set_tolerances(S->gg, rtol, atol);
+}
+
+static int percell_alloc(SharedInt* S) {
+  if (S->pc_alloc) return 0;
+  const NetDev& D = S->D;
+  const size_t nv = (size_t)D.n * D.nb;
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 1)) != cudaSuccess) { *p = nullptr; return BDFB_MEM_FAIL; }
+    S->bufs.push_back(*p);
+    return 0;
+  };
+  int r = alloc((void**)&S->z, (QMAX + 1) * nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->zs, (QMAX + 1) * nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->acor, nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->acorp, nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->ewt, nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->yout, nv * sizeof(double));
+  if (!r) r = alloc((void**)&S->st, (size_t)D.nb * sizeof(NetCellState));
+  if (!r) r = alloc((void**)&S->dstatus, (size_t)D.nb * sizeof(int32_t));
+  if (!r) r = alloc((void**)&S->dworst, sizeof(int));
+  if (!r && (cudaEventCreate(&S->e0) != cudaSuccess || cudaEventCreate(&S->e1) != cudaSuccess)) r = BDFB_CUDA_FAIL;
+  if (r) return r;
+  S->pc_alloc = true;
+  return 0;
+}
 
 int shared_set_option(SharedInt* S, const char* key, int64_t v) {
+  if (!std::strcmp(key, "grouped")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 0) {
+      const int r = percell_alloc(S);
+      if (r) return r;
+    }
+    S->percell = v == 0;
+    return 0;
+  }
+  if (!std::strcmp(key, "mxstep") && v >= 1) S->mxstep = v;
+  if (!std::strcmp(key, "qmax") && v >= 1 && v <= QMAX) S->qmax = (int)v;
+  if (!std::strcmp(key, "interp") && (v == 0 || v == 1)) S->interp = (int)v;
   if (!std::strcmp(key, "mxstep") || !std::strcmp(key, "qmax") || !std::strcmp(key, "interp"))
     return grid_set_option(S->gg, key, v);
   return BDFB_ILL_INPUT;
 }
 
-int shared_init(SharedInt* S, double t0, const double* y0, int mem) { return grid_init(S->gg, t0, y0, mem); }
+bool shared_percell(const SharedInt* S) { return S->percell; }
+
+int shared_init(SharedInt* S, double t0, const double* y0, int mem) {
+  const int r = grid_init(S->gg, t0, y0, mem);
+  if (r || !S->pc_alloc) return r;
+  // per-cell state: history plane 0 = y0 (species-major, as the grouped state)
+  const NetDev& D = S->D;
+  const size_t nv = (size_t)D.n * D.nb;
+  BDFB_CUDA(cudaMemsetAsync(S->z, 0, (QMAX + 1) * nv * sizeof(double), S->s));
+  BDFB_CUDA(cudaMemsetAsync(S->acorp, 0, nv * sizeof(double), S->s));
+  BDFB_CUDA(cudaMemcpyAsync(S->z, y0, nv * sizeof(double),
+                            mem == BDFB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, S->s));
+  std::vector<NetCellState> st((size_t)D.nb);
+  for (auto& c : st) {
+    std::memset(&c, 0, sizeof c);
+    c.t = t0;
+    c.q = 1;
+    c.crate = 1.0;
+  }
+  BDFB_CUDA(cudaMemcpyAsync(S->st, st.data(), st.size() * sizeof(NetCellState), cudaMemcpyHostToDevice, S->s));
+  BDFB_CUDA(cudaStreamSynchronize(S->s));
+  return 0;
+}
 
 int shared_integrate(SharedInt* S, double tout, double* y, int mem) { return grid_integrate(S->gg, tout, y, mem); }
+
+// per-cell mode: every cell to tout with its own step size and order;
+// per-cell statuses to status (may be null); returns the worst status
+int shared_integrate_cells(SharedInt* S, double tout, double* y, int32_t* status, int mem) {
+  const NetDev& D = S->D;
+  const size_t nv = (size_t)D.n * D.nb;
+  NetCellArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.D = D;
+  A.z = S->z; A.zs = S->zs; A.acor = S->acor; A.acorp = S->acorp; A.ewt = S->ewt;
+  A.y = S->yv; A.x = S->xv; A.lu = S->lu; A.rates = S->rates;
+  A.st = S->st;
+  A.status = S->dstatus;
+  A.yout = S->yout;
+  A.worst = S->dworst;
+  A.tout = tout; A.rtol = S->rtol; A.atol = S->atol;
+  A.mxstep = (int32_t)std::min<int64_t>(S->mxstep, 0x7fffffff);
+  A.qmax = S->qmax;
+  A.interp = S->interp;
+  static const Consts K = make_consts();
+  A.K = K;
+  BDFB_CUDA(cudaMemsetAsync(S->dworst, 0, sizeof(int), S->s));
+  BDFB_CUDA(cudaEventRecord(S->e0, S->s));
+  k_net_cells<<<grid_for(D.nb), ST, 0, S->s>>>(A);
+  BDFB_CUDA(cudaGetLastError());
+  BDFB_CUDA(cudaEventRecord(S->e1, S->s));
+  const cudaMemcpyKind kind = mem == BDFB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (y) BDFB_CUDA(cudaMemcpyAsync(y, S->yout, nv * sizeof(double), kind, S->s));
+  if (status) BDFB_CUDA(cudaMemcpyAsync(status, S->dstatus, D.nb * sizeof(int32_t), kind, S->s));
+  int worst = 0;
+  BDFB_CUDA(cudaMemcpyAsync(&worst, S->dworst, sizeof(int), cudaMemcpyDeviceToHost, S->s));
+  BDFB_CUDA(cudaStreamSynchronize(S->s));
+  cudaEventElapsedTime(&S->last_ms, S->e0, S->e1);
+  return worst;
+}
+
+// per-cell mode: rows nst, nfe, nsetups, nni, ncfn, netf, qlast, hlast bits
+int shared_cell_stats(SharedInt* S, std::vector<int64_t>& rows, double* last_ms) {
+  const int64_t nb = S->D.nb;
+  std::vector<NetCellState> st((size_t)nb);
+  BDFB_CUDA(cudaMemcpy(st.data(), S->st, nb * sizeof(NetCellState), cudaMemcpyDeviceToHost));
+  rows.assign(8 * (size_t)nb, 0);
+  for (int64_t c = 0; c < nb; ++c) {
+    const NetCellState& s = st[c];
+    int64_t* o = rows.data() + 8 * c;
+    int64_t hb;
+    std::memcpy(&hb, &s.hlast, sizeof hb);
+    o[0] = s.nst; o[1] = s.nfe; o[2] = s.nsetups; o[3] = s.nni;
+    o[4] = s.ncfn; o[5] = s.netf; o[6] = s.qlast; o[7] = hb;
+  }
+  *last_ms = S->last_ms;
+  return 0;
+}
 
 void shared_stats(SharedInt* S, int64_t out[8], double* last_ms, int* q, double* h) {
   grid_stats(S->gg, out, last_ms);

@@ -4,6 +4,8 @@
 // share one (larger, sparse) mass-action network.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace bdfb {
@@ -21,6 +23,12 @@ void shared_set_tolerances(SharedInt* S, double rtol, double atol);
 int shared_set_option(SharedInt* S, const char* key, int64_t v);
 int shared_init(SharedInt* S, double t0, const double* y0, int mem);
 int shared_integrate(SharedInt* S, double tout, double* y, int mem);
+// option "grouped" 0: every cell with its own step size and order, one
+// thread per cell on the shared sparse pattern (set before shared_init)
+bool shared_percell(const SharedInt* S);
+int shared_integrate_cells(SharedInt* S, double tout, double* y, int32_t* status, int mem);
+// per-cell mode: rows of nst, nfe, nsetups, nni, ncfn, netf, qlast, hlast bits
+int shared_cell_stats(SharedInt* S, std::vector<int64_t>& rows, double* last_ms);
 // nst, nfe, nsetups, nni (summed over cells), ncfn, netf, LU entries of the
 // shared pattern (with fill), entries of M's pattern; *q, *h of the next step
 void shared_stats(SharedInt* S, int64_t out[8], double* last_ms, int* q, double* h);

@@ -173,3 +173,91 @@ def test_full_size_100k_cells_128_species():
     # grouped oracle runs of 512-768 mixed cells reach 11-52 weighted units
     assert rms(e) <= 1.0 and e.max() <= 50.0, (rms(e), e.max())
     assert stats["max_steps"] == stats["min_steps"] > 0
+
+
+# ------------------------------------ per-cell step control on the shared pattern
+def run_percell(p, tout, rtol, atol, interp=0, y0=None):
+    """option grouped=0: every cell with its own step size and order, one
+    thread per cell on the shared sparse LU; returns cell-major y, statuses,
+    per-cell counters and totals"""
+    with bdfb.Integrator(p, rtol=rtol, atol=atol, shared_network=True, grouped=0, interp=interp) as I:
+        y0 = p.y0 if y0 is None else y0
+        I.init(0.0, torch.from_numpy(bdfb.species_major(p, y0)).cuda())
+        y = torch.empty(p.y0.size, dtype=torch.float64, device="cuda")
+        st = torch.empty(p.ncell, dtype=torch.int32, device="cuda")
+        r = I.integrate(tout, y, st)
+        torch.cuda.synchronize()
+        return r, bdfb.cell_major(p, y.cpu().numpy()), st.cpu().numpy(), I.cell_stats(), I.stats()
+
+
+@pytest.mark.parametrize("which", ["shared10", "shared40"])
+def test_percell_shared_network_against_oracle(which):
+    """cell by cell against the oracle's per-cell integration of the same
+    cells (dense pivoted LU there, the shared sparse LU here: the same method
+    up to rounding) with the tiers of the per-cell parity tests"""
+    from test_gpu_cells import check_against_oracle
+    p = gen.mass_action_shared(1000, n=10) if which == "shared10" else gen.mass_action_shared(200, n=40)
+    r, y, st, cs, stats = run_percell(p, 1e-3, 1e-6, 1e-10)
+    assert r == 0 and np.all(st == 0)
+    assert cs.shape == (p.ncell, 8) and stats["nsteps"] == cs[:, 0].sum()
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
+    check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs, min_seq=0.4)
+
+
+def test_percell_banded_128_against_oracle():
+    """the 128-species banded network (the per-cell dense path holds at most
+    56 species): per cell against the oracle"""
+    from test_gpu_cells import check_against_oracle
+    p = gen.mass_action_banded(96, n=128)
+    r, y, st, cs, _ = run_percell(p, 1e-3, 1e-6, 1e-10)
+    assert r == 0 and np.all(st == 0)
+    check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs, min_seq=0.4)
+
+
+def test_percell_interp_and_continuation():
+    """interpolated output against the oracle in the same mode; a later call
+    continues from where the cells stopped"""
+    from test_gpu_cells import check_against_oracle
+    p = gen.mass_action_shared(512, n=10, seed=31)
+    r, y, st, cs, _ = run_percell(p, 1e-3, 1e-6, 1e-10, interp=1)
+    assert r == 0 and np.all(st == 0)
+    check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs, min_seq=0.4, interp=True)
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, shared_network=True, grouped=0) as I:
+        I.init(0.0, bdfb.species_major(p))
+        y1 = np.empty(p.y0.size)
+        assert I.integrate(5e-4, y1) == 0 and I.integrate(1e-3, y1) == 0
+    # two calls (a fresh Jacobian and a clamped step at 5e-4) make another
+    # valid integration: each cell within the range of the oracle's errors
+    yt, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-10, 1e-14, threads=THREADS)
+    yo, _, _ = oracle.integrate_cells(p, 0.0, 1e-3, 1e-6, 1e-10, threads=THREADS)
+    w = lambda v: np.maximum.reduceat(np.abs(v - yt) / (1e-6 * np.abs(yt) + 1e-10), p.y_off[:-1])
+    assert w(bdfb.cell_major(p, y1)).max() <= max(10.0, 1.5 * w(yo).max())
+
+
+def test_percell_failing_cell_is_isolated():
+    """a cell whose state is NaN fails its right-hand side alone"""
+    p = gen.mass_action_shared(64, n=10, seed=32)
+    y0 = p.y0.copy()
+    y0[p.y_off[5]] = np.nan
+    r, y, st, cs, _ = run_percell(p, 1e-3, 1e-6, 1e-10, y0=y0)
+    assert r == bdfb.RHSFUNC_FAIL and st[5] == bdfb.RHSFUNC_FAIL
+    assert np.all(np.delete(st, 5) == 0)
+
+
+def test_percell_full_size_100k_cells_128_species():
+    p = gen.mass_action_banded(100_000, n=128)
+    r, y, st, cs, stats = run_percell(p, 1e-3, 1e-6, 1e-10)
+    assert r == 0 and np.all(st == 0)
+    s0 = np.add.reduceat(p.y0, p.y_off[:-1])
+    assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0) / np.abs(s0)) <= 1e-12
+    cells = np.sort(np.random.default_rng(6).choice(p.ncell, 64, replace=False))
+    sub = p.subset(cells)
+    ys = np.concatenate([y[p.y_off[c]:p.y_off[c + 1]] for c in cells])
+    yt, stt, _ = oracle.integrate_cells(sub, 0.0, 1e-3, 1e-10, 1e-14, threads=THREADS)
+    yo, so, _ = oracle.integrate_cells(sub, 0.0, 1e-3, 1e-6, 1e-10, threads=THREADS)
+    assert np.all(stt == 0) and np.all(so == 0)
+    w = lambda v: np.maximum.reduceat(np.abs(v - yt) / (1e-6 * np.abs(yt) + 1e-10), sub.y_off[:-1])
+    eg, eo = w(ys), w(yo)
+    assert np.all(eg <= np.maximum(3.0 * eo + 10.0, max(10.0, 1.5 * eo.max())))
+    assert stats["max_steps"] >= stats["min_steps"] > 0
