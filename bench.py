@@ -669,9 +669,10 @@ def shared_sparse_workload(torch, bdfb, gen, ncell=100_000, n=128, reps=1):
     """Cells sharing one sparse network (the submodel case with one pattern
     for every block, Sec. 5): a banded n-species mechanism (reactions within
     windows of 6 species), integrated as one grouped system with task-local
-    Newton solves on the shared sparse LU (BDFB_MASSACTION_SHARED); and the
-    10-species shared network of the learned-guess leg on both the shared
-    sparse path and the per-cell dense path."""
+    Newton solves on the shared sparse LU (BDFB_MASSACTION_SHARED) and with
+    per-cell step control on the same LU (option grouped 0); and the
+    10-species shared network of the learned-guess leg on those paths and on
+    the per-cell dense path."""
     out = {}
     for name, p in ((f"banded_{n}_species", gen.mass_action_banded(ncell, n=n)),
                     ("network_10_species", gen.mass_action_shared(ncell, n=10))):
@@ -681,12 +682,20 @@ def shared_sparse_workload(torch, bdfb, gen, ncell=100_000, n=128, reps=1):
             t = timed_integrations(torch, I, y0, y, TOUT, reps)
             st, row = I.stats(), I.cell_stats()[0]
         yc = bdfb.cell_major(p, y.cpu().numpy())
+        # every cell with its own step size and order on the same sparse LU
+        with bdfb.Integrator(p, rtol=RTOL, atol=ATOL, shared_network=True, grouped=0) as I:
+            tp = timed_integrations(torch, I, y0, y, TOUT, reps)
+            stp = I.stats()
+        per_cell_sparse = {"cells_per_s": ncell / tp, "s": tp, "steps_per_cell": stp["nsteps"] / ncell,
+                           "max_steps": stp["max_steps"],
+                           "accuracy": accuracy(p, bdfb.cell_major(p, y.cpu().numpy()), ncheck=128)}
         out[name] = {"workload": f"{ncell} cells sharing one {int(p.n[0])}-species network "
                                  f"({int(p.rxn_off[1])} reactions), t in [0,1e-3], rtol 1e-6, atol 1e-10",
                      "cells_per_s": ncell / t, "s": t, "steps": st["max_steps"],
                      "newton_iters_per_cell": st["nniters"] / ncell,
                      "lu_entries_with_fill": int(row[6]), "matrix_entries": int(row[7]),
-                     "accuracy": accuracy(p, yc, ncheck=128)}
+                     "accuracy": accuracy(p, yc, ncheck=128),
+                     "per_cell_sparse": per_cell_sparse}
         if int(p.n[0]) <= 56:
             yd = torch.from_numpy(p.y0).cuda()
             yo = torch.empty_like(yd)

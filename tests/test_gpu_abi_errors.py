@@ -77,13 +77,13 @@ def test_grid_context_rejects_cell_only_options():
 
 
 def test_shared_network_and_line_reject_foreign_options():
-    """a shared-network context takes mxstep, qmax, interp and lsolver 0
-    only; the line's own options take 0/1 (device_loop also -1); each refusal
-    leaves the context integrating"""
+    """a shared-network context takes mxstep, qmax, interp, grouped (0 or 1)
+    and lsolver 0 only; the line's own options take 0/1 (device_loop also
+    -1); each refusal leaves the context integrating"""
     p = gen.mass_action_banded(32, n=40)
     with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, shared_network=True) as S:
         for key, v in ((b"mapping", 32), (b"precision", 1), (b"graph", 1), (b"autotune", 1),
-                       (b"grouped", 1), (b"predictor", 1), (b"lsolver", 1), (b"interp", 2),
+                       (b"grouped", 2), (b"predictor", 1), (b"lsolver", 1), (b"interp", 2),
                        (b"qmax", 6), (b"mxstep", 0)):
             assert L.bdfb_set_option(S.h, key, v) == ILL, key
         S.set_option("lsolver", 0)
