@@ -134,6 +134,21 @@ template <int NMAX, int PREC>
 struct UsesDr {
   static constexpr bool value = PREC == 1 || NMAX >= 16;
 };
+// the largest FP64 cells keep those derivatives (touched only at a setup) in a
+// per-warp global workspace instead: their shared memory bounds residency,
+// and 8 rather than 7 warps per SM fit without them
+template <int NMAX, int PREC>
+struct DrGlobal {
+  static constexpr bool value = PREC != 1 && NMAX >= 56;
+};
+
+// the history saved before a step attempt (absent where it stays in registers)
+template <bool REG, int NMAX>
+struct ZsBuf {
+  double zs[ZCOLS][NMAX];
+};
+template <int NMAX>
+struct ZsBuf<true, NMAX> {};
 
 // per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
 // (mixed precision): M and its Gauss-Jordan inverse in FP32.  PREC = 2: M
@@ -142,13 +157,14 @@ struct UsesDr {
 // gathered into the rows of J; mixed precision reuses them in the refinement
 // residual).
 template <int NMAX, int PREC = 0>
-struct CellSmem : RateBufs<NMAX, PREC != 1, UsesDr<NMAX, PREC>::value> {
+struct CellSmem : RateBufs<NMAX, PREC != 1, UsesDr<NMAX, PREC>::value && !DrGlobal<NMAX, PREC>::value>,
+                  ZsBuf<PREC != 1 && NMAX >= 56, NMAX> {
   static constexpr bool DR = UsesDr<NMAX, PREC>::value;
+  static constexpr bool DRG = DrGlobal<NMAX, PREC>::value;   // derivatives in global memory
   typename std::conditional<PREC == 1, float, double>::type M[NMAX][NMAX + 1];
-  // history saved before a step attempt; the FP64 kernel of the largest
-  // cells keeps it in registers instead (its shared memory bounds residency)
+  // history saved before a step attempt (zs, the base); the FP64 kernel of
+  // the largest cells keeps it in registers instead
   static constexpr bool ZREG = PREC != 1 && NMAX >= 56;
-  double zs[ZREG ? 1 : ZCOLS][NMAX];
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side
   int16_t perm[NMAX];         // row i of P M is row perm[i] of M

@@ -449,9 +449,13 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       bool direct = true;
       if constexpr (CellSmem<NMAX, PREC>::DR) {
         if (cd.kind == BDFB_MASSACTION) {
-          // each reaction's derivatives once, then gathered into the rows
-          reaction_derivs<G, NPL, NMAX>(g, cd, S, y, -C.gamma);
-          form_M64_scaled<G, NPL, NMAX>(g, cd, S, S.M);
+          // each reaction's derivatives once (scaled by -gamma), then
+          // gathered into the rows; the largest cells keep them in their
+          // warp's global workspace (Mg points there)
+          double (*drg)[2 * NMAX] = reinterpret_cast<double (*)[2 * NMAX]>(Mg);
+          if (CellSmem<NMAX, PREC>::DRG && !drg) { C.status = BDFB_MEM_FAIL; return true; }
+          reaction_derivs<G, NPL, NMAX>(g, cd, S, y, -C.gamma, drg);
+          form_M64_scaled<G, NPL, NMAX>(g, cd, S, S.M, drg);
           direct = false;
         }
       }
@@ -680,8 +684,10 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
   CellSmem<NMAX, PREC>& S = reinterpret_cast<CellSmem<NMAX, PREC>*>(smem)[gid];
-  double (*Mg)[NMAX + 1] =
-      fb ? reinterpret_cast<double (*)[NMAX + 1]>(fb + (int64_t)gid * NMAX * (NMAX + 1)) : nullptr;
+  // mixed precision: this group's FP64 fallback matrix; the largest FP64
+  // cells: their derivative workspace (the same pointer)
+  constexpr int64_t WS = PREC == 1 ? (int64_t)NMAX * (NMAX + 1) : 8LL * NMAX;
+  double (*Mg)[NMAX + 1] = fb ? reinterpret_cast<double (*)[NMAX + 1]>(fb + (int64_t)gid * WS) : nullptr;
   bool active = gid < td.count;
   int64_t c = 0;
   CellDesc cd;
@@ -784,11 +790,25 @@ constexpr int VAR_LEARN[NVAR] = {0, 0, 0, 0, 0, 1, 0, 0};
 constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W32, VAR_W16, VAR_H16, 2, 1, 0};
 // warps per SM each variant should keep resident (the shared-memory limit of
 // the largest ones): bounds the registers ptxas may use
-constexpr int VAR_MINB[NVAR] = {12, 12, 12, 8, 7, 12, 12, 12};
+constexpr int VAR_MINB[NVAR] = {12, 12, 12, 8, 8, 12, 12, 12};
 // mixed precision: M in FP32 halves the shared memory, so registers bound the
 // residency of the two largest tilings
 constexpr int var_minb(int v, int prec) { return prec == 1 && (v == 3 || v == 4) ? 10 : VAR_MINB[v]; }
 static_assert(CLS_G[0] == VAR_G[0] && CLS_NMAX[4] == VAR_NMAX[4], "variants 0..4 are the class tilings");
+
+// doubles of global workspace one warp of variant v needs: mixed precision,
+// the FP64 fallback matrices of its cells; the FP64 kernels of the largest
+// cells, their reaction derivatives (4 reactant slots x 2 NMAX reactions);
+// others none
+constexpr int64_t workspace_doubles_per_warp(int v, int pr) {
+  return pr == 1 ? (int64_t)(32 / VAR_G[v]) * VAR_NMAX[v] * (VAR_NMAX[v] + 1)
+                 : (VAR_NMAX[v] >= 56 ? (int64_t)(32 / VAR_G[v]) * 8 * VAR_NMAX[v] : 0);
+}
+template <int V, int PREC>
+struct VarWs {
+  static constexpr int64_t value = PREC == 1 ? (int64_t)(32 / VAR_G[V]) * VAR_NMAX[V] * (VAR_NMAX[V] + 1)
+                                             : (VAR_NMAX[V] >= 56 ? (int64_t)(32 / VAR_G[V]) * 8 * VAR_NMAX[V] : 0);
+};
 
 template <int V, int PREC>
 struct VarSmem {
@@ -804,7 +824,7 @@ __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_co
                                                            unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31;
-  constexpr int64_t FB = (int64_t)(32 / VAR_G[V]) * VAR_NMAX[V] * (VAR_NMAX[V] + 1);
+  constexpr int64_t FB = VarWs<V, PREC>::value;
   double* fb = fbws ? fbws + (int64_t)blockIdx.x * FB : nullptr;
   for (;;) {
     int t = 0;
@@ -816,10 +836,6 @@ __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_co
   }
 }
 
-// doubles of FP64 fallback workspace one warp of variant v needs
-static int64_t fallback_doubles_per_warp(int v) {
-  return (int64_t)(32 / VAR_G[v]) * VAR_NMAX[v] * (VAR_NMAX[v] + 1);
-}
 
 typedef void (*cells_kernel_t)(const Params, int, int, unsigned*, double*);
 constexpr int NKPREC = 3;   // kernel rows: FP64 LU, FP32 inverse + refinement, FP64 inverse
@@ -910,7 +926,7 @@ __device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& G
   double crate = GP.crate[c];
   if (GP.setup) {
     bool direct = true;
-    if constexpr (CellSmem<NMAX, 0>::DR) {
+    if constexpr (CellSmem<NMAX, 0>::DR && !CellSmem<NMAX, 0>::DRG) {
       if (cd.kind == BDFB_MASSACTION) {
         reaction_derivs<G, NPL, NMAX>(g, cd, S, z0, -GP.gamma);
         form_M64_scaled<G, NPL, NMAX>(g, cd, S, S.M);
@@ -1217,7 +1233,7 @@ struct bdfb_ctx {
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
   cudaEvent_t evjoin[NVAR] = {};
-  double* d_fbws[NVAR] = {};        // FP64 fallback workspace per variant (mixed precision, lazy)
+  double* d_fbws[NKPREC][NVAR] = {};   // global workspace per kernel row and variant (lazy)
   cudaStream_t cstream[NVAR] = {};  // one per variant, forked from `stream`
   float last_ms = 0.f;
   int pgrid[NKPREC][NVAR] = {};   // persistent grid size [kernel row][variant]
@@ -1268,7 +1284,8 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
   cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status); cudaFree(c->d_yout);
-  for (int k = 0; k < NVAR; ++k) cudaFree(c->d_fbws[k]);
+  for (int pr = 0; pr < NKPREC; ++pr)
+    for (int k = 0; k < NVAR; ++k) cudaFree(c->d_fbws[pr][k]);
   for (int m = 0; m < 3; ++m) { cudaFree(c->sched[m].d_tiles); cudaFree(c->sched[m].d_tcells); }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cgraph) cudaGraphDestroy(c->cgraph);
@@ -1756,13 +1773,14 @@ static Params base_params(bdfb_ctx* ctx, double tout) {
   return P;
 }
 
-// FP64 fallback workspace of a size-class variant (mixed precision): one
+// global workspace of a kernel variant (workspace_doubles_per_warp): one
 // slice per resident warp, allocated on first use
-static int ensure_fbws(bdfb_ctx* ctx, int v) {
-  if (ctx->d_fbws[v]) return 0;
-  const size_t bytes = (size_t)ctx->pgrid[1][v] * fallback_doubles_per_warp(v) * sizeof(double);
-  if (cudaMalloc(&ctx->d_fbws[v], bytes) != cudaSuccess) {
-    ctx->d_fbws[v] = nullptr;
+static int ensure_fbws(bdfb_ctx* ctx, int pr, int v) {
+  const int64_t per = workspace_doubles_per_warp(v, pr);
+  if (per == 0 || ctx->d_fbws[pr][v]) return 0;
+  const size_t bytes = (size_t)ctx->pgrid[pr][v] * per * sizeof(double);
+  if (cudaMalloc(&ctx->d_fbws[pr][v], bytes) != cudaSuccess) {
+    ctx->d_fbws[pr][v] = nullptr;
     return BDFB_MEM_FAIL;
   }
   return 0;
@@ -1785,11 +1803,11 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, in
     const cells_kernel_t kf = var_kernel(pr, kv);
     if (!kf) return BDFB_ILL_INPUT;
     // mixed precision: the launched variant's FP64 fallback workspace must exist
-    if (pr == 1 && !ctx->d_fbws[kv]) return BDFB_MEM_FAIL;
+    if (workspace_doubles_per_warp(kv, pr) && !ctx->d_fbws[pr][kv]) return BDFB_MEM_FAIL;
     cudaStream_t cs = ctx->cstream[v];
     BDFB_CUDA(cudaStreamWaitEvent(cs, ctx->evfork, 0));
     const int grid = std::min(ctx->pgrid[pr][kv], t1 - t0);
-    kf<<<grid, 32, var_smem(pr, kv), cs>>>(P, t0, t1, ctx->d_counter + v, pr == 1 ? ctx->d_fbws[kv] : nullptr);
+    kf<<<grid, 32, var_smem(pr, kv), cs>>>(P, t0, t1, ctx->d_counter + v, ctx->d_fbws[pr][kv]);
     BDFB_CUDA(cudaGetLastError());
     BDFB_CUDA(cudaEventRecord(ctx->evjoin[v], cs));
     BDFB_CUDA(cudaStreamWaitEvent(s, ctx->evjoin[v], 0));
@@ -1896,7 +1914,7 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
     if (cand.size() == 1) continue;
     float best = 0.f;
     for (int v : cand) {
-      if (pr == 1 && ensure_fbws(ctx, v)) { fail(BDFB_MEM_FAIL); break; }
+      if (ensure_fbws(ctx, pr, v)) { fail(BDFB_MEM_FAIL); break; }
       for (int32_t c : members[cl]) var[c] = (int8_t)v;
       std::vector<TileDesc> tiles;
       std::vector<int32_t> tcells;
@@ -1935,7 +1953,7 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
         }
         cudaEventRecord(e0, s);
         kf<<<std::min(ctx->pgrid[pr][v], nt), 32, var_smem(pr, v), s>>>(
-            Pt, 0, nt, cnt2, pr == 1 ? ctx->d_fbws[v] : nullptr);
+            Pt, 0, nt, cnt2, ctx->d_fbws[pr][v]);
         cudaEventRecord(e1, s);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
           fail(BDFB_CUDA_FAIL);
@@ -2137,15 +2155,13 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   P.tiles = S.d_tiles;
   P.tile_cells = S.d_tcells;
   P.ntiles = S.ntiles;
-  if (pr == 1) {
-    // the workspace of the variant each range is launched on (variant 4's
-    // range runs on `single` under the one-warp-per-cell schedule)
-    for (int v = 0; v < NVAR; ++v)
-      if (S.vend[v] > S.vbeg[v]) {
-        const int r = ensure_fbws(ctx, v == 4 ? single : v);
-        if (r) return r;
-      }
-  }
+  // the workspace of the variant each range is launched on (variant 4's
+  // range runs on `single` under the one-warp-per-cell schedule)
+  for (int v = 0; v < NVAR; ++v)
+    if (S.vend[v] > S.vbeg[v]) {
+      const int r = ensure_fbws(ctx, pr, v == 4 ? single : v);
+      if (r) return r;
+    }
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
   if (ctx->graph) {
     const int r = launch_graph(ctx, P, m, pr, single, s);

@@ -34,13 +34,17 @@ __device__ __forceinline__ float bcastf(const Grp<G>& g, float v, int src) {
 }
 
 // scale * d rate_r / d y_{s_a} for every reaction r and reactant slot a at y
-// (FP64), into S.dr; lanes over reactions.  scale = 1: the derivatives
+// (FP64), into S.dr (or drg, the per-warp global workspace of the cells whose
+// shared memory holds no derivatives); lanes over reactions.  scale = 1: the derivatives
 // themselves (kept by mixed precision for its residual); scale = -gamma:
 // their contributions to M = I - gamma J (form_M64_scaled).
 template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void reaction_derivs(const Grp<G>& g, const CellDesc& c,
                                                 CellSmem<NMAX, PREC>& S, const double (&y)[NPL],
-                                                double scale = 1.0) {
+                                                double scale = 1.0, double (*drg)[2 * NMAX] = nullptr) {
+  double (*dr)[2 * NMAX];
+  if constexpr (CellSmem<NMAX, PREC>::DRG) dr = drg;      // the per-warp global workspace
+  else dr = S.dr;
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   for (int r = g.rank; r < c.nr; r += G) {
     const uint32_t rc = __ldg(c.reac + r);
@@ -56,7 +60,7 @@ __device__ __forceinline__ void reaction_derivs(const Grp<G>& g, const CellDesc&
           if (b != a && sb != 255u) d *= S.ybuf[sb];
         }
       }
-      S.dr[a][r] = d;
+      dr[a][r] = d;
     }
   }
   g.sync();
@@ -142,7 +146,10 @@ __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc
 // diagonal -- no separate pass forming 1 - gamma J
 template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void form_M64_scaled(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, PREC>& S,
-                                                double (*Mg)[NMAX + 1]) {
+                                                double (*Mg)[NMAX + 1], const double (*drg)[2 * NMAX] = nullptr) {
+  const double (*dr)[2 * NMAX];
+  if constexpr (CellSmem<NMAX, PREC>::DRG) dr = drg;
+  else dr = S.dr;
   const int n = c.n;
   g.sync();
 #pragma unroll
@@ -160,7 +167,7 @@ __device__ __forceinline__ void form_M64_scaled(const Grp<G>& g, const CellDesc&
       for (int a = 0; a < 4; ++a) {
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
-        const double d = S.dr[a][r];
+        const double d = dr[a][r];
         row[s] = (v & 1u) ? row[s] + d : row[s] - d;
       }
     }
