@@ -299,6 +299,26 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 
+// a + b for a produced species (plus = 1), a - b for a consumed one: one FP64
+// add of b with its sign bit set from the flag on the integer pipe (a - b is
+// a + (-b) exactly), where a select between the two sums would issue both
+__device__ __forceinline__ double add_signed(double a, double b, uint32_t plus) {
+  return a + __longlong_as_double(__double_as_longlong(b) ^ ((long long)(~plus & 1u) << 63));
+}
+__device__ __forceinline__ float add_signed(float a, float b, uint32_t plus) {
+  return a + __uint_as_float(__float_as_uint(b) ^ ((~plus & 1u) << 31));
+}
+
+// 1 / a for a finite nonzero a: recip_nr of |a| with a's sign put back on
+// the integer pipe (four FP64 FMAs where a division issues many more)
+__device__ __forceinline__ double recip_signed(double a) {
+  const long long sgn = __double_as_longlong(a) & (long long)0x8000000000000000ULL;
+  const double r = recip_nr(__longlong_as_double(__double_as_longlong(a) ^ sgn));
+  return __longlong_as_double(__double_as_longlong(r) ^ sgn);
+}
+__device__ __forceinline__ float recip_t(float a) { return 1.0f / a; }
+__device__ __forceinline__ double recip_t(double a) { return recip_signed(a); }
+
 template <int G, int NPL>
 __device__ __forceinline__ bool all_finite(const Grp<G>& g, int n, const double (&x)[NPL]) {
   bool bad = false;
@@ -339,7 +359,7 @@ __device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& 
     if (e < e1) {
       const uint32_t v = __ldg(c.inc + e);
       const double rt = vals[v >> 1];
-      acc = (v & 1u) ? acc + rt : acc - rt;
+      acc = add_signed(acc, rt, v);
       ++e;
     } else {
       place(out, p, acc);
@@ -431,7 +451,7 @@ __device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellS
             const uint32_t sb = (rc >> (8 * b)) & 255u;
             if (b != a && sb != 255u) d *= S.ybuf[sb];
           }
-          row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+          row[s] = add_signed(row[s], d, v);
         }
       }
     }
@@ -484,7 +504,7 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
       }
     }
     g.sync();
-    const T rinv = (T)1 / M[k][k];
+    const T rinv = recip_t(M[k][k]);
     if (g.rank == 0) dinv[k] = rinv;
     for (int i = k + 1 + g.rank; i < n; i += G) M[i][k] *= rinv;
     g.sync();
@@ -589,7 +609,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     const int k1 = k + 1, k2 = k + 2;
     // ---- column k
     if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k, pivk)) return k + 1;
-    const T r0 = (T)1 / M[k][k];
+    const T r0 = recip_t(M[k][k]);
     if (g.rank == 0) dinv[k] = r0;
     for (int i = k1 + g.rank; i < n; i += G) {
       const T l = M[i][k] * r0;
@@ -599,7 +619,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     g.sync();
     // ---- column k+1
     if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k1, pivk)) return k1 + 1;
-    const T r1 = (T)1 / M[k1][k1];
+    const T r1 = recip_t(M[k1][k1]);
     if (g.rank == 0) dinv[k1] = r1;
     for (int i = k2 + g.rank; i < n; i += G) M[i][k1] *= r1;
     {
@@ -638,7 +658,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
   }
   if (k < n) {                        // the last pivot of an odd order
     if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k, pivk)) return k + 1;
-    if (g.rank == 0) dinv[k] = (T)1 / M[k][k];
+    if (g.rank == 0) dinv[k] = recip_t(M[k][k]);
     g.sync();
   }
   return 0;
@@ -661,13 +681,20 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
     if (i < n) x[p] = buf[perm[i]];
   }
   g.sync();
-  for (int j = 0; j < n; ++j) {                 // L y = P b (unit lower)
-    const double xj = g.bcast(pick(x, j / G), j % G);
+  // L y = P b (unit lower).  Columns j in [G s - 1, G (s + 1) - 1) have rows
+  // below them only in slots s.. NPL-1: the slots are split at compile time,
+  // since a predicated-off FP64 instruction costs an issue like a live one
+  int j = 0;
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      if (G * (p + 1) - 1 <= j) continue;      // no row of this slot is below j
-      const int i = g.rank + G * p;
-      if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
+  for (int s = 0; s < NPL; ++s) {
+    const int jend = min(n - 1, G * (s + 1) - 1);
+    for (; j < jend; ++j) {
+      const double xj = g.bcast(pick(x, j / G), j % G);
+#pragma unroll
+      for (int p = s; p < NPL; ++p) {
+        const int i = g.rank + G * p;
+        if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
+      }
     }
   }
   if constexpr (UNITU) {                         // y <- D^{-1} y
@@ -677,18 +704,24 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
       if (i < n) x[p] *= (double)dinv[i];
     }
   }
-  for (int j = n - 1; j >= 0; --j) {            // U x = y (U' x = y when UNITU)
-    const int owner = j % G, slot = j / G;
-    double xj = g.bcast(pick(x, slot), owner);
-    if constexpr (!UNITU) {
-      xj *= (double)dinv[j];
-      if (g.rank == owner) place(x, slot, xj);
-    }
+  // U x = y (U' x = y when UNITU).  Columns j in (G s, G (s + 1)] have rows
+  // above them only in slots 0..s
+  j = n - 1;
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      if (G * p >= j) continue;                 // no row of this slot is above j
-      const int i = g.rank + G * p;
-      if (i < j) x[p] = fma(-(double)M[i][j], xj, x[p]);
+  for (int s = NPL - 1; s >= 0; --s) {
+    const int jlo = (s == 0 && !UNITU) ? -1 : G * s;   // column 0 scales its own entry
+    for (; j > jlo; --j) {
+      const int owner = j % G, slot = j / G;
+      double xj = g.bcast(pick(x, slot), owner);
+      if constexpr (!UNITU) {
+        xj *= (double)dinv[j];
+        if (g.rank == owner) place(x, slot, xj);
+      }
+#pragma unroll
+      for (int p = 0; p <= s; ++p) {
+        const int i = g.rank + G * p;
+        if (i < j) x[p] = fma(-(double)M[i][j], xj, x[p]);
+      }
     }
   }
 }

@@ -28,6 +28,22 @@ __device__ __forceinline__ double gmaxd(const Grp<G>& g, double v) {
   return v;
 }
 
+// max |v| over the group on the integer pipe: the bit patterns of
+// non-negative doubles order like their values (a NaN's key lies above
+// infinity's, so a NaN wins and fails every later <= test)
+__device__ __forceinline__ long long abs_key(double v) {
+  return __double_as_longlong(v) & 0x7fffffffffffffffLL;
+}
+template <int G>
+__device__ __forceinline__ double gmax_key(const Grp<G>& g, long long k) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(g.mask, k, o, G);
+    k = ok > k ? ok : k;
+  }
+  return __longlong_as_double(k);
+}
+
 template <int G>
 __device__ __forceinline__ float bcastf(const Grp<G>& g, float v, int src) {
   return G > 1 ? __shfl_sync(g.mask, v, src, G) : v;
@@ -91,7 +107,7 @@ __device__ __forceinline__ double form_M32(const Grp<G>& g, const CellDesc& c, C
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
         const float d = (float)S.dr[a][r];
-        row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+        row[s] = add_signed(row[s], d, v);
       }
     }
     float rs = 0.0f;
@@ -132,7 +148,7 @@ __device__ __forceinline__ void form_M64_from_dr(const Grp<G>& g, const CellDesc
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
         const double d = S.dr[a][r];
-        row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+        row[s] = add_signed(row[s], d, v);
       }
     }
     for (int j = 0; j < n; ++j) row[j] = __dsub_rn(i == j ? 1.0 : 0.0, __dmul_rn(gamma, row[j]));
@@ -168,7 +184,7 @@ __device__ __forceinline__ void form_M64_scaled(const Grp<G>& g, const CellDesc&
         const uint32_t s = (rc >> (8 * a)) & 255u;
         if (s == 255u) continue;
         const double d = dr[a][r];
-        row[s] = (v & 1u) ? row[s] + d : row[s] - d;
+        row[s] = add_signed(row[s], d, v);
       }
     }
     row[i] += 1.0;
@@ -305,34 +321,36 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
   float* buf = reinterpret_cast<float*>(S.ybuf);
   const int n = c.n;
   double x[NPL], r[NPL], jx[NPL];
-  double bn = 0.0;
+  // norms as integer keys and FP32 <-> FP64 conversions on the integer pipe
+  // (to_f32 flushes magnitudes below 2^-126: a residual that small in every
+  // entry ends the sweeps unconverged and takes the FP64 fallback)
+  long long bk = 0;
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     x[p] = 0.0;
     r[p] = b[p];
-    if (g.rank + G * p < n) bn = fmax(bn, fabs(b[p]));
+    if (g.rank + G * p < n) bk = max(bk, abs_key(b[p]));
   }
-  bn = gmaxd(g, bn);
+  const double bn = gmax_key(g, bk);
   int sweeps = -1;
   for (int it = 1; it <= MAXREF; ++it) {
     float r32[NPL], c32[NPL];
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
+    for (int p = 0; p < NPL; ++p) r32[p] = to_f32(r[p]);
     apply_inverse<G, NPL, NMAX, float>(g, S.M, buf, n, r32, c32);
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
+    for (int p = 0; p < NPL; ++p) x[p] += to_f64(c32[p]);
     jac_vec<G, NPL, NMAX>(g, c, S, x, jx);
-    double rn = 0.0, xn = 0.0;
+    long long rk = 0, xk = 0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
       r[p] = b[p] - fma(-gammap, jx[p], x[p]);
       if (g.rank + G * p < n) {
-        rn = fmax(rn, fabs(r[p]));
-        xn = fmax(xn, fabs(x[p]));
+        rk = max(rk, abs_key(r[p]));
+        xk = max(xk, abs_key(x[p]));
       }
     }
-    rn = gmaxd(g, rn);
-    xn = gmaxd(g, xn);
+    const double rn = gmax_key(g, rk), xn = gmax_key(g, xk);
     if (rn <= BERR_TOL * (mnorm * xn + bn)) { sweeps = it; break; }
   }
 #pragma unroll
