@@ -332,7 +332,7 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *              Sec. 7, for any block size) and each Newton solve is one
  *              matrix-vector product.  Equal to LU in exact arithmetic;
  *              three times the setup flops, no dependent triangular chain
- *              in the solves.  With "precision" 1 the FP32 inverse of that
+ *              in the solves.  With "precision" 1 the FP32 LU of that
  *              mode is used either way.  Not with "predictor", a recording
  *              or "grouped".  Grid and shared-network contexts accept 0
  *              only (GMRES, sparse LU).

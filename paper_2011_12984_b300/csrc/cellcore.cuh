@@ -59,7 +59,26 @@ struct Grp {
   __device__ __forceinline__ int bcast(int v, int src) const {
     return G > 1 ? __shfl_sync(mask, v, src, G) : v;
   }
+  __device__ __forceinline__ float bcast(float v, int src) const {
+    return G > 1 ? __shfl_sync(mask, v, src, G) : v;
+  }
 };
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// |a| as an integer key (the bit patterns of non-negative IEEE values order
+// like the values; a NaN's key exceeds infinity's), and infinity's key
+__device__ __forceinline__ long long abs_key_t(double a) {
+  return __double_as_longlong(a) & 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ long long abs_key_t(float a) {
+  return (long long)(__float_as_uint(a) & 0x7fffffffu);
+}
+template <typename T>
+__host__ __device__ constexpr long long inf_key() {
+  return sizeof(T) == 8 ? 0x7ff0000000000000LL : 0x7f800000LL;
+}
 
 // lane grid for 2-D work on a group's matrix: R rows x C columns of lanes
 template <int G>
@@ -151,8 +170,9 @@ template <int NMAX>
 struct ZsBuf<true, NMAX> {};
 
 // per-cell shared memory.  PREC = 0: M and its LU factors in FP64.  PREC = 1
-// (mixed precision): M and its Gauss-Jordan inverse in FP32.  PREC = 2: M
-// and its Gauss-Jordan inverse in FP64.  All keep the
+// (mixed precision): M and its LU factors in FP32 (pivot reciprocals in the
+// float view of dinv).  PREC = 2: M and its Gauss-Jordan inverse in FP64.
+// All keep the
 // FP64 reaction derivatives of the last setup (computed once per reaction, then
 // gathered into the rows of J; mixed precision reuses them in the refinement
 // residual).
@@ -480,7 +500,7 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
     long long best = -1;
     int p = n;
     for (int i = k + g.rank; i < n; i += G) {
-      const long long v = __double_as_longlong(fabs((double)M[i][k]));
+      const long long v = abs_key_t(M[i][k]);
       if (v > best) { best = v; p = i; }
     }
 #pragma unroll
@@ -489,7 +509,7 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
       const int op = __shfl_xor_sync(g.mask, p, o, G);
       if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
     }
-    if (p >= n || !(__longlong_as_double(best) > 0.0) || best >= 0x7ff0000000000000LL) return k + 1;
+    if (p >= n || best <= 0 || best >= inf_key<T>()) return k + 1;
     if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
     if (p != k) {
       for (int j = g.rank; j < n; j += G) {
@@ -529,7 +549,7 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
         for (int b = 0; b < NJ; ++b) {
           if (b >= nbu) break;
           const int j = k + 1 + lj + C * b;
-          if (j < n) M[i][j] = fma(-lik, u[b], M[i][j]);
+          if (j < n) M[i][j] = fma_t(-lik, u[b], M[i][j]);
         }
       }
       if constexpr (UNITU) {
@@ -553,7 +573,7 @@ __device__ __forceinline__ bool pivot_swap(const Grp<G>& g, T (*M)[NMAX + 1], in
   long long best = -1;
   int p = n;
   for (int i = k + g.rank; i < n; i += G) {
-    const long long v = __double_as_longlong(fabs((double)M[i][k]));
+    const long long v = abs_key_t(M[i][k]);
     if (v > best) { best = v; p = i; }
   }
 #pragma unroll
@@ -562,7 +582,7 @@ __device__ __forceinline__ bool pivot_swap(const Grp<G>& g, T (*M)[NMAX + 1], in
     const int op = __shfl_xor_sync(g.mask, p, o, G);
     if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
   }
-  if (p >= n || best <= 0 || best >= 0x7ff0000000000000LL) return false;
+  if (p >= n || best <= 0 || best >= inf_key<T>()) return false;
   if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
   if (p != k) {
     for (int j = g.rank; j < n; j += G) {
@@ -614,7 +634,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     for (int i = k1 + g.rank; i < n; i += G) {
       const T l = M[i][k] * r0;
       M[i][k] = l;
-      M[i][k1] = fma(-l, M[k][k1], M[i][k1]);     // column k+1 gets step k's update
+      M[i][k1] = fma_t(-l, M[k][k1], M[i][k1]);     // column k+1 gets step k's update
     }
     g.sync();
     // ---- column k+1
@@ -624,7 +644,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     for (int i = k2 + g.rank; i < n; i += G) M[i][k1] *= r1;
     {
       const T l = M[k1][k];                        // row k+1 gets step k's update
-      for (int j = k2 + g.rank; j < n; j += G) M[k1][j] = fma(-l, M[k][j], M[k1][j]);
+      for (int j = k2 + g.rank; j < n; j += G) M[k1][j] = fma_t(-l, M[k][j], M[k1][j]);
     }
     g.sync();
     // ---- both updates of the trailing block, lanes on an R x C grid; column
@@ -645,7 +665,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
         for (int b = 0; b < NJ; ++b) {
           if (b >= nbu) break;
           const int j = k2 + lj + C * b;
-          if (j < n) M[i][j] = fma(-a1, u1[b], fma(-a0, u0[b], M[i][j]));
+          if (j < n) M[i][j] = fma_t(-a1, u1[b], fma_t(-a0, u0[b], M[i][j]));
         }
       }
       if constexpr (UNITU) {
@@ -665,10 +685,11 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
   }
 }
 
-// x <- (P M)^{-1} P x with the factors above; x distributed over the group.
-template <int G, int NPL, int NMAX, typename T, bool UNITU = false>
+// x <- (P M)^{-1} P x with the factors above; x distributed over the group,
+// held and updated in type V (FP64, or FP32 with FP32 factors)
+template <int G, int NPL, int NMAX, typename T, bool UNITU = false, typename V = double>
 __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1], const T* dinv,
-                         const int16_t* perm, double* buf, int n, double (&x)[NPL]) {
+                         const int16_t* perm, V* buf, int n, V (&x)[NPL]) {
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     const int i = g.rank + G * p;
@@ -689,11 +710,11 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
   for (int s = 0; s < NPL; ++s) {
     const int jend = min(n - 1, G * (s + 1) - 1);
     for (; j < jend; ++j) {
-      const double xj = g.bcast(pick(x, j / G), j % G);
+      const V xj = g.bcast(pick(x, j / G), j % G);
 #pragma unroll
       for (int p = s; p < NPL; ++p) {
         const int i = g.rank + G * p;
-        if (i > j && i < n) x[p] = fma(-(double)M[i][j], xj, x[p]);
+        if (i > j && i < n) x[p] = fma_t(-(V)M[i][j], xj, x[p]);
       }
     }
   }
@@ -701,7 +722,7 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
       const int i = g.rank + G * p;
-      if (i < n) x[p] *= (double)dinv[i];
+      if (i < n) x[p] *= (V)dinv[i];
     }
   }
   // U x = y (U' x = y when UNITU).  Columns j in (G s, G (s + 1)] have rows
@@ -712,15 +733,15 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
     const int jlo = (s == 0 && !UNITU) ? -1 : G * s;   // column 0 scales its own entry
     for (; j > jlo; --j) {
       const int owner = j % G, slot = j / G;
-      double xj = g.bcast(pick(x, slot), owner);
+      V xj = g.bcast(pick(x, slot), owner);
       if constexpr (!UNITU) {
-        xj *= (double)dinv[j];
+        xj *= (V)dinv[j];
         if (g.rank == owner) place(x, slot, xj);
       }
 #pragma unroll
       for (int p = 0; p <= s; ++p) {
         const int i = g.rank + G * p;
-        if (i < j) x[p] = fma(-(double)M[i][j], xj, x[p]);
+        if (i < j) x[p] = fma_t(-(V)M[i][j], xj, x[p]);
       }
     }
   }

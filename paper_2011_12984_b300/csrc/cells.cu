@@ -439,11 +439,11 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
     int info;
     if constexpr (PREC == 1) {
-      // FP32 Gauss-Jordan inverse of M; FP64 reaction derivatives kept for
-      // the refinement residual
+      // FP32 LU of M (its pivot reciprocals in the float view of dinv);
+      // FP64 reaction derivatives kept for the refinement residual
       reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
       C.mnorm = form_M32<G, NPL, NMAX>(g, cd, S, C.gamma);
-      info = gj_inverse<G, NMAX, float>(g, S.M, S.perm, reinterpret_cast<float*>(S.ybuf), n);
+      info = lu_factor<G, NMAX, float, true>(g, S.M, reinterpret_cast<float*>(S.dinv), S.perm, n);
       C.fp64mode = 0;
     } else {
       bool direct = true;
@@ -817,7 +817,7 @@ struct VarSmem {
 
 // Persistent kernel of one variant: each warp takes the next tile of the
 // range [t0, t1) from `counter` until none is left.  PREC 0: FP64 LU
-// factorisation; PREC 1: FP32 inverse with FP64 refinement; PREC 2: FP64
+// factorisation; PREC 1: FP32 LU with FP64 refinement; PREC 2: FP64
 // Gauss-Jordan inverse (Newton solves by one matrix-vector product).
 template <int V, int PREC>
 __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_constant__ Params P, int t0, int t1,
@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_co
 
 
 typedef void (*cells_kernel_t)(const Params, int, int, unsigned*, double*);
-constexpr int NKPREC = 3;   // kernel rows: FP64 LU, FP32 inverse + refinement, FP64 inverse
+constexpr int NKPREC = 3;   // kernel rows: FP64 LU, FP32 LU + refinement, FP64 inverse
 static const cells_kernel_t CELLS_KERNELS[NKPREC][NVAR] = {
     {k_cells<0, 0>, k_cells<1, 0>, k_cells<2, 0>, k_cells<3, 0>, k_cells<4, 0>, k_cells<5, 0>, k_cells<6, 0>,
      k_cells<7, 0>},
@@ -1079,8 +1079,8 @@ __global__ void __launch_bounds__(32) k_lu_solve(int64_t nb, int n, const double
 }
 
 // Mixed-precision solve of dense blocks, the same scheme as the integrator's:
-// FP32 Gauss-Jordan inverse of each block, FP64 dense residual r = b - A x,
-// x += inv32 r until |r|/(|A| |x| + |b|) <= 1e-12 (at most MAXREF sweeps);
+// FP32 LU of each block, FP64 dense residual r = b - A x, x += (LU32)^{-1} r
+// until |r|/(|A| |x| + |b|) <= 1e-12 (at most MAXREF sweeps);
 // a block that does not get there is solved by FP64 LU (sweeps[b] = 0), and
 // sweeps[b] = -2 only when that factorisation meets a zero pivot too.
 __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const double* a,
@@ -1110,7 +1110,8 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
       }
     }
     anorm = gmaxd(g, anorm);
-    const int info = gj_inverse<32, LU_NMAX, float>(g, M32, S.perm, reinterpret_cast<float*>(S.ybuf), n);
+    float* dinv32 = reinterpret_cast<float*>(S.dinv);
+    const int info = lu_factor<32, LU_NMAX, float, true>(g, M32, dinv32, S.perm, n);
     double b[NPL], x[NPL], r[NPL];
     double bn = 0.0;
 #pragma unroll
@@ -1124,10 +1125,11 @@ __global__ void __launch_bounds__(32) k_solve_mixed(int64_t nb, int n, const dou
     bn = gmaxd(g, bn);
     int sw = -1;
     for (int it = 1; it <= MAXREF && !info; ++it) {
-      float r32[NPL], c32[NPL];
+      float c32[NPL];
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) r32[p] = (float)r[p];
-      apply_inverse<32, NPL, LU_NMAX, float>(g, M32, reinterpret_cast<float*>(S.ybuf), n, r32, c32);
+      for (int p = 0; p < NPL; ++p) c32[p] = (float)r[p];
+      lu_solve<32, NPL, LU_NMAX, float, true, float>(g, M32, dinv32, S.perm, reinterpret_cast<float*>(S.ybuf), n,
+                                                     c32);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) x[p] += (double)c32[p];
       g.sync();
@@ -1725,7 +1727,7 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
   return BDFB_SUCCESS;
 }
 
-// kernel row of the factorisation options: FP32 inverse with refinement
+// kernel row of the factorisation options: FP32 LU with refinement
 // (precision 1), FP64 Gauss-Jordan inverse (lsolver 1) or FP64 LU
 static int kernel_row(const bdfb_ctx* ctx) { return ctx->precision == 1 ? 1 : ctx->lsolver ? 2 : 0; }
 

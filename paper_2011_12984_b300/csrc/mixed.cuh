@@ -2,9 +2,11 @@
 // refinement, per cell (mass-action cells).
 //
 // B300 runs FP32 FMAs 64x faster than FP64 ones, so the block is factored in
-// FP32 - as an explicit Gauss-Jordan inverse, which turns every correction
-// into a fully parallel matrix-vector product instead of two dependent
-// triangular sweeps - and only the refinement residual r = b - M x is FP64.
+// FP32 (LU with partial pivoting, the FP64 path's elimination in FP32; each
+// correction is an FP32 forward and back substitution) and only the
+// refinement residual r = b - M x is FP64.  An explicit FP32 Gauss-Jordan
+// inverse (parallel matrix-vector corrections) issued three times the
+// setup's instructions and was slower on B300.
 // The residual does not store the FP64 matrix: M x = x - gamma J x with J x
 // assembled from the reaction derivatives d rate_r / d y_s kept (FP64) from
 // the setup point, reaction by reaction and species by species in the same
@@ -212,8 +214,6 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
   g.sync();
 }
 
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 // In-place Gauss-Jordan inverse with partial pivoting (ties to the lowest
 // row) of the n x n matrix A (FP32 or FP64); the block inverse the paper
@@ -334,10 +334,11 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
   const double bn = gmax_key(g, bk);
   int sweeps = -1;
   for (int it = 1; it <= MAXREF; ++it) {
-    float r32[NPL], c32[NPL];
+    float c32[NPL];
 #pragma unroll
-    for (int p = 0; p < NPL; ++p) r32[p] = to_f32(r[p]);
-    apply_inverse<G, NPL, NMAX, float>(g, S.M, buf, n, r32, c32);
+    for (int p = 0; p < NPL; ++p) c32[p] = to_f32(r[p]);
+    lu_solve<G, NPL, NMAX, float, true, float>(g, S.M, reinterpret_cast<const float*>(S.dinv), S.perm, buf, n,
+                                               c32);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) x[p] += to_f64(c32[p]);
     jac_vec<G, NPL, NMAX>(g, c, S, x, jx);
