@@ -377,10 +377,15 @@ __device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& 
   else p = NPL;
   while (p < NPL) {
     if (e < e1) {
-      const uint32_t v = __ldg(c.inc + e);
-      const double rt = vals[v >> 1];
-      acc = add_signed(acc, rt, v);
-      ++e;
+      // two entries per trip: their index and value loads are in flight
+      // together, the adds stay in list order
+      const bool two = e + 1 < e1;
+      const uint32_t v0 = __ldg(c.inc + e);
+      const uint32_t v1 = two ? __ldg(c.inc + e + 1) : 0u;
+      const double r0 = vals[v0 >> 1], r1 = vals[v1 >> 1];
+      acc = add_signed(acc, r0, v0);
+      if (two) acc = add_signed(acc, r1, v1);
+      e += two ? 2 : 1;
     } else {
       place(out, p, acc);
       acc = 0.0;
