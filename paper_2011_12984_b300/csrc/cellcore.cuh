@@ -377,15 +377,19 @@ __device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& 
   else p = NPL;
   while (p < NPL) {
     if (e < e1) {
-      // two entries per trip: their index and value loads are in flight
+      // four entries per trip: their index and value loads are in flight
       // together, the adds stay in list order
-      const bool two = e + 1 < e1;
-      const uint32_t v0 = __ldg(c.inc + e);
-      const uint32_t v1 = two ? __ldg(c.inc + e + 1) : 0u;
-      const double r0 = vals[v0 >> 1], r1 = vals[v1 >> 1];
-      acc = add_signed(acc, r0, v0);
-      if (two) acc = add_signed(acc, r1, v1);
-      e += two ? 2 : 1;
+      const int m = min(4, e1 - e);
+      uint32_t v[4];
+      double r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = u < m ? __ldg(c.inc + e + u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = vals[v[u] >> 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < m) acc = add_signed(acc, r[u], v[u]);
+      e += m;
     } else {
       place(out, p, acc);
       acc = 0.0;
