@@ -806,6 +806,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     step_s, kern_s = [], []
+    phases = os.environ.get("BDFB_LIBRARY") == "phases"
+    if phases:
+        bdfb.phase_cycles(reset=True)      # the profiling build: count the timed steps only
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(float(len(step_s)))       # evict L2 between steps
@@ -823,6 +826,13 @@ def run_ours(args):
     value = ws * NCELL / t_step
     cs = integ.cell_stats()
     yh = y.cpu().numpy()
+    phase_line = None
+    if phases:
+        pc = bdfb.phase_cycles(reset=True)
+        nst = args.steps * integ.stats()["nsteps"]      # every timed integration takes the same steps
+        tot = sum(pc.values())
+        phase_line = {"cycles_per_step": {k: v / nst for k, v in pc.items()},
+                      "share": {k: v / tot for k, v in pc.items()}, "steps": nst}
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -832,7 +842,8 @@ def run_ours(args):
                               "precision": args.precision, "stats": integ.stats(),
                               "mapping_by_class": mp.tolist(), "autotune_trial_ms": trial_ms.tolist(),
                               "steps_per_cell": float(cs[:, 0].mean()),
-                              "fp64_tflops_algorithmic": algorithmic_flops(prob, cs) / (sum(kern_s) / len(kern_s)) / 1e12}))
+                              "fp64_tflops_algorithmic": algorithmic_flops(prob, cs) / (sum(kern_s) / len(kern_s)) / 1e12,
+                              "phases": phase_line}))
         integ.close()
         if dist:
             dist.destroy_process_group()

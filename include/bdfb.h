@@ -400,6 +400,23 @@ int bdfb_get_cell_stats(bdfb_ctx* ctx, int64_t* out, int32_t mem);
  * [8c + v] (0: not tried). */
 int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms);
 
+/* Phase timers of the per-cell step kernels, for profiling; no counterpart in
+ * the paper.  A library built with the phase timers compiled in
+ * (python -m paper_2011_12984_b300.build --phases, which writes
+ * libbdfb_phases.so) charges the SM clock cycles of lane 0 of every warp to
+ * the part of the BDF step it is in.  out (host, nphase >= 14 entries)
+ * receives the cycles summed over all warps since the last reset, in the
+ * order: step control and error weights; prediction; Jacobian and M;
+ * factorisation pivoting (search, swap, column scaling); factorisation
+ * trailing updates; right-hand side reaction rates; right-hand side species
+ * sums; triangular solves; refinement residual (mixed precision); refinement
+ * norms and conversions; Newton tests and updates; error test, correction
+ * and step/order choice; failure handling; tile loads and stores.  reset != 0
+ * zeroes the counters afterwards.  Synchronises the device.  Returns the
+ * number of phases (14), or BDFB_ILL_INPUT from a library built without the
+ * timers or for a short or null out. */
+int bdfb_phase_cycles(uint64_t* out, int nphase, int reset);
+
 /* ------------------------------------- learned Newton initial guess (MLP)
  * Not part of the paper: a 12 -> 64 -> 64 -> 10 ReLU network predicts the
  * Newton correction Delta of a step, in error-weight units (Delta_i ewt_i),

@@ -14,10 +14,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbdfb.so")
+# BDFB_LIBRARY=phases loads the profiling build with the step-phase timers
+# (python -m paper_2011_12984_b300.build --phases)
+LIB_PATH = os.path.join(_HERE, "libbdfb_phases.so" if os.environ.get("BDFB_LIBRARY") == "phases" else "libbdfb.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libbdfb.so not built ({LIB_PATH}); run python -m paper_2011_12984_b300.build")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run python -m paper_2011_12984_b300.build")
 
 lib = C.CDLL(LIB_PATH)
 
@@ -103,6 +105,7 @@ _sig("bdfb_get_stats", C.c_int, [_vp, C.POINTER(Stats)])
 _sig("bdfb_get_cell_stats", C.c_int, [_vp, _vp, _i32])
 _sig("bdfb_get_op_profile", C.c_int, [_vp, _vp, _i32])
 _sig("bdfb_get_mapping", C.c_int, [_vp, _vp, _vp])
+_sig("bdfb_phase_cycles", C.c_int, [_vp, C.c_int, C.c_int])
 _sig("bdfb_mlp_nparam", _i64, [])
 _sig("bdfb_mlp_packed_bytes", _i64, [])
 _sig("bdfb_mlp_pack", C.c_int, [_vp, _vp, _vp])
@@ -131,6 +134,20 @@ def check(code, what=""):
     if code != SUCCESS:
         raise BdfbError(code, what)
     return code
+
+
+PHASES = ("control", "predict", "jacobian", "factor_pivot", "factor_update", "rhs_rates", "rhs_gather",
+          "triangular_solve", "residual", "refine_norms", "newton", "accept", "failure", "tile")
+
+
+def phase_cycles(reset=True):
+    """Cycles per step phase from a library built with the phase timers
+    (``BDFB_LIBRARY=phases``), as a dict in ``PHASES`` order."""
+    out = np.zeros(len(PHASES), dtype=np.uint64)
+    r = lib.bdfb_phase_cycles(out.ctypes.data, len(PHASES), int(reset))
+    if r < 0:
+        raise BdfbError(r, "bdfb_phase_cycles (library built without the phase timers?)")
+    return dict(zip(PHASES, (int(v) for v in out)))
 
 
 def strerror(code):

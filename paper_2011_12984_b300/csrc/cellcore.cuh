@@ -17,6 +17,47 @@
 
 namespace bdfb {
 
+// ------------------------------------------------------------- phase timers
+// Builds with -DBDFB_PHASES only (a plain build compiles the marks away):
+// lane 0 of each one-warp block charges the SM clock cycles between marks to
+// the phase it leaves, in one of 256 rows of counters (rows by block, so the
+// fire-and-forget atomic adds do not contend); the clock and the current
+// phase live in the block's shared memory, so any device function can mark.
+// Cycles a warp waits for a pipe that its neighbours keep busy count in the
+// phase it waits in: the shares show where a step's time goes.  Only the
+// per-cell step kernels start the clock.
+enum {
+  PH_CTRL, PH_PRED, PH_JAC, PH_LU_PIV, PH_LU_UPD, PH_RATES, PH_GATHER, PH_TRI, PH_RES, PH_NORM,
+  PH_NEWT, PH_ACCEPT, PH_FAIL, PH_TILE, NPHASE
+};
+#ifdef BDFB_PHASES
+__device__ unsigned long long g_phase_cycles[256][NPHASE];
+__device__ __forceinline__ long long& ph_clock() {
+  __shared__ long long t;
+  return t;
+}
+__device__ __forceinline__ int& ph_current() {
+  __shared__ int k;
+  return k;
+}
+__device__ __forceinline__ void ph_start(int k) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) { ph_clock() = clock64(); ph_current() = k; }
+  __syncwarp();
+}
+__device__ __forceinline__ void ph_mark(int k) {
+  if ((threadIdx.x & 31) == 0) {
+    const long long now = clock64();
+    atomicAdd(&g_phase_cycles[blockIdx.x & 255][ph_current()], (unsigned long long)(now - ph_clock()));
+    ph_clock() = now;
+    ph_current() = k;
+  }
+}
+#else
+__device__ __forceinline__ void ph_start(int) {}
+__device__ __forceinline__ void ph_mark(int) {}
+#endif
+
 // ------------------------------------------------------------------ groups
 template <int G>
 struct Grp {
@@ -212,6 +253,10 @@ struct CellDesc {
   const uint32_t* reac;     // 4 reactant species packed in bytes (255 = none)
   const int32_t* inc_off;   // species i of this cell: entries inc_off[i] .. inc_off[i+1)
   const uint16_t* inc;      // (reaction << 1) | (1 if produced, 0 if consumed)
+  // one-warp cells of more than 32 species: the species whose sums lane l
+  // forms (gs[l], up to four species bytes, low byte first, 255 = none), or
+  // null; see gather_species_bal
+  const uint32_t* gs;
 };
 
 // sqrt(sum (x_i w_i)^2 / n) over the group's elements
@@ -401,6 +446,51 @@ __device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& 
   }
 }
 
+// The same sums for a one-warp cell of more than 32 species, with the
+// species spread over the lanes by a schedule built when the problem is
+// created (longest lists first, each to the lane with the least work), so that
+// the warp waits for about the mean of the lanes' list lengths instead of the
+// longest pair of lists.  Every species is still summed alone, from zero, in
+// incidence-list order, so the sums equal gather_species's bit for bit; they
+// go through `sums` (n doubles of shared memory, free while the gather runs)
+// to the lanes that own the species.
+template <int G, int NPL>
+__device__ __forceinline__ void gather_species_bal(const Grp<G>& g, const CellDesc& c, const double* vals,
+                                                   double* sums, double (&out)[NPL]) {
+  uint32_t sl = __ldg(c.gs + g.rank);
+  int sp = (int)(sl & 255u);
+  int e = 0, e1 = 0;
+  double acc = 0.0;
+  if (sp != 255) { e = __ldg(c.inc_off + sp); e1 = __ldg(c.inc_off + sp + 1); }
+  while (sp != 255) {
+    if (e < e1) {
+      const int m = min(4, e1 - e);
+      uint32_t v[4];
+      double r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = u < m ? __ldg(c.inc + e + u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = vals[v[u] >> 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < m) acc = add_signed(acc, r[u], v[u]);
+      e += m;
+    } else {
+      sums[sp] = acc;
+      acc = 0.0;
+      sl = (sl >> 8) | 0xff000000u;
+      sp = (int)(sl & 255u);
+      if (sp != 255) { e = __ldg(c.inc_off + sp); e1 = __ldg(c.inc_off + sp + 1); }
+    }
+  }
+  g.sync();
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const int i = g.rank + G * p;
+    out[p] = i < c.n ? sums[i] : 0.0;
+  }
+}
+
 // ------------------------------------------------------------ right-hand side
 // f = f(y).  Mass action: rate_r = k_r prod_{s in R(r)} y_s, then each species
 // sums -rate over reactions consuming it and +rate over reactions producing
@@ -408,6 +498,7 @@ __device__ __forceinline__ void gather_species(const Grp<G>& g, const CellDesc& 
 template <int G, int NPL, int NMAX, int PREC>
 __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem<NMAX, PREC>& S, const double (&y)[NPL],
                     double (&f)[NPL]) {
+  ph_mark(PH_RATES);
   scatter_y<G, NPL, NMAX>(g, S, c.n, y);
   if (c.kind == BDFB_ROBERTSON) {
     const double* k = c.k;
@@ -434,7 +525,9 @@ __device__ __forceinline__ void rhs(const Grp<G>& g, const CellDesc& c, CellSmem
       S.rates[r] = rate;
     }
     g.sync();
-    gather_species<G, NPL>(g, c, S.rates, f);
+    ph_mark(PH_GATHER);
+    if (G == 32 && NPL > 1 && c.gs) gather_species_bal<G, NPL>(g, c, S.rates, S.ybuf, f);
+    else gather_species<G, NPL>(g, c, S.rates, f);
   }
   g.sync();
 }
@@ -490,6 +583,43 @@ __device__ __forceinline__ void form_M(const Grp<G>& g, const CellDesc& c, CellS
 }
 
 // ---------------------------------------------------------------- dense LU
+// Partial pivoting's row choice at column k: the row i in [k, n) of largest
+// |M[i][k]| (ties to the lowest row) and its key (the bit pattern of |M[i][k]|,
+// which orders like the value; a NaN's key exceeds infinity's), -1 when the
+// group holds no row.  Each lane scans its rows, then warp reductions on the
+// integer pipe (redux.sync) combine the lanes: an FP32 key in one maximum, an
+// FP64 key by its high word and then its low word, then the lowest row that
+// holds the maximum -- three dependent reductions where a shuffle butterfly
+// takes log2(G) rounds of three shuffles each.
+template <int G, int NMAX, typename T>
+__device__ __forceinline__ int pivot_search(const Grp<G>& g, const T (*M)[NMAX + 1], int n, int k,
+                                            long long& key) {
+  long long best = -1;
+  int p = n;
+  for (int i = k + g.rank; i < n; i += G) {
+    const long long v = abs_key_t(M[i][k]);
+    if (v > best) { best = v; p = i; }
+  }
+  if constexpr (G == 1) {
+    key = best;
+    return p;
+  } else if constexpr (sizeof(T) == 4) {
+    const unsigned u = (unsigned)(best + 1);          // keys < 2^31; 0: no row
+    const unsigned m = __reduce_max_sync(g.mask, u);
+    const unsigned r = __reduce_min_sync(g.mask, (m != 0u && u == m) ? (unsigned)p : 0xffffffffu);
+    key = (long long)m - 1;
+    return m ? (int)r : n;
+  } else {
+    const unsigned hi = best >= 0 ? (unsigned)(best >> 32) + 1u : 0u;   // 0: no row
+    const unsigned mh = __reduce_max_sync(g.mask, hi);
+    const bool top = mh != 0u && hi == mh;
+    const unsigned ml = __reduce_max_sync(g.mask, top ? (unsigned)best : 0u);
+    const unsigned r = __reduce_min_sync(g.mask, (top && (unsigned)best == ml) ? (unsigned)p : 0xffffffffu);
+    key = mh ? (((long long)(mh - 1u) << 32) | (long long)ml) : -1;
+    return mh ? (int)r : n;
+  }
+}
+
 // Right-looking LU with partial pivoting of the n x n matrix in S.M (ties in
 // |pivot| go to the lowest row).  Returns 0 or k + 1 when pivot k is zero (or
 // no finite pivot exists).  pivk (optional) records the pivot row of each step.
@@ -503,21 +633,10 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
   for (int i = g.rank; i < n; i += G) perm[i] = (int16_t)i;
   g.sync();
   for (int k = 0; k < n; ++k) {
-    // pivot search on integer keys: the bit patterns of non-negative IEEE
-    // doubles order like their values, so |a| compares on the integer pipe
-    // (a NaN key exceeds every finite one and is rejected below)
-    long long best = -1;
-    int p = n;
-    for (int i = k + g.rank; i < n; i += G) {
-      const long long v = abs_key_t(M[i][k]);
-      if (v > best) { best = v; p = i; }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const long long ob = __shfl_xor_sync(g.mask, best, o, G);
-      const int op = __shfl_xor_sync(g.mask, p, o, G);
-      if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
-    }
+    // pivot search on integer keys (a NaN key exceeds every finite one and
+    // is rejected below)
+    long long best;
+    const int p = pivot_search<G, NMAX, T>(g, M, n, k, best);
     if (p >= n || best <= 0 || best >= inf_key<T>()) return k + 1;
     if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
     if (p != k) {
@@ -579,18 +698,8 @@ __device__ __forceinline__ int lu_factor1(const Grp<G>& g, T (*M)[NMAX + 1], T* 
 template <int G, int NMAX, typename T>
 __device__ __forceinline__ bool pivot_swap(const Grp<G>& g, T (*M)[NMAX + 1], int16_t* perm, int n, int k,
                                            int16_t* pivk) {
-  long long best = -1;
-  int p = n;
-  for (int i = k + g.rank; i < n; i += G) {
-    const long long v = abs_key_t(M[i][k]);
-    if (v > best) { best = v; p = i; }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const long long ob = __shfl_xor_sync(g.mask, best, o, G);
-    const int op = __shfl_xor_sync(g.mask, p, o, G);
-    if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
-  }
+  long long best;
+  const int p = pivot_search<G, NMAX, T>(g, M, n, k, best);
   if (p >= n || best <= 0 || best >= inf_key<T>()) return false;
   if (pivk && g.rank == 0) pivk[k] = (int16_t)p;
   if (p != k) {
@@ -636,6 +745,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
   int k = 0;
   for (; k + 1 < n; k += 2) {
     const int k1 = k + 1, k2 = k + 2;
+    ph_mark(PH_LU_PIV);
     // ---- column k
     if (!pivot_swap<G, NMAX, T>(g, M, perm, n, k, pivk)) return k + 1;
     const T r0 = recip_t(M[k][k]);
@@ -658,6 +768,7 @@ __device__ __forceinline__ int lu_factor(const Grp<G>& g, T (*M)[NMAX + 1], T* d
     g.sync();
     // ---- both updates of the trailing block, lanes on an R x C grid; column
     // slots past the trailing width would issue predicated-off FP64 work
+    ph_mark(PH_LU_UPD);
     {
       const int nbu = (n - k2 + C - 1) / C;
       T u0[NJ], u1[NJ];
@@ -714,10 +825,13 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
   // L y = P b (unit lower).  Columns j in [G s - 1, G (s + 1) - 1) have rows
   // below them only in slots s.. NPL-1: the slots are split at compile time,
   // since a predicated-off FP64 instruction costs an issue like a live one
+  // (the column loops are kept rolled: unrolled by 2 or 4 they ran 1-7 %
+  // slower, FP64 and FP32 alike)
   int j = 0;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int jend = min(n - 1, G * (s + 1) - 1);
+#pragma unroll 1
     for (; j < jend; ++j) {
       const V xj = g.bcast(pick(x, j / G), j % G);
 #pragma unroll
@@ -740,6 +854,7 @@ __device__ __forceinline__ void lu_solve(const Grp<G>& g, const T (*M)[NMAX + 1]
 #pragma unroll
   for (int s = NPL - 1; s >= 0; --s) {
     const int jlo = (s == 0 && !UNITU) ? -1 : G * s;   // column 0 scales its own entry
+#pragma unroll 1
     for (; j > jlo; --j) {
       const int owner = j % G, slot = j / G;
       V xj = g.bcast(pick(x, slot), owner);

@@ -60,6 +60,7 @@ struct Params {
   const double* k;
   const int32_t* inc_off;
   const uint16_t* inc;
+  const uint32_t* gsched;     // per species slot: gather schedules of the cells of > 32 species, or null
   const TileDesc* tiles;
   const int32_t* tile_cells;
   int ntiles;
@@ -380,6 +381,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   constexpr int NPL = Cell<G, NMAX>::NPL;
   static_assert(!LEARN || (G == 32 && NPL == 1 && PREC == 0), "learned guess: one warp per cell, FP64");
   const int n = cd.n;
+  ph_mark(PH_CTRL);
   if (!(C.flags & F_STARTED)) {
     if (P.tout == C.t) { C.status = 0; return true; }   // first step waits for tout != t0
     const int r = start_cell(g, P, cd, S, C);
@@ -405,6 +407,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   C.retry = 0;
   if (C.t + C.h == C.t) { C.status = BDFB_ERR_FAILURE; return true; }
   const int q = C.q;
+  ph_mark(PH_PRED);
   // save and predict: z_{j-1} += z_j repeatedly (Pascal triangle)
   if constexpr (CellSmem<NMAX, PREC>::ZREG) {
 #pragma unroll
@@ -434,6 +437,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   // |gamma / gamma_setup - 1| > 0.3 tested without a division
   const double dgam = C.gamma - C.gammap;
   if (!C.setup_done || C.force_setup || fabs(dgam) > 0.3 * fabs(C.gammap) || C.nst >= C.nstlp + 20) {
+    ph_mark(PH_JAC);
     double y[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) y[p] = C.z[0][p];
@@ -443,6 +447,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
       // FP64 reaction derivatives kept for the refinement residual
       reaction_derivs<G, NPL, NMAX>(g, cd, S, y);
       C.mnorm = form_M32<G, NPL, NMAX>(g, cd, S, C.gamma);
+      ph_mark(PH_LU_PIV);
       info = lu_factor<G, NMAX, float, true>(g, S.M, reinterpret_cast<float*>(S.dinv), S.perm, n);
       C.fp64mode = 0;
     } else {
@@ -460,6 +465,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         }
       }
       if (direct) form_M<G, NPL, NMAX>(g, cd, S, y, C.gamma);
+      ph_mark(PH_LU_PIV);
       if constexpr (PREC == 2)   // explicit inverse: each Newton solve is one product
         info = gj_inverse<G, NMAX, double>(g, S.M, S.perm, S.ybuf, n);
       else
@@ -475,6 +481,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     if (info) { fail = true; C.setup_done = 0; }
   }
   // ---- Newton iteration (norms compared squared, in FP64)
+  ph_mark(PH_NEWT);
   // a stale M's step scaling 2 / (1 + gamma / gamma_setup), once per attempt
   const double scst = C.gamma != C.gammap ? 2.0 * C.gammap / (C.gammap + C.gamma) : 1.0;
   double acnrm2 = 0.0;
@@ -527,6 +534,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         if (!all_finite(g, n, C.f)) break;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) C.b[p] = C.gamma * C.f[p] - C.z[1][p] * rl1 - C.acor[p];
+        ph_mark(PH_TRI);
         if constexpr (PREC == 1) {
           bool solved = false;
           if (!C.fp64mode) {
@@ -558,6 +566,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
         } else {
           lu_solve<G, NPL, NMAX, double, true>(g, S.M, S.dinv, S.perm, S.ybuf, n, C.b);
         }
+        ph_mark(PH_NEWT);
         // a stale M's step scaling, except on the first step from a nonzero
         // guess: unscaled, that step gives w.Delta = -w.z1 / l1 for every w
         // with w^T J = 0 (w^T M = w^T), so the linear invariants of the ODE
@@ -599,6 +608,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     if (!conv) fail = true;
   }
   if (fail) {
+    ph_mark(PH_FAIL);
     restore_z(g, n, S, C);
     if (!jcur && !C.tried_fresh && C.setup_done) {   // stale M: retry once with a fresh one
       C.force_setup = 1;
@@ -616,9 +626,11 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     return false;
   }
   C.tried_fresh = 0;
+  ph_mark(PH_ACCEPT);
   // ---- local error test
   const double dsm2 = acnrm2 * Eq * Eq;    // (E_q ||Delta||)^2
   if (!(dsm2 <= 1.0)) {
+    ph_mark(PH_FAIL);
     restore_z(g, n, S, C);
     C.nef++;
     C.netf++;
@@ -692,6 +704,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   int64_t c = 0;
   CellDesc cd;
   Cell<G, NMAX> C;
+  ph_start(PH_TILE);
   int64_t yo = 0;
   if (active) {
     c = P.tile_cells[td.first + gid];
@@ -702,6 +715,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
       cd.reac = nullptr;
       cd.inc_off = nullptr;
       cd.inc = nullptr;
+      cd.gs = nullptr;
       yo = 3 * c;
     } else {
       cd.n = P.n[c];
@@ -712,6 +726,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
       cd.reac = P.reac + ro;
       cd.inc_off = P.inc_off + yo;
       cd.inc = P.inc;
+      cd.gs = (P.gsched && cd.n > 32) ? P.gsched + yo : nullptr;
     }
     cd.kind = P.kind;
     const CellState s = P.st[c];
@@ -738,6 +753,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   while (__any_sync(FULL_MASK, active)) {
     if (active) {
       if (attempt<G, NMAX, PREC, LEARN>(g, P, cd, S, C, Mg)) {
+        ph_mark(PH_TILE);
         active = false;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
@@ -774,6 +790,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
       }
     }
   }
+  ph_mark(PH_TILE);
 }
 
 // Kernel variants (cell-to-lane mappings): G lanes per cell for cells of at
@@ -890,6 +907,7 @@ __device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& G
   int64_t yo;
   if (P.kind == BDFB_ROBERTSON) {
     cd.n = 3; cd.nr = 0; cd.k = P.k + 3 * c; cd.reac = nullptr; cd.inc_off = nullptr; cd.inc = nullptr;
+    cd.gs = nullptr;
     yo = 3 * c;
   } else {
     cd.n = P.n[c];
@@ -900,6 +918,7 @@ __device__ __forceinline__ void group_cell(const Grp<G>& g, const GroupParams& G
     cd.reac = P.reac + ro;
     cd.inc_off = P.inc_off + yo;
     cd.inc = P.inc;
+    cd.gs = nullptr;
   }
   cd.kind = P.kind;
   const int n = cd.n;
@@ -1206,6 +1225,7 @@ struct bdfb_ctx {
   double* d_k = nullptr;
   int32_t* d_incoff = nullptr;
   uint16_t* d_inc = nullptr;
+  uint32_t* d_gsched = nullptr;   // gather schedules (cells of more than 32 species), or null
   CellState* d_state = nullptr;
   double* d_z = nullptr;
   double* d_acorp = nullptr;
@@ -1284,7 +1304,7 @@ static void free_ctx(bdfb_ctx* c) {
   cudaFree(c->d_glu); cudaFree(c->d_gluoff); cudaFree(c->d_gdinv); cudaFree(c->d_gperm);
   cudaFree(c->d_gcrate); cudaFree(c->d_gflag); cudaFree(c->d_giters);
   cudaFree(c->d_n); cudaFree(c->d_yoff); cudaFree(c->d_rxnoff); cudaFree(c->d_reac);
-  cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_state);
+  cudaFree(c->d_k); cudaFree(c->d_incoff); cudaFree(c->d_inc); cudaFree(c->d_gsched); cudaFree(c->d_state);
   cudaFree(c->d_z); cudaFree(c->d_acorp); cudaFree(c->d_counter); cudaFree(c->d_status); cudaFree(c->d_yout);
   for (int pr = 0; pr < NKPREC; ++pr)
     for (int k = 0; k < NVAR; ++k) cudaFree(c->d_fbws[pr][k]);
@@ -1554,6 +1574,41 @@ extern "C" int bdfb_create(const bdfb_problem* prob, bdfb_ctx** out) {
     TRY(dev_alloc_copy(&c->d_reac, reac32.data(), reac32.size()));
     TRY(dev_alloc_copy(&c->d_incoff, incoff.data(), incoff.size()));
     TRY(dev_alloc_copy(&c->d_inc, inc.data(), inc.size()));
+    // gather schedules of the cells of more than 32 species (one warp per
+    // cell): entries y_off .. y_off + 31 of a per-species array hold lane l's
+    // species, up to four bytes (255 = none).  Species in decreasing order of
+    // cost (4-entry trips of the gather loop, plus one for the switch), ties
+    // by index, each to the lane with the least cost so far (ties: lowest
+    // lane) that has a free byte.
+    bool any_big = false;
+    for (int64_t cc = 0; cc < C; ++cc) any_big = any_big || n[cc] > 32;
+    if (any_big) {
+      std::vector<uint32_t> gs(c->ny, 0xffffffffu);
+      std::vector<int> ord;
+      for (int64_t cc = 0; cc < C; ++cc) {
+        const int nn = n[cc];
+        if (nn <= 32) continue;
+        auto cost = [&](int sp) {
+          const int len = incoff[yoff[cc] + sp + 1] - incoff[yoff[cc] + sp];
+          return (len + 3) / 4 + 1;
+        };
+        ord.resize(nn);
+        for (int sp = 0; sp < nn; ++sp) ord[sp] = sp;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a2, int b2) { return cost(a2) > cost(b2); });
+        int load[32] = {0}, cnt[32] = {0};
+        for (int sp : ord) {
+          int best = -1;
+          for (int l = 0; l < 32; ++l)
+            if (cnt[l] < 4 && (best < 0 || load[l] < load[best])) best = l;
+          if (best < 0) { free_ctx(c); return BDFB_ILL_INPUT; }   // n > 128: not a one-warp cell
+          uint32_t& w = gs[yoff[cc] + best];
+          w = (w & ~(0xffu << (8 * cnt[best]))) | ((uint32_t)sp << (8 * cnt[best]));
+          cnt[best]++;
+          load[best] += cost(sp);
+        }
+      }
+      TRY(dev_alloc_copy(&c->d_gsched, gs.data(), gs.size()));
+    }
   }
   TRY(dev_alloc_copy(&c->d_k, k.data(), k.size()));
   // schedules: [0] tiles by size class, largest class first; [1] one cell
@@ -1753,6 +1808,7 @@ static Params base_params(bdfb_ctx* ctx, double tout) {
   P.k = ctx->d_k;
   P.inc_off = ctx->d_incoff;
   P.inc = ctx->d_inc;
+  P.gsched = ctx->d_gsched;
   P.tile_counter = ctx->d_counter;
   P.worst = reinterpret_cast<int*>(ctx->d_counter + NVAR);
   P.st = ctx->d_state;
@@ -2201,6 +2257,27 @@ extern "C" int bdfb_get_op_profile(bdfb_ctx* ctx, double* out, int32_t nkinds) {
   if (!ctx || !out || !ctx->grid || nkinds < GOP_N) return BDFB_ILL_INPUT;
   grid_profile(ctx->grid, out);
   return GOP_N;
+}
+
+extern "C" int bdfb_phase_cycles(uint64_t* out, int nphase, int reset) {
+#ifdef BDFB_PHASES
+  if (!out || nphase < bdfb::NPHASE) return BDFB_ILL_INPUT;
+  static unsigned long long h[256][bdfb::NPHASE];
+  BDFB_CUDA(cudaDeviceSynchronize());
+  BDFB_CUDA(cudaMemcpyFromSymbol(h, bdfb::g_phase_cycles, sizeof h));
+  for (int k = 0; k < bdfb::NPHASE; ++k) {
+    out[k] = 0;
+    for (int r = 0; r < 256; ++r) out[k] += h[r][k];
+  }
+  if (reset) {
+    std::memset(h, 0, sizeof h);
+    BDFB_CUDA(cudaMemcpyToSymbol(bdfb::g_phase_cycles, h, sizeof h));
+  }
+  return bdfb::NPHASE;
+#else
+  (void)out; (void)nphase; (void)reset;
+  return BDFB_ILL_INPUT;
+#endif
 }
 
 extern "C" int bdfb_get_stats(bdfb_ctx* ctx, bdfb_stats* out) {

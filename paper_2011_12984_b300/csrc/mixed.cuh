@@ -32,18 +32,22 @@ __device__ __forceinline__ double gmaxd(const Grp<G>& g, double v) {
 
 // max |v| over the group on the integer pipe: the bit patterns of
 // non-negative doubles order like their values (a NaN's key lies above
-// infinity's, so a NaN wins and fails every later <= test)
+// infinity's, so a NaN wins and fails every later <= test); the maximum of
+// the keys' high words, then of the low words of the keys that hold it (two
+// redux.sync reductions)
 __device__ __forceinline__ long long abs_key(double v) {
   return __double_as_longlong(v) & 0x7fffffffffffffffLL;
 }
 template <int G>
 __device__ __forceinline__ double gmax_key(const Grp<G>& g, long long k) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const long long ok = __shfl_xor_sync(g.mask, k, o, G);
-    k = ok > k ? ok : k;
+  if constexpr (G == 1) {
+    return __longlong_as_double(k);
+  } else {
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    const unsigned mh = __reduce_max_sync(g.mask, hi);
+    const unsigned ml = __reduce_max_sync(g.mask, hi == mh ? lo : 0u);
+    return __longlong_as_double((long long)(((unsigned long long)mh << 32) | ml));
   }
-  return __longlong_as_double(k);
 }
 
 template <int G>
@@ -210,7 +214,8 @@ __device__ __forceinline__ void jac_vec(const Grp<G>& g, const CellDesc& c, Cell
     S.rates[r] = s;
   }
   g.sync();
-  gather_species<G, NPL>(g, c, S.rates, jx);
+  if (G == 32 && NPL > 1 && c.gs) gather_species_bal<G, NPL>(g, c, S.rates, S.ybuf, jx);
+  else gather_species<G, NPL>(g, c, S.rates, jx);
   g.sync();
 }
 
@@ -325,6 +330,7 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
   // (to_f32 flushes magnitudes below 2^-126: a residual that small in every
   // entry ends the sweeps unconverged and takes the FP64 fallback)
   long long bk = 0;
+  ph_mark(PH_NORM);
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
     x[p] = 0.0;
@@ -337,11 +343,13 @@ __device__ __forceinline__ int refined_solve(const Grp<G>& g, const CellDesc& c,
     float c32[NPL];
 #pragma unroll
     for (int p = 0; p < NPL; ++p) c32[p] = to_f32(r[p]);
-    lu_solve<G, NPL, NMAX, float, true, float>(g, S.M, reinterpret_cast<const float*>(S.dinv), S.perm, buf, n,
-                                               c32);
+    ph_mark(PH_TRI);
+    lu_solve<G, NPL, NMAX, float, true, float>(g, S.M, reinterpret_cast<const float*>(S.dinv), S.perm, buf, n, c32);
+    ph_mark(PH_RES);
 #pragma unroll
     for (int p = 0; p < NPL; ++p) x[p] += to_f64(c32[p]);
     jac_vec<G, NPL, NMAX>(g, c, S, x, jx);
+    ph_mark(PH_NORM);
     long long rk = 0, xk = 0;
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
