@@ -279,7 +279,12 @@ int bdfb_set_tolerances(bdfb_ctx* ctx, double rtol, double atol);
  *  "mapping"   0 = automatic tiles by cell size (default), 32 = one warp per
  *              cell for every cell in input order (the plain form)
  *  "precision" 0 = FP64 factorisation (default), 1 = FP32 factorisation with
- *              FP64 iterative refinement to 1e-12 backward error
+ *              FP64 iterative refinement to 1e-12 backward error for the
+ *              cells of more than 32 species (where the factorisation
+ *              dominates a step); smaller cells keep FP64 factors, which
+ *              are faster there on B300, unless "mixed_small" is 1
+ *  "mixed_small" 1 = precision 1 factors every cell in FP32 (mass action;
+ *              default 0)
  *  "graph"     1 = capture integrate's launch sequence (counter reset, one
  *              persistent launch per kernel variant on forked streams, join)
  *              into a CUDA graph once and replay it; a call that differs only

@@ -1244,13 +1244,14 @@ struct bdfb_ctx {
   cudaGraph_t cgraph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   Params gkey;                     // Params of the capture with tout = 0
-  int gkey_gen = -1, gkey_m = -1, gkey_single = -1;
+  int gkey_gen = -1, gkey_m = -1, gkey_single = -1, gkey_rows = -1;
   int64_t graph_launches = 0, graph_captures = 0;
   int32_t* d_status = nullptr;
   double rtol = 1e-6, atol = 1e-10;
   int64_t mxstep = 100000;
   int mapping = 0, precision = 0, graph = 0, qmax = QMAX;
   int lsolver = 0;            // 1: FP64 Gauss-Jordan inverse instead of LU
+  int mixed_small = 0;        // precision 1: cells of at most 32 species get FP32 factors too
   double t0 = 0.0;
   bool initialized = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evfork = nullptr;
@@ -1711,6 +1712,10 @@ extern "C" int bdfb_set_option(bdfb_ctx* ctx, const char* key, int64_t v) {
     if (v == 1 && ctx->kind != BDFB_MASSACTION) return BDFB_ILL_INPUT;  // residual needs reaction data
     if (v == 1 && (ctx->predictor || ctx->rec_x)) return BDFB_ILL_INPUT;
     ctx->precision = (int)v;
+  } else if (!std::strcmp(key, "mixed_small")) {
+    if (v != 0 && v != 1) return BDFB_ILL_INPUT;
+    if (v == 1 && ctx->kind != BDFB_MASSACTION) return BDFB_ILL_INPUT;
+    ctx->mixed_small = (int)v;
   } else if (!std::strcmp(key, "graph")) {
     if (v != 0 && v != 1) return BDFB_ILL_INPUT;
     ctx->graph = (int)v;
@@ -1784,12 +1789,26 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
 
 // kernel row of the factorisation options: FP32 LU with refinement
 // (precision 1), FP64 Gauss-Jordan inverse (lsolver 1) or FP64 LU
-static int kernel_row(const bdfb_ctx* ctx) { return ctx->precision == 1 ? 1 : ctx->lsolver ? 2 : 0; }
+// Kernel row (0 FP64 LU, 1 FP32 LU with FP64 refinement, 2 FP64
+// Gauss-Jordan inverse) of variant v.  Precision 1 factors in FP32 the cells
+// of more than 32 species (the NMAX 56 kernels), where the n^3 factorisation
+// dominates a step; smaller cells keep FP64 factors unless mixed_small is set:
+// on B300 two FP64 refinement residuals per solve cost more there than the
+// FP64 factorisations they replace (measured per size class: n = 54 1.11x
+// faster in FP32, n = 32 1.10x, n = 10 1.48x and n = 3 1.56x slower).
+constexpr int MIXED_NMAX = 56;
+static int row_of(const bdfb_ctx* ctx, int v) {
+  if (ctx->precision == 1 && (ctx->mixed_small || VAR_NMAX[v] >= MIXED_NMAX)) return 1;
+  return ctx->lsolver ? 2 : 0;
+}
+// the configuration the kernel rows follow (a tuned schedule or a captured
+// graph is valid for one value)
+static int rows_key(const bdfb_ctx* ctx) { return ctx->precision + 2 * ctx->lsolver + 4 * ctx->mixed_small; }
 
 // The one-warp-per-cell kernel of mapping 32 (and of the learned guess): the
 // smallest shared-memory layout every cell fits
 static int one_warp_variant(const bdfb_ctx* ctx, bool learn) {
-  if (learn || (ctx->fits_w16 && ctx->precision == 0 && !ctx->lsolver)) return VAR_W16;
+  if (learn || (ctx->fits_w16 && row_of(ctx, VAR_W16) == 0)) return VAR_W16;
   if (ctx->fits_w32) return VAR_W32;
   return 4;
 }
@@ -1849,8 +1868,7 @@ static int ensure_fbws(bdfb_ctx* ctx, int pr, int v) {
 // largest cells first, each on its own stream so that smaller cells fill
 // the SMs the larger ones release, and join.  `single`: the variant the
 // one-cell tiles of the one-warp-per-cell schedule (variant 4's range) run on.
-static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, int single,
-                      cudaStream_t s) {
+static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int single, cudaStream_t s) {
   BDFB_CUDA(cudaMemsetAsync(ctx->d_counter, 0, (NVAR + 1) * sizeof(unsigned), s));
   BDFB_CUDA(cudaEventRecord(ctx->evfork, s));
   for (int k = 0; k < NVAR; ++k) {
@@ -1858,6 +1876,7 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, in
     const int t0 = S.vbeg[v], t1 = S.vend[v];
     if (t1 <= t0) continue;
     const int kv = v == 4 ? single : v;
+    const int pr = row_of(ctx, kv);
     const cells_kernel_t kf = var_kernel(pr, kv);
     if (!kf) return BDFB_ILL_INPUT;
     // mixed precision: the launched variant's FP64 fallback workspace must exist
@@ -1876,18 +1895,19 @@ static int launch_all(bdfb_ctx* ctx, const Params& P, const Sched& S, int pr, in
 // Option "graph": the launch sequence is captured once into a CUDA graph
 // and replayed; a later call with the same parameters but another tout
 // patches tout into the kernel nodes; anything else recaptures.
-static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, int single, cudaStream_t s) {
+static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int single, cudaStream_t s) {
   Params key = P;
   key.tout = 0.0;
   const bool same = ctx->gexec && ctx->gkey_gen == ctx->sched_gen && ctx->gkey_m == m &&
-                    ctx->gkey_single == single && !std::memcmp(&key, &ctx->gkey, sizeof key);
+                    ctx->gkey_single == single && ctx->gkey_rows == rows_key(ctx) &&
+                    !std::memcmp(&key, &ctx->gkey, sizeof key);
   if (!same) {
     if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
     if (ctx->cgraph) { cudaGraphDestroy(ctx->cgraph); ctx->cgraph = nullptr; }
     // captured on a stream of the context (the legacy default stream cannot
     // be captured); the graph is launched on s
     BDFB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int r = launch_all(ctx, P, ctx->sched[m], pr, single, ctx->cap_stream);
+    const int r = launch_all(ctx, P, ctx->sched[m], single, ctx->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (r || e != cudaSuccess) {
@@ -1900,6 +1920,7 @@ static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, int singl
     ctx->gkey_gen = ctx->sched_gen;
     ctx->gkey_m = m;
     ctx->gkey_single = single;
+    ctx->gkey_rows = rows_key(ctx);
     ctx->graph_captures++;
   } else {
     size_t nn = 0;
@@ -1936,7 +1957,7 @@ static int launch_graph(bdfb_ctx* ctx, const Params& P, int m, int pr, int singl
 // on scratch copies of the state, time each launch with events, and keep
 // the fastest (another variant must beat the class's own by 3%).  The
 // context's state is not touched.  Builds schedule 2.
-static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s) {
+static int run_autotune(bdfb_ctx* ctx, const Params& P0, cudaStream_t s) {
   const int64_t C = ctx->ncell;
   constexpr int64_t SAMPLE = 16384;
   std::vector<std::vector<int32_t>> members(NCLASS);
@@ -1968,10 +1989,11 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
     // more warps in flight); nothing to time when there is no alternative
     std::vector<int> cand = {cl};
     for (int v = 0; v < NVAR; ++v)
-      if (v != cl && var_kernel(pr, v) && VAR_NMAX[v] >= CLS_NMAX[cl]) cand.push_back(v);
+      if (v != cl && var_kernel(row_of(ctx, v), v) && VAR_NMAX[v] >= CLS_NMAX[cl]) cand.push_back(v);
     if (cand.size() == 1) continue;
     float best = 0.f;
     for (int v : cand) {
+      const int pr = row_of(ctx, v);
       if (ensure_fbws(ctx, pr, v)) { fail(BDFB_MEM_FAIL); break; }
       for (int32_t c : members[cl]) var[c] = (int8_t)v;
       std::vector<TileDesc> tiles;
@@ -2039,7 +2061,7 @@ static int run_autotune(bdfb_ctx* ctx, const Params& P0, int pr, cudaStream_t s)
   }
   const int r = upload_sched(ctx, 2, launch_order(var, ctx->h_n, all), var, false);
   if (r) return r;
-  ctx->tuned_prec = pr;
+  ctx->tuned_prec = rows_key(ctx);
   return 0;
 }
 
@@ -2192,7 +2214,6 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   if (ctx->grouped) return grouped_integrate(ctx, tout, y, status, mem);
   if (ctx->predictor && !ctx->mlp) return BDFB_ILL_INPUT;
   cudaStream_t s = ctx->stream;
-  const int pr = kernel_row(ctx);
   const bool learn = ctx->predictor || ctx->rec_x;
   // one warp per cell: the NMAX 16 kernel when every cell fits it
   // one warp per cell: the smallest one-warp kernel every cell fits
@@ -2200,11 +2221,11 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   int m = (ctx->mapping == 32 || learn) ? 1 : 0;
   Params P = base_params(ctx, tout);
   if (m == 0 && ctx->autotune) {
-    if (ctx->tuned_prec != pr) {
+    if (ctx->tuned_prec != rows_key(ctx)) {
       P.tiles = ctx->sched[0].d_tiles;
       P.tile_cells = ctx->sched[0].d_tcells;
       P.ntiles = ctx->sched[0].ntiles;
-      int r = run_autotune(ctx, P, pr, s);
+      int r = run_autotune(ctx, P, s);
       if (r) return r;
     }
     m = 2;
@@ -2217,15 +2238,16 @@ extern "C" int bdfb_integrate(bdfb_ctx* ctx, double tout, double* y, int32_t* st
   // range runs on `single` under the one-warp-per-cell schedule)
   for (int v = 0; v < NVAR; ++v)
     if (S.vend[v] > S.vbeg[v]) {
-      const int r = ensure_fbws(ctx, pr, v == 4 ? single : v);
+      const int kv = v == 4 ? single : v;
+      const int r = ensure_fbws(ctx, row_of(ctx, kv), kv);
       if (r) return r;
     }
   BDFB_CUDA(cudaEventRecord(ctx->ev0, s));
   if (ctx->graph) {
-    const int r = launch_graph(ctx, P, m, pr, single, s);
+    const int r = launch_graph(ctx, P, m, single, s);
     if (r) return r;
   } else {
-    const int r = launch_all(ctx, P, S, pr, single, s);
+    const int r = launch_all(ctx, P, S, single, s);
     if (r) return r;
   }
   BDFB_CUDA(cudaEventRecord(ctx->ev1, s));
@@ -2456,7 +2478,7 @@ extern "C" int bdfb_get_mapping(bdfb_ctx* ctx, int32_t* out, float* trial_ms) {
     if (!out[3 * cl + 2]) continue;
     int v = cl;
     if (learn || ctx->mapping == 32) v = one_warp_variant(ctx, learn);
-    else if (ctx->autotune && ctx->tuned_prec == kernel_row(ctx)) v = ctx->tuned_var[cl];
+    else if (ctx->autotune && ctx->tuned_prec == rows_key(ctx)) v = ctx->tuned_var[cl];
     out[3 * cl] = VAR_G[v];
     out[3 * cl + 1] = VAR_NMAX[v];
     if (trial_ms && ctx->autotune && ctx->tuned_prec >= 0)

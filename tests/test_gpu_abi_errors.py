@@ -84,7 +84,7 @@ def test_shared_network_and_line_reject_foreign_options():
     with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, shared_network=True) as S:
         for key, v in ((b"mapping", 32), (b"precision", 1), (b"graph", 1), (b"autotune", 1),
                        (b"grouped", 2), (b"predictor", 1), (b"lsolver", 1), (b"interp", 2),
-                       (b"qmax", 6), (b"mxstep", 0)):
+                       (b"qmax", 6), (b"mxstep", 0), (b"mixed_small", 1)):
             assert L.bdfb_set_option(S.h, key, v) == ILL, key
         S.set_option("lsolver", 0)
         S.init(0.0, torch.from_numpy(bdfb.species_major(p)).cuda())
@@ -96,7 +96,7 @@ def test_shared_network_and_line_reject_foreign_options():
     q = gen.brusselator1d(64, length=10.0)
     with bdfb.Integrator(q, rtol=1e-6, atol=1e-10) as Q:
         for key, v in ((b"imex", 2), (b"device_loop", 2), (b"device_loop", -2), (b"precision", 2),
-                       (b"maxl", 0), (b"mapping", 32)):
+                       (b"maxl", 0), (b"mapping", 32), (b"mixed_small", 1)):
             assert L.bdfb_set_option(Q.h, key, v) == ILL, key
         Q.set_option("imex", 1)
         Q.init(0.0, torch.from_numpy(q.y0).cuda())

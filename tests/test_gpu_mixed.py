@@ -105,11 +105,36 @@ def test_mixed_one_warp_per_cell():
     assert np.max(np.abs(np.add.reduceat(y, p.y_off[:-1]) - s0)) <= 5e-11
     check_against_oracle(p, 1e-3, 1e-6, 1e-10, y, cs)
     # cells small enough for the 32-species kernel only (its workspace is
-    # then the only one)
+    # then the only one), with FP32 factors for the small cells too
     q = gen.mass_action(100000, sizes=(3, 10, 32), seed=23).subset(np.arange(512))
-    ret, y, st, cs, _ = run_gpu(q, 0.0, 1e-3, 1e-6, 1e-10, precision=1, mapping=32)
+    ret, y, st, cs, stats = run_gpu(q, 0.0, 1e-3, 1e-6, 1e-10, precision=1, mapping=32, mixed_small=1)
     assert ret == 0 and np.all(st == 0)
+    assert stats["nrefine"] >= stats["nniters"]
     check_against_oracle(q, 1e-3, 1e-6, 1e-10, y, cs)
+
+
+@pytest.mark.parametrize("mapping", [0, 32])
+def test_mixed_factors_only_the_largest_cells_by_default(mapping):
+    """precision 1 factors in FP32 only the cells of more than 32 species
+    (their kernels): a batch of smaller cells runs FP64 factors (no refinement
+    sweep) unless mixed_small is set; both meet the same bar"""
+    q = gen.mass_action(100000, sizes=(3, 10, 32), seed=24).subset(np.arange(384))
+    for small in (0, 1):
+        ret, y, st, cs, stats = run_gpu(q, 0.0, 1e-3, 1e-6, 1e-10, precision=1, mapping=mapping,
+                                        mixed_small=small)
+        assert ret == 0 and np.all(st == 0)
+        if small:
+            assert stats["nrefine"] >= stats["nniters"]
+        else:
+            assert stats["nrefine"] == 0 and stats["nrefine_fallback"] == 0
+        check_against_oracle(q, 1e-3, 1e-6, 1e-10, y, cs)
+
+
+def test_mixed_small_option_rejected_off_mass_action():
+    with bdfb.Integrator(gen.robertson(4)) as I:
+        with pytest.raises(bdfb.BdfbError):
+            I.set_option("mixed_small", 1)
+        I.set_option("mixed_small", 0)
 
 
 def test_mixed_rejected_for_robertson():
