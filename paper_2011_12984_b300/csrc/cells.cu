@@ -690,8 +690,13 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
 
 // fb: this warp's slice of the FP64 fallback workspace (mixed precision;
 // (32 / G) matrices of NMAX x (NMAX + 1) doubles), else null
+// Cells [c0, c1) of P.tile_cells on this warp: every group of G lanes takes
+// the next cell from `counter` as soon as its own cell is finished, not when
+// the warp's last cell is, so cells of unequal step counts that share a warp
+// leave no group idle until the range is exhausted.
 template <int G, int NMAX, int PREC, int LEARN = 0>
-__device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, char* smem, double* fb) {
+__device__ __forceinline__ void run_cells(const Params& P, int c0, int c1, unsigned* counter, char* smem,
+                                          double* fb) {
   constexpr int NPL = Cell<G, NMAX>::NPL;
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
@@ -700,93 +705,99 @@ __device__ __forceinline__ void run_tile(const Params& P, const TileDesc td, cha
   // cells: their derivative workspace (the same pointer)
   constexpr int64_t WS = PREC == 1 ? (int64_t)NMAX * (NMAX + 1) : 8LL * NMAX;
   double (*Mg)[NMAX + 1] = fb ? reinterpret_cast<double (*)[NMAX + 1]>(fb + (int64_t)gid * WS) : nullptr;
-  bool active = gid < td.count;
+  bool active = false, more = true;
   int64_t c = 0;
   CellDesc cd;
   Cell<G, NMAX> C;
   ph_start(PH_TILE);
   int64_t yo = 0;
-  if (active) {
-    c = P.tile_cells[td.first + gid];
-    if (P.kind == BDFB_ROBERTSON) {
-      cd.n = 3;
-      cd.nr = 0;
-      cd.k = P.k + 3 * c;
-      cd.reac = nullptr;
-      cd.inc_off = nullptr;
-      cd.inc = nullptr;
-      cd.gs = nullptr;
-      yo = 3 * c;
-    } else {
-      cd.n = P.n[c];
-      yo = P.y_off[c];
-      const int64_t ro = P.rxn_off[c];
-      cd.nr = (int)(P.rxn_off[c + 1] - ro);
-      cd.k = P.k + ro;
-      cd.reac = P.reac + ro;
-      cd.inc_off = P.inc_off + yo;
-      cd.inc = P.inc;
-      cd.gs = (P.gsched && cd.n > 32) ? P.gsched + yo : nullptr;
-    }
-    cd.kind = P.kind;
-    const CellState s = P.st[c];
-    C.t = s.t; C.h = s.h; C.gammap = s.gammap; C.crate = s.crate; C.hlast = s.hlast;
-    C.q = s.q; C.qwait = s.qwait; C.nst = s.nst; C.nstlp = s.nstlp;
-    C.nfe = s.nfe; C.nsetups = s.nsetups; C.nni = s.nni; C.ncfn = s.ncfn;
-    C.netf = s.netf; C.flags = s.flags; C.status = 0; C.qlast = s.qlast;
-    C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
-    C.rn = 1.0 / (double)cd.n;
-    C.nref = s.nrefine; C.nref_fb = s.nrefine_fb; C.fp64mode = 0; C.mnorm = 0.0;
-    C.nguess = s.nguess; C.nguess_fb = s.nguess_fb; C.lastit = 0;
-    C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
-#pragma unroll
-    for (int p = 0; p < NPL; ++p) {
-      const int i = g.rank + G * p;
-      const bool in = i < cd.n;
-#pragma unroll
-      for (int j = 0; j <= QMAX; ++j) C.z[j][p] = in ? P.z[(int64_t)j * P.ny + yo + i] : 0.0;
-      C.acorp[p] = in ? P.acorp[yo + i] : 0.0;
-      C.acor[p] = 0.0;
-      C.ewt[p] = 0.0;
-    }
-  }
-  while (__any_sync(FULL_MASK, active)) {
-    if (active) {
-      if (attempt<G, NMAX, PREC, LEARN>(g, P, cd, S, C, Mg)) {
-        ph_mark(PH_TILE);
-        active = false;
+  for (;;) {
+    if (!active && more) {
+      int pos = 0;
+      if (g.rank == 0) pos = c0 + (int)atomicAdd(counter, 1u);
+      pos = g.bcast(pos, 0);
+      more = pos < c1;
+      if (more) {
+        active = true;
+        c = P.tile_cells[pos];
+        if (P.kind == BDFB_ROBERTSON) {
+          cd.n = 3;
+          cd.nr = 0;
+          cd.k = P.k + 3 * c;
+          cd.reac = nullptr;
+          cd.inc_off = nullptr;
+          cd.inc = nullptr;
+          cd.gs = nullptr;
+          yo = 3 * c;
+        } else {
+          cd.n = P.n[c];
+          yo = P.y_off[c];
+          const int64_t ro = P.rxn_off[c];
+          cd.nr = (int)(P.rxn_off[c + 1] - ro);
+          cd.k = P.k + ro;
+          cd.reac = P.reac + ro;
+          cd.inc_off = P.inc_off + yo;
+          cd.inc = P.inc;
+          cd.gs = (P.gsched && cd.n > 32) ? P.gsched + yo : nullptr;
+        }
+        cd.kind = P.kind;
+        const CellState s = P.st[c];
+        C.t = s.t; C.h = s.h; C.gammap = s.gammap; C.crate = s.crate; C.hlast = s.hlast;
+        C.q = s.q; C.qwait = s.qwait; C.nst = s.nst; C.nstlp = s.nstlp;
+        C.nfe = s.nfe; C.nsetups = s.nsetups; C.nni = s.nni; C.ncfn = s.ncfn;
+        C.netf = s.netf; C.flags = s.flags; C.status = 0; C.qlast = s.qlast;
+        C.nst0 = C.nst; C.setup_done = 0; C.force_setup = 0; C.tried_fresh = 0;
+        C.rn = 1.0 / (double)cd.n;
+        C.nref = s.nrefine; C.nref_fb = s.nrefine_fb; C.fp64mode = 0; C.mnorm = 0.0;
+        C.nguess = s.nguess; C.nguess_fb = s.nguess_fb; C.lastit = 0;
+        C.newstep = 1; C.retry = 0; C.last = 0; C.ncf = 0; C.nef = 0; C.gamma = 0.0;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
           const int i = g.rank + G * p;
-          if (i < cd.n) {
+          const bool in = i < cd.n;
 #pragma unroll
-            for (int j = 0; j <= QMAX; ++j) P.z[(int64_t)j * P.ny + yo + i] = C.z[j][p];
-            P.acorp[yo + i] = C.acorp[p];
-            if (P.yout) {
-              // the history polynomial at tout, sum_j z_j s^j with s = (tout - t) / h
-              // (Horner), for a cell past tout; otherwise its current state
-              double v = C.z[0][p];
-              if (P.interp && C.status == 0 && (C.flags & F_STARTED) && C.t != P.tout) {
-                const double sv = (P.tout - C.t) / C.h;
-                v = C.z[QMAX][p];
+          for (int j = 0; j <= QMAX; ++j) C.z[j][p] = in ? P.z[(int64_t)j * P.ny + yo + i] : 0.0;
+          C.acorp[p] = in ? P.acorp[yo + i] : 0.0;
+          C.acor[p] = 0.0;
+          C.ewt[p] = 0.0;
+        }
+      }
+    }
+    if (!__any_sync(FULL_MASK, active)) break;
+    if (active && attempt<G, NMAX, PREC, LEARN>(g, P, cd, S, C, Mg)) {
+      ph_mark(PH_TILE);
+      active = false;
 #pragma unroll
-                for (int j = QMAX - 1; j >= 0; --j) v = j < C.q ? v * sv + C.z[j][p] : C.z[j][p];
-              }
-              P.yout[yo + i] = v;
+      for (int p = 0; p < NPL; ++p) {
+        const int i = g.rank + G * p;
+        if (i < cd.n) {
+#pragma unroll
+          for (int j = 0; j <= QMAX; ++j) P.z[(int64_t)j * P.ny + yo + i] = C.z[j][p];
+          P.acorp[yo + i] = C.acorp[p];
+          if (P.yout) {
+            // the history polynomial at tout, sum_j z_j s^j with s = (tout - t) / h
+            // (Horner), for a cell past tout; otherwise its current state
+            double v = C.z[0][p];
+            if (P.interp && C.status == 0 && (C.flags & F_STARTED) && C.t != P.tout) {
+              const double sv = (P.tout - C.t) / C.h;
+              v = C.z[QMAX][p];
+#pragma unroll
+              for (int j = QMAX - 1; j >= 0; --j) v = j < C.q ? v * sv + C.z[j][p] : C.z[j][p];
             }
+            P.yout[yo + i] = v;
           }
         }
-        if (g.rank == 0) {
-          CellState s;
-          s.t = C.t; s.h = C.h; s.gammap = C.gammap; s.crate = C.crate; s.hlast = C.hlast;
-          s.q = C.q; s.qwait = C.qwait; s.nst = C.nst; s.nstlp = C.nstlp;
-          s.nfe = C.nfe; s.nsetups = C.nsetups; s.nni = C.nni; s.ncfn = C.ncfn;
-          s.netf = C.netf; s.flags = C.flags; s.status = C.status; s.qlast = C.qlast;
-          s.nrefine = C.nref; s.nrefine_fb = C.nref_fb; s.nguess = C.nguess; s.nguess_fb = C.nguess_fb;
-          P.st[c] = s;
-          if (P.status) P.status[c] = C.status;
-          if (C.status < 0) atomicMin(P.worst, C.status);
-        }
+      }
+      if (g.rank == 0) {
+        CellState s;
+        s.t = C.t; s.h = C.h; s.gammap = C.gammap; s.crate = C.crate; s.hlast = C.hlast;
+        s.q = C.q; s.qwait = C.qwait; s.nst = C.nst; s.nstlp = C.nstlp;
+        s.nfe = C.nfe; s.nsetups = C.nsetups; s.nni = C.nni; s.ncfn = C.ncfn;
+        s.netf = C.netf; s.flags = C.flags; s.status = C.status; s.qlast = C.qlast;
+        s.nrefine = C.nref; s.nrefine_fb = C.nref_fb; s.nguess = C.nguess; s.nguess_fb = C.nguess_fb;
+        P.st[c] = s;
+        if (P.status) P.status[c] = C.status;
+        if (C.status < 0) atomicMin(P.worst, C.status);
       }
     }
   }
@@ -832,25 +843,21 @@ struct VarSmem {
   static constexpr int bytes = (32 / VAR_G[V]) * (int)sizeof(CellSmem<VAR_NMAX[V], PREC>);
 };
 
-// Persistent kernel of one variant: each warp takes the next tile of the
-// range [t0, t1) from `counter` until none is left.  PREC 0: FP64 LU
+// Persistent kernel of one variant: the cells of the tiles [t0, t1) (one
+// contiguous range of P.tile_cells), each group of G lanes taking the next
+// cell from `counter` until none is left.  PREC 0: FP64 LU
 // factorisation; PREC 1: FP32 LU with FP64 refinement; PREC 2: FP64
 // Gauss-Jordan inverse (Newton solves by one matrix-vector product).
 template <int V, int PREC>
 __global__ void __launch_bounds__(32, var_minb(V, PREC)) k_cells(const __grid_constant__ Params P, int t0, int t1,
                                                            unsigned* counter, double* fbws) {
   extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31;
   constexpr int64_t FB = VarWs<V, PREC>::value;
   double* fb = fbws ? fbws + (int64_t)blockIdx.x * FB : nullptr;
-  for (;;) {
-    int t = 0;
-    if (lane == 0) t = t0 + (int)atomicAdd(counter, 1u);
-    t = __shfl_sync(FULL_MASK, t, 0);
-    if (t >= t1) break;
-    run_tile<VAR_G[V], VAR_NMAX[V], PREC, VAR_LEARN[V]>(P, P.tiles[t], smem, fb);
-    __syncwarp();
-  }
+  if (t1 <= t0) return;
+  const int c0 = P.tiles[t0].first;
+  const TileDesc last = P.tiles[t1 - 1];
+  run_cells<VAR_G[V], VAR_NMAX[V], PREC, VAR_LEARN[V]>(P, c0, last.first + last.count, counter, smem, fb);
 }
 
 

@@ -8,8 +8,11 @@
 // per-block partial sums (warp shuffles, then shared memory) go to a
 // caller-owned workspace, and the last block to finish adds the partials in
 // a fixed order and resets the arrival counter.
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -30,6 +33,29 @@ static int grid_for(int64_t items, int threads, int per_sm) {
   int64_t cap = (int64_t)sm_count() * per_sm;
   if (want > cap) want = cap;
   return want < 1 ? 1 : (int)want;
+}
+
+// Blocks of `kernel` (at `threads` threads) that fit on one SM at once, from
+// the occupancy calculator, cached per kernel and device.  A grid-stride
+// kernel whose grid exceeds what is resident runs a second, partial wave of
+// equally loaded blocks: its grid is capped at the resident count instead.
+static int resident_per_sm(const void* kernel, int threads) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(kernel, dev);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) b = 1;
+  cache[key] = b;
+  return b;
+}
+template <typename K>
+static int grid_of(K kernel, int64_t items, int threads, int per_sm) {
+  return grid_for(items, threads, std::min(per_sm, resident_per_sm(reinterpret_cast<const void*>(kernel), threads)));
 }
 
 // ------------------------------------------------------------ LinearSum
@@ -116,11 +142,11 @@ static int launch_unary(int64_t n, const double* x, double a, double b, double* 
   const bool al = aligned16(z) && (OP == UOP_CONST || aligned16(x));
   const int64_t n2 = n >> 1;
   if (al && n2) {
-    k_unary2<OP><<<grid_for(n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(
+    k_unary2<OP><<<grid_of(k_unary2<OP>, n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(
         n2, reinterpret_cast<const double2*>(x), a, b, reinterpret_cast<double2*>(z));
     if (n & 1) k_unary1<OP><<<1, 32, 0, s>>>(1, OP == UOP_CONST ? x : x + n - 1, a, b, z + n - 1);
   } else {
-    k_unary1<OP><<<grid_for(n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, x, a, b, z);
+    k_unary1<OP><<<grid_of(k_unary1<OP>, n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, x, a, b, z);
   }
   BDFB_CUDA(cudaGetLastError());
   return BDFB_SUCCESS;
@@ -388,16 +414,18 @@ extern "C" int bdfb_nv_linear_sum(int64_t n, double a, const double* x, double b
     if (n2) {
       const double2 *x2 = reinterpret_cast<const double2*>(x), *y2 = reinterpret_cast<const double2*>(y);
       double2* z2 = reinterpret_cast<double2*>(z);
-      const int g = grid_for(n2, ST_THREADS, 8);
-      if (b == 1.0) k_linear_sum2<0, 1><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
-      else if (b == -1.0) k_linear_sum2<0, -1><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
-      else if (a == 1.0) k_linear_sum2<1, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
-      else if (a == -1.0) k_linear_sum2<-1, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
-      else k_linear_sum2<0, 0><<<g, ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2);
+#define LS_CALL(SA, SB) \
+  k_linear_sum2<SA, SB><<<grid_of(k_linear_sum2<SA, SB>, n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(n2, a, x2, b, y2, z2)
+      if (b == 1.0) LS_CALL(0, 1);
+      else if (b == -1.0) LS_CALL(0, -1);
+      else if (a == 1.0) LS_CALL(1, 0);
+      else if (a == -1.0) LS_CALL(-1, 0);
+      else LS_CALL(0, 0);
+#undef LS_CALL
     }
     if (n & 1) k_linear_sum1<<<1, 32, 0, s>>>(1, a, x + n - 1, b, y + n - 1, z + n - 1);
   } else {
-    k_linear_sum1<<<grid_for(n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, a, x, b, y, z);
+    k_linear_sum1<<<grid_of(k_linear_sum1, n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, a, x, b, y, z);
   }
   BDFB_CUDA(cudaGetLastError());
   return BDFB_SUCCESS;
@@ -439,9 +467,9 @@ extern "C" int bdfb_nv_linear_combination(int64_t n, int nv, const double* c,
   cudaStream_t s = as_stream(stream);
   int64_t n2 = n >> 1;
   if (al && n2) {
-    int g = grid_for(n2, ST_THREADS, 8);
     double2* z2 = reinterpret_cast<double2*>(z);
-#define LC_CALL(K) k_linear_combination2<K><<<g, ST_THREADS, 0, s>>>(n2, A, z2)
+#define LC_CALL(K) \
+  k_linear_combination2<K><<<grid_of(k_linear_combination2<K>, n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(n2, A, z2)
     BDFB_NV_SWITCH(nv, LC_CALL)
 #undef LC_CALL
     if (n & 1) {
@@ -450,7 +478,7 @@ extern "C" int bdfb_nv_linear_combination(int64_t n, int nv, const double* c,
       k_linear_combination1<<<1, 32, 0, s>>>(1, nv, T, z + n - 1);
     }
   } else {
-    k_linear_combination1<<<grid_for(n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, nv, A, z);
+    k_linear_combination1<<<grid_of(k_linear_combination1, n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, nv, A, z);
   }
   BDFB_CUDA(cudaGetLastError());
   return BDFB_SUCCESS;
@@ -473,9 +501,9 @@ extern "C" int bdfb_nv_scale_add_multi(int64_t n, int nv, const double* a, const
   cudaStream_t s = as_stream(stream);
   int64_t n2 = n >> 1;
   if (al && n2) {
-    int g = grid_for(n2, ST_THREADS, 8);
     const double2* x2 = reinterpret_cast<const double2*>(x);
-#define SAM_CALL(K) k_scale_add_multi2<K><<<g, ST_THREADS, 0, s>>>(n2, x2, A)
+#define SAM_CALL(K) \
+  k_scale_add_multi2<K><<<grid_of(k_scale_add_multi2<K>, n2, ST_THREADS, 8), ST_THREADS, 0, s>>>(n2, x2, A)
     BDFB_NV_SWITCH(nv, SAM_CALL)
 #undef SAM_CALL
     if (n & 1) {
@@ -484,7 +512,7 @@ extern "C" int bdfb_nv_scale_add_multi(int64_t n, int nv, const double* a, const
       k_scale_add_multi1<<<1, 32, 0, s>>>(1, nv, x + n - 1, T);
     }
   } else {
-    k_scale_add_multi1<<<grid_for(n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, nv, x, A);
+    k_scale_add_multi1<<<grid_of(k_scale_add_multi1, n, ST_THREADS, 8), ST_THREADS, 0, s>>>(n, nv, x, A);
   }
   BDFB_CUDA(cudaGetLastError());
   return BDFB_SUCCESS;
