@@ -202,8 +202,17 @@ struct DrGlobal {
   static constexpr bool value = PREC != 1 && NMAX >= 56;
 };
 
-// the history saved before a step attempt (absent where it stays in registers)
-template <bool REG, int NMAX>
+// where the history saved before a step attempt lives: 0 the group's shared
+// memory, 1 registers (the FP64 kernels of the largest cells), 2 the warp's
+// global workspace beside the FP64 fallback matrix (the mixed-precision
+// kernels of the largest cells, whose registers are taken: leaving shared
+// memory lets 12 warps per SM fit instead of 10).  It is written once per
+// attempt and read back only when the attempt fails.
+template <int NMAX, int PREC>
+struct ZHome {
+  static constexpr int value = NMAX >= 56 ? (PREC == 1 ? 2 : 1) : 0;
+};
+template <bool AWAY, int NMAX>
 struct ZsBuf {
   double zs[ZCOLS][NMAX];
 };
@@ -219,13 +228,14 @@ struct ZsBuf<true, NMAX> {};
 // residual).
 template <int NMAX, int PREC = 0>
 struct CellSmem : RateBufs<NMAX, PREC != 1, UsesDr<NMAX, PREC>::value && !DrGlobal<NMAX, PREC>::value>,
-                  ZsBuf<PREC != 1 && NMAX >= 56, NMAX> {
+                  ZsBuf<ZHome<NMAX, PREC>::value != 0, NMAX> {
   static constexpr bool DR = UsesDr<NMAX, PREC>::value;
   static constexpr bool DRG = DrGlobal<NMAX, PREC>::value;   // derivatives in global memory
   typename std::conditional<PREC == 1, float, double>::type M[NMAX][NMAX + 1];
   // history saved before a step attempt (zs, the base); the FP64 kernel of
   // the largest cells keeps it in registers instead
-  static constexpr bool ZREG = PREC != 1 && NMAX >= 56;
+  static constexpr bool ZREG = ZHome<NMAX, PREC>::value == 1;
+  static constexpr bool ZGLOB = ZHome<NMAX, PREC>::value == 2;
   double dinv[NMAX];          // 1 / U_kk
   double ybuf[NMAX];          // gathered state / right-hand side
   int16_t perm[NMAX];         // row i of P M is row perm[i] of M

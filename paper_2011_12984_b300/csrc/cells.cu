@@ -321,12 +321,21 @@ __device__ __forceinline__ void select_next(const Grp<G>& g, const Params& P, in
 
 template <int G, int NMAX, int PREC>
 __device__ __forceinline__ void restore_z(const Grp<G>& g, int n, const CellSmem<NMAX, PREC>& S,
-                                          Cell<G, NMAX>& C) {
+                                          Cell<G, NMAX>& C, const double* zg) {
   if constexpr (CellSmem<NMAX, PREC>::ZREG) {
 #pragma unroll
     for (int p = 0; p < Cell<G, NMAX>::NPL; ++p)
 #pragma unroll
       for (int j = 0; j <= QMAX; ++j) C.z[j][p] = C.zsave[j][p];
+  } else if constexpr (CellSmem<NMAX, PREC>::ZGLOB) {
+#pragma unroll
+    for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j <= QMAX; ++j) C.z[j][p] = zg[j * NMAX + i];
+      }
+    }
   } else {
 #pragma unroll
     for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
@@ -382,6 +391,13 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   static_assert(!LEARN || (G == 32 && NPL == 1 && PREC == 0), "learned guess: one warp per cell, FP64");
   const int n = cd.n;
   ph_mark(PH_CTRL);
+  // the saved history of the kernels that keep it in the global workspace
+  // (after the fallback matrix); without a workspace nothing has changed yet
+  double* zg = nullptr;
+  if constexpr (CellSmem<NMAX, PREC>::ZGLOB) {
+    if (Mg == nullptr) { C.status = BDFB_MEM_FAIL; return true; }
+    zg = reinterpret_cast<double*>(Mg) + NMAX * (NMAX + 1);
+  }
   if (!(C.flags & F_STARTED)) {
     if (P.tout == C.t) { C.status = 0; return true; }   // first step waits for tout != t0
     const int r = start_cell(g, P, cd, S, C);
@@ -414,6 +430,15 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
     for (int p = 0; p < NPL; ++p)
 #pragma unroll
       for (int j = 0; j <= QMAX; ++j) C.zsave[j][p] = C.z[j][p];
+  } else if constexpr (CellSmem<NMAX, PREC>::ZGLOB) {
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) {
+      const int i = g.rank + G * p;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j <= QMAX; ++j) zg[j * NMAX + i] = C.z[j][p];
+      }
+    }
   } else {
 #pragma unroll
     for (int p = 0; p < NPL; ++p) {
@@ -548,7 +573,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
             } else {
               // refinement stalled: factor this setup's M in FP64 instead (in
               // the cell's global workspace) until the next setup
-              if (Mg == nullptr) { restore_z(g, n, S, C); C.status = BDFB_MEM_FAIL; return true; }  // never write through null
+              if (Mg == nullptr) { restore_z(g, n, S, C, zg); C.status = BDFB_MEM_FAIL; return true; }  // never write through null
               C.nref_fb++;
               form_M64_from_dr<G, NPL, NMAX>(g, cd, S, C.gammap, Mg);
               if (lu_factor1<G, NMAX, double, true>(g, Mg, S.dinv, S.perm, n)) {
@@ -609,7 +634,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   }
   if (fail) {
     ph_mark(PH_FAIL);
-    restore_z(g, n, S, C);
+    restore_z(g, n, S, C, zg);
     if (!jcur && !C.tried_fresh && C.setup_done) {   // stale M: retry once with a fresh one
       C.force_setup = 1;
       C.tried_fresh = 1;
@@ -631,7 +656,7 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   const double dsm2 = acnrm2 * Eq * Eq;    // (E_q ||Delta||)^2
   if (!(dsm2 <= 1.0)) {
     ph_mark(PH_FAIL);
-    restore_z(g, n, S, C);
+    restore_z(g, n, S, C, zg);
     C.nef++;
     C.netf++;
     if (C.nef >= 7) { C.status = BDFB_ERR_FAILURE; return true; }
@@ -688,6 +713,14 @@ __device__ __forceinline__ bool attempt(const Grp<G>& g, const Params& P, const 
   return false;
 }
 
+// doubles of one group's slice of the per-warp global workspace: mixed
+// precision, the FP64 fallback matrix and, for the largest cells, the saved
+// history (ZCOLS x NMAX); FP64, the largest cells' reaction derivatives
+__host__ __device__ constexpr int64_t group_ws_doubles(int nmax, int pr) {
+  return pr == 1 ? (int64_t)nmax * (nmax + 1) + (nmax >= 56 ? (int64_t)ZCOLS * nmax : 0)
+                 : (nmax >= 56 ? 8LL * nmax : 0);
+}
+
 // fb: this warp's slice of the FP64 fallback workspace (mixed precision;
 // (32 / G) matrices of NMAX x (NMAX + 1) doubles), else null
 // Cells [c0, c1) of P.tile_cells on this warp: every group of G lanes takes
@@ -701,9 +734,10 @@ __device__ __forceinline__ void run_cells(const Params& P, int c0, int c1, unsig
   Grp<G> g;
   const int gid = (threadIdx.x & 31) / G;
   CellSmem<NMAX, PREC>& S = reinterpret_cast<CellSmem<NMAX, PREC>*>(smem)[gid];
-  // mixed precision: this group's FP64 fallback matrix; the largest FP64
-  // cells: their derivative workspace (the same pointer)
-  constexpr int64_t WS = PREC == 1 ? (int64_t)NMAX * (NMAX + 1) : 8LL * NMAX;
+  // mixed precision: this group's FP64 fallback matrix (then, for the
+  // largest cells, its saved history); the largest FP64 cells: their
+  // derivative workspace (the same pointer)
+  constexpr int64_t WS = group_ws_doubles(NMAX, PREC);
   double (*Mg)[NMAX + 1] = fb ? reinterpret_cast<double (*)[NMAX + 1]>(fb + (int64_t)gid * WS) : nullptr;
   bool active = false, more = true;
   int64_t c = 0;
@@ -820,8 +854,9 @@ constexpr int VAR_ORDER[NVAR] = {4, 3, VAR_W32, VAR_W16, VAR_H16, 2, 1, 0};
 // the largest ones): bounds the registers ptxas may use
 constexpr int VAR_MINB[NVAR] = {12, 12, 12, 8, 8, 12, 12, 12};
 // mixed precision: M in FP32 halves the shared memory, so registers bound the
-// residency of the two largest tilings
-constexpr int var_minb(int v, int prec) { return prec == 1 && (v == 3 || v == 4) ? 10 : VAR_MINB[v]; }
+// residency of the two largest tilings (the largest cells' saved history in
+// the global workspace lets 12 warps fit)
+constexpr int var_minb(int v, int prec) { return prec == 1 && v == 4 ? 12 : prec == 1 && v == 3 ? 10 : VAR_MINB[v]; }
 static_assert(CLS_G[0] == VAR_G[0] && CLS_NMAX[4] == VAR_NMAX[4], "variants 0..4 are the class tilings");
 
 // doubles of global workspace one warp of variant v needs: mixed precision,
@@ -829,13 +864,11 @@ static_assert(CLS_G[0] == VAR_G[0] && CLS_NMAX[4] == VAR_NMAX[4], "variants 0..4
 // cells, their reaction derivatives (4 reactant slots x 2 NMAX reactions);
 // others none
 constexpr int64_t workspace_doubles_per_warp(int v, int pr) {
-  return pr == 1 ? (int64_t)(32 / VAR_G[v]) * VAR_NMAX[v] * (VAR_NMAX[v] + 1)
-                 : (VAR_NMAX[v] >= 56 ? (int64_t)(32 / VAR_G[v]) * 8 * VAR_NMAX[v] : 0);
+  return (int64_t)(32 / VAR_G[v]) * group_ws_doubles(VAR_NMAX[v], pr);
 }
 template <int V, int PREC>
 struct VarWs {
-  static constexpr int64_t value = PREC == 1 ? (int64_t)(32 / VAR_G[V]) * VAR_NMAX[V] * (VAR_NMAX[V] + 1)
-                                             : (VAR_NMAX[V] >= 56 ? (int64_t)(32 / VAR_G[V]) * 8 * VAR_NMAX[V] : 0);
+  static constexpr int64_t value = workspace_doubles_per_warp(V, PREC);
 };
 
 template <int V, int PREC>
