@@ -925,7 +925,12 @@ def run_ours(args):
             if name == "batched_mixed_fp32_lu":
                 variants["mixed_accuracy"] = accuracy(prob, y.cpu().numpy())
                 mst = vi.stats()
-                variants["mixed_refine_sweeps_per_solve"] = mst["nrefine"] / max(1, mst["nniters"])
+                # precision 1 factors in FP32 the cells of more than 32 species
+                # (the others keep FP64 factors): sweeps per Newton solve of those
+                big = np.diff(prob.y_off) > 32
+                nni_big = int(vi.cell_stats()[:, 3][big].sum())
+                variants["mixed_fp32_factored_cells"] = int(big.sum())
+                variants["mixed_refine_sweeps_per_solve"] = mst["nrefine"] / max(1, nni_big)
                 variants["mixed_fp64_fallbacks"] = mst["nrefine_fallback"]
     traffic = K_CELLS_STEP_DRAM_BYTES if (NCELL == 100_000 and SIZES == (3, 10, 32, 54) and not args.mapping
                                           and args.precision == 0) else None
