@@ -166,7 +166,8 @@ __device__ __forceinline__ void set_ewt(const Grp<G>& g, const Params& P, int n,
 #pragma unroll
   for (int p = 0; p < Cell<G, NMAX>::NPL; ++p) {
     const int i = g.rank + G * p;
-    C.ewt[p] = i < n ? 1.0 / (P.rtol * fabs(C.z[0][p]) + P.atol) : 0.0;
+    // the Newton-Raphson reciprocal: four FP64 FMAs where a division issues more
+    C.ewt[p] = i < n ? recip_nr(P.rtol * fabs(C.z[0][p]) + P.atol) : 0.0;
   }
 }
 
