@@ -785,8 +785,11 @@ def run_ours(args):
     y = torch.empty_like(y0)
     st = torch.empty(prob.ncell, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # the step's launch sequence (counter reset, one persistent launch per
+    # kernel variant on forked streams, join) is captured in a CUDA graph on
+    # the first integrate and replayed on every later one
     integ = bdfb.Integrator(prob, rtol=RTOL, atol=ATOL, mapping=args.mapping, precision=args.precision,
-                            autotune=0 if args.no_autotune or args.mapping else 1)
+                            autotune=0 if args.no_autotune or args.mapping else 1, graph=0 if args.no_graph else 1)
 
     def step():
         integ.init(0.0, y0)
@@ -946,6 +949,10 @@ def run_ours(args):
                    "mapping": ("one warp per cell" if args.mapping else
                                "size-class tiles" + ("" if args.no_autotune else ", autotuned")),
                    "lanes_per_cell_and_nmax_by_class": [[int(g), int(nm)] if c else None for g, nm, c in mp],
+                   "launch": ("per step: one CUDA graph replay (captured once) of the persistent launches, "
+                              "one per kernel variant, on forked streams" if not args.no_graph else
+                              "per step: the persistent launches, one per kernel variant, on forked streams"),
+                   "graph_launches": int(st_sum["graph_launches"]), "graph_captures": int(st_sum["graph_captures"]),
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "accuracy": acc,
         "integrator_stats": {"steps_per_cell": st_sum["nsteps"] / NCELL,
@@ -1027,6 +1034,8 @@ def main():
                     help="time the device path only (no e2e, accuracy, CPU or vector legs)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP64 factorisation; 1: FP32 factorisation + FP64 refinement")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step kernels directly instead of replaying a captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run each size class on its own tiling instead of the autotuned one")
     ap.add_argument("--no-configs", action="store_true",
