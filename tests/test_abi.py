@@ -140,3 +140,15 @@ def test_shared_network_rejected_without_gpu(lib):
                 dict(n=3, rxn=1, reac=ok_r, prod=ok_p, ncell=0)):       # no cells
         p, keep = make(**bad)
         assert L.bdfb_create(C.byref(p), C.byref(h)) == ILL, bad
+
+
+def test_phase_timers_absent_from_the_plain_build(lib):
+    """the product library compiles the step-phase timers away: reading them
+    is refused (without touching the GPU), whatever the buffer"""
+    L, _ = lib
+    f = L.bdfb_phase_cycles
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    out = (C.c_uint64 * 16)()
+    assert f(out, 16, 0) == -22
+    assert f(None, 16, 1) == -22
