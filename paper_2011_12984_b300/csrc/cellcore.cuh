@@ -45,10 +45,15 @@ __device__ __forceinline__ void ph_start(int k) {
   if ((threadIdx.x & 31) == 0) { ph_clock() = clock64(); ph_current() = k; }
   __syncwarp();
 }
+// Kernels that never start the clock (the grouped and standalone solvers
+// reach these marks through shared helpers) hold no valid phase: the index is
+// checked before any counter is touched.
 __device__ __forceinline__ void ph_mark(int k) {
   if ((threadIdx.x & 31) == 0) {
     const long long now = clock64();
-    atomicAdd(&g_phase_cycles[blockIdx.x & 255][ph_current()], (unsigned long long)(now - ph_clock()));
+    const unsigned cur = (unsigned)ph_current();
+    if (cur < (unsigned)NPHASE)
+      atomicAdd(&g_phase_cycles[blockIdx.x & 255][cur], (unsigned long long)(now - ph_clock()));
     ph_clock() = now;
     ph_current() = k;
   }
