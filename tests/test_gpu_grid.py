@@ -63,6 +63,23 @@ def test_grid_matches_oracle(nx, tout, precision):
     check_system(y, gs, yo, so, yt, rtol, atol, precision)
 
 
+def test_grid_64_matches_oracle():
+    """64^3 (786 432 unknowns, 91 steps to t = 0.05): the multi-block reductions
+    and the 3-D launch tiling at a size where every kernel runs many blocks per
+    SM; in both precisions every counter equals the oracle's and the states
+    agree within the match tolerance"""
+    p = gen.brusselator3d(64, seed=64)
+    rtol, atol, tout = 1e-6, 1e-10, 0.05
+    ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
+    assert ro == 0
+    for precision in (0, 1):
+        ret, y, gs, _ = run_grid(p, tout, rtol, atol, precision=precision)
+        assert ret == 0
+        assert np.array_equal(gs[:8], so[:8]), (precision, gs[:8], so[:8])
+        d = np.max(np.abs(y - yo) / (rtol * np.abs(yo) + atol))
+        assert d <= MATCH_TOL[precision], (precision, d)
+
+
 def test_grid_steady_state_stays():
     p = gen.brusselator3d(8, noise=0.0)
     ret, y, _, _ = run_grid(p, 0.1, 1e-6, 1e-10)
