@@ -156,10 +156,27 @@ def test_mass_action_mixed_sizes(mapping):
 
 def test_mass_action_full_size_sampled():
     """The full 100 000-cell workload in the launch configuration the benchmark
-    times; every cell checked for status and conservation, 256 sampled cells
-    against the truth."""
+    times (autotuned variants, the step's launches captured in a CUDA graph on
+    the first integration and replayed on the second, which must reproduce it
+    bit for bit); every cell checked for status and conservation, 256 sampled
+    cells against the truth."""
     p = gen.mass_action(100000)
-    ret, y, st, cs, stats = run_gpu(p, 0.0, 1e-3, 1e-6, 1e-10)
+    y0 = torch.from_numpy(p.y0).cuda()
+    ys = []
+    with bdfb.Integrator(p, rtol=1e-6, atol=1e-10, autotune=1, graph=1) as I:
+        for _ in range(2):
+            I.init(0.0, y0)
+            yd = torch.empty(p.y0.size, dtype=torch.float64, device="cuda")
+            sd = torch.empty(p.ncell, dtype=torch.int32, device="cuda")
+            ret = I.integrate(1e-3, yd, sd)
+            torch.cuda.synchronize()
+            assert ret == 0
+            ys.append(yd.cpu().numpy())
+            st = sd.cpu().numpy()
+        cs, stats = I.cell_stats(), I.stats()
+    assert stats["graph_captures"] == 1 and stats["graph_launches"] == 2
+    assert np.array_equal(ys[0], ys[1])
+    y = ys[1]
     assert ret == 0 and np.all(st == 0)
     s0 = np.add.reduceat(p.y0, p.y_off[:-1])
     s1 = np.add.reduceat(y, p.y_off[:-1])
