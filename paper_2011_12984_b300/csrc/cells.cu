@@ -1835,8 +1835,11 @@ extern "C" int bdfb_init(bdfb_ctx* ctx, double t0, const double* y0, int32_t mem
 // of more than 32 species (the NMAX 56 kernels), where the n^3 factorisation
 // dominates a step; smaller cells keep FP64 factors unless mixed_small is set:
 // on B300 two FP64 refinement residuals per solve cost more there than the
-// FP64 factorisations they replace (measured per size class: n = 54 1.11x
-// faster in FP32, n = 32 1.10x, n = 10 1.48x and n = 3 1.56x slower).
+// FP64 factorisations they replace (measured per size class on its own
+// tiling: n = 54 1.11x faster in FP32, n = 32 1.10x, n = 10 1.48x and n = 3
+// 1.56x slower; n = 32 on one warp per cell 1.04x faster, n = 10 1.32x
+// slower -- a row is chosen per kernel, and the one-warp 32-species kernel
+// also takes the small cells of mapping 32).
 constexpr int MIXED_NMAX = 56;
 static int row_of(const bdfb_ctx* ctx, int v) {
   if (ctx->precision == 1 && (ctx->mixed_small || VAR_NMAX[v] >= MIXED_NMAX)) return 1;
