@@ -141,6 +141,23 @@ def test_line_matches_oracle(nx, length, tout, precision):
     check_system(y, gs, yo, so, yt, rtol, atol, precision)
 
 
+def test_line_50k_points_matches_oracle():
+    """The demo problem at the benchmark's grid spacing (5e4 points on a line
+    of length 5, dx = 1e-4, 125 steps to t = 1): in both precisions every
+    counter equals the oracle's and the states agree within the match
+    tolerance"""
+    p = gen.brusselator1d(50_000, length=5.0)
+    rtol, atol, tout = 1e-6, 1e-10, 1.0
+    ro, yo, so = oracle.bruss_integrate(p, 0.0, tout, rtol, atol, maxl=5)
+    assert ro == 0
+    for precision in (0, 1):
+        ret, y, gs, _ = run_grid(p, tout, rtol, atol, precision=precision)
+        assert ret == 0
+        assert np.array_equal(gs[:8], so[:8]), (precision, gs[:8], so[:8])
+        d = np.max(np.abs(y - yo) / (rtol * np.abs(yo) + atol))
+        assert d <= MATCH_TOL[precision], (precision, d)
+
+
 def test_line_uniform_steady_state_stays_at_1e6_points():
     nx = 1_000_000
     u, v, w = gen.brusselator_steady_state(1.0, 3.5, 5e-6)
